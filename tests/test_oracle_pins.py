@@ -1,0 +1,494 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix
+(closed forms, library routines, invariants, brute force). No GPU needed."""
+import ctypes
+import ctypes.util
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special, stats
+
+from paper_2511_19633_gb300 import inputs
+
+MZ = 91.1876
+CF, TR = 4.0 / 3.0, 0.5
+
+
+# --------------------------------------------------------------------------- RNG
+def _curand():
+    for cand in ("/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")):
+        if cand and os.path.exists(cand) if cand.startswith("/") else cand:
+            try:
+                return ctypes.CDLL(cand)
+            except OSError:
+                pass
+    return None
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF])
+def test_philox_matches_curand_host_generator(oracle_mod, seed):
+    """cuRAND's Philox4_32_10 host generator (an independent implementation of
+    Salmon et al. 2011) emits block i from counter (0, 0, i, 0), key = seed."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not available")
+    g = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(g), 161) == 0  # PHILOX4_32_10
+    assert lib.curandSetPseudoRandomGeneratorSeed(g, ctypes.c_ulonglong(seed)) == 0
+    n = 4 * 300
+    out = (ctypes.c_uint * n)()
+    assert lib.curandGenerate(g, out, n) == 0
+    lib.curandDestroyGenerator(g)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for i in range(300):
+        assert oracle_mod.philox((0, 0, i, 0), key) == list(out[4 * i:4 * i + 4]), i
+
+
+def test_philox_counter_words_all_matter(oracle_mod):
+    base = oracle_mod.philox((5, 6, 7, 8), (9, 10))
+    for w in range(4):
+        c = [5, 6, 7, 8]
+        c[w] ^= 1
+        assert oracle_mod.philox(tuple(c), (9, 10)) != base
+    assert oracle_mod.philox((5, 6, 7, 8), (9, 11)) != base
+
+
+def test_uniform_mapping(oracle_mod):
+    assert oracle_mod.uniform(0, 0) == 0.5 * 2.0 ** -53
+    assert oracle_mod.uniform(0xFFFFFFFF, 0xFFFFFFFF) == (2.0 ** 53 - 0.5) * 2.0 ** -53
+    assert oracle_mod.uniform(0, 0x80000000) == 0.5 + 0.5 * 2.0 ** -53
+    # the low 11 bits are dropped
+    assert oracle_mod.uniform(0x7FF, 0) == oracle_mod.uniform(0, 0)
+
+
+# --------------------------------------------------------------------------- PDF
+def test_pdf_nodes_equal_closed_form(oracle_mod, pdf):
+    xs = inputs.x_nodes()
+    qs = inputs.q2_nodes()
+    for f, name in enumerate(inputs.FLAVOURS):
+        exact = inputs.synthetic_flavour_xf(name, xs).astype(np.float32).astype(np.float64)
+        for k in range(0, 99, 7):
+            v = oracle_mod.pdf_xf(pdf, f, xs[k], qs[(3 * k) % 50])
+            assert v == pytest.approx(exact[k], rel=1e-12, abs=1e-300), (name, k)
+
+
+def test_pdf_between_nodes_within_interpolation_bound(oracle_mod, pdf):
+    """Linear interpolation in ln x of g(l) = xf(e^l) errs by at most
+    h^2/8 max|g''| on a cell of width h."""
+    xs = inputs.x_nodes()
+    h = math.log(xs[1] / xs[0])
+    for f in (0, 1, 2, 7):
+        name = inputs.FLAVOURS[f]
+        for k in range(0, 98, 5):
+            l0 = math.log(xs[k])
+            ls = np.linspace(l0, l0 + h, 41)
+            g = inputs.synthetic_flavour_xf(name, np.exp(ls))
+            d2 = np.abs(np.gradient(np.gradient(g, ls), ls)).max()
+            lm = l0 + 0.37 * h
+            v = oracle_mod.pdf_xf(pdf, f, math.exp(lm), 100.0)
+            ex = inputs.synthetic_flavour_xf(name, np.array([math.exp(lm)]))[0]
+            assert abs(v - ex) <= 1.2 * h * h / 8 * d2 + 1e-6 * abs(ex), (name, k)
+
+
+def test_pdf_zero_outside_grid_and_q2_independent(oracle_mod, pdf):
+    assert oracle_mod.pdf_xf(pdf, 2, 0.9e-6, 10.0) == 0.0
+    assert oracle_mod.pdf_xf(pdf, 2, 1.0, 10.0) == 0.0
+    assert oracle_mod.pdf_xf(pdf, 2, 0.1, 0.4) == 0.0
+    assert oracle_mod.pdf_xf(pdf, 2, 0.1, 13601.0 ** 2) == 0.0
+    a = oracle_mod.pdf_xf(pdf, 0, 0.013, 3.0)
+    b = oracle_mod.pdf_xf(pdf, 0, 0.013, 5e6)
+    assert a == pytest.approx(b, rel=1e-14)
+
+
+def test_valence_sum_rules(pdf):
+    """int u_v dx = 2, int d_v dx = 1 (the normalisations of the synthetic set)."""
+    for name, target in (("uv", 2.0), ("dv", 1.0)):
+        val, _ = integrate.quad(lambda x: inputs.synthetic_xf(name, np.array([x]))[0] / x, 0, 1,
+                                points=[1e-6, 1e-3], limit=200)
+        assert val == pytest.approx(target, rel=1e-6)
+
+
+@pytest.mark.parametrize("num,den", [(2, 2), (0, 2), (0, 0), (11, 0), (7, 7), (1, 1)])
+def test_pdf_ratio_bound_is_a_bound(oracle_mod, pdf, num, den):
+    rng = np.random.default_rng(3)
+    xs = np.exp(np.linspace(math.log(1e-6), math.log(1 - 1e-6), 4000))
+    q2s = [0.5, 10.0, 1e4, 1e8]
+
+    def F(f, x, q):
+        if f == 11:
+            return sum(oracle_mod.pdf_xf_batch(pdf, k, x, q) for k in range(1, 11))
+        return oracle_mod.pdf_xf_batch(pdf, f, x, q)
+    for eta in np.exp(rng.uniform(math.log(2e-6), math.log(0.95), 25)):
+        B = oracle_mod.pdf_bound(pdf, num, den, eta)
+        for q in q2s:
+            xp = xs[xs >= eta]
+            r = F(num, xp, np.full_like(xp, q)).max() / F(den, np.array([eta]), np.array([q]))[0]
+            assert r <= B * (1 + 1e-12), (num, den, eta, q, r, B)
+
+
+# --------------------------------------------------------------------------- alpha_s
+def test_alpha_s_one_loop(oracle_mod):
+    st = oracle_mod.Settings()
+    assert oracle_mod.alpha_s(st, MZ * MZ) == pytest.approx(0.118, rel=1e-15)
+    beta0 = 23.0 / (12.0 * math.pi)
+    for t in (1.0, 30.0, 1e4, 1e7):
+        a = oracle_mod.alpha_s(st, t)
+        h = 1e-4
+        d = (oracle_mod.alpha_s(st, t * math.exp(h)) - oracle_mod.alpha_s(st, t * math.exp(-h))) / (2 * h)
+        assert d == pytest.approx(-beta0 * a * a, rel=1e-6)  # d alpha/d ln t = -beta0 alpha^2
+    fixed = oracle_mod.Settings(fixed_alpha=True)
+    assert oracle_mod.alpha_s(fixed, 2.0) == 0.118
+
+
+# --------------------------------------------------------------------------- NLO pieces
+def test_li2_against_scipy_spence(oracle_mod):
+    for x in (0.0, 1e-8, 0.1, 0.3, 0.5, 0.5000001, 0.8, 0.99, 1 - 1e-9, 1.0):
+        assert oracle_mod.li2(x) == pytest.approx(float(special.spence(1.0 - x)), rel=1e-13, abs=1e-15)
+    assert oracle_mod.li2(0.5) == pytest.approx(math.pi ** 2 / 12 - math.log(2) ** 2 / 2, rel=1e-14)
+
+
+@pytest.mark.parametrize("eta", [1e-4, 0.01, 0.3, 0.9])
+@pytest.mark.parametrize("L", [0.0, 0.7])
+def test_Bqq_is_integral_of_gqq(oracle_mod, eta, L):
+    """B^qq(eta) = int_0^eta g^qq(x) dx (the plus-prescription bookkeeping of App. C.3)."""
+    val, _ = integrate.quad(lambda x: oracle_mod.collinear(0.118, L, "g", x), 0, eta,
+                            limit=400, epsabs=1e-14, epsrel=1e-11)
+    assert oracle_mod.collinear(0.118, L, "B", eta) == pytest.approx(val, rel=1e-8, abs=1e-12)
+
+
+def test_Aqq_is_sum_of_delta_coefficients(oracle_mod):
+    """A^qq = delta(1-x) coefficients of Kbar (-(5-pi^2)), Ktilde (-pi^2/3) and P (-3/2 L)."""
+    for L in (0.0, 1.3):
+        pre = CF * 0.118 / (2 * math.pi)
+        expect = pre * (-(5.0 - math.pi ** 2) - math.pi ** 2 / 3.0 - 1.5 * L)
+        assert oracle_mod.collinear(0.118, L, "A") == pytest.approx(expect, rel=1e-14)
+
+
+def test_bvi_factor():
+    """B+V+I: the poles of V and I cancel and leave (1 + C_F alpha_s/2pi * 2) ~ 1.05."""
+    assert 1 + CF * 0.118 / (2 * math.pi) * 2 == pytest.approx(1.05, abs=1e-3)
+
+
+def test_born_me2_matches_textbook_partonic_cross_section(oracle_mod):
+    """sigma_hat(q qbar -> Z) = (pi/3) sqrt2 G_F m^2 (v^2 + a^2) delta(s - m^2),
+    v = T3 - 2 Q sin^2, a = T3, so (pi/s)|M|^2 = that prefactor at s = m^2."""
+    GF, s2w = 1.16638e-5, 0.2312
+    for f, (Q, T3) in ((1, (-1 / 3, -0.5)), (2, (2 / 3, 0.5)), (5, (-1 / 3, -0.5))):
+        v, a = T3 - 2 * Q * s2w, T3
+        expect = (math.pi / 3) * math.sqrt(2) * GF * MZ ** 2 * (v * v + a * a)
+        assert math.pi / MZ ** 2 * oracle_mod.born_me2(f) == pytest.approx(expect, rel=1e-12)
+
+
+def test_lo_cross_section_and_rapidity_shape(oracle_mod, pdf):
+    """Paper's P3: sigma_LO = int dy sum_pairs pi F_a F_b |M|^2/m^4 by quadrature
+    against the mean Monte Carlo weight, and dsigma/dy per bin."""
+    sqrt_s = 13600.0
+    st = oracle_mod.Settings(process=1, sqrt_s=sqrt_s)
+    Y = math.log(sqrt_s / MZ)
+
+    def dsdy(y):
+        ea, eb = math.exp(y) * MZ / sqrt_s, math.exp(-y) * MZ / sqrt_s
+        return sum(oracle_mod.born_density(st, pdf, k, ea, eb) for k in range(10)) * 0.3893794e9
+    sigma, _ = integrate.quad(dsdy, -Y, Y, limit=200, epsrel=1e-8)
+    n = 200_000
+    r = oracle_mod.run(st, 0, n, pdf, hard_only=True, threads=4)
+    w = r["weight"]
+    assert w.mean() == pytest.approx(sigma, rel=5 * w.std() / math.sqrt(n) / sigma)
+    Zp = r["p"][:, 2, :]
+    y = 0.5 * np.log((Zp[:, 0] + Zp[:, 3]) / (Zp[:, 0] - Zp[:, 3]))
+    edges = np.linspace(-Y, Y, 13)
+    hw, _ = np.histogram(y, edges, weights=w)
+    hw2, _ = np.histogram(y, edges, weights=w * w)
+    expect = np.array([integrate.quad(dsdy, a, b)[0] for a, b in zip(edges[:-1], edges[1:])]) * n
+    chi2 = np.sum((hw - expect) ** 2 / np.maximum(hw2, 1e-300))
+    assert stats.chi2.sf(chi2, len(hw)) > 1e-4, chi2
+
+
+def test_s_event_collinear_terms_by_quadrature(oracle_mod, pdf):
+    """S events at fixed y and flavour pair: the mean weight over the collinear
+    x samples equals B (1 + C_F as/pi + sum_legs [A - B(eta) + int_eta^1 ...])."""
+    sqrt_s, y, pair = 13600.0, 0.8, 1  # pair 1 = (u, ubar)
+    st_s = oracle_mod.Settings(process=2, sqrt_s=sqrt_s, p_s=1.0, y_fixed=y, pair_fixed=pair)
+    st_b = oracle_mod.Settings(process=1, sqrt_s=sqrt_s, y_fixed=y, pair_fixed=pair)
+    n = 100_000
+    ws = oracle_mod.run(st_s, 0, n, pdf, hard_only=True, threads=4)["weight"]
+    wb = oracle_mod.run(st_b, 0, 4, pdf, hard_only=True)["weight"][0]
+    ea, eb = math.exp(y) * MZ / sqrt_s, math.exp(-y) * MZ / sqrt_s
+    mz2 = MZ * MZ
+
+    def leg(fidx, eta):
+        F0 = oracle_mod.pdf_xf(pdf, fidx, eta, mz2)
+
+        def integrand(x):
+            rq = oracle_mod.pdf_xf(pdf, fidx, eta / x, mz2) / F0
+            rg = oracle_mod.pdf_xf(pdf, 0, eta / x, mz2) / F0
+            return ((rq - 1) * oracle_mod.collinear(0.118, 0, "g", x)
+                    + rq * oracle_mod.collinear(0.118, 0, "hqq", x)
+                    + rg * oracle_mod.collinear(0.118, 0, "hqg", x))
+        val, _ = integrate.quad(integrand, eta, 1, limit=400, epsrel=1e-9)
+        return oracle_mod.collinear(0.118, 0, "A") - oracle_mod.collinear(0.118, 0, "B", eta) + val
+    expect = wb * (1 + CF * 0.118 / math.pi + leg(2, ea) + leg(7, eb))
+    assert ws.mean() == pytest.approx(expect, rel=5 * ws.std() / math.sqrt(n) / expect)
+
+
+def _pdf_vec(pdf, f, x):
+    """vectorised bilinear (ln x) interpolation at fixed Q^2 of the synthetic
+    table (Q^2-independent), used only to integrate the H-event density."""
+    lx0, lx1 = math.log(1e-6), math.log(1 - 1e-6)
+    u = (np.log(x) - lx0) / ((lx1 - lx0) / 99)
+    ix = np.clip(np.floor(u).astype(int), 0, 98)
+    fx = u - ix
+    col = pdf[f, :, 0].astype(np.float64)
+    v = (1 - fx) * col[ix] + fx * col[np.minimum(ix + 1, 99)]
+    return np.where((x >= 1e-6) & (x <= 1 - 1e-6), v, 0.0)
+
+
+def test_h_event_cross_section_by_quadrature(oracle_mod, pdf):
+    """H events (R - S, Appendix C.2): mean weight vs a Gauss-Legendre product
+    rule over (x, v, y) of sum_pairs F_a F_b (R-S)/(16 pi m^2)."""
+    sqrt_s = 13600.0
+    S = sqrt_s ** 2
+    st = oracle_mod.Settings(process=2, sqrt_s=sqrt_s, p_s=0.0)
+    n = 200_000
+    w = oracle_mod.run(st, 0, n, pdf, hard_only=True, threads=4)["weight"]
+    m2 = MZ * MZ
+    GF, s2w, a_s = 1.16638e-5, 0.2312, 0.118
+    me2 = {}
+    for f in range(1, 6):
+        Q, T3 = ((2 / 3, 0.5) if f in (2, 4) else (-1 / 3, -0.5))
+        V, A = 2 * T3 - 4 * Q * s2w, 2 * T3
+        me2[f] = (1 / 3) * 0.25 * math.sqrt(2) * GF * m2 * m2 * (V * V + A * A)
+    gx, gw = np.polynomial.legendre.leggauss(96)
+    xlo = m2 / S
+    # x in [xlo, 1): map through log(1-x) to resolve the endpoint
+    a, b = math.log(1 - xlo), math.log(1e-12)
+    lu = 0.5 * (b - a) * gx + 0.5 * (a + b)
+    X = 1 - np.exp(lu)
+    WX = 0.5 * (a - b) * gw * np.exp(lu)  # |dx| = e^lu |dlu|
+    V = 0.5 * (gx + 1)
+    WV = 0.5 * gw
+    Yg, WY = gx, gw
+    total = 0.0
+    for xi, wxi in zip(X, WX):
+        sbar = m2 / xi
+        Ymax = 0.5 * math.log(S / sbar)
+        v = V * (1 - xi)
+        wv = WV * (1 - xi)
+        y = Yg * Ymax
+        wy = WY * Ymax
+        e1 = np.exp(y) * math.sqrt(sbar / S)
+        e2 = np.exp(-y) * math.sqrt(sbar / S)
+        Fg1, Fg2 = _pdf_vec(pdf, 0, e1), _pdf_vec(pdf, 0, e2)
+        acc = np.zeros((len(v), len(y)))
+        for f in range(1, 6):
+            q1, q2 = _pdf_vec(pdf, f, e1), _pdf_vec(pdf, f, e2)
+            qb1, qb2 = _pdf_vec(pdf, f + 5, e1), _pdf_vec(pdf, f + 5, e2)
+            rs_qq = 8 * math.pi * a_s * CF / m2 * me2[f] * (-2.0)
+            rs_gq = 8 * math.pi * a_s * TR / m2 * me2[f] * (2 * m2 + v[:, None] * sbar) / sbar
+            acc += rs_qq * (q1 * qb2 + qb1 * q2)[None, :]
+            acc += rs_gq * (Fg1 * q2 + Fg1 * qb2 + q1 * Fg2 + qb1 * Fg2)[None, :]
+        total += wxi * np.sum(wv[:, None] * wy[None, :] * acc) / (16 * math.pi * m2)
+    sigma = total * 0.3893794e9
+    assert w.mean() == pytest.approx(sigma, abs=5 * w.std() / math.sqrt(n))
+    assert np.all(w != 0)
+
+
+# --------------------------------------------------------------------------- maps
+@pytest.mark.parametrize("r,z", [(1e-3, 0.3), (1e-6, 0.9), (0.02, 0.6), (1e-8, 0.999)])
+def test_if_map_round_trip_and_jacobian(oracle_mod, r, z):
+    ok, (x, omx, u, omu) = oracle_mod.if_map(r, z, 1 - z)
+    assert ok
+    assert x + omx == pytest.approx(1.0, abs=1e-15) and u + omu == pytest.approx(1.0, abs=1e-15)
+    assert 1 - (1 - x) * (1 - u) == pytest.approx(z, rel=1e-13)       # z = 1-(1-x)(1-u)
+    assert u * (1 - u) * (1 - x) / x == pytest.approx(r, rel=1e-11)   # t = u(1-u)(1-x)/x s
+    h = 1e-6
+
+    def lxu(lr, zz):
+        _, o = oracle_mod.if_map(math.exp(lr), zz, 1 - zz)
+        return np.array([math.log(o[0]), math.log(o[2])])
+    lr = math.log(r)
+    d_lr = (lxu(lr + h, z) - lxu(lr - h, z)) / (2 * h)
+    d_z = (lxu(lr, z + h * z * (1 - z)) - lxu(lr, z - h * z * (1 - z))) / (2 * h * z * (1 - z))
+    jac = abs(d_lr[0] * d_z[1] - d_lr[1] * d_z[0])
+    assert jac == pytest.approx(1.0 / (u + x - 2 * u * x), rel=1e-5)  # dx/x du/u = J dt/t dz
+
+
+@pytest.mark.parametrize("r,z", [(1e-3, 0.3), (1e-6, 0.9), (0.02, 0.6)])
+def test_ii_map_round_trip_and_jacobian(oracle_mod, r, z):
+    ok, (x, omx, v) = oracle_mod.ii_map(r, z, 1 - z)
+    assert ok
+    assert x + v == pytest.approx(z, rel=1e-14)                        # z = x + v
+    assert v * (1 - x - v) / x == pytest.approx(r, rel=1e-12)          # t = v(1-x-v)/x s
+    h = 1e-6
+
+    def lxv(lr, zz):
+        _, o = oracle_mod.ii_map(math.exp(lr), zz, 1 - zz)
+        return np.array([math.log(o[0]), math.log(o[2])])
+    lr = math.log(r)
+    d_lr = (lxv(lr + h, z) - lxv(lr - h, z)) / (2 * h)
+    d_z = (lxv(lr, z + h) - lxv(lr, z - h)) / (2 * h)
+    jac = abs(d_lr[0] * d_z[1] - d_lr[1] * d_z[0])
+    assert jac == pytest.approx(1.0 / z, rel=1e-5)
+
+
+@pytest.mark.parametrize("eta,s,t", [(0.01, 1e4, 4.0), (0.1, 2e3, 10.0), (0.3, 500.0, 30.0)])
+def test_z_limits_are_the_x_equals_eta_boundary(oracle_mod, eta, s, t):
+    """The printed z+- of FI, IF and II are exactly where x reaches eta."""
+    ok, zm, d = oracle_mod.z_limits(1, t, s, eta)
+    for z, omz in ((zm, 1 - zm), (1 - d, d)):
+        x = 1.0 / (1.0 + t / (z * omz * s))
+        assert x == pytest.approx(eta, rel=1e-9)
+    for typ, fn in ((2, oracle_mod.if_map), (3, oracle_mod.ii_map)):
+        ok, zm, d = oracle_mod.z_limits(typ, t, s, eta)
+        assert ok
+        for z, omz in ((zm, 1 - zm), (1 - d, d)):
+            _, o = fn(t / s, z, omz)
+            assert o[0] == pytest.approx(eta, rel=1e-9)
+    # FF limits match the naive formula and vanish at t = s/4
+    ok, zm, d = oracle_mod.z_limits(0, t, s, 0.0)
+    assert zm == pytest.approx(0.5 * (1 - math.sqrt(1 - 4 * t / s)), rel=1e-12)
+    assert not oracle_mod.z_limits(0, s / 4 * 1.000001, s, 0.0)[0]
+
+
+def test_shape_sampling_inverts_cdf(oracle_mod):
+    zm, d = 0.01, 1e-4
+    for shape, pdfn in ((0, lambda z: 1 / (1 - z)), (1, lambda z: 1.0),
+                        (2, lambda z: 1 / (z * (1 - z))), (3, lambda z: 1 / z)):
+        tot = integrate.quad(pdfn, zm, 1 - d, limit=200)[0]
+        assert oracle_mod.shape_integral(shape, zm, d) == pytest.approx(tot, rel=1e-9)
+        for R in (0.1, 0.5, 0.93):
+            z, omz = oracle_mod.shape_sample(shape, zm, d, R)
+            assert z + omz == pytest.approx(1.0, abs=1e-15)
+            assert integrate.quad(pdfn, zm, z, limit=200)[0] / tot == pytest.approx(R, rel=1e-8)
+
+
+def test_transverse_basis(oracle_mod):
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        def lightlike():
+            v = rng.normal(size=3) * rng.uniform(0.1, 100)
+            return np.array([np.linalg.norm(v), *v])
+        P, K = lightlike(), lightlike()
+        e1, e2 = oracle_mod.basis(P, K)
+        mk = lambda a, b: a[0] * b[0] - a[1:] @ b[1:]
+        for e in (e1, e2):
+            assert abs(mk(e, P)) < 1e-9 * P[0] and abs(mk(e, K)) < 1e-9 * K[0]
+            assert mk(e, e) == pytest.approx(-1.0, abs=1e-12)
+        assert abs(mk(e1, e2)) < 1e-12
+
+
+# --------------------------------------------------------------------------- full events
+def _conservation(r, sqrt_s, pp):
+    P, ini = r["p"], r["initial"]
+    fin = np.where(ini[..., None] == 0, P, 0).sum(1)
+    inc = np.where(ini[..., None] == 1, P, 0).sum(1)
+    if not pp:
+        inc = np.zeros_like(fin)
+        inc[:, 0] = sqrt_s
+    return np.abs(fin - inc).max(1)
+
+
+@pytest.mark.parametrize("process,sqrt_s,n", [(0, 91.2, 3000), (0, 500.0, 1500), (1, 13600.0, 1500),
+                                               (2, 13600.0, 1500)])
+def test_events_conserve_momentum_colour_and_flavour(oracle_mod, pdf, process, sqrt_s, n):
+    """Paper's P4 and the bookkeeping invariants of every showered event."""
+    st = oracle_mod.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
+    r = oracle_mod.run(st, 0, n, pdf, threads=4)
+    assert np.all(r["status"] == 1)
+    # the II kick in strongly boosted events loses ~gamma^2 ulps: 1e-11 sqrt(s)
+    assert _conservation(r, sqrt_s, process > 0).max() < 1e-11 * sqrt_s
+    assert r["counters"][:, 5].sum() == 0  # no overestimate violations
+    for e in range(n):
+        m = r["npart"][e]
+        p = r["p"][e, :m]
+        fl, col, acol, ini = r["flav"][e, :m], r["col"][e, :m], r["acol"][e, :m], r["initial"][e, :m]
+        m2 = p[:, 0] ** 2 - (p[:, 1:] ** 2).sum(1)
+        parton = fl != 23
+        # on-shell to rounding of the largest momentum in the event (boosted II kicks)
+        assert np.all(np.abs(m2[parton]) <= 1e-12 * p[:, 0].max() ** 2 + 1e-12)
+        if process > 0:
+            assert m2[2] == pytest.approx(MZ * MZ, rel=1e-7)
+        tags = np.concatenate([col[col != 0], acol[acol != 0]])
+        u, c = np.unique(tags, return_counts=True)
+        assert np.all(c == 2)
+        assert set(col[col != 0]) == set(acol[acol != 0])
+        g = fl == 21
+        assert np.all((col[g] != 0) & (acol[g] != 0))
+        q = (fl != 21) & parton
+        assert np.all((col[q] != 0) ^ (acol[q] != 0))
+        # crossed colours: an incoming quark carries an anticolour tag
+        cross = np.where(ini == 1, -1, 1)
+        qn = np.where(np.abs(fl) <= 5, np.sign(fl), 0) * cross
+        assert qn.sum() == 0 if process > 0 else True
+        if process > 0:
+            assert np.all(ini[:2] == 1) and np.all(ini[2:] == 0)
+            eta = r["eta"][e]
+            assert p[0, 0] == pytest.approx(eta[0] * sqrt_s / 2, rel=1e-12)
+            assert p[1, 0] == pytest.approx(eta[1] * sqrt_s / 2, rel=1e-12)
+
+
+def test_seeds_and_event_ids_are_reproducible(oracle_mod, pdf):
+    st = oracle_mod.Settings(process=2, sqrt_s=13600.0, nmax=128)
+    a = oracle_mod.run(st, 100, 20, pdf)
+    b = oracle_mod.run(st, 95, 30, pdf, threads=3)
+    assert np.array_equal(a["p"], b["p"][5:25])
+    st2 = oracle_mod.Settings(process=2, sqrt_s=13600.0, nmax=128, seed=2)
+    c = oracle_mod.run(st2, 100, 20, pdf)
+    assert not np.array_equal(a["p"], c["p"])
+
+
+# --------------------------------------------------------------------------- observables
+def _rand_event(rng, n):
+    p = rng.normal(size=(n, 3))
+    p -= p.mean(0)
+    E = np.linalg.norm(p, axis=1)
+    return np.column_stack([E, p])
+
+
+def test_thrust_matches_axis_search(oracle_mod):
+    """T = max_n sum|p.n|/sum|p|: the oracle's value is attained by some axis
+    (lower bound by a dense random search) and no sampled axis beats it."""
+    rng = np.random.default_rng(11)
+    axes = rng.normal(size=(200_000, 3))
+    axes /= np.linalg.norm(axes, axis=1)[:, None]
+    for n in (3, 5, 9, 12, 13, 17):
+        p = _rand_event(rng, n)
+        T = 1 - oracle_mod.ee_shapes(p)[0]
+        tv = np.abs(axes @ p[:, 1:].T).sum(1) / np.linalg.norm(p[:, 1:], axis=1).sum()
+        assert tv.max() <= T + 1e-12
+        assert tv.max() >= T - 2e-3
+    # three partons: T = 2 max|p| / sum |p|
+    p = _rand_event(rng, 3)
+    mags = np.linalg.norm(p[:, 1:], axis=1)
+    assert 1 - oracle_mod.ee_shapes(p)[0] == pytest.approx(2 * mags.max() / mags.sum(), rel=1e-12)
+    # two back-to-back partons: T = 1
+    p2 = np.array([[5.0, 0, 0, 5.0], [5.0, 0, 0, -5.0]])
+    assert oracle_mod.ee_shapes(p2)[0] == pytest.approx(0.0, abs=1e-15)
+
+
+def test_durham_three_partons(oracle_mod):
+    rng = np.random.default_rng(2)
+    p = _rand_event(rng, 3)
+    ev = p[:, 0].sum()
+    ys = []
+    for i in range(3):
+        for j in range(i + 1, 3):
+            c = p[i, 1:] @ p[j, 1:] / (np.linalg.norm(p[i, 1:]) * np.linalg.norm(p[j, 1:]))
+            ys.append(2 * min(p[i, 0], p[j, 0]) ** 2 * (1 - c) / ev ** 2)
+    o = oracle_mod.ee_shapes(p)
+    assert o[1] == pytest.approx(min(ys), rel=1e-12) and o[2] == 0.0
+
+
+def test_antikt_simple_cases(oracle_mod):
+    def parton(pt, y, phi):
+        return np.array([pt * math.cosh(y), pt * math.cos(phi), pt * math.sin(phi), pt * math.sinh(y)])
+    near = np.array([parton(50, 0.0, 0.0), parton(10, 0.2, 0.2)])      # dR = 0.28 < 0.4
+    far = np.array([parton(50, 0.0, 0.0), parton(10, 0.3, 0.3)])       # dR = 0.42 > 0.4
+    j = oracle_mod.antikt(near)
+    assert len(j) == 1 and np.allclose(j[0], near.sum(0))
+    assert len(oracle_mod.antikt(far)) == 2
+    # a soft particle within R of a hard one joins it even if close to another soft one
+    three = np.array([parton(100, 0, 0), parton(1, 0.35, 0), parton(1, 0.7, 0)])
+    j = oracle_mod.antikt(three)
+    assert len(j) == 2
