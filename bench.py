@@ -1,0 +1,344 @@
+"""Benchmark: showered events per second on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic events:
+hard process, shower and observables with histogram filling, all in the CUDA
+library, with the batch's records resident in HBM. Different steps use
+different event ranges (no cached work). Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank showers its own event range (independent
+events, weak scaling, no data-path collective); the time is the maximum over
+ranks and the value is all ranks' events divided by it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "showered events/sec on 1 GB300 (learned+compacted vs plain GPU) at oracle-matched chi2/ndf<1.2"
+
+WORKLOADS = {
+    # name: (process, sqrt_s, events per step, precision, description)
+    "pp_lo_1e6_fp64": (1, 13600.0, 1_000_000, 0,
+                       "pp -> Z at 13.6 TeV, LO + initial/final-state shower, synthetic 100x50 PDF, "
+                       "1e6 events, FP64 (per-event oracle parity)"),
+    "pp_nlo_1e6_fp64": (2, 13600.0, 1_000_000, 0,
+                        "NLO-matched pp -> Z at 13.6 TeV, 1e6 events per step, FP64"),
+    "ee91_1e4_fp64": (0, 91.2, 10_000, 0, "e+e- -> q qbar at 91.2 GeV, FSR only, 1e4 events, FP64"),
+}
+DEFAULT_WORKLOAD = "pp_lo_1e6_fp64"
+
+# Algorithmic FP64 work per unit, counted from the formulas of one trial,
+# one initial-state trial's extra bound lookup and one accepted emission; a
+# log, exp or sqrt counts as 20 FLOP (a degree ~10 polynomial with range
+# reduction). See the design notes for the derivation.
+FLOP_PER_TRIAL = 85.0
+FLOP_PER_ISR_TRIAL = 16.0
+FLOP_PER_STEP = 160.0
+FLOP_PER_ACCEPT = 300.0
+# FP64 peak of one GB300: 1.25 TFLOP/s nominal (dense, vector + tensor).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def algorithmic_flops(stats: dict) -> float:
+    return (stats["trials"] * FLOP_PER_TRIAL + stats["isr_trials"] * FLOP_PER_ISR_TRIAL
+            + stats["steps"] * FLOP_PER_STEP + stats["accepts"] * FLOP_PER_ACCEPT)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def rank_first_event(rank: int, step: int, events_per_step: int, steps_total: int) -> int:
+    """Event range of (rank, step): ranks own disjoint contiguous blocks."""
+    return (rank * steps_total + step) * events_per_step
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def cpu_baseline(process: int, sqrt_s: float, target_s: float = 12.0) -> dict:
+    """The FP64 oracle as it stands, on all host cores, over a bounded sample."""
+    from oracle import oracle as O
+    from paper_2511_19633_gb300 import inputs
+    pdf = inputs.synthetic_pdf_grid()
+    cores = os.cpu_count() or 1
+    st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
+    probe = 500 * cores
+    t0 = time.perf_counter()
+    O.run(st, 10_000_000_000, probe, pdf if process else None, threads=cores)
+    dt = time.perf_counter() - t0
+    n = max(probe, int(probe * target_s / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    O.run(st, 20_000_000_000, n, pdf if process else None, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": "%d events of the same workload (event ids from 2e10), %.1f s" % (n, dt)}
+
+
+def run_reference(args, ws, rank):
+    name = args.workload
+    process, sqrt_s, per_step, precision, desc = WORKLOADS[name]
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2511_19633_gb300 import inputs
+    pdf = inputs.synthetic_pdf_grid()
+    cores = os.cpu_count() or 1
+    st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
+    # calibrate a per-step sample of about 20 s of CPU work
+    probe = 200 * cores
+    t0 = time.perf_counter()
+    O.run(st, 30_000_000_000, probe, pdf if process else None, threads=cores)
+    rate = probe / (time.perf_counter() - t0)
+    n = max(probe, int(rate * 20.0 / max(1, args.steps + args.warmup) * 3))
+    for w in range(args.warmup):
+        O.run(st, 31_000_000_000 + w * n, min(n, probe), pdf if process else None, threads=cores)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.run(st, 32_000_000_000 + k * n, n, pdf if process else None, threads=cores)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "description": desc, "events_per_step": n},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "events/s",
+                             "sample": "%d events per step on %d threads" % (n, cores)},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2511_19633_gb300 import build
+    build.build()
+    from paper_2511_19633_gb300 import gaps as G
+    from paper_2511_19633_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    name = args.workload
+    process, sqrt_s, per_step, precision, desc = WORKLOADS[name]
+    if args.events:
+        per_step = args.events
+    nmax = 128
+    pdf = inputs.synthetic_pdf_grid()
+    cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=nmax, seed=1,
+                        precision=precision, block_size=args.block, schedule=args.schedule,
+                        blocks_per_sm=args.bps)
+    ctx = G.gaps_init(cfg)
+    buf = G.EventBuffers.allocate(per_step, nmax)
+    ev = buf.view()
+    obs = torch.zeros((G.GAPS_NOBS, per_step), dtype=torch.float64, device="cuda")
+    hw = torch.zeros((G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
+    hw2 = torch.zeros_like(hw)
+    hists = G.GapsHists(hw.data_ptr(), hw2.data_ptr())
+    stream = torch.cuda.current_stream()
+    steps_total = args.warmup + args.steps
+
+    def step(k, ev_sh=None):
+        first = rank_first_event(rank, k, per_step, steps_total)
+        G.gaps_generate_hard(ctx, first, per_step, ev, stream)
+        if ev_sh:
+            ev_sh[0].record(stream)
+        G.gaps_shower(ctx, first, per_step, ev, stream)
+        if ev_sh:
+            ev_sh[1].record(stream)
+        G.gaps_observables(ctx, per_step, ev, obs, hists, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    G.gaps_reset_stats(ctx, stream)
+    shower_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            step(args.warmup + k, shower_ev[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    shower_ms = [a.elapsed_time(b) for a, b in shower_ev]
+    stats = G.gaps_get_stats(ctx, stream)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_events = per_step * args.steps * ws
+    value = total_events / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: PDF grid from pinned host
+    # memory into a new context, the full path, per-event observables and the
+    # histograms back into pinned host memory
+    pdf_host = torch.from_numpy(pdf).pin_memory() if process else None
+    obs_host = torch.empty((G.GAPS_NOBS, per_step), dtype=torch.float64).pin_memory()
+    h_host = torch.empty((2, G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        c2 = G.make_config(process, sqrt_s, pdf_grid=None, nmax=nmax, seed=1, precision=precision,
+                           block_size=args.block, schedule=args.schedule, blocks_per_sm=args.bps)
+        if pdf_host is not None:
+            c2.pdf_grid = pdf_host.data_ptr()
+        ctx2 = G.gaps_init(c2)
+        hw.zero_(); hw2.zero_()
+        first = rank_first_event(rank, k, per_step, steps_total) + (1 << 50)
+        G.gaps_generate_hard(ctx2, first, per_step, ev, stream)
+        G.gaps_shower(ctx2, first, per_step, ev, stream)
+        G.gaps_observables(ctx2, per_step, ev, obs, hists, stream)
+        obs_host.copy_(obs, non_blocking=True)
+        h_host[0].copy_(hw, non_blocking=True)
+        h_host[1].copy_(hw2, non_blocking=True)
+        torch.cuda.synchronize()
+        G.gaps_destroy(ctx2)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = per_step * e2e_steps * ws / e2e_s
+    h2d = pdf.nbytes if process else 0
+    d2h = obs_host.numel() * 8 + h_host.numel() * 8
+
+    flops = algorithmic_flops(stats)
+    mean_shower_s = sum(shower_ms) / len(shower_ms) / 1e3
+    achieved = flops / args.steps / mean_shower_s / 1e12
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == 0 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": name, "description": desc, "events_per_step": per_step,
+                   "parallelism": "independent event ranges per GPU" if ws > 1 else "single GPU",
+                   "schedule": "persistent" if args.schedule else "per-event",
+                   "block": args.block or 128, "blocks_per_sm": args.bps,
+                   "l2": "records of %.1f GB per step regenerated each step (> 129 MB L2)"
+                         % (per_step * nmax * 44 / 1e9)},
+        "roofline": {"bound": "alu", "kernel": "shower", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 (dense) from the profiling recipe",
+                     "shower_ms": mean_shower_s * 1e3,
+                     "flop_per_event": flops / max(1, stats["events"])},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "shower_stats": {k: stats[k] for k in ("events", "steps", "trials", "isr_trials", "vetoes",
+                                                "accepts", "violations", "err_capacity",
+                                                "err_iter_cap", "err_numeric")},
+        "hbm_gbs_measured": peaks.get("hbm_gbs"),
+    }
+    G.gaps_destroy(ctx)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(process, sqrt_s)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--events", type=int, default=0, help="override events per step")
+    ap.add_argument("--schedule", type=int, default=1)
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--bps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * gaps.h - C interface of the GB300 (sm_103a) parton-shower library.
+ *
+ * The library generates hard events, showers them with the dipole-shower
+ * max-veto algorithm (Seymour & Sule, arXiv:2511.19633, Section 2 and Fig. 1)
+ * with initial- and final-state dipoles (Appendix B), the PDF-ratio veto for
+ * backward initial-state evolution (Appendix A), Catani-Seymour recoil
+ * kinematics (Appendix B.2-B.5) and the MC@NLO-like matching for on-shell Z
+ * production (Appendix C), and computes per-event observables and weighted
+ * histograms (Section 4.1). One event per CUDA thread.
+ *
+ * Conventions shared by every entry point:
+ *   - Four-vectors are (E, px, py, pz) in GeV, metric (+,-,-,-).
+ *   - Incoming partons carry their physical momenta and crossed colour tags
+ *     (an incoming quark holds an anticolour tag), so that partons i and k
+ *     form a dipole when col[i] == acol[k] or acol[i] == col[k].
+ *   - pp events: slot 0 = parton from beam 1 (+z), slot 1 = beam 2 (-z),
+ *     slot 2 = the Z boson (flavour 23), then final-state partons.
+ *     e+e- events: slot 0 = quark, slot 1 = antiquark, then emissions.
+ *   - Flavours: 21 gluon, 1..5 d u s c b, negative = antiquark, 23 = Z.
+ *   - Random numbers: Philox-4x32-10 (Salmon et al., SC'11) with key =
+ *     (seed_lo, seed_hi) and counter = (event_lo, event_hi, draw_lo, draw_hi);
+ *     event k of a seed is identical whatever the chunking or launch shape.
+ *   - Every call is asynchronous on the given stream (a cudaStream_t passed
+ *     as void*, NULL = legacy default stream). Return values report argument
+ *     and launch errors; errors found on the device (capacity, iteration cap,
+ *     non-finite values) are stored per event in `status` and counted by
+ *     gaps_get_stats, which synchronises the stream.
+ *   - Device buffers are owned by the caller; the library owns only its copy
+ *     of the PDF grid, its bound tables and its counters.
+ */
+#ifndef GAPS_H
+#define GAPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes (0 or negative) */
+#define GAPS_OK                0
+#define GAPS_ERR_INVALID_ARG  -1
+#define GAPS_ERR_CAPACITY     -2   /* an event reached nmax partons */
+#define GAPS_ERR_ITER_CAP     -3   /* an event exceeded the step cap */
+#define GAPS_ERR_NUMERIC      -4   /* a non-finite scale or weight */
+#define GAPS_ERR_CUDA         -5   /* a CUDA runtime call failed */
+#define GAPS_ERR_NO_DEVICE    -6
+
+/* processes (Section 4.1; e+e- as in GAPS 1) */
+#define GAPS_EE_QQ       0   /* e+e- -> Z/gamma* -> q qbar, final-state shower */
+#define GAPS_PP_Z_LO     1   /* pp -> Z at LO, initial- and final-state shower */
+#define GAPS_PP_Z_NLO    2   /* pp -> Z, S and H events of Appendix C.4 */
+
+/* arithmetic of the shower */
+#define GAPS_FP64        0   /* all FP64; matches the reference per event */
+#define GAPS_MIXED       1   /* FP32 trials, PDF and bounds; FP64 kinematics */
+
+/* launch schedules of the shower */
+#define GAPS_SCHED_PER_EVENT  0   /* one thread per event, run to completion */
+#define GAPS_SCHED_PERSISTENT 1   /* persistent grid, finished lanes take the next event */
+
+/* per-event status values; negative values are the error codes above */
+#define GAPS_STATUS_ACTIVE 0
+#define GAPS_STATUS_DONE   1
+
+/* PDF grid geometry: value = x f(x, Q^2), layout [GAPS_PDF_NFL][NX][NQ],
+ * flavour order g d u s c b dbar ubar sbar cbar bbar; nodes uniform in ln x
+ * over [GAPS_PDF_XMIN, GAPS_PDF_XMAX] and in ln Q^2 over [Q2MIN, Q2MAX].
+ * Bilinear interpolation in (ln x, ln Q^2); zero outside (Appendix B.6). */
+#define GAPS_PDF_NFL   11
+#define GAPS_PDF_NX    100
+#define GAPS_PDF_NQ    50
+#define GAPS_PDF_XMIN  1e-6
+#define GAPS_PDF_XMAX  (1.0 - 1e-6)
+#define GAPS_PDF_Q2MIN 0.5
+#define GAPS_PDF_Q2MAX (13600.0 * 13600.0)
+
+#define GAPS_NOBS      8     /* per-event observables, see gaps_observables */
+#define GAPS_NHIST     6     /* histograms per process family */
+#define GAPS_HIST_BINS 66    /* per histogram: underflow, 64 bins, overflow */
+
+typedef struct gaps_ctx gaps_ctx;  /* opaque, owned by the library */
+
+/* Configuration, copied by gaps_init. */
+typedef struct {
+    int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO or GAPS_PP_Z_NLO */
+    int precision;        /* GAPS_FP64 or GAPS_MIXED */
+    int nf;               /* active flavours for g -> q qbar (5) */
+    int nmax_partons;     /* capacity per event, 4..128 */
+    double sqrt_s;        /* collider energy, GeV */
+    double alpha_s_mz;    /* alpha_s(m_Z^2); one-loop running with 5 flavours */
+    double t_cut;         /* shower cutoff on t = pT^2, GeV^2, >= GAPS_PDF_Q2MIN */
+    double p_s;           /* probability of an S event in GAPS_PP_Z_NLO, in (0,1) */
+    uint64_t seed;        /* Philox key */
+    const float* pdf_grid;/* host pointer to the PDF grid (pp processes), copied */
+    int block_size;       /* threads per block for the shower, 0 = library default */
+    int schedule;         /* GAPS_SCHED_PER_EVENT or GAPS_SCHED_PERSISTENT */
+    int blocks_per_sm;    /* persistent schedule: resident blocks per SM, 0 = default */
+} gaps_config;
+
+/* Event records: structure of arrays in device memory, caller-owned, event
+ * index fastest so that a warp's loads are coalesced. `capacity` is the
+ * allocated number of events (row stride) and `nmax` the slots per event. */
+typedef struct {
+    uint64_t capacity;
+    int nmax;
+    double* p;        /* [4][nmax][capacity] momenta */
+    int32_t* flav;    /* [nmax][capacity] */
+    int32_t* col;     /* [nmax][capacity] colour tag (crossed for incoming) */
+    int32_t* acol;    /* [nmax][capacity] anticolour tag */
+    int32_t* npart;   /* [capacity] partons in the record */
+    int32_t* status;  /* [capacity] GAPS_STATUS_* or a negative error code */
+    int32_t* n_emit;  /* [capacity] accepted emissions */
+    double* weight;   /* [capacity] event weight, pb (may be negative for H) */
+    double* t;        /* [capacity] current evolution scale */
+    double* eta;      /* [2][capacity] momentum fractions of slots 0 and 1 */
+    uint64_t* draw;   /* [capacity] next Philox block of the event's stream */
+} gaps_events;
+
+/* Weighted histograms in device memory, caller-owned and zeroed by the
+ * caller: sumw and sumw2 are [GAPS_NHIST][GAPS_HIST_BINS] doubles; the
+ * binning of each histogram is returned by gaps_hist_binning. */
+typedef struct {
+    double* sumw;
+    double* sumw2;
+} gaps_hists;
+
+/* Counters accumulated over all gaps_shower calls of a context. */
+typedef struct {
+    uint64_t events;      /* events finished */
+    uint64_t steps;       /* max-veto cycles (Fig. 1) */
+    uint64_t trials;      /* dipole-channel trials with a non-zero overestimate */
+    uint64_t isr_trials;  /* of which with an initial-state emitter */
+    uint64_t vetoes;      /* rejected winners */
+    uint64_t accepts;     /* accepted emissions */
+    uint64_t violations;  /* acceptance weights above one (overestimate failures) */
+    uint64_t err_capacity, err_iter_cap, err_numeric;
+    uint64_t lane_steps;  /* active lanes summed over warp steps (divergence) */
+    uint64_t warp_steps;  /* warp steps x 32 */
+} gaps_stats;
+
+/* Creates a context on the current CUDA device: validates `cfg`, copies the
+ * PDF grid and builds the certified PDF-ratio bound tables of Appendix A.2
+ * (reading: a strict bound replaces the paper's percentile fit).
+ * Returns GAPS_ERR_INVALID_ARG for a bad configuration (process, sqrt_s,
+ * t_cut below the grid, nmax out of range, missing grid for pp), and
+ * GAPS_ERR_NO_DEVICE / GAPS_ERR_CUDA on device errors; *out is set only on
+ * success. */
+int gaps_init(gaps_ctx** out, const gaps_config* cfg);
+
+/* Hard events (Appendix C.1-C.4; e+e- from the textbook LO formula):
+ * fills records first_event .. first_event + n - 1 into slots 0 .. n-1 of
+ * `ev` (n <= ev->capacity), sets status ACTIVE, draw = 0 and the starting
+ * scale t = s (power shower, Appendix C.4). */
+int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
+                       const gaps_events* ev, void* stream);
+
+/* Shower (Section 2, Fig. 1; Appendices A-B): evolves every ACTIVE record
+ * among the first n until its winner scale falls below t_cut. Records are
+ * read and written in place; first_event must be the value given to
+ * gaps_generate_hard (it keys the random streams). */
+int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
+                const gaps_events* ev, void* stream);
+
+/* Observables (Section 4.1): writes obs[GAPS_NOBS][capacity] (device) and,
+ * when hists != NULL, adds every event with status DONE to the histograms.
+ *   e+e-: 0 1-T, 1 y23, 2 y34 (Durham), 3 final partons, 4 emissions
+ *   pp  : 0 Z pT, 1 Z rapidity, 2 Z phi (0 without emission), 3 anti-kT
+ *         R=0.4 jets with pT > 5 GeV and |eta| < 5, 4 leading jet pT,
+ *         5 leading jet eta, 6 final partons, 7 emissions */
+int gaps_observables(gaps_ctx* ctx, uint64_t n, const gaps_events* ev,
+                     double* obs, const gaps_hists* hists, void* stream);
+
+/* Binning of histogram h (0 .. GAPS_NHIST-1) of the context's process:
+ * lo, hi, number of regular bins (<= 64), observable index and whether the
+ * observable is binned in log10. Returns GAPS_ERR_INVALID_ARG for bad h. */
+int gaps_hist_binning(const gaps_ctx* ctx, int h, double* lo, double* hi,
+                      int* nbins, int* obs_index, int* log10_axis);
+
+/* Synchronises `stream` and copies the accumulated counters. */
+int gaps_get_stats(gaps_ctx* ctx, gaps_stats* out, void* stream);
+
+/* Zeroes the counters (asynchronously on `stream`). */
+int gaps_reset_stats(gaps_ctx* ctx, void* stream);
+
+/* Static description of a return code; never NULL. */
+const char* gaps_error_string(int code);
+
+/* Frees the context and its device memory. NULL is ignored. */
+void gaps_destroy(gaps_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAPS_H */

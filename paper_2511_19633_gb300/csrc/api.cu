@@ -1,0 +1,267 @@
+// C ABI of the shower library (include/gaps.h): configuration checks, the
+// library-owned device state (PDF grid, certified bound tables, counters) and
+// the launches of the hard-process, shower and observable kernels.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gaps {
+cudaError_t launch_generate_hard(const DevParams&, const DevEvents&, uint64_t, uint64_t, cudaStream_t);
+cudaError_t launch_shower_fp64(const DevParams&, const DevEvents&, uint64_t, uint64_t, int, int,
+                               unsigned long long*, cudaStream_t);
+cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, double*, const HistDef&,
+                               double*, double*, cudaStream_t);
+}  // namespace gaps
+
+using namespace gaps;
+
+struct gaps_ctx {
+  gaps_config cfg;
+  int device = 0;
+  int n_sm = 0;
+  float* d_grid = nullptr;
+  double* d_tables = nullptr;  // umax [12][100], sufmax [12][101], lmin [12][100]
+  unsigned long long* d_counters = nullptr;  // C_NCOUNTERS + 1 (work counter)
+  DevParams P;
+  HistDef H;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? GAPS_OK : GAPS_ERR_CUDA; }
+
+bool events_ok(const gaps_ctx* c, const gaps_events* ev, uint64_t n) {
+  if (!ev || !ev->p || !ev->flav || !ev->col || !ev->acol || !ev->npart || !ev->status ||
+      !ev->n_emit || !ev->weight || !ev->t || !ev->eta || !ev->draw)
+    return false;
+  if (n > ev->capacity) return false;
+  if (ev->nmax != c->cfg.nmax_partons) return false;
+  return true;
+}
+
+DevEvents dev_events(const gaps_events* ev) {
+  DevEvents E;
+  E.cap = ev->capacity; E.nmax = ev->nmax; E.p = ev->p; E.flav = ev->flav; E.col = ev->col;
+  E.acol = ev->acol; E.npart = ev->npart; E.status = ev->status; E.n_emit = ev->n_emit;
+  E.weight = ev->weight; E.t = ev->t; E.eta = ev->eta; E.draw = ev->draw;
+  return E;
+}
+
+// Per-node extrema of the grid over Q^2 and their suffix maxima in x: the
+// ingredients of the certified PDF-ratio bound (index 11 = sum of the ten
+// quark and antiquark densities).
+void build_bound_tables(const float* g, std::vector<double>& out) {
+  const int NX = GAPS_PDF_NX, NQ = GAPS_PDF_NQ;
+  out.assign(12 * NX + 12 * (NX + 1) + 12 * NX, 0.0);
+  double* umax = out.data();
+  double* sufmax = umax + 12 * NX;
+  double* lmin = sufmax + 12 * (NX + 1);
+  auto node = [&](int f, int ix, int iq) -> double {
+    if (f < 11) return (double)g[((size_t)f * NX + ix) * NQ + iq];
+    double s = 0.0;
+    for (int k = 1; k <= 10; ++k) s += (double)g[((size_t)k * NX + ix) * NQ + iq];
+    return s;
+  };
+  for (int f = 0; f < 12; ++f) {
+    for (int ix = 0; ix < NX; ++ix) {
+      double mx = node(f, ix, 0), mn = mx;
+      for (int iq = 1; iq < NQ; ++iq) {
+        double v = node(f, ix, iq);
+        if (v > mx) mx = v;
+        if (v < mn) mn = v;
+      }
+      umax[f * NX + ix] = mx;
+      lmin[f * NX + ix] = mn;
+    }
+    sufmax[f * (NX + 1) + NX] = 0.0;
+    for (int ix = NX - 1; ix >= 0; --ix) {
+      double a = umax[f * NX + ix], b = sufmax[f * (NX + 1) + ix + 1];
+      sufmax[f * (NX + 1) + ix] = a > b ? a : b;
+    }
+  }
+}
+
+void set_hist_defs(int process, HistDef& H) {
+  const double pi = 3.14159265358979323846;
+  if (process == GAPS_EE_QQ) {
+    // 1-T, log10 y23, log10 y34, final partons, emissions, log10(1-T)
+    const double lo[6] = {0.0, -5.0, -5.0, -0.5, -0.5, -4.0};
+    const double hi[6] = {0.5, 0.0, 0.0, 63.5, 63.5, 0.0};
+    const int nb[6] = {50, 50, 50, 64, 64, 40}, ob[6] = {0, 1, 2, 3, 4, 0}, lg[6] = {0, 1, 1, 0, 0, 1};
+    for (int h = 0; h < 6; ++h) { H.lo[h] = lo[h]; H.hi[h] = hi[h]; H.nb[h] = nb[h]; H.obs[h] = ob[h]; H.logx[h] = lg[h]; }
+  } else {
+    // log10 Z pT, Z y, Z phi, jets, log10 leading-jet pT, final partons
+    const double lo[6] = {-1.0, -6.0, -pi, -0.5, 0.5, -0.5};
+    const double hi[6] = {3.0, 6.0, pi, 15.5, 3.5, 127.5};
+    const int nb[6] = {40, 48, 32, 16, 30, 64}, ob[6] = {0, 1, 2, 3, 4, 6}, lg[6] = {1, 0, 0, 0, 1, 0};
+    for (int h = 0; h < 6; ++h) { H.lo[h] = lo[h]; H.hi[h] = hi[h]; H.nb[h] = nb[h]; H.obs[h] = ob[h]; H.logx[h] = lg[h]; }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gaps_error_string(int code) {
+  switch (code) {
+    case GAPS_OK: return "ok";
+    case GAPS_ERR_INVALID_ARG: return "invalid argument";
+    case GAPS_ERR_CAPACITY: return "an event exceeded its parton capacity";
+    case GAPS_ERR_ITER_CAP: return "an event exceeded the shower step cap";
+    case GAPS_ERR_NUMERIC: return "non-finite scale or weight";
+    case GAPS_ERR_CUDA: return "CUDA runtime error";
+    case GAPS_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
+  if (!out || !cfg) return GAPS_ERR_INVALID_ARG;
+  const gaps_config& c = *cfg;
+  if (c.process < GAPS_EE_QQ || c.process > GAPS_PP_Z_NLO) return GAPS_ERR_INVALID_ARG;
+  if (c.precision != GAPS_FP64 && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  if (!(c.sqrt_s > 0.0) || !std::isfinite(c.sqrt_s)) return GAPS_ERR_INVALID_ARG;
+  if (c.process != GAPS_EE_QQ && !(c.sqrt_s > 91.1876 && c.sqrt_s <= 13600.0)) return GAPS_ERR_INVALID_ARG;
+  if (!(c.t_cut >= GAPS_PDF_Q2MIN) || !std::isfinite(c.t_cut)) return GAPS_ERR_INVALID_ARG;
+  if (!(c.alpha_s_mz > 0.0 && c.alpha_s_mz < 1.0)) return GAPS_ERR_INVALID_ARG;
+  if (c.nf < 1 || c.nf > 5) return GAPS_ERR_INVALID_ARG;
+  if (c.nmax_partons < 4 || c.nmax_partons > 128) return GAPS_ERR_INVALID_ARG;
+  if (c.process == GAPS_PP_Z_NLO && !(c.p_s > 0.0 && c.p_s < 1.0)) return GAPS_ERR_INVALID_ARG;
+  if (c.process != GAPS_EE_QQ && !c.pdf_grid) return GAPS_ERR_INVALID_ARG;
+  if (c.block_size < 0 || c.block_size > 1024 || (c.block_size % 32) != 0) return GAPS_ERR_INVALID_ARG;
+  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT) return GAPS_ERR_INVALID_ARG;
+  if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
+  // one-loop running must stay below its pole down to the cutoff
+  const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
+  double den = 1.0 + c.alpha_s_mz * beta0 * std::log(c.t_cut / (91.1876 * 91.1876));
+  if (!(den > 0.0)) return GAPS_ERR_INVALID_ARG;
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return GAPS_ERR_NO_DEVICE;
+  gaps_ctx* ctx = new (std::nothrow) gaps_ctx();
+  if (!ctx) return GAPS_ERR_CUDA;
+  ctx->cfg = c;
+  ctx->cfg.pdf_grid = nullptr;
+  cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  int rc = GAPS_OK;
+  do {
+    const size_t gsz = (size_t)GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ;
+    if ((rc = cuda_fail(cudaMalloc(&ctx->d_grid, gsz * sizeof(float))))) break;
+    std::vector<float> zero;
+    const float* g = c.pdf_grid;
+    if (!g) { zero.assign(gsz, 0.0f); g = zero.data(); }
+    for (size_t q = 0; q < gsz; ++q)
+      if (!std::isfinite(g[q]) || g[q] < 0.0f) { rc = GAPS_ERR_INVALID_ARG; break; }
+    if (rc) break;
+    if ((rc = cuda_fail(cudaMemcpy(ctx->d_grid, g, gsz * sizeof(float), cudaMemcpyHostToDevice)))) break;
+    std::vector<double> tables;
+    build_bound_tables(g, tables);
+    if ((rc = cuda_fail(cudaMalloc(&ctx->d_tables, tables.size() * sizeof(double))))) break;
+    if ((rc = cuda_fail(cudaMemcpy(ctx->d_tables, tables.data(), tables.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice)))) break;
+    if ((rc = cuda_fail(cudaMalloc(&ctx->d_counters, (C_NCOUNTERS + 1) * sizeof(unsigned long long))))) break;
+    if ((rc = cuda_fail(cudaMemset(ctx->d_counters, 0, (C_NCOUNTERS + 1) * sizeof(unsigned long long))))) break;
+  } while (false);
+  if (rc != GAPS_OK) {
+    gaps_destroy(ctx);
+    return rc;
+  }
+  DevParams& P = ctx->P;
+  P.process = c.process;
+  P.nf = c.nf;
+  P.nmax = c.nmax_partons;
+  P.sqrt_s = c.sqrt_s;
+  P.s_had = c.sqrt_s * c.sqrt_s;
+  P.t_cut = c.t_cut;
+  P.as_mz = c.alpha_s_mz;
+  P.beta0 = beta0;
+  P.as_over = c.alpha_s_mz / den;  // alpha_s(t_cut), the overestimate of Appendix A.2
+  P.p_s = c.p_s;
+  P.seed = c.seed;
+  P.grid = ctx->d_grid;
+  P.umax = ctx->d_tables;
+  P.sufmax = ctx->d_tables + 12 * GAPS_PDF_NX;
+  P.lmin = ctx->d_tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
+  P.lxmin = std::log(GAPS_PDF_XMIN);
+  P.dlx = (std::log(GAPS_PDF_XMAX) - P.lxmin) / (GAPS_PDF_NX - 1);
+  P.lqmin = std::log(GAPS_PDF_Q2MIN);
+  P.dlq = (std::log(GAPS_PDF_Q2MAX) - P.lqmin) / (GAPS_PDF_NQ - 1);
+  P.counters = ctx->d_counters;
+  set_hist_defs(c.process, ctx->H);
+  *out = ctx;
+  return GAPS_OK;
+}
+
+int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
+                       void* stream) {
+  if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
+  return cuda_fail(launch_generate_hard(ctx->P, dev_events(ev), first_event, n, (cudaStream_t)stream));
+}
+
+int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, void* stream) {
+  if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
+  const gaps_config& c = ctx->cfg;
+  int bs = c.block_size > 0 ? c.block_size : 128;
+  int pblocks = 0;
+  if (c.schedule == GAPS_SCHED_PERSISTENT) {
+    int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
+    pblocks = ctx->n_sm * per_sm;
+  }
+  return cuda_fail(launch_shower_fp64(ctx->P, dev_events(ev), first_event, n, bs, pblocks,
+                                      ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
+}
+
+int gaps_observables(gaps_ctx* ctx, uint64_t n, const gaps_events* ev, double* obs,
+                     const gaps_hists* hists, void* stream) {
+  if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
+  if (hists && (!hists->sumw || !hists->sumw2)) return GAPS_ERR_INVALID_ARG;
+  return cuda_fail(launch_observables(ctx->P, dev_events(ev), n, obs, ctx->H,
+                                      hists ? hists->sumw : nullptr, hists ? hists->sumw2 : nullptr,
+                                      (cudaStream_t)stream));
+}
+
+int gaps_hist_binning(const gaps_ctx* ctx, int h, double* lo, double* hi, int* nbins, int* obs_index,
+                      int* log10_axis) {
+  if (!ctx || h < 0 || h >= GAPS_NHIST) return GAPS_ERR_INVALID_ARG;
+  if (lo) *lo = ctx->H.lo[h];
+  if (hi) *hi = ctx->H.hi[h];
+  if (nbins) *nbins = ctx->H.nb[h];
+  if (obs_index) *obs_index = ctx->H.obs[h];
+  if (log10_axis) *log10_axis = ctx->H.logx[h];
+  return GAPS_OK;
+}
+
+int gaps_get_stats(gaps_ctx* ctx, gaps_stats* out, void* stream) {
+  if (!ctx || !out) return GAPS_ERR_INVALID_ARG;
+  unsigned long long h[C_NCOUNTERS];
+  cudaError_t e = cudaMemcpyAsync(h, ctx->d_counters, sizeof h, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return GAPS_ERR_CUDA;
+  out->events = h[C_EVENTS]; out->steps = h[C_STEPS]; out->trials = h[C_TRIALS];
+  out->isr_trials = h[C_ISR_TRIALS]; out->vetoes = h[C_VETOES]; out->accepts = h[C_ACCEPTS];
+  out->violations = h[C_VIOLATIONS]; out->err_capacity = h[C_ERR_CAP];
+  out->err_iter_cap = h[C_ERR_ITER]; out->err_numeric = h[C_ERR_NUM];
+  out->lane_steps = h[C_LANE_STEPS]; out->warp_steps = h[C_WARP_STEPS];
+  return GAPS_OK;
+}
+
+int gaps_reset_stats(gaps_ctx* ctx, void* stream) {
+  if (!ctx) return GAPS_ERR_INVALID_ARG;
+  return cuda_fail(cudaMemsetAsync(ctx->d_counters, 0, C_NCOUNTERS * sizeof(unsigned long long),
+                                   (cudaStream_t)stream));
+}
+
+void gaps_destroy(gaps_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->d_grid) cudaFree(ctx->d_grid);
+  if (ctx->d_tables) cudaFree(ctx->d_tables);
+  if (ctx->d_counters) cudaFree(ctx->d_counters);
+  delete ctx;
+}
+
+}  // extern "C"

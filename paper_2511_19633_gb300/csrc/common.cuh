@@ -1,0 +1,125 @@
+// Shared device definitions of the GB300 shower library: parameters, event
+// record view, Philox-4x32-10, PDF interpolation and its certified ratio
+// bound, running coupling and the dipole-shower helpers of Appendix B.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gaps.h"
+
+namespace gaps {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kCF = 4.0 / 3.0, kCA = 3.0, kTR = 0.5, kNc = 3.0;
+constexpr double kMZ = 91.1876, kGZ = 2.4952;
+constexpr double kSin2W = 0.2312, kGF = 1.16638e-5, kAlphaEM = 1.0 / 128.9;
+constexpr double kGeV2pb = 0.3893794e9;
+constexpr int kNX = GAPS_PDF_NX, kNQ = GAPS_PDF_NQ;
+constexpr double kXMin = GAPS_PDF_XMIN, kXMax = GAPS_PDF_XMAX;
+constexpr double kQ2Min = GAPS_PDF_Q2MIN, kQ2Max = GAPS_PDF_Q2MAX;
+constexpr uint64_t kHardDrawBase = 0x8000000000000000ull;
+constexpr int kMaxSteps = 200000;
+
+// counters in the device stats block (uint64 each)
+enum Counter {
+  C_EVENTS = 0, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
+  C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_NCOUNTERS
+};
+
+struct DevParams {
+  int process, nf, nmax;
+  double sqrt_s, s_had, t_cut, as_mz, as_over, beta0, p_s;
+  uint64_t seed;
+  const float* grid;      // [11][100][50] x f
+  const double* umax;     // [12][100] max over Q^2 nodes (index 11 = sum of quarks)
+  const double* sufmax;   // [12][101] suffix max over x nodes of umax
+  const double* lmin;     // [12][100] min over Q^2 nodes
+  double lxmin, dlx, lqmin, dlq;
+  unsigned long long* counters;  // [C_NCOUNTERS]
+};
+
+// histogram binning of one process family
+struct HistDef {
+  double lo[GAPS_NHIST], hi[GAPS_NHIST];
+  int nb[GAPS_NHIST], obs[GAPS_NHIST], logx[GAPS_NHIST];
+};
+
+struct DevEvents {
+  uint64_t cap;
+  int nmax;
+  double* p;
+  int32_t* flav;
+  int32_t* col;
+  int32_t* acol;
+  int32_t* npart;
+  int32_t* status;
+  int32_t* n_emit;
+  double* weight;
+  double* t;
+  double* eta;
+  uint64_t* draw;
+
+  __device__ __forceinline__ double& P(int mu, int slot, uint64_t e) const {
+    return p[((uint64_t)mu * nmax + slot) * cap + e];
+  }
+  __device__ __forceinline__ int32_t& F(int slot, uint64_t e) const { return flav[(uint64_t)slot * cap + e]; }
+  __device__ __forceinline__ int32_t& C(int slot, uint64_t e) const { return col[(uint64_t)slot * cap + e]; }
+  __device__ __forceinline__ int32_t& A(int slot, uint64_t e) const { return acol[(uint64_t)slot * cap + e]; }
+};
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// (top 53 bits of hi:lo + 0.5) * 2^-53, in (0, 1)
+__device__ __forceinline__ double u01(uint32_t lo, uint32_t hi) {
+  uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return ((double)(w >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+struct Rng {
+  uint32_t k0, k1, e0, e1;
+  uint64_t draw;
+  __device__ __forceinline__ void init(uint64_t seed, uint64_t event, uint64_t d) {
+    k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
+    e0 = (uint32_t)event; e1 = (uint32_t)(event >> 32);
+    draw = d;
+  }
+  __device__ __forceinline__ void next2(double& a, double& b) {
+    uint32_t w[4];
+    philox(e0, e1, (uint32_t)draw, (uint32_t)(draw >> 32), k0, k1, w);
+    draw += 1;
+    a = u01(w[0], w[1]);
+    b = u01(w[2], w[3]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// flavours
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pdf_index(int fl) {
+  if (fl == 21) return 0;
+  if (fl >= 1 && fl <= 5) return fl;
+  if (fl <= -1 && fl >= -5) return 5 - fl;
+  return -1;
+}
+
+__device__ __forceinline__ double dot4(const double a[4], const double b[4]) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+}  // namespace gaps

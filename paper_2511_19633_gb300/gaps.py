@@ -1,0 +1,236 @@
+"""Python binding of the C ABI in include/gaps.h (ctypes).
+
+Argument marshalling only: every step of the hard process, the shower and the
+observables runs in the CUDA library libgaps.so. There is no CPU fallback;
+importing this module without the built library raises.
+PyTorch is used for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgaps.so")
+
+GAPS_OK = 0
+GAPS_ERR_INVALID_ARG = -1
+GAPS_ERR_CAPACITY = -2
+GAPS_ERR_ITER_CAP = -3
+GAPS_ERR_NUMERIC = -4
+GAPS_ERR_CUDA = -5
+GAPS_ERR_NO_DEVICE = -6
+
+GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO = 0, 1, 2
+GAPS_FP64, GAPS_MIXED = 0, 1
+GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT = 0, 1
+GAPS_STATUS_ACTIVE, GAPS_STATUS_DONE = 0, 1
+GAPS_NOBS, GAPS_NHIST, GAPS_HIST_BINS = 8, 6, 66
+
+
+class GapsConfig(ctypes.Structure):
+    _fields_ = [
+        ("process", ctypes.c_int), ("precision", ctypes.c_int), ("nf", ctypes.c_int),
+        ("nmax_partons", ctypes.c_int), ("sqrt_s", ctypes.c_double),
+        ("alpha_s_mz", ctypes.c_double), ("t_cut", ctypes.c_double), ("p_s", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("pdf_grid", ctypes.c_void_p), ("block_size", ctypes.c_int),
+        ("schedule", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+    ]
+
+
+class GapsEvents(ctypes.Structure):
+    _fields_ = [
+        ("capacity", ctypes.c_uint64), ("nmax", ctypes.c_int),
+        ("p", ctypes.c_void_p), ("flav", ctypes.c_void_p), ("col", ctypes.c_void_p),
+        ("acol", ctypes.c_void_p), ("npart", ctypes.c_void_p), ("status", ctypes.c_void_p),
+        ("n_emit", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("t", ctypes.c_void_p),
+        ("eta", ctypes.c_void_p), ("draw", ctypes.c_void_p),
+    ]
+
+
+class GapsHists(ctypes.Structure):
+    _fields_ = [("sumw", ctypes.c_void_p), ("sumw2", ctypes.c_void_p)]
+
+
+STAT_FIELDS = ("events", "steps", "trials", "isr_trials", "vetoes", "accepts", "violations",
+               "err_capacity", "err_iter_cap", "err_numeric", "lane_steps", "warp_steps")
+
+
+class GapsStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in STAT_FIELDS]
+
+
+EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
+           "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
+           "gaps_destroy")
+
+
+class GapsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s failed: %s (%d)" % (where, gaps_error_string(code), code))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgaps.so is not built (run __graft_entry__.build()); "
+                          "the shower has no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, vp, i, u64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+    lib.gaps_init.argtypes = [P(vp), P(GapsConfig)]
+    lib.gaps_generate_hard.argtypes = [vp, u64, u64, P(GapsEvents), vp]
+    lib.gaps_shower.argtypes = [vp, u64, u64, P(GapsEvents), vp]
+    lib.gaps_observables.argtypes = [vp, u64, P(GapsEvents), vp, P(GapsHists), vp]
+    d = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.gaps_hist_binning.argtypes = [vp, i, d, d, ip, ip, ip]
+    lib.gaps_get_stats.argtypes = [vp, P(GapsStats), vp]
+    lib.gaps_reset_stats.argtypes = [vp, vp]
+    lib.gaps_error_string.argtypes = [i]
+    lib.gaps_error_string.restype = ctypes.c_char_p
+    lib.gaps_destroy.argtypes = [vp]
+    lib.gaps_destroy.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != GAPS_OK:
+        raise GapsError(rc, where)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+def gaps_error_string(code: int) -> str:
+    return _lib.gaps_error_string(code).decode()
+
+
+def gaps_init(cfg: GapsConfig) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib.gaps_init(ctypes.byref(h), ctypes.byref(cfg)), "gaps_init")
+    return h
+
+
+def gaps_generate_hard(ctx, first_event: int, n: int, ev: GapsEvents, stream=None):
+    _check(_lib.gaps_generate_hard(ctx, first_event, n, ctypes.byref(ev), _stream_ptr(stream)),
+           "gaps_generate_hard")
+
+
+def gaps_shower(ctx, first_event: int, n: int, ev: GapsEvents, stream=None):
+    _check(_lib.gaps_shower(ctx, first_event, n, ctypes.byref(ev), _stream_ptr(stream)), "gaps_shower")
+
+
+def gaps_observables(ctx, n: int, ev: GapsEvents, obs: torch.Tensor | None,
+                     hists: GapsHists | None, stream=None):
+    _check(_lib.gaps_observables(ctx, n, ctypes.byref(ev), None if obs is None else obs.data_ptr(),
+                                 None if hists is None else ctypes.byref(hists), _stream_ptr(stream)),
+           "gaps_observables")
+
+
+def gaps_hist_binning(ctx, h: int) -> dict:
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    nb, ob, lg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.gaps_hist_binning(ctx, h, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(nb),
+                                  ctypes.byref(ob), ctypes.byref(lg)), "gaps_hist_binning")
+    return {"lo": lo.value, "hi": hi.value, "nbins": nb.value, "obs": ob.value, "log10": bool(lg.value)}
+
+
+def gaps_get_stats(ctx, stream=None) -> dict:
+    st = GapsStats()
+    _check(_lib.gaps_get_stats(ctx, ctypes.byref(st), _stream_ptr(stream)), "gaps_get_stats")
+    return {n: int(getattr(st, n)) for n in STAT_FIELDS}
+
+
+def gaps_reset_stats(ctx, stream=None):
+    _check(_lib.gaps_reset_stats(ctx, _stream_ptr(stream)), "gaps_reset_stats")
+
+
+def gaps_destroy(ctx):
+    _lib.gaps_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# device buffers (torch-allocated) for the structure-of-arrays records
+# ---------------------------------------------------------------------------
+@dataclass
+class EventBuffers:
+    capacity: int
+    nmax: int
+    p: torch.Tensor       # [4][nmax][capacity] f64
+    flav: torch.Tensor    # [nmax][capacity] i32
+    col: torch.Tensor
+    acol: torch.Tensor
+    npart: torch.Tensor   # [capacity] i32
+    status: torch.Tensor
+    n_emit: torch.Tensor
+    weight: torch.Tensor  # [capacity] f64
+    t: torch.Tensor
+    eta: torch.Tensor     # [2][capacity] f64
+    draw: torch.Tensor    # [capacity] i64 (uint64 bits)
+
+    @staticmethod
+    def allocate(capacity: int, nmax: int, device="cuda") -> "EventBuffers":
+        f64, i32 = torch.float64, torch.int32
+        return EventBuffers(
+            capacity, nmax,
+            torch.zeros((4, nmax, capacity), dtype=f64, device=device),
+            torch.zeros((nmax, capacity), dtype=i32, device=device),
+            torch.zeros((nmax, capacity), dtype=i32, device=device),
+            torch.zeros((nmax, capacity), dtype=i32, device=device),
+            torch.zeros(capacity, dtype=i32, device=device),
+            torch.zeros(capacity, dtype=i32, device=device),
+            torch.zeros(capacity, dtype=i32, device=device),
+            torch.zeros(capacity, dtype=f64, device=device),
+            torch.zeros(capacity, dtype=f64, device=device),
+            torch.zeros((2, capacity), dtype=f64, device=device),
+            torch.zeros(capacity, dtype=torch.int64, device=device),
+        )
+
+    def view(self) -> GapsEvents:
+        return GapsEvents(self.capacity, self.nmax, self.p.data_ptr(), self.flav.data_ptr(),
+                          self.col.data_ptr(), self.acol.data_ptr(), self.npart.data_ptr(),
+                          self.status.data_ptr(), self.n_emit.data_ptr(), self.weight.data_ptr(),
+                          self.t.data_ptr(), self.eta.data_ptr(), self.draw.data_ptr())
+
+    def to_host(self, n: int) -> dict:
+        """Per-event arrays of the first n records, event index first (numpy)."""
+        out = {
+            "p": self.p[:, :, :n].permute(2, 1, 0).cpu().numpy(),
+            "flav": self.flav[:, :n].T.cpu().numpy(),
+            "col": self.col[:, :n].T.cpu().numpy(),
+            "acol": self.acol[:, :n].T.cpu().numpy(),
+            "npart": self.npart[:n].cpu().numpy(),
+            "status": self.status[:n].cpu().numpy(),
+            "n_emit": self.n_emit[:n].cpu().numpy(),
+            "weight": self.weight[:n].cpu().numpy(),
+            "t": self.t[:n].cpu().numpy(),
+            "eta": self.eta[:, :n].T.cpu().numpy(),
+        }
+        return out
+
+
+def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.0,
+                alpha_s_mz: float = 0.118, nf: int = 5, nmax: int = 128, seed: int = 1,
+                p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
+                schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0) -> GapsConfig:
+    """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
+    must stay alive until gaps_init returns (it is copied)."""
+    ptr = None if pdf_grid is None else pdf_grid.ctypes.data
+    return GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
+                      block_size, schedule, blocks_per_sm)
