@@ -26,8 +26,10 @@
  *     and launch errors; errors found on the device (capacity, iteration cap,
  *     non-finite values) are stored per event in `status` and counted by
  *     gaps_get_stats, which synchronises the stream.
- *   - Device buffers are owned by the caller; the library owns only its copy
- *     of the PDF grid, its bound tables and its counters.
+ *   - Device buffers are owned by the caller; the library owns its copy of
+ *     the PDF grid, its bound tables, its counters and, for GAPS_MIXED, a
+ *     working set of nmax partons per resident thread (allocated by the
+ *     first mixed gaps_shower call; about 100 B x nmax x resident threads).
  */
 #ifndef GAPS_H
 #define GAPS_H
@@ -98,6 +100,8 @@ typedef struct {
     int block_size;       /* threads per block for the shower, 0 = library default */
     int schedule;         /* GAPS_SCHED_PER_EVENT or GAPS_SCHED_PERSISTENT */
     int blocks_per_sm;    /* persistent schedule: resident blocks per SM, 0 = default */
+    int refill_period;    /* GAPS_MIXED: idle lanes take new events at most every
+                             this many cycles (compaction period), 0 = 1 */
 } gaps_config;
 
 /* Event records: structure of arrays in device memory, caller-owned, event
@@ -160,7 +164,11 @@ int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
 /* Shower (Section 2, Fig. 1; Appendices A-B): evolves every ACTIVE record
  * among the first n until its winner scale falls below t_cut. Records are
  * read and written in place; first_event must be the value given to
- * gaps_generate_hard (it keys the random streams). */
+ * gaps_generate_hard (it keys the random streams). GAPS_FP64 reproduces the
+ * FP64 reference evaluation bit for bit; GAPS_MIXED runs the trials, PDF and
+ * acceptance in FP32 with FP64 kinematics on a persistent grid with live-event
+ * refill, and agrees with it in distribution. Returns GAPS_ERR_CUDA if the
+ * working set cannot be allocated. */
 int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
                 const gaps_events* ev, void* stream);
 

@@ -102,6 +102,87 @@ struct Stream {
 constexpr uint64_t kHardDrawBase = 0x8000000000000000ull;  // hard process draws
 
 // ---------------------------------------------------------------------------
+// Elementary functions of the shower and the hard process, built only from
+// IEEE-754 operations that are exactly rounded (+ - * / sqrt, floor, frexp,
+// ldexp), so that every evaluation of the same steps gives the same bits:
+//   ex(x): Cody-Waite reduction x = k ln2 + r with ln2 split into a 32-bit
+//          head and a tail, then the Taylor series of e^r to degree 14
+//          (|r| <= 0.35, truncation < 1e-19), scaled by 2^k;
+//   lg(x): x = m 2^e with m in [1/sqrt2, sqrt2), ln m = 2 atanh(s),
+//          s = (m-1)/(m+1), odd series to s^23 (|s| < 0.172);
+//   cos/sin(2 pi R): exact reduction of R to v in [-1/8, 1/8] plus a
+//          quadrant, Taylor series of cos (degree 18) and sin (degree 19) on
+//          |2 pi v| <= pi/4.
+// Accuracy (about 1 ulp) is pinned against the C library in the tests.
+// ---------------------------------------------------------------------------
+constexpr double kLn2Hi = 0x1.62e42fee00000p-1;
+constexpr double kLn2Lo = 0x1.a39ef35793c76p-33;
+constexpr double kInvLn2 = 0x1.71547652b82fep+0;
+constexpr double kTwoPi = 0x1.921fb54442d18p+2;
+constexpr double kSqrtHalf = 0x1.6a09e667f3bcdp-1;
+
+double ex(double x) {
+  if (!(x == x)) return x;
+  if (x > 709.8) return std::numeric_limits<double>::infinity();
+  if (x < -745.2) return 0.0;
+  double k = std::floor(x * kInvLn2 + 0.5);
+  double r = (x - k * kLn2Hi) - k * kLn2Lo;
+  // Taylor coefficients 1/j!, j = 14 .. 1
+  const double c[14] = {1.0 / 87178291200.0, 1.0 / 6227020800.0, 1.0 / 479001600.0,
+                        1.0 / 39916800.0, 1.0 / 3628800.0, 1.0 / 362880.0, 1.0 / 40320.0,
+                        1.0 / 5040.0, 1.0 / 720.0, 1.0 / 120.0, 1.0 / 24.0, 1.0 / 6.0, 1.0 / 2.0, 1.0};
+  double p = c[0];
+  for (int j = 1; j < 14; ++j) p = p * r + c[j];
+  p = p * r + 1.0;
+  return std::ldexp(p, (int)k);
+}
+
+double lg(double x) {
+  if (!(x == x) || x < 0.0) return std::numeric_limits<double>::quiet_NaN();
+  if (x == 0.0) return -std::numeric_limits<double>::infinity();
+  if (x > 1.7976931348623157e308) return x;
+  int e;
+  double m = std::frexp(x, &e);  // x = m 2^e, m in [0.5, 1)
+  if (m < kSqrtHalf) { m = m * 2.0; e -= 1; }
+  double s = (m - 1.0) / (m + 1.0);
+  double z = s * s;
+  // 1/(2j+1), j = 11 .. 1
+  const double c[11] = {1.0 / 23.0, 1.0 / 21.0, 1.0 / 19.0, 1.0 / 17.0, 1.0 / 15.0, 1.0 / 13.0,
+                        1.0 / 11.0, 1.0 / 9.0, 1.0 / 7.0, 1.0 / 5.0, 1.0 / 3.0};
+  double p = c[0];
+  for (int j = 1; j < 11; ++j) p = p * z + c[j];
+  p = p * z + 1.0;
+  double lm = 2.0 * s * p;
+  double de = (double)e;
+  return de * kLn2Hi + (de * kLn2Lo + lm);
+}
+
+// cos(2 pi R) and sin(2 pi R)
+void sincos2pi(double R, double& c, double& s) {
+  double u = R - std::floor(R + 0.5);        // [-1/2, 1/2), exact
+  double n = std::floor(4.0 * u + 0.5);      // quadrant in {-2, ..., 2}
+  double v = u - 0.25 * n;                   // [-1/8, 1/8], exact
+  double th = kTwoPi * v;
+  double z = th * th;
+  // sin: th (1 - z/3! + z^2/5! - ... - z^9/19!); cos: 1 - z/2! + ... + z^9/18!
+  const double cs[9] = {-1.0 / 121645100408832000.0, 1.0 / 355687428096000.0, -1.0 / 1307674368000.0,
+                        1.0 / 6227020800.0, -1.0 / 39916800.0, 1.0 / 362880.0, -1.0 / 5040.0,
+                        1.0 / 120.0, -1.0 / 6.0};
+  const double cc[9] = {1.0 / 6402373705728000.0, -1.0 / 20922789888000.0, 1.0 / 87178291200.0,
+                        -1.0 / 479001600.0, 1.0 / 3628800.0, -1.0 / 40320.0, 1.0 / 720.0,
+                        -1.0 / 24.0, 1.0 / 2.0};
+  double ps = cs[0], pc = cc[0];
+  for (int j = 1; j < 9; ++j) { ps = ps * z + cs[j]; pc = pc * z + cc[j]; }
+  double sn = th + th * (z * ps);
+  double cn = 1.0 - z * pc;
+  int q = (int)n;
+  if (q == 0) { c = cn; s = sn; }
+  else if (q == 1) { c = -sn; s = cn; }
+  else if (q == -1) { c = sn; s = -cn; }
+  else { c = -cn; s = -sn; }
+}
+
+// ---------------------------------------------------------------------------
 // Flavours: PDG-like codes 21 = gluon, 1..5 = d u s c b, negative = antiquark,
 // 23 = Z. PDF table index: g -> 0, q -> 1..5, qbar -> 6..10, and 11 = the sum
 // of all ten quark and antiquark densities (used by the g <- q backward step).
@@ -138,10 +219,10 @@ struct Pdf {
 
   void init(const float* g) {
     grid = g;
-    lxmin = std::log(kXMin);
-    dlx = (std::log(kXMax) - lxmin) / (kNX - 1);
-    lqmin = std::log(kQ2Min);
-    dlq = (std::log(kQ2Max) - lqmin) / (kNQ - 1);
+    lxmin = lg(kXMin);
+    dlx = (lg(kXMax) - lxmin) / (kNX - 1);
+    lqmin = lg(kQ2Min);
+    dlq = (lg(kQ2Max) - lqmin) / (kNQ - 1);
     for (int f = 0; f < 12; ++f) {
       for (int ix = 0; ix < kNX; ++ix) {
         double mx = -1.0, mn = 0.0;
@@ -162,7 +243,7 @@ struct Pdf {
   // locate x in the grid: cell index and the fraction inside the cell
   bool locate_x(double x, int& ix, double& fx) const {
     if (!(x >= kXMin && x <= kXMax)) return false;
-    double u = (std::log(x) - lxmin) / dlx;
+    double u = (lg(x) - lxmin) / dlx;
     ix = (int)std::floor(u);
     if (ix < 0) ix = 0;
     if (ix > kNX - 2) ix = kNX - 2;
@@ -171,7 +252,7 @@ struct Pdf {
   }
   bool locate_q(double q2, int& iq, double& fq) const {
     if (!(q2 >= kQ2Min && q2 <= kQ2Max)) return false;
-    double u = (std::log(q2) - lqmin) / dlq;
+    double u = (lg(q2) - lqmin) / dlq;
     iq = (int)std::floor(u);
     if (iq < 0) iq = 0;
     if (iq > kNQ - 2) iq = kNQ - 2;
@@ -238,7 +319,7 @@ struct Physics {
 
   double alpha_s(double t) const {
     if (cfg.fixed_alpha) return cfg.alpha_s_mz;
-    return cfg.alpha_s_mz / (1.0 + cfg.alpha_s_mz * beta0 * std::log(t / (kMZ * kMZ)));
+    return cfg.alpha_s_mz / (1.0 + cfg.alpha_s_mz * beta0 * lg(t / (kMZ * kMZ)));
   }
 };
 
@@ -353,10 +434,10 @@ struct Collinear {
   double pre_t() const { return kTR * as / (2.0 * kPi); }
   double A() const { return pre_f() * (-5.0 + 2.0 * kPi * kPi / 3.0 - 1.5 * L); }
   double B(double eta) const {
-    double l1 = std::log(1.0 - eta);
+    double l1 = lg(1.0 - eta);
     return pre_f() * (2.0 * (l1 * L + kPi * kPi / 6.0 - l1 * l1 - li2(1.0 - eta)));
   }
-  double logs(double x) const { return std::log((1.0 - x) / x) + std::log(1.0 - x) - L; }
+  double logs(double x) const { return lg((1.0 - x) / x) + lg(1.0 - x) - L; }
   double g(double x) const { return pre_f() * (2.0 / (1.0 - x) * logs(x)); }
   double hqq(double x) const { return pre_f() * (-(1.0 + x) * logs(x) + (1.0 - x)); }
   double hqg(double x) const {
@@ -383,7 +464,7 @@ double collinear_leg(const Physics& ph, int fl, double eta, double R) {
 double li2(double x) {
   if (x == 0.0) return 0.0;
   if (x == 1.0) return kPi * kPi / 6.0;
-  if (x > 0.5) return kPi * kPi / 6.0 - std::log(x) * std::log(1.0 - x) - li2(1.0 - x);
+  if (x > 0.5) return kPi * kPi / 6.0 - lg(x) * lg(1.0 - x) - li2(1.0 - x);
   double sum = 0.0, xk = x;
   for (int k = 1; k < 200; ++k) {
     sum += xk / ((double)k * (double)k);
@@ -498,10 +579,10 @@ double t_kin_max(int type, double s, double eta) {
 double shape_integral(Shape sh, double zm, double delta) {
   double zp = 1.0 - delta;
   switch (sh) {
-    case kSoft: return std::log((1.0 - zm) / delta);
+    case kSoft: return lg((1.0 - zm) / delta);
     case kFlat: return zp - zm;
-    case kBoth: return std::log(zp / zm) + std::log((1.0 - zm) / delta);
-    default: return std::log(zp / zm);
+    case kBoth: return lg(zp / zm) + lg((1.0 - zm) / delta);
+    default: return lg(zp / zm);
   }
 }
 
@@ -511,7 +592,7 @@ void shape_sample(Shape sh, double zm, double delta, double R, double& z, double
   double zp = 1.0 - delta;
   switch (sh) {
     case kSoft:
-      omz = (1.0 - zm) * std::exp(R * std::log(delta / (1.0 - zm)));
+      omz = (1.0 - zm) * ex(R * lg(delta / (1.0 - zm)));
       z = 1.0 - omz;
       break;
     case kFlat:
@@ -519,15 +600,15 @@ void shape_sample(Shape sh, double zm, double delta, double R, double& z, double
       omz = 1.0 - z;
       break;
     case kBoth: {
-      double lm = std::log(zm / (1.0 - zm)), lp = std::log(zp / delta);
+      double lm = lg(zm / (1.0 - zm)), lp = lg(zp / delta);
       double L = lm + R * (lp - lm);
-      double em = std::exp(-L);
+      double em = ex(-L);
       z = 1.0 / (1.0 + em);
       omz = em / (1.0 + em);
       break;
     }
     default:
-      z = zm * std::exp(R * std::log(zp / zm));
+      z = zm * ex(R * lg(zp / zm));
       omz = 1.0 - z;
       break;
   }
@@ -665,7 +746,7 @@ void shower_step(const Physics& ph, Event& ev) {
         if (!(cc > 0.0)) continue;
         ev.cnt.trials += 1;
         if (type != kFF && type != kFI) ev.cnt.isr_trials += 1;
-        double tt = tmax * std::exp(std::log(Rt) / cc);
+        double tt = tmax * ex(lg(Rt) / cc);
         if (tt > best.t) {
           best.i = i; best.k = k; best.side = side; best.ch = ch; best.type = type;
           best.t = tt; best.Rz = Rz; best.c = cc; best.shape = ov.shape; best.coef = ov.coef;
@@ -798,8 +879,8 @@ void shower_step(const Physics& ph, Event& ev) {
   std::memcpy(K, Pk.p, sizeof K);
   double e1[4], e2[4];
   transverse_basis(P, K, e1, e2);
-  double phi = 2.0 * kPi * Rphi;
-  double st = std::sqrt(t), cph = std::cos(phi), sph = std::sin(phi);
+  double st = std::sqrt(t), cph, sph;
+  sincos2pi(Rphi, cph, sph);  // phi = 2 pi R_phi
   double kt[4];
   for (int mu = 0; mu < 4; ++mu) kt[mu] = st * (cph * e1[mu] + sph * e2[mu]);
   Parton J;
@@ -902,12 +983,13 @@ void generate_hard(const Physics& ph, Event& ev, uint64_t event_id) {
   if (cf.process == 0) {
     ev.pp = false;
     double c = 2.0 * R0 - 1.0;
-    double phi = 2.0 * kPi * R1;
+    double cph, sph;
+    sincos2pi(R1, cph, sph);  // phi = 2 pi R1
     int f = 1 + (int)std::floor(R2 * cf.nf);
     if (f > cf.nf) f = cf.nf;
     double st = std::sqrt((1.0 - c) * (1.0 + c));
     double E = 0.5 * cf.sqrt_s;
-    double n[3] = {st * std::cos(phi), st * std::sin(phi), c};
+    double n[3] = {st * cph, st * sph, c};
     Parton q{{E, E * n[0], E * n[1], E * n[2]}, f, 1, 0, false};
     Parton qb{{E, -E * n[0], -E * n[1], -E * n[2]}, -f, 0, 1, false};
     ev.parts.push_back(q);
@@ -925,10 +1007,10 @@ void generate_hard(const Physics& ph, Event& ev, uint64_t event_id) {
   }
   if (!hevent) {
     // Born kinematics: y uniform in [-Y, Y], eta_{1,2} = e^{+-y} m_Z/sqrt(s)
-    double Y = std::log(cf.sqrt_s / kMZ);
+    double Y = lg(cf.sqrt_s / kMZ);
     double y = std::isfinite(cf.y_fixed) ? cf.y_fixed : (2.0 * R1 - 1.0) * Y;
     double tau = kMZ / cf.sqrt_s;
-    double ea = std::exp(y) * tau, eb = std::exp(-y) * tau;
+    double ea = ex(y) * tau, eb = ex(-y) * tau;
     double dens[10], tot = 0.0;
     for (int k = 0; k < 10; ++k) { dens[k] = born_pair_density(ph, k, ea, eb); tot += dens[k]; }
     int pick = 9;
@@ -966,12 +1048,12 @@ void generate_hard(const Physics& ph, Event& ev, uint64_t event_id) {
   double xlo = mz2 / s;
   double x = xlo + R3 * (1.0 - xlo);
   double v = R4 * (1.0 - x);
-  double phi = 2.0 * kPi * R5;
+
   double sbar = mz2 / x;
-  double Y = 0.5 * std::log(s / sbar);
+  double Y = 0.5 * lg(s / sbar);
   double y = (2.0 * R1 - 1.0) * Y;
   double rt = std::sqrt(sbar / s);
-  double e1 = std::exp(y) * rt, e2 = std::exp(-y) * rt;
+  double e1 = ex(y) * rt, e2 = ex(-y) * rt;
   double as = cf.alpha_s_mz;
   double m2 = mz2;
   // thirty ordered pairs: 0..9 q qbar -> Z g (pair k as in born_pair),
@@ -1030,7 +1112,8 @@ void generate_hard(const Physics& ph, Event& ev, uint64_t event_id) {
   double ea[4], eb[4];
   transverse_basis(Pt, Bt, ea, eb);
   double t = v * (1.0 - x - v) / x * m2;
-  double st = std::sqrt(t), cph = std::cos(phi), sph = std::sin(phi);
+  double st = std::sqrt(t), cph, sph;
+  sincos2pi(R5, cph, sph);  // phi = 2 pi R5
   Parton& J = ev.parts[3];
   Parton& Z = ev.parts[2];
   for (int mu = 0; mu < 4; ++mu) {
@@ -1228,7 +1311,7 @@ Physics make_physics(const Config& c) {
   ph.beta0 = (33.0 - 2.0 * 5.0) / (12.0 * kPi);
   ph.as_over = c.fixed_alpha ? c.alpha_s_mz : 0.0;
   if (!c.fixed_alpha) {
-    ph.as_over = c.alpha_s_mz / (1.0 + c.alpha_s_mz * ph.beta0 * std::log(c.t_cut / (kMZ * kMZ)));
+    ph.as_over = c.alpha_s_mz / (1.0 + c.alpha_s_mz * ph.beta0 * lg(c.t_cut / (kMZ * kMZ)));
   }
   return ph;
 }
@@ -1472,6 +1555,9 @@ double oracle_alpha_s(const OracleConfig* c, double t) {
   return ph.alpha_s(t);
 }
 double oracle_li2(double x) { return li2(x); }
+double oracle_exp(double x) { return ex(x); }
+double oracle_log(double x) { return lg(x); }
+void oracle_sincos2pi(double R, double out[2]) { sincos2pi(R, out[0], out[1]); }
 // collinear pieces with ln(mu_F^2/m^2) = L: which = 0 A, 1 B(x), 2 g(x),
 // 3 h_qq(x), 4 h_qg(x)
 double oracle_collinear(double as, double L, int which, double x) {

@@ -8,6 +8,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 
@@ -15,7 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "gaps_oracle.cpp")
-LIB = os.path.join(HERE, "liboracle.so")
+LIB = os.path.join(HERE, "liboracle_%s.so" % platform.machine())
 
 CFLAGS = ["-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-pthread"]
 
@@ -72,6 +73,11 @@ def lib():
         _lib.oracle_alpha_s.restype = d
         _lib.oracle_li2.argtypes = [d]
         _lib.oracle_li2.restype = d
+        _lib.oracle_exp.argtypes = [d]
+        _lib.oracle_exp.restype = d
+        _lib.oracle_log.argtypes = [d]
+        _lib.oracle_log.restype = d
+        _lib.oracle_sincos2pi.argtypes = [d, vp]
         _lib.oracle_collinear.argtypes = [d, d, i, d]
         _lib.oracle_collinear.restype = d
         _lib.oracle_born_me2.argtypes = [i]
@@ -187,6 +193,20 @@ def alpha_s(settings: Settings, t: float) -> float:
 
 def li2(x: float) -> float:
     return lib().oracle_li2(x)
+
+
+def exp(x: float) -> float:
+    return lib().oracle_exp(x)
+
+
+def log(x: float) -> float:
+    return lib().oracle_log(x)
+
+
+def sincos2pi(R: float):
+    o = np.zeros(2)
+    lib().oracle_sincos2pi(R, _ptr(o))
+    return float(o[0]), float(o[1])
 
 
 def collinear(as_: float, L: float, which: str, x: float = 0.0) -> float:

@@ -24,6 +24,7 @@ UNITS = {
     "hard.cu": ["-fmad=false"],
     "shower_fp64.cu": ["-fmad=false"],
     "observables.cu": ["-fmad=false"],
+    "shower_mixed.cu": [],
 }
 
 

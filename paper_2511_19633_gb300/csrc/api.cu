@@ -8,11 +8,16 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gmath.cuh"
 
 namespace gaps {
 cudaError_t launch_generate_hard(const DevParams&, const DevEvents&, uint64_t, uint64_t, cudaStream_t);
 cudaError_t launch_shower_fp64(const DevParams&, const DevEvents&, uint64_t, uint64_t, int, int,
                                unsigned long long*, cudaStream_t);
+size_t workset_bytes(int lanes, int nmax);
+void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
+cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, uint64_t, uint64_t, int,
+                                int, int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, double*, const HistDef&,
                                double*, double*, cudaStream_t);
 }  // namespace gaps
@@ -28,6 +33,9 @@ struct gaps_ctx {
   unsigned long long* d_counters = nullptr;  // C_NCOUNTERS + 1 (work counter)
   DevParams P;
   HistDef H;
+  int q_independent = 0;     // every Q^2 column of the grid is identical
+  void* d_work = nullptr;    // mixed-precision working set
+  size_t work_bytes = 0;
 };
 
 namespace {
@@ -135,9 +143,13 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
   if (c.block_size < 0 || c.block_size > 1024 || (c.block_size % 32) != 0) return GAPS_ERR_INVALID_ARG;
   if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT) return GAPS_ERR_INVALID_ARG;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
+  if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
+  if (c.precision == GAPS_MIXED && c.block_size != 0 && c.block_size != 64 && c.block_size != 128 &&
+      c.block_size != 256)
+    return GAPS_ERR_INVALID_ARG;
   // one-loop running must stay below its pole down to the cutoff
   const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
-  double den = 1.0 + c.alpha_s_mz * beta0 * std::log(c.t_cut / (91.1876 * 91.1876));
+  double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
   if (!(den > 0.0)) return GAPS_ERR_INVALID_ARG;
 
   int ndev = 0;
@@ -159,6 +171,10 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
       if (!std::isfinite(g[q]) || g[q] < 0.0f) { rc = GAPS_ERR_INVALID_ARG; break; }
     if (rc) break;
     if ((rc = cuda_fail(cudaMemcpy(ctx->d_grid, g, gsz * sizeof(float), cudaMemcpyHostToDevice)))) break;
+    ctx->q_independent = 1;
+    for (size_t q = 0; q < gsz && ctx->q_independent; q += GAPS_PDF_NQ)
+      for (int iq = 1; iq < GAPS_PDF_NQ; ++iq)
+        if (g[q + iq] != g[q]) { ctx->q_independent = 0; break; }
     std::vector<double> tables;
     build_bound_tables(g, tables);
     if ((rc = cuda_fail(cudaMalloc(&ctx->d_tables, tables.size() * sizeof(double))))) break;
@@ -187,10 +203,10 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
   P.umax = ctx->d_tables;
   P.sufmax = ctx->d_tables + 12 * GAPS_PDF_NX;
   P.lmin = ctx->d_tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
-  P.lxmin = std::log(GAPS_PDF_XMIN);
-  P.dlx = (std::log(GAPS_PDF_XMAX) - P.lxmin) / (GAPS_PDF_NX - 1);
-  P.lqmin = std::log(GAPS_PDF_Q2MIN);
-  P.dlq = (std::log(GAPS_PDF_Q2MAX) - P.lqmin) / (GAPS_PDF_NQ - 1);
+  P.lxmin = gm_log(GAPS_PDF_XMIN);
+  P.dlx = (gm_log(GAPS_PDF_XMAX) - P.lxmin) / (GAPS_PDF_NX - 1);
+  P.lqmin = gm_log(GAPS_PDF_Q2MIN);
+  P.dlq = (gm_log(GAPS_PDF_Q2MAX) - P.lqmin) / (GAPS_PDF_NQ - 1);
   P.counters = ctx->d_counters;
   set_hist_defs(c.process, ctx->H);
   *out = ctx;
@@ -206,6 +222,25 @@ int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const ga
 int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, void* stream) {
   if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
   const gaps_config& c = ctx->cfg;
+  if (c.precision == GAPS_MIXED) {
+    int bs = c.block_size > 0 ? c.block_size : 128;
+    int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
+    int blocks = ctx->n_sm * per_sm;
+    int lanes = blocks * bs;
+    size_t need = workset_bytes(lanes, c.nmax_partons);
+    if (need > ctx->work_bytes) {
+      if (ctx->d_work) cudaFree(ctx->d_work);
+      ctx->d_work = nullptr;
+      ctx->work_bytes = 0;
+      if (cudaMalloc(&ctx->d_work, need) != cudaSuccess) return GAPS_ERR_CUDA;
+      ctx->work_bytes = need;
+    }
+    WorkSet W;
+    workset_carve(ctx->d_work, lanes, c.nmax_partons, W);
+    return cuda_fail(launch_shower_mixed(ctx->P, dev_events(ev), W, first_event, n, blocks, bs,
+                                         c.refill_period, ctx->q_independent,
+                                         ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
+  }
   int bs = c.block_size > 0 ? c.block_size : 128;
   int pblocks = 0;
   if (c.schedule == GAPS_SCHED_PERSISTENT) {
@@ -261,6 +296,7 @@ void gaps_destroy(gaps_ctx* ctx) {
   if (ctx->d_grid) cudaFree(ctx->d_grid);
   if (ctx->d_tables) cudaFree(ctx->d_tables);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
+  if (ctx->d_work) cudaFree(ctx->d_work);
   delete ctx;
 }
 

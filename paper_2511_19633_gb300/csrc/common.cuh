@@ -39,6 +39,14 @@ struct DevParams {
   unsigned long long* counters;  // [C_NCOUNTERS]
 };
 
+// per-lane working set of the mixed-precision persistent shower
+struct WorkSet {
+  double* p;
+  uint32_t* tag;
+  float4* end;
+  int lanes;
+};
+
 // histogram binning of one process family
 struct HistDef {
   double lo[GAPS_NHIST], hi[GAPS_NHIST];

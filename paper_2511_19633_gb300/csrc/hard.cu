@@ -68,7 +68,7 @@ __device__ double li2(double x) {
   if (x > 0.5) {
     double y = 1.0 - x;
     double r = (y == 0.0) ? 0.0 : li2_series(y);
-    return kPi * kPi / 6.0 - log(x) * log(1.0 - x) - r;
+    return kPi * kPi / 6.0 - gm_log(x) * gm_log(1.0 - x) - r;
   }
   return li2_series(x);
 }
@@ -85,12 +85,12 @@ __device__ double collinear_leg(const DevParams& P, int fl, double eta, double R
   double Fq = pdf_xf(P, pdf_index(fl), eta, mz2);
   double rq = pdf_xf(P, pdf_index(fl), eta / x, mz2) / Fq;
   double rg = pdf_xf(P, 0, eta / x, mz2) / Fq;
-  double logs = log((1.0 - x) / x) + log(1.0 - x) - L;
+  double logs = gm_log((1.0 - x) / x) + gm_log(1.0 - x) - L;
   double g = pf * (2.0 / (1.0 - x) * logs);
   double hqq = pf * (-(1.0 + x) * logs + (1.0 - x));
   double hqg = pt * (2.0 * x * (1.0 - x) + (x * x + (1.0 - x) * (1.0 - x)) * logs);
   double A = pf * (-5.0 + 2.0 * kPi * kPi / 3.0 - 1.5 * L);
-  double l1 = log(1.0 - eta);
+  double l1 = gm_log(1.0 - eta);
   double B = pf * (2.0 * (l1 * L + kPi * kPi / 6.0 - l1 * l1 - li2(1.0 - eta)));
   double integrand = (rq - 1.0) * g + rq * hqq + rg * hqg;
   return A - B + (1.0 - eta) * integrand;
@@ -130,12 +130,13 @@ __global__ void k_generate_hard(DevParams P, DevEvents E, uint64_t first, uint64
   E.eta[E.cap + e] = 0.0;
   if (P.process == GAPS_EE_QQ) {
     double c = 2.0 * R0 - 1.0;
-    double phi = 2.0 * kPi * R1;
+    double cph, sph;
+    gm_sincos2pi(R1, cph, sph);  // phi = 2 pi R1
     int f = 1 + (int)floor(R2 * P.nf);
     if (f > P.nf) f = P.nf;
     double st = sqrt((1.0 - c) * (1.0 + c));
     double En = 0.5 * P.sqrt_s;
-    double n0 = st * cos(phi), n1 = st * sin(phi), n2 = c;
+    double n0 = st * cph, n1 = st * sph, n2 = c;
     rec.set(0, En, En * n0, En * n1, En * n2, f, 1, 0);
     rec.set(1, En, -En * n0, -En * n1, -En * n2, -f, 0, 1);
     E.npart[e] = 2;
@@ -150,10 +151,10 @@ __global__ void k_generate_hard(DevParams P, DevEvents E, uint64_t first, uint64
     wsel = hevent ? 1.0 / (1.0 - P.p_s) : 1.0 / P.p_s;
   }
   if (!hevent) {
-    double Y = log(P.sqrt_s / kMZ);
+    double Y = gm_log(P.sqrt_s / kMZ);
     double y = (2.0 * R1 - 1.0) * Y;
     double tau = kMZ / P.sqrt_s;
-    double ea = exp(y) * tau, eb = exp(-y) * tau;
+    double ea = gm_exp(y) * tau, eb = gm_exp(-y) * tau;
     double dens[10], tot = 0.0;
     for (int k = 0; k < 10; ++k) { dens[k] = born_pair_density(P, k, ea, eb); tot += dens[k]; }
     int pick = 9;
@@ -185,12 +186,11 @@ __global__ void k_generate_hard(DevParams P, DevEvents E, uint64_t first, uint64
   double xlo = mz2 / s;
   double x = xlo + R3 * (1.0 - xlo);
   double v = R4 * (1.0 - x);
-  double phi = 2.0 * kPi * R5;
   double sbar = mz2 / x;
-  double Y = 0.5 * log(s / sbar);
+  double Y = 0.5 * gm_log(s / sbar);
   double y = (2.0 * R1 - 1.0) * Y;
   double rt = sqrt(sbar / s);
-  double e1 = exp(y) * rt, e2 = exp(-y) * rt;
+  double e1 = gm_exp(y) * rt, e2 = gm_exp(-y) * rt;
   double as = P.as_mz;
   double m2 = mz2;
   // 0..9 q qbar -> Z g, 10..14 g q, 15..19 g qbar (gluon from beam 1),
@@ -246,7 +246,8 @@ __global__ void k_generate_hard(DevParams P, DevEvents E, uint64_t first, uint64
     double ea4[4], eb4[4];
     transverse_basis(Pt, Bt, ea4, eb4);
     double t = v * (1.0 - x - v) / x * m2;
-    double st = sqrt(t), cph = cos(phi), sph = sin(phi);
+    double st = sqrt(t), cph, sph;
+    gm_sincos2pi(R5, cph, sph);  // phi = 2 pi R5
     double pj[4], pz[4];
     for (int mu = 0; mu < 4; ++mu) {
       double kt = st * (cph * ea4[mu] + sph * eb4[mu]);

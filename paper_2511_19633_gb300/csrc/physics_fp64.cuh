@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "gmath.cuh"
 
 namespace gaps {
 
@@ -21,7 +22,7 @@ __device__ __forceinline__ double pdf_node(const DevParams& P, int f, int ix, in
 
 __device__ __forceinline__ bool pdf_locate_x(const DevParams& P, double x, int& ix, double& fx) {
   if (!(x >= kXMin && x <= kXMax)) return false;
-  double u = (log(x) - P.lxmin) / P.dlx;
+  double u = (gm_log(x) - P.lxmin) / P.dlx;
   ix = (int)floor(u);
   if (ix < 0) ix = 0;
   if (ix > kNX - 2) ix = kNX - 2;
@@ -31,7 +32,7 @@ __device__ __forceinline__ bool pdf_locate_x(const DevParams& P, double x, int& 
 
 __device__ __forceinline__ bool pdf_locate_q(const DevParams& P, double q2, int& iq, double& fq) {
   if (!(q2 >= kQ2Min && q2 <= kQ2Max)) return false;
-  double u = (log(q2) - P.lqmin) / P.dlq;
+  double u = (gm_log(q2) - P.lqmin) / P.dlq;
   iq = (int)floor(u);
   if (iq < 0) iq = 0;
   if (iq > kNQ - 2) iq = kNQ - 2;
@@ -66,7 +67,7 @@ __device__ __forceinline__ double pdf_ratio_bound(const DevParams& P, int num, i
 
 // one-loop alpha_s(t) from alpha_s(m_Z^2)
 __device__ __forceinline__ double alpha_s(const DevParams& P, double t) {
-  return P.as_mz / (1.0 + P.as_mz * P.beta0 * log(t / (kMZ * kMZ)));
+  return P.as_mz / (1.0 + P.as_mz * P.beta0 * gm_log(t / (kMZ * kMZ)));
 }
 
 // --- dipole types, channels and overestimates -----------------------------
@@ -118,10 +119,10 @@ __device__ __forceinline__ double t_kin_max(int type, double s, double eta) {
 __device__ __forceinline__ double shape_integral(int sh, double zm, double delta) {
   double zp = 1.0 - delta;
   switch (sh) {
-    case kSoft: return log((1.0 - zm) / delta);
+    case kSoft: return gm_log((1.0 - zm) / delta);
     case kFlat: return zp - zm;
-    case kBoth: return log(zp / zm) + log((1.0 - zm) / delta);
-    default: return log(zp / zm);
+    case kBoth: return gm_log(zp / zm) + gm_log((1.0 - zm) / delta);
+    default: return gm_log(zp / zm);
   }
 }
 
@@ -130,7 +131,7 @@ __device__ __forceinline__ void shape_sample(int sh, double zm, double delta, do
   double zp = 1.0 - delta;
   switch (sh) {
     case kSoft:
-      omz = (1.0 - zm) * exp(R * log(delta / (1.0 - zm)));
+      omz = (1.0 - zm) * gm_exp(R * gm_log(delta / (1.0 - zm)));
       z = 1.0 - omz;
       break;
     case kFlat:
@@ -138,15 +139,15 @@ __device__ __forceinline__ void shape_sample(int sh, double zm, double delta, do
       omz = 1.0 - z;
       break;
     case kBoth: {
-      double lm = log(zm / (1.0 - zm)), lp = log(zp / delta);
+      double lm = gm_log(zm / (1.0 - zm)), lp = gm_log(zp / delta);
       double L = lm + R * (lp - lm);
-      double em = exp(-L);
+      double em = gm_exp(-L);
       z = 1.0 / (1.0 + em);
       omz = em / (1.0 + em);
       break;
     }
     default:
-      z = zm * exp(R * log(zp / zm));
+      z = zm * gm_exp(R * gm_log(zp / zm));
       omz = 1.0 - z;
       break;
   }

@@ -82,7 +82,7 @@ __device__ int shower_step(const DevParams& P, const DevEvents& E, uint64_t e, i
         if (!(cc > 0.0)) continue;
         cnt.trials += 1;
         if (type == kIF || type == kII) cnt.isr_trials += 1;
-        double tt = tmax * exp(log(Rt) / cc);
+        double tt = tmax * gm_exp(gm_log(Rt) / cc);
         if (tt > best.t) {
           best.i = i; best.k = k; best.side = side; best.ch = ch; best.type = type;
           best.t = tt; best.Rz = Rz; best.shape = shape; best.coef = coef;
@@ -199,8 +199,8 @@ __device__ int shower_step(const DevParams& P, const DevEvents& E, uint64_t e, i
   for (int mu = 0; mu < 4; ++mu) { Pm[mu] = E.P(mu, bi, e); K[mu] = E.P(mu, bk, e); }
   double e1[4], e2[4];
   transverse_basis(Pm, K, e1, e2);
-  double phi = 2.0 * kPi * Rphi;
-  double st = sqrt(tw), cph = cos(phi), sph = sin(phi);
+  double st = sqrt(tw), cph, sph;
+  gm_sincos2pi(Rphi, cph, sph);  // phi = 2 pi R_phi
   double kt[4];
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) kt[mu] = st * (cph * e1[mu] + sph * e2[mu]);

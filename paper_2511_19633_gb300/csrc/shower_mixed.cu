@@ -1,0 +1,661 @@
+// Mixed-precision persistent shower (Section 2 / Fig. 1 and Appendices A-B
+// of arXiv:2511.19633; the partitioning of Section 3.1 becomes live-event
+// refill). FP32 in the trial loop, the PDF interpolation, the bounds and the
+// acceptance weight; FP64 for dipole invariants, emission kinematics and the
+// II Lorentz kick. The random stream (one Philox block per dipole-end channel
+// in canonical order, two after a winner) is the same as in the FP64 kernel,
+// so most events follow the same history; the histograms agree within
+// statistics.
+//
+// Layout: every lane of the persistent grid owns a working set indexed
+// [..][slot][lane] (coalesced whatever event the lane holds):
+//   p    f64 [4][nmax][L]    momenta
+//   tag  u32 [nmax][L]       flavour | colour << 8 | anticolour << 16
+//   end  f32x4 [2][nmax][L]  per colour end: {c0, c1, ln t_kin, partner}
+// `end` caches the overestimate coefficients of the end's channels (c < 0:
+// channel absent, c = 0: no phase space) and is rebuilt after every accepted
+// emission. Lanes whose event has finished take new events in warp-aggregated
+// batches, at most every `period` cycles.
+#include "physics_fp64.cuh"
+
+namespace gaps {
+
+namespace {
+
+constexpr int kSmNX = GAPS_PDF_NX;
+
+struct SmemPdf {
+  float xf[12][kSmNX];      // Q^2-independent grids: x f per flavour (11 = sum of quarks)
+  float umax[12][kSmNX];
+  float sufmax[12][kSmNX + 1];
+  float lmin[12][kSmNX];
+};
+
+struct MixedCtx {
+  DevParams P;
+  DevEvents E;
+  WorkSet W;
+  uint64_t first, n;
+  unsigned long long* next;
+  int q_independent;   // grid equal for every Q^2 node: use the staged x table
+  int period;          // refill at most every `period` cycles
+  float lnTc, asOver2pi, lxminf, dlxf, lqminf, dlqf;
+};
+
+__device__ __forceinline__ float u24(uint32_t w) { return ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f); }
+
+__device__ __forceinline__ uint32_t pack_tag(int fl, int c, int a) {
+  return ((uint32_t)(fl & 0xff)) | ((uint32_t)(c & 0xff) << 8) | ((uint32_t)(a & 0xff) << 16);
+}
+__device__ __forceinline__ int tag_fl(uint32_t t) { return (int)(int8_t)(t & 0xff); }
+__device__ __forceinline__ int tag_col(uint32_t t) { return (int)((t >> 8) & 0xff); }
+__device__ __forceinline__ int tag_acol(uint32_t t) { return (int)((t >> 16) & 0xff); }
+
+struct Lane {
+  uint64_t ev;      // record index in the caller's arrays
+  int n, n_emit, status, steps;
+  float lnT;        // ln of the current evolution scale
+  double eta0, eta1;
+  uint64_t draw;
+};
+
+// ---- FP32 PDF -------------------------------------------------------------
+__device__ __forceinline__ bool loc_x(const MixedCtx& M, float x, int& ix, float& fx) {
+  if (!(x >= (float)kXMin && x <= (float)kXMax)) return false;
+  float u = (__logf(x) - M.lxminf) / M.dlxf;
+  ix = (int)floorf(u);
+  ix = min(max(ix, 0), kNX - 2);
+  fx = u - (float)ix;
+  return true;
+}
+
+__device__ __forceinline__ float pdf32(const MixedCtx& M, const SmemPdf& S, int f, float x, float q2) {
+  if (f < 0 || f > 11) return 0.0f;
+  int ix;
+  float fx;
+  if (!loc_x(M, x, ix, fx)) return 0.0f;
+  if (!(q2 >= (float)kQ2Min && q2 <= (float)kQ2Max)) return 0.0f;
+  if (M.q_independent) return (1.0f - fx) * S.xf[f][ix] + fx * S.xf[f][ix + 1];
+  float u = (__logf(q2) - M.lqminf) / M.dlqf;
+  int iq = min(max((int)floorf(u), 0), kNQ - 2);
+  float fq = u - (float)iq;
+  auto node = [&](int xx, int qq) -> float {
+    if (f < 11) return __ldg(&M.P.grid[((size_t)f * kNX + xx) * kNQ + qq]);
+    float s = 0.0f;
+    for (int k = 1; k <= 10; ++k) s += __ldg(&M.P.grid[((size_t)k * kNX + xx) * kNQ + qq]);
+    return s;
+  };
+  float lo = (1.0f - fx) * node(ix, iq) + fx * node(ix + 1, iq);
+  float hi = (1.0f - fx) * node(ix, iq + 1) + fx * node(ix + 1, iq + 1);
+  return lo * (1.0f - fq) + hi * fq;
+}
+
+__device__ __forceinline__ float bound32(const MixedCtx& M, const SmemPdf& S, int num, int den, float eta) {
+  if (num < 0 || num > 11 || den < 0 || den > 11) return 0.0f;
+  int ix;
+  float fx;
+  if (!loc_x(M, eta, ix, fx)) return 0.0f;
+  float uin = (1.0f - fx) * S.umax[num][ix] + fx * S.umax[num][ix + 1];
+  float un = fmaxf(uin, S.sufmax[num][ix + 1]);
+  float ld = (1.0f - fx) * S.lmin[den][ix] + fx * S.lmin[den][ix + 1];
+  if (!(ld > 0.0f)) return 0.0f;
+  // relative slack for the rounding of the FP32 interpolation
+  return un / ld * 1.0001f;
+}
+
+// ---- FP32 kinematic limits and overestimate shapes -------------------------
+__device__ __forceinline__ bool zlim32(int type, float t, float s, float eta, float& zm, float& delta) {
+  float e;
+  if (type == kFF) e = 4.0f * t / s;
+  else if (type == kFI) e = 4.0f * t / s * eta / (1.0f - eta);
+  else if (type == kIF) e = 4.0f * t * eta / (s * (1.0f - eta));
+  else e = 4.0f * t * eta / (s * (1.0f - eta) * (1.0f - eta));
+  float D = 1.0f - e;
+  if (!(D > 0.0f)) return false;
+  float sq = sqrtf(D);
+  if (type == kFF || type == kFI) { delta = 0.5f * e / (1.0f + sq); zm = delta; }
+  else { delta = 0.5f * (1.0f - eta) * e / (1.0f + sq); zm = eta + delta; }
+  return true;
+}
+
+__device__ __forceinline__ float tkin32(int type, float s, float eta) {
+  if (type == kFF) return 0.25f * s;
+  if (type == kFI || type == kIF) return 0.25f * s * (1.0f - eta) / eta;
+  return 0.25f * s * (1.0f - eta) * (1.0f - eta) / eta;
+}
+
+__device__ __forceinline__ float shape_int32(int sh, float zm, float delta) {
+  float zp = 1.0f - delta;
+  switch (sh) {
+    case kSoft: return __logf((1.0f - zm) / delta);
+    case kFlat: return zp - zm;
+    case kBoth: return __logf(zp / zm) + __logf((1.0f - zm) / delta);
+    default: return __logf(zp / zm);
+  }
+}
+
+__device__ __forceinline__ void shape_sample32(int sh, float zm, float delta, float R, float& z, float& omz) {
+  float zp = 1.0f - delta;
+  switch (sh) {
+    case kSoft:
+      omz = (1.0f - zm) * __expf(R * __logf(delta / (1.0f - zm)));
+      z = 1.0f - omz;
+      break;
+    case kFlat:
+      z = zm + R * (zp - zm);
+      omz = 1.0f - z;
+      break;
+    case kBoth: {
+      float lm = __logf(zm / (1.0f - zm)), lp = __logf(zp / delta);
+      float em = __expf(-(lm + R * (lp - lm)));
+      z = 1.0f / (1.0f + em);
+      omz = em / (1.0f + em);
+      break;
+    }
+    default:
+      z = zm * __expf(R * __logf(zp / zm));
+      omz = 1.0f - z;
+      break;
+  }
+}
+
+__device__ __forceinline__ float shape_val32(int sh, float coef, float z, float omz) {
+  switch (sh) {
+    case kSoft: return coef / omz;
+    case kFlat: return coef;
+    case kBoth: return coef / (z * omz);
+    default: return coef / z;
+  }
+}
+
+// ---- working-set access ------------------------------------------------------
+struct WS {
+  const WorkSet& W;
+  int lane, nmax;
+  __device__ __forceinline__ double& P(int mu, int slot) const {
+    return W.p[((size_t)mu * nmax + slot) * W.lanes + lane];
+  }
+  __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(size_t)slot * W.lanes + lane]; }
+  __device__ __forceinline__ float4& End(int side, int slot) const {
+    return W.end[((size_t)side * nmax + slot) * W.lanes + lane];
+  }
+};
+
+__device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side, int tag) {
+  for (int m = 0; m < n; ++m) {
+    if (m == i) continue;
+    uint32_t t = w.T(m);
+    if (side == 0 ? (tag_acol(t) == tag) : (tag_col(t) == tag)) return m;
+  }
+  return -1;
+}
+
+// Rebuild the cached overestimate coefficients of every colour end.
+__device__ void rebuild_ends(const MixedCtx& M, const SmemPdf& S, const WS& w, const Lane& L) {
+  const bool pp = M.P.process != GAPS_EE_QQ;
+  for (int i = 0; i < L.n; ++i) {
+    uint32_t ti = w.T(i);
+    int fi = tag_fl(ti);
+    bool ini = pp && i < 2;
+    for (int side = 0; side < 2; ++side) {
+      int tag = side == 0 ? tag_col(ti) : tag_acol(ti);
+      float4 rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
+      int k = tag ? find_partner(w, L.n, i, side, tag) : -1;
+      if (k >= 0) {
+        bool ink = pp && k < 2;
+        int type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
+        double pi[4], pk[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) { pi[mu] = w.P(mu, i); pk[mu] = w.P(mu, k); }
+        float s = (float)(2.0 * dot4(pi, pk));
+        float eta = 0.0f;
+        if (type == kFI) eta = (float)(k == 0 ? L.eta0 : L.eta1);
+        if (type == kIF || type == kII) eta = (float)(i == 0 ? L.eta0 : L.eta1);
+        int first = ini ? (fi == 21 ? 5 : 3) : (fi == 21 ? 1 : 0);
+        int nch = (!ini && fi != 21) ? 1 : 2;
+        float tk = tkin32(type, s, eta);
+        float zm, delta;
+        bool ok = tk > __expf(M.lnTc) && zlim32(type, __expf(M.lnTc), s, eta, zm, delta);
+        float cs[2] = {0.0f, -1.0f};
+        for (int c = 0; c < nch; ++c) {
+          cs[c] = 0.0f;
+          if (!ok) continue;
+          int ch = first + c;
+          int shape;
+          double coefd;
+          channel_over(ch, type, M.P.nf, shape, coefd);
+          float B = 1.0f;
+          if (type == kFI) {
+            int f = pdf_index(tag_fl(w.T(k)));
+            B = bound32(M, S, f, f, eta);
+          } else if (type == kIF || type == kII) {
+            int num, den;
+            isr_pdf_indices(ch, fi, num, den);
+            B = bound32(M, S, num, den, eta);
+          }
+          float cc = M.asOver2pi * B * (float)coefd * shape_int32(shape, zm, delta);
+          cs[c] = cc > 0.0f ? cc : 0.0f;
+        }
+        rec = make_float4(cs[0], cs[1], __logf(tk), __int_as_float(k));
+      }
+      w.End(side, i) = rec;
+    }
+  }
+}
+
+struct Counters32 {
+  unsigned long long steps = 0, trials = 0, isr_trials = 0, vetoes = 0, accepts = 0, violations = 0;
+};
+
+// One max-veto cycle on the working set. Returns the new status.
+__device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L, uint64_t id,
+                          Counters32& cnt) {
+  const bool pp = M.P.process != GAPS_EE_QQ;
+  cnt.steps += 1;
+  const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+  float best = -INFINITY;
+  int bi = -1, bside = 0, bch = 0;
+  float bRz = 0.5f;
+  uint64_t d = L.draw;
+  for (int i = 0; i < L.n; ++i) {
+    for (int side = 0; side < 2; ++side) {
+      float4 rec = w.End(side, i);
+      if (__float_as_int(rec.w) < 0) continue;
+      float lnTmax = fminf(L.lnT, rec.z);
+      bool live = lnTmax > M.lnTc;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float cc = c == 0 ? rec.x : rec.y;
+        if (cc < 0.0f) continue;  // channel absent for this emitter
+        uint64_t dd = d++;
+        if (!(live && cc > 0.0f)) continue;
+        uint32_t out[4];
+        philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+        cnt.trials += 1;
+        if (pp && i < 2) cnt.isr_trials += 1;
+        float lt = lnTmax + __logf(u24(out[1])) / cc;
+        if (lt > best) { best = lt; bi = i; bside = side; bch = c; bRz = u24(out[3]); }
+      }
+    }
+  }
+  L.draw = d;
+  if (bi < 0 || best < M.lnTc) return GAPS_STATUS_DONE;
+  uint32_t o1[4], o2[4];
+  philox(e0, e1, (uint32_t)L.draw, (uint32_t)(L.draw >> 32), k0, k1, o1);
+  philox(e0, e1, (uint32_t)(L.draw + 1), (uint32_t)((L.draw + 1) >> 32), k0, k1, o2);
+  L.draw += 2;
+  const float Rveto = u24(o1[1]);
+  const double Rphi = u01(o1[2], o1[3]);
+  const float Rfl = u24(o2[1]);
+  L.lnT = best;
+  const float tw = __expf(best);
+
+  // the winner's dipole, re-derived
+  const uint32_t ti = w.T(bi);
+  const int fl_i = tag_fl(ti);
+  const bool ini = pp && bi < 2;
+  const int k = __float_as_int(w.End(bside, bi).w);
+  const bool ink = pp && k < 2;
+  const int type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
+  const int ch = (ini ? (fl_i == 21 ? 5 : 3) : (fl_i == 21 ? 1 : 0)) + bch;
+  double Pm[4], K[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) { Pm[mu] = w.P(mu, bi); K[mu] = w.P(mu, k); }
+  const double sd = 2.0 * dot4(Pm, K);
+  const float s = (float)sd;
+  float eta = 0.0f;
+  if (type == kFI) eta = (float)(k == 0 ? L.eta0 : L.eta1);
+  if (type == kIF || type == kII) eta = (float)(bi == 0 ? L.eta0 : L.eta1);
+  int shape;
+  double coefd;
+  channel_over(ch, type, M.P.nf, shape, coefd);
+  const float coef = (float)coefd;
+  float zm, delta;
+  zlim32(type, __expf(M.lnTc), s, eta, zm, delta);
+  float z, omz;
+  shape_sample32(shape, zm, delta, bRz, z, omz);
+  float zm_t, delta_t;
+  if (!zlim32(type, tw, s, eta, zm_t, delta_t) || !(omz > delta_t) || !(z > zm_t)) {
+    cnt.vetoes += 1;
+    return GAPS_STATUS_ACTIVE;
+  }
+  const float pover = shape_val32(shape, coef, z, omz);
+  const float as_t = (float)M.P.as_mz / (1.0f + (float)M.P.as_mz * (float)M.P.beta0 * __logf(tw / (float)(kMZ * kMZ)));
+  const float as_ratio = as_t / (M.asOver2pi * 2.0f * (float)kPi);
+  float w8 = 0.0f, y = 0.0f, rho = 0.0f, x = 1.0f, omx = 0.0f, u = 0.0f, omu = 1.0f, v = 0.0f;
+  int new_fl_i = fl_i, fl_j = 21;
+  float sumF = 0.0f, B = 1.0f;
+  if (type == kFF) {
+    y = tw / (z * omz * s);
+    float den = omz + z * y, kk;
+    if (ch == 0) kk = (float)kCF * (2.0f / den - (1.0f + z));
+    else if (ch == 1) kk = (float)kCA * 0.5f * (2.0f / den - 2.0f + z * omz);
+    else kk = M.P.nf * (float)kTR * 0.5f * (1.0f - 2.0f * z * omz);
+    w8 = as_ratio * (1.0f - y) * kk / pover;
+  } else if (type == kFI) {
+    rho = tw / (z * omz * s);
+    x = 1.0f / (1.0f + rho);
+    omx = rho / (1.0f + rho);
+    float den = omz + omx, kk;
+    if (ch == 0) kk = (float)kCF * (2.0f / den - (1.0f + z));
+    else if (ch == 1) kk = (float)kCA * 0.5f * (2.0f / den - 2.0f + z * omz);
+    else kk = M.P.nf * (float)kTR * 0.5f * (1.0f - 2.0f * z * omz);
+    int f = pdf_index(tag_fl(w.T(k)));
+    B = bound32(M, S, f, f, eta);
+    float F1 = pdf32(M, S, f, eta * (1.0f + rho), tw);
+    float F0 = pdf32(M, S, f, eta, tw);
+    float ratio = F0 > 0.0f ? x * F1 / F0 : 0.0f;
+    w8 = as_ratio * kk / pover * ratio / B;
+  } else {
+    float r = tw / s, J;
+    if (type == kIF) {
+      float q = omz + r;
+      float disc = 1.0f - 4.0f * r * z * omz / (q * q);
+      if (!(disc >= 0.0f)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+      x = 2.0f * z * omz / (q * (1.0f + sqrtf(disc)));
+      u = x * r / omz;
+      omu = 1.0f - u;
+      if (!(omu > 0.0f)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+      omx = omz / omu;
+      J = 1.0f / (x * omu + u * omx);
+    } else {
+      x = z * omz / (omz + r);
+      omx = (omz * omz + r) / (omz + r);
+      v = x * r / omz;
+      if (!(omx - v > 0.0f)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+      J = 1.0f / z;
+    }
+    if (!(x > eta)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+    float soft = (type == kIF) ? (omx + u) : omx, kk;
+    if (ch == 3) kk = (float)kCF * (2.0f / soft - (1.0f + x));
+    else if (ch == 4) kk = (float)kTR * (1.0f - 2.0f * x * omx);
+    else if (ch == 5) kk = (float)kCA * (1.0f / soft + omx / x - 1.0f + x * omx);
+    else kk = (float)kCF * 0.5f * (x + 2.0f * omx / x);
+    int num, den;
+    isr_pdf_indices(ch, fl_i, num, den);
+    B = bound32(M, S, num, den, eta);
+    float F0 = pdf32(M, S, den, eta, tw);
+    float F1 = pdf32(M, S, num, eta / x, tw);
+    if (ch == 6) sumF = F1;
+    float Fratio = F0 > 0.0f ? F1 / F0 : 0.0f;
+    w8 = as_ratio * kk * J * x / pover * Fratio / B;
+    if (ch == 4) { new_fl_i = 21; fl_j = -fl_i; }
+    if (ch == 5) { new_fl_i = 21; fl_j = 21; }
+  }
+  if (!isfinite(w8)) return GAPS_ERR_NUMERIC;
+  if (w8 > 1.0f) cnt.violations += 1;
+  if (!(Rveto < w8)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+
+  if (ch == 2) {
+    int f = 1 + (int)floorf(Rfl * M.P.nf);
+    if (f > M.P.nf) f = M.P.nf;
+    new_fl_i = f; fl_j = -f;
+  } else if (ch == 6) {
+    float target = Rfl * sumF, acc = 0.0f;
+    int pick = 10;
+    for (int f = 1; f <= 10; ++f) {
+      acc += pdf32(M, S, f, eta / x, tw);
+      if (target < acc) { pick = f; break; }
+    }
+    int fl = pick <= 5 ? pick : -(pick - 5);
+    new_fl_i = fl; fl_j = fl;
+  }
+  if (L.n >= M.P.nmax) return GAPS_ERR_CAPACITY;
+
+  // ---- FP64 emission kinematics ----
+  const double t = (double)tw;
+  const double zd = (double)z, omzd = (double)omz;
+  double e1v[4], e2v[4];
+  transverse_basis(Pm, K, e1v, e2v);
+  double cph, sph;
+  gm_sincos2pi(Rphi, cph, sph);
+  const double st = sqrt(t);
+  double kt[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) kt[mu] = st * (cph * e1v[mu] + sph * e2v[mu]);
+  const int j = L.n;
+  double pj[4];
+  if (type == kFF) {
+    const double yd = t / (zd * omzd * sd);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      w.P(mu, bi) = zd * Pm[mu] + (yd * omzd) * K[mu] + kt[mu];
+      pj[mu] = omzd * Pm[mu] + (yd * zd) * K[mu] - kt[mu];
+      w.P(mu, k) = (1.0 - yd) * K[mu];
+    }
+  } else if (type == kFI) {
+    const double rhod = t / (zd * omzd * sd);
+    const double xinv = 1.0 + rhod;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      w.P(mu, bi) = zd * Pm[mu] + (omzd * rhod) * K[mu] + kt[mu];
+      pj[mu] = omzd * Pm[mu] + (zd * rhod) * K[mu] - kt[mu];
+      w.P(mu, k) = xinv * K[mu];
+    }
+    if (k == 0) L.eta0 *= xinv; else L.eta1 *= xinv;
+  } else if (type == kIF) {
+    double xd, omxd, ud, omud;
+    if (!if_map(t / sd, zd, omzd, xd, omxd, ud, omud)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      w.P(mu, bi) = Pm[mu] / xd;
+      pj[mu] = (omud * omxd / xd) * Pm[mu] + ud * K[mu] - kt[mu];
+      w.P(mu, k) = (ud * omxd / xd) * Pm[mu] + omud * K[mu] + kt[mu];
+    }
+    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
+  } else {
+    double xd, omxd, vd;
+    if (!ii_map(t / sd, zd, omzd, xd, omxd, vd)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+    double pa[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      pa[mu] = Pm[mu] / xd;
+      w.P(mu, bi) = pa[mu];
+      pj[mu] = ((omxd - vd) / xd) * Pm[mu] + vd * K[mu] - kt[mu];
+    }
+    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
+    double Kp[4], Kn[4], KK[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      Kp[mu] = Pm[mu] + K[mu];
+      Kn[mu] = (pa[mu] + K[mu]) - pj[mu];
+      KK[mu] = Kp[mu] + Kn[mu];
+    }
+    const double KK2 = dot4(KK, KK), Kp2 = dot4(Kp, Kp);
+    for (int m = 2; m < L.n; ++m) {
+      double q[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) q[mu] = w.P(mu, m);
+      const double a = 2.0 * dot4(KK, q) / KK2, b = 2.0 * dot4(Kp, q) / Kp2;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) w.P(mu, m) = q[mu] - a * KK[mu] + b * Kn[mu];
+    }
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) w.P(mu, j) = pj[mu];
+
+  // colours
+  const int T = 100 + L.n;
+  int ci = tag_col(ti), ai = tag_acol(ti), cj = 0, aj = 0;
+  if (ch == 0 || ch == 1 || ch == 3 || ch == 5) {
+    if (bside == 0) { cj = ci; aj = T; ci = T; }
+    else { aj = ai; cj = T; ai = T; }
+  } else if (ch == 2) {
+    aj = ai; cj = 0; ai = 0;
+  } else if (ch == 4) {
+    if (ai != 0) { ci = T; aj = T; cj = 0; }
+    else { ai = T; cj = T; aj = 0; }
+  } else {
+    int A = ci, Bt = ai;
+    if (new_fl_i > 0) { ci = 0; ai = Bt; cj = A; aj = 0; }
+    else { ci = A; ai = 0; cj = 0; aj = Bt; }
+  }
+  w.T(bi) = pack_tag(new_fl_i, ci, ai);
+  w.T(j) = pack_tag(fl_j, cj, aj);
+  L.n += 1;
+  L.n_emit += 1;
+  cnt.accepts += 1;
+  rebuild_ends(M, S, w, L);
+  return GAPS_STATUS_ACTIVE;
+}
+
+__device__ void load_event(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L, uint64_t e) {
+  const DevEvents& E = M.E;
+  L.ev = e;
+  L.status = E.status[e];
+  L.n = E.npart[e];
+  L.n_emit = E.n_emit[e];
+  L.steps = 0;
+  L.eta0 = E.eta[e];
+  L.eta1 = E.eta[E.cap + e];
+  L.draw = E.draw[e];
+  L.lnT = __logf((float)E.t[e]);
+  if (L.status != GAPS_STATUS_ACTIVE) return;
+  if (L.n < 2 || L.n > M.P.nmax) { L.status = GAPS_ERR_NUMERIC; return; }
+  for (int s = 0; s < L.n; ++s) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) w.P(mu, s) = E.P(mu, s, e);
+    w.T(s) = pack_tag(E.F(s, e), E.C(s, e), E.A(s, e));
+  }
+  rebuild_ends(M, S, w, L);
+}
+
+__device__ void store_event(const MixedCtx& M, const WS& w, const Lane& L) {
+  const DevEvents& E = M.E;
+  const uint64_t e = L.ev;
+  if (L.n >= 2 && L.n <= M.P.nmax) {
+    for (int s = 0; s < L.n; ++s) {
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) E.P(mu, s, e) = w.P(mu, s);
+      uint32_t t = w.T(s);
+      E.F(s, e) = tag_fl(t);
+      E.C(s, e) = tag_col(t);
+      E.A(s, e) = tag_acol(t);
+    }
+    E.npart[e] = L.n;
+  }
+  E.n_emit[e] = L.n_emit;
+  E.status[e] = L.status;
+  E.t[e] = (double)__expf(L.lnT);
+  E.eta[e] = L.eta0;
+  E.eta[E.cap + e] = L.eta1;
+  E.draw[e] = L.draw;
+}
+
+__global__ void __launch_bounds__(256) k_shower_mixed(MixedCtx M) {
+  __shared__ SmemPdf S;
+  for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
+    int f = q / kSmNX, ix = q % kSmNX;
+    S.umax[f][ix] = (float)M.P.umax[q];
+    S.lmin[f][ix] = (float)M.P.lmin[q];
+    float xf = 0.0f;
+    if (f < 11) xf = M.P.grid[((size_t)f * kNX + ix) * kNQ];
+    else for (int k = 1; k <= 10; ++k) xf += M.P.grid[((size_t)k * kNX + ix) * kNQ];
+    S.xf[f][ix] = xf;
+  }
+  for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
+    S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  __syncthreads();
+
+  const int lane_id = threadIdx.x & 31;
+  const int gl = blockIdx.x * blockDim.x + threadIdx.x;
+  WS w{M.W, gl, M.P.nmax};
+  Lane L;
+  bool active = false;
+  bool exhausted = false;
+  Counters32 cnt;
+  unsigned long long finished = 0, err_cap = 0, err_iter = 0, err_num = 0;
+  unsigned long long lane_steps = 0, warp_steps = 0;
+  int since_refill = M.period;
+  while (true) {
+    // warp-aggregated refill of idle lanes
+    unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (idle && !exhausted && since_refill >= M.period) {
+      since_refill = 0;
+      int cnt_idle = __popc(idle);
+      unsigned long long base = 0;
+      if (lane_id == 0) base = atomicAdd(M.next, (unsigned long long)cnt_idle);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= M.n) exhausted = true;
+      if (!active) {
+        int rank = __popc(idle & ((1u << lane_id) - 1u));
+        uint64_t e = base + rank;
+        if (e < M.n) {
+          load_event(M, S, w, L, e);
+          if (L.status == GAPS_STATUS_ACTIVE) active = true;
+          else { store_event(M, w, L); finished += 1; }
+        }
+      }
+    }
+    unsigned act = __ballot_sync(0xffffffffu, active);
+    if (act == 0) {
+      if (exhausted) break;
+      since_refill = M.period;
+      continue;
+    }
+    since_refill += 1;
+    lane_steps += __popc(act);
+    warp_steps += 32;
+    if (active) {
+      int st = step_mixed(M, S, w, L, M.first + L.ev, cnt);
+      if (++L.steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
+      if (st != GAPS_STATUS_ACTIVE) {
+        L.status = st;
+        store_event(M, w, L);
+        active = false;
+        finished += 1;
+        if (st == GAPS_ERR_CAPACITY) err_cap += 1;
+        else if (st == GAPS_ERR_ITER_CAP) err_iter += 1;
+        else if (st == GAPS_ERR_NUMERIC) err_num += 1;
+      }
+    }
+  }
+  // counters: warp sums, one atomic per warp and counter
+  unsigned long long v[12] = {finished, cnt.steps, cnt.trials, cnt.isr_trials, cnt.vetoes, cnt.accepts,
+                              cnt.violations, err_cap, err_iter, err_num,
+                              lane_id == 0 ? lane_steps : 0ull, lane_id == 0 ? warp_steps : 0ull};
+  const int idx[12] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
+                       C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS};
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    unsigned long long x = v[q];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane_id == 0 && x) atomicAdd(&M.P.counters[idx[q]], x);
+  }
+}
+
+}  // namespace
+
+size_t workset_bytes(int lanes, int nmax) {
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+}
+
+void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
+  char* p = (char*)base;
+  W.lanes = lanes;
+  W.p = (double*)p;
+  p += (size_t)lanes * nmax * 4 * sizeof(double);
+  W.end = (float4*)p;
+  p += (size_t)lanes * nmax * 2 * sizeof(float4);
+  W.tag = (uint32_t*)p;
+}
+
+cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, uint64_t first,
+                                uint64_t n, int blocks, int block_size, int period, int q_independent,
+                                unsigned long long* next, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  MixedCtx M;
+  M.P = P; M.E = E; M.W = W; M.first = first; M.n = n; M.next = next;
+  M.q_independent = q_independent;
+  M.period = period < 1 ? 1 : period;
+  M.lnTc = (float)gm_log(P.t_cut);
+  M.asOver2pi = (float)(P.as_over / (2.0 * kPi));
+  M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
+  cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
+  if (err != cudaSuccess) return err;
+  k_shower_mixed<<<blocks, block_size, 0, stream>>>(M);
+  return cudaGetLastError();
+}
+
+}  // namespace gaps

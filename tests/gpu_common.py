@@ -45,6 +45,23 @@ def run_oracle(O, process, sqrt_s, first, n, pdf, nmax=128, seed=1, threads=8, t
     return O.run(st, first, n, pdf if process else None, threads=threads)
 
 
+def identical(gpu, orc):
+    """Indices of events whose records are not bit-identical to the oracle's."""
+    n = len(gpu["npart"])
+    bad = []
+    for e in range(n):
+        m = int(orc["npart"][e])
+        same = (gpu["npart"][e] == m and gpu["status"][e] == orc["status"][e]
+                and np.array_equal(gpu["flav"][e, :m], orc["flav"][e, :m])
+                and np.array_equal(gpu["col"][e, :m], orc["col"][e, :m])
+                and np.array_equal(gpu["acol"][e, :m], orc["acol"][e, :m])
+                and np.array_equal(gpu["p"][e, :m], orc["p"][e, :m])
+                and gpu["weight"][e] == orc["weight"][e])
+        if not same:
+            bad.append(e)
+    return bad
+
+
 def compare(gpu, orc, rel=1e-12):
     """Indices of events that differ: structure (multiplicity, flavours,
     colours, status, emissions) exactly; momenta to rel x the largest energy of

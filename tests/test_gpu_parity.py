@@ -3,7 +3,7 @@ by event, for every process, launch schedule and the edge cases."""
 import numpy as np
 import pytest
 
-from tests.gpu_common import PROCESS, compare, gaps, run_gpu, run_oracle
+from tests.gpu_common import PROCESS, compare, gaps, identical, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,10 @@ def test_fp64_per_event_parity(G, oracle_mod, pdf, name):
     bad = compare(g, o)
     assert len(bad) <= _max_mismatch(n), ("mismatching events", bad[:20])
     assert np.all(g["status"] == 1)
+    # both sides evaluate the same exactly rounded operations (their own
+    # elementary functions, no FMA contraction): records are bit-identical
+    not_exact = identical(g, o)
+    assert not_exact == [], ("events not bit-identical", not_exact[:20])
     # counters: trials / vetoes / emissions summed over events agree
     if not bad:
         c = o["counters"].astype(np.int64).sum(0)

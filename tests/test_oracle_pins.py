@@ -62,6 +62,47 @@ def test_uniform_mapping(oracle_mod):
     assert oracle_mod.uniform(0x7FF, 0) == oracle_mod.uniform(0, 0)
 
 
+# --------------------------------------------------------------------------- elementary functions
+def _ulps(a, b):
+    a, b = np.float64(a), np.float64(b)
+    if a == b:
+        return 0.0
+    return float(abs(a - b) / np.spacing(max(abs(a), abs(b))))
+
+
+def test_exp_log_within_two_ulp_of_libm(oracle_mod):
+    rng = np.random.default_rng(9)
+    xs = np.concatenate([rng.uniform(-740, 705, 4000), rng.uniform(-1, 1, 4000),
+                         rng.uniform(-1e-6, 1e-6, 500), [0.0, -0.0, 1e-300, 700.0, -700.0]])
+    worst = max(_ulps(oracle_mod.exp(float(x)), math.exp(float(x))) for x in xs)
+    assert worst <= 2.0, worst
+    ys = np.concatenate([np.exp(rng.uniform(-700, 700, 4000)), rng.uniform(0.5, 2.0, 4000),
+                         1.0 + rng.uniform(-1e-9, 1e-9, 500), [1.0, 2.0, 0.5, 1e-310, 1e300]])
+    worst = 0.0
+    for y in ys:
+        ref = math.log(float(y))
+        got = oracle_mod.log(float(y))
+        if ref == 0.0:
+            assert got == 0.0
+            continue
+        worst = max(worst, _ulps(got, ref))
+    assert worst <= 2.0, worst
+    assert oracle_mod.exp(-800.0) == 0.0 and math.isinf(oracle_mod.exp(800.0))
+    assert math.isinf(oracle_mod.log(0.0)) and math.isnan(oracle_mod.log(-1.0))
+
+
+def test_sincos2pi_within_two_ulp_of_exact(oracle_mod):
+    """cos and sin of 2 pi R against 40-digit values (sympy) of the exact R."""
+    import sympy as sp
+    rng = np.random.default_rng(10)
+    Rs = list(rng.uniform(0, 1, 400)) + [0.0, 0.125, 0.25, 0.375, 0.5, 0.75, 1 - 2 ** -53, 2 ** -40]
+    for R in Rs:
+        c, s = oracle_mod.sincos2pi(float(R))
+        arg = 2 * sp.pi * sp.Rational(float(R))
+        cr, sr = float(sp.cos(arg).evalf(40)), float(sp.sin(arg).evalf(40))
+        assert abs(c - cr) <= 2.3e-16 and abs(s - sr) <= 2.3e-16, (R, c - cr, s - sr)
+
+
 # --------------------------------------------------------------------------- PDF
 def test_pdf_nodes_equal_closed_form(oracle_mod, pdf):
     xs = inputs.x_nodes()
