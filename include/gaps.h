@@ -102,6 +102,9 @@ typedef struct {
     int blocks_per_sm;    /* persistent schedule: resident blocks per SM, 0 = default */
     int refill_period;    /* GAPS_MIXED: idle lanes take new events at most every
                              this many cycles (compaction period), 0 = 1 */
+    int emit_batch;       /* GAPS_MIXED: accepted emissions of a warp are built
+                             together once this many lanes wait (or after 4x
+                             this many cycles), 1..32, 0 = 1 */
 } gaps_config;
 
 /* Event records: structure of arrays in device memory, caller-owned, event

@@ -1,0 +1,65 @@
+"""Launch-shape autotuner for the persistent mixed-precision shower.
+
+Sweeps threads per block x resident blocks per SM x refill (compaction)
+period x emission batch on a sample of the workload, timing gaps_shower with
+CUDA events, and returns the fastest shape with the whole table. The paper
+tunes a single block size for all its kernels by hand (Section 3.2); here the
+persistent kernel's shape is tuned per workload.
+"""
+from __future__ import annotations
+
+import itertools
+
+import torch
+
+from . import gaps as G
+
+DEFAULT_GRID = {
+    "block_size": (128, 256),
+    "blocks_per_sm": (2, 4),
+    "refill_period": (1, 4),
+    "emit_batch": (1, 4, 8),
+}
+
+
+def time_shape(process, sqrt_s, pdf, shape: dict, n_events: int, precision=G.GAPS_MIXED,
+               first: int = 1 << 44, reps: int = 1) -> dict:
+    cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=128,
+                        precision=precision, schedule=G.GAPS_SCHED_PERSISTENT, **shape)
+    ctx = G.gaps_init(cfg)
+    try:
+        buf = G.EventBuffers.allocate(n_events, 128)
+        ev = buf.view()
+        s = torch.cuda.current_stream()
+        best = float("inf")
+        for r in range(reps + 1):
+            f0 = first + r * n_events
+            G.gaps_generate_hard(ctx, f0, n_events, ev, s)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            G.gaps_shower(ctx, f0, n_events, ev, s)
+            b.record(s)
+            torch.cuda.synchronize()
+            if r:  # the first pass allocates the working set and warms up
+                best = min(best, a.elapsed_time(b))
+            else:
+                G.gaps_reset_stats(ctx, s)
+        st = G.gaps_get_stats(ctx, s)
+    finally:
+        G.gaps_destroy(ctx)
+    return {**shape, "ms": best, "events_per_s": n_events / best * 1e3,
+            "lane_efficiency": st["lane_steps"] / max(1, st["warp_steps"])}
+
+
+def autotune(process, sqrt_s, pdf, n_events: int = 1 << 19, grid: dict | None = None,
+             precision=G.GAPS_MIXED) -> dict:
+    grid = grid or DEFAULT_GRID
+    keys = list(grid)
+    table = []
+    for values in itertools.product(*(grid[k] for k in keys)):
+        shape = dict(zip(keys, values))
+        table.append(time_shape(process, sqrt_s, pdf, shape, n_events, precision))
+    best = min(table, key=lambda r: r["ms"])
+    return {"best": {k: best[k] for k in keys}, "best_events_per_s": best["events_per_s"],
+            "sample_events": n_events, "table": table}

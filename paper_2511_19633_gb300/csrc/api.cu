@@ -17,7 +17,7 @@ cudaError_t launch_shower_fp64(const DevParams&, const DevEvents&, uint64_t, uin
 size_t workset_bytes(int lanes, int nmax);
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
 cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, uint64_t, uint64_t, int,
-                                int, int, int, unsigned long long*, cudaStream_t);
+                                int, int, int, int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, double*, const HistDef&,
                                double*, double*, cudaStream_t);
 }  // namespace gaps
@@ -144,6 +144,7 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
   if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT) return GAPS_ERR_INVALID_ARG;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
   if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
+  if (c.emit_batch < 0 || c.emit_batch > 32) return GAPS_ERR_INVALID_ARG;
   if (c.precision == GAPS_MIXED && c.block_size != 0 && c.block_size != 64 && c.block_size != 128 &&
       c.block_size != 256)
     return GAPS_ERR_INVALID_ARG;
@@ -237,8 +238,8 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
     }
     WorkSet W;
     workset_carve(ctx->d_work, lanes, c.nmax_partons, W);
-    return cuda_fail(launch_shower_mixed(ctx->P, dev_events(ev), W, first_event, n, blocks, bs,
-                                         c.refill_period, ctx->q_independent,
+    return cuda_fail(launch_shower_mixed(ctx->P, dev_events(ev), W, first_event, n, blocks, bs, ctx->n_sm,
+                                         c.refill_period, c.emit_batch, ctx->q_independent,
                                          ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
   }
   int bs = c.block_size > 0 ? c.block_size : 128;

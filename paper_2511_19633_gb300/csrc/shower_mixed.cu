@@ -11,10 +11,12 @@
 // [..][slot][lane] (coalesced whatever event the lane holds):
 //   p    f64 [4][nmax][L]    momenta
 //   tag  u32 [nmax][L]       flavour | colour << 8 | anticolour << 16
-//   end  f32x4 [2][nmax][L]  per colour end: {c0, c1, ln t_kin, partner}
-// `end` caches the overestimate coefficients of the end's channels (c < 0:
-// channel absent, c = 0: no phase space) and is rebuilt after every accepted
-// emission. Lanes whose event has finished take new events in warp-aggregated
+//   end  f32x4 [2 nmax][L]   the event's colour ends in canonical order
+//                             (emitter ascending, colour side first):
+//                             {1/c0, 1/c1, ln t_kin, emitter | side << 8 | partner << 16}
+// `end` caches the inverse overestimate coefficients of the end's channels
+// (< 0: channel absent, 0: no phase space) and is rebuilt after every
+// accepted emission. Lanes whose event has finished take new events in warp-aggregated
 // batches, at most every `period` cycles.
 #include "physics_fp64.cuh"
 
@@ -39,6 +41,8 @@ struct MixedCtx {
   unsigned long long* next;
   int q_independent;   // grid equal for every Q^2 node: use the staged x table
   int period;          // refill at most every `period` cycles
+  int emit_batch;      // build parked emissions once this many lanes of a warp wait
+  int emit_wait;       // ... or after this many cycles
   float lnTc, asOver2pi, lxminf, dlxf, lqminf, dlqf;
 };
 
@@ -176,9 +180,7 @@ struct WS {
     return W.p[((size_t)mu * nmax + slot) * W.lanes + lane];
   }
   __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(size_t)slot * W.lanes + lane]; }
-  __device__ __forceinline__ float4& End(int side, int slot) const {
-    return W.end[((size_t)side * nmax + slot) * W.lanes + lane];
-  }
+  __device__ __forceinline__ float4& End(int q) const { return W.end[(size_t)q * W.lanes + lane]; }
 };
 
 __device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side, int tag) {
@@ -190,57 +192,180 @@ __device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side,
   return -1;
 }
 
-// Rebuild the cached overestimate coefficients of every colour end.
-__device__ void rebuild_ends(const MixedCtx& M, const SmemPdf& S, const WS& w, const Lane& L) {
+// Cached record of colour end q = 2 slot + side of an event: {1/c0, 1/c1,
+// ln t_kin, partner} (partner -1: no dipole on this side).
+__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, int n, double eta0,
+                             double eta1, int q) {
   const bool pp = M.P.process != GAPS_EE_QQ;
-  for (int i = 0; i < L.n; ++i) {
-    uint32_t ti = w.T(i);
-    int fi = tag_fl(ti);
-    bool ini = pp && i < 2;
-    for (int side = 0; side < 2; ++side) {
-      int tag = side == 0 ? tag_col(ti) : tag_acol(ti);
-      float4 rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
-      int k = tag ? find_partner(w, L.n, i, side, tag) : -1;
-      if (k >= 0) {
-        bool ink = pp && k < 2;
-        int type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
-        double pi[4], pk[4];
+  const int i = q >> 1, side = q & 1;
+  const uint32_t ti = w.T(i);
+  const int tag = side == 0 ? tag_col(ti) : tag_acol(ti);
+  const int k = tag ? find_partner(w, n, i, side, tag) : -1;
+  if (k < 0) return make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
+  const int fi = tag_fl(ti);
+  const bool ini = pp && i < 2, ink = pp && k < 2;
+  const int type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
+  double pi[4], pk[4];
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) { pi[mu] = w.P(mu, i); pk[mu] = w.P(mu, k); }
-        float s = (float)(2.0 * dot4(pi, pk));
-        float eta = 0.0f;
-        if (type == kFI) eta = (float)(k == 0 ? L.eta0 : L.eta1);
-        if (type == kIF || type == kII) eta = (float)(i == 0 ? L.eta0 : L.eta1);
-        int first = ini ? (fi == 21 ? 5 : 3) : (fi == 21 ? 1 : 0);
-        int nch = (!ini && fi != 21) ? 1 : 2;
-        float tk = tkin32(type, s, eta);
-        float zm, delta;
-        bool ok = tk > __expf(M.lnTc) && zlim32(type, __expf(M.lnTc), s, eta, zm, delta);
-        float cs[2] = {0.0f, -1.0f};
-        for (int c = 0; c < nch; ++c) {
-          cs[c] = 0.0f;
-          if (!ok) continue;
-          int ch = first + c;
-          int shape;
-          double coefd;
-          channel_over(ch, type, M.P.nf, shape, coefd);
-          float B = 1.0f;
-          if (type == kFI) {
-            int f = pdf_index(tag_fl(w.T(k)));
-            B = bound32(M, S, f, f, eta);
-          } else if (type == kIF || type == kII) {
-            int num, den;
-            isr_pdf_indices(ch, fi, num, den);
-            B = bound32(M, S, num, den, eta);
-          }
-          float cc = M.asOver2pi * B * (float)coefd * shape_int32(shape, zm, delta);
-          cs[c] = cc > 0.0f ? cc : 0.0f;
-        }
-        rec = make_float4(cs[0], cs[1], __logf(tk), __int_as_float(k));
-      }
-      w.End(side, i) = rec;
+  for (int mu = 0; mu < 4; ++mu) { pi[mu] = w.P(mu, i); pk[mu] = w.P(mu, k); }
+  const float s = (float)(2.0 * dot4(pi, pk));  // FP64: near-collinear invariant
+  float eta = 0.0f;
+  if (type == kFI) eta = (float)(k == 0 ? eta0 : eta1);
+  if (type == kIF || type == kII) eta = (float)(i == 0 ? eta0 : eta1);
+  const int first = ini ? (fi == 21 ? 5 : 3) : (fi == 21 ? 1 : 0);
+  const int nch = (!ini && fi != 21) ? 1 : 2;
+  const float tc = __expf(M.lnTc);
+  const float tk = tkin32(type, s, eta);
+  float zm, delta;
+  const bool ok = tk > tc && zlim32(type, tc, s, eta, zm, delta);
+  float ic[2] = {0.0f, -1.0f};
+  for (int c = 0; c < nch; ++c) {
+    ic[c] = 0.0f;
+    if (!ok) continue;
+    const int ch = first + c;
+    int shape;
+    double coefd;
+    channel_over(ch, type, M.P.nf, shape, coefd);
+    float B = 1.0f;
+    if (type == kFI) {
+      const int f = pdf_index(tag_fl(w.T(k)));
+      B = bound32(M, S, f, f, eta);
+    } else if (type == kIF || type == kII) {
+      int num, den;
+      isr_pdf_indices(ch, fi, num, den);
+      B = bound32(M, S, num, den, eta);
+    }
+    const float cc = M.asOver2pi * B * (float)coefd * shape_int32(shape, zm, delta);
+    ic[c] = cc > 0.0f ? 1.0f / cc : 0.0f;
+  }
+  return make_float4(ic[0], ic[1], __logf(tk), __int_as_float(k));
+}
+
+// The whole warp rebuilds the colour-end table of the event held by lane
+// `src` (one end per lane), after an emission or a refill of that lane.
+__device__ __noinline__ void rebuild_coop(const MixedCtx& M, const SmemPdf& S, int src_global, int n,
+                                          double eta0, double eta1, int lane_id) {
+  const WS w{M.W, src_global, M.P.nmax};
+  for (int q = lane_id; q < 2 * n; q += 32) w.End(q) = end_record(M, S, w, n, eta0, eta1, q);
+}
+
+struct Emission {
+  int bi, k, bside, ch, type, new_fl_i, fl_j;
+  float z, omz, tw;
+  double Rphi;
+  uint32_t ti;
+};
+
+// Accepted emission: FP64 kinematics (Appendix B maps, II Lorentz kick) and
+// colour update; the warp then rebuilds the event's end table cooperatively.
+// Kept out of line: it runs on the parked lanes of a warp only.
+__device__ __noinline__ bool emit(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L,
+                                  const Emission& em) {
+  const int bi = em.bi, k = em.k, bside = em.bside, ch = em.ch, type = em.type;
+  const int new_fl_i = em.new_fl_i, fl_j = em.fl_j;
+  const float z = em.z, omz = em.omz, tw = em.tw;
+  const double Rphi = em.Rphi;
+  const uint32_t ti = em.ti;
+  double Pm[4], K[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) { Pm[mu] = w.P(mu, bi); K[mu] = w.P(mu, k); }
+  const double sd = 2.0 * dot4(Pm, K);
+  // ---- FP64 emission kinematics ----
+  const double t = (double)tw;
+  // the smaller of z, 1-z carries the FP32 sample's relative precision; the
+  // other is formed in FP64 so that z + (1-z) = 1 and the maps conserve momentum
+  const double zd = omz < 0.5f ? 1.0 - (double)omz : (double)z;
+  const double omzd = omz < 0.5f ? (double)omz : 1.0 - (double)z;
+  double e1v[4], e2v[4];
+  transverse_basis(Pm, K, e1v, e2v);
+  double cph, sph;
+  gm_sincos2pi(Rphi, cph, sph);
+  const double st = sqrt(t);
+  double kt[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) kt[mu] = st * (cph * e1v[mu] + sph * e2v[mu]);
+  const int j = L.n;
+  double pj[4];
+  if (type == kFF) {
+    const double yd = t / (zd * omzd * sd);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      w.P(mu, bi) = zd * Pm[mu] + (yd * omzd) * K[mu] + kt[mu];
+      pj[mu] = omzd * Pm[mu] + (yd * zd) * K[mu] - kt[mu];
+      w.P(mu, k) = (1.0 - yd) * K[mu];
+    }
+  } else if (type == kFI) {
+    const double rhod = t / (zd * omzd * sd);
+    const double xinv = 1.0 + rhod;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      w.P(mu, bi) = zd * Pm[mu] + (omzd * rhod) * K[mu] + kt[mu];
+      pj[mu] = omzd * Pm[mu] + (zd * rhod) * K[mu] - kt[mu];
+      w.P(mu, k) = xinv * K[mu];
+    }
+    if (k == 0) L.eta0 *= xinv; else L.eta1 *= xinv;
+  } else if (type == kIF) {
+    double xd, omxd, ud, omud;
+    if (!if_map(t / sd, zd, omzd, xd, omxd, ud, omud)) return false;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      w.P(mu, bi) = Pm[mu] / xd;
+      pj[mu] = (omud * omxd / xd) * Pm[mu] + ud * K[mu] - kt[mu];
+      w.P(mu, k) = (ud * omxd / xd) * Pm[mu] + omud * K[mu] + kt[mu];
+    }
+    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
+  } else {
+    double xd, omxd, vd;
+    if (!ii_map(t / sd, zd, omzd, xd, omxd, vd)) return false;
+    double pa[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      pa[mu] = Pm[mu] / xd;
+      w.P(mu, bi) = pa[mu];
+      pj[mu] = ((omxd - vd) / xd) * Pm[mu] + vd * K[mu] - kt[mu];
+    }
+    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
+    double Kp[4], Kn[4], KK[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      Kp[mu] = Pm[mu] + K[mu];
+      Kn[mu] = (pa[mu] + K[mu]) - pj[mu];
+      KK[mu] = Kp[mu] + Kn[mu];
+    }
+    const double KK2 = dot4(KK, KK), Kp2 = dot4(Kp, Kp);
+    for (int m = 2; m < L.n; ++m) {
+      double q[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) q[mu] = w.P(mu, m);
+      const double a = 2.0 * dot4(KK, q) / KK2, b = 2.0 * dot4(Kp, q) / Kp2;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) w.P(mu, m) = q[mu] - a * KK[mu] + b * Kn[mu];
     }
   }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) w.P(mu, j) = pj[mu];
+
+  // colours
+  const int T = 100 + L.n;
+  int ci = tag_col(ti), ai = tag_acol(ti), cj = 0, aj = 0;
+  if (ch == 0 || ch == 1 || ch == 3 || ch == 5) {
+    if (bside == 0) { cj = ci; aj = T; ci = T; }
+    else { aj = ai; cj = T; ai = T; }
+  } else if (ch == 2) {
+    aj = ai; cj = 0; ai = 0;
+  } else if (ch == 4) {
+    if (ai != 0) { ci = T; aj = T; cj = 0; }
+    else { ai = T; cj = T; aj = 0; }
+  } else {
+    int A = ci, Bt = ai;
+    if (new_fl_i > 0) { ci = 0; ai = Bt; cj = A; aj = 0; }
+    else { ci = A; ai = 0; cj = 0; aj = Bt; }
+  }
+  w.T(bi) = pack_tag(new_fl_i, ci, ai);
+  w.T(j) = pack_tag(fl_j, cj, aj);
+  L.n += 1;
+  L.n_emit += 1;
+  return true;
 }
 
 struct Counters32 {
@@ -249,35 +374,52 @@ struct Counters32 {
 
 // One max-veto cycle on the working set. Returns the new status.
 __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L, uint64_t id,
-                          Counters32& cnt) {
+                          Counters32& cnt, Emission& pend, bool& parked) {
   const bool pp = M.P.process != GAPS_EE_QQ;
   cnt.steps += 1;
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
   const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
   float best = -INFINITY;
-  int bi = -1, bside = 0, bch = 0;
+  int bq = -1, bch = 0;
   float bRz = 0.5f;
   uint64_t d = L.draw;
-  for (int i = 0; i < L.n; ++i) {
-    for (int side = 0; side < 2; ++side) {
-      float4 rec = w.End(side, i);
-      if (__float_as_int(rec.w) < 0) continue;
-      float lnTmax = fminf(L.lnT, rec.z);
-      bool live = lnTmax > M.lnTc;
+  // one overestimate trial per channel of every colour end, in canonical order
+  auto trial = [&](const float4& rec, int q) {
+    const float lnTmax = fminf(L.lnT, rec.z);
+    const bool live = lnTmax > M.lnTc;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float cc = c == 0 ? rec.x : rec.y;
-        if (cc < 0.0f) continue;  // channel absent for this emitter
-        uint64_t dd = d++;
-        if (!(live && cc > 0.0f)) continue;
-        uint32_t out[4];
-        philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
-        cnt.trials += 1;
-        if (pp && i < 2) cnt.isr_trials += 1;
-        float lt = lnTmax + __logf(u24(out[1])) / cc;
-        if (lt > best) { best = lt; bi = i; bside = side; bch = c; bRz = u24(out[3]); }
-      }
+    for (int c = 0; c < 2; ++c) {
+      const float ic = c == 0 ? rec.x : rec.y;  // 1/c
+      if (ic < 0.0f) continue;  // channel absent for this emitter
+      const uint64_t dd = d++;
+      if (!(live && ic > 0.0f)) continue;
+      uint32_t out[4];
+      philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+      cnt.trials += 1;
+      if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
+      const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);  // ln(t_max R^(1/c))
+      if (lt > best) { best = lt; bq = q; bch = c; bRz = u24(out[3]); }
     }
+  };
+  const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
+  int q = 0;
+  // four independent loads in flight per iteration
+  for (; q + 4 <= ne; q += 4) {
+    const float4 r0 = w.End(q), r1 = w.End(q + 1), r2 = w.End(q + 2), r3 = w.End(q + 3);
+    if (__float_as_int(r0.w) >= 0) trial(r0, q);
+    if (__float_as_int(r1.w) >= 0) trial(r1, q + 1);
+    if (__float_as_int(r2.w) >= 0) trial(r2, q + 2);
+    if (__float_as_int(r3.w) >= 0) trial(r3, q + 3);
+  }
+  for (; q < ne; ++q) {
+    const float4 r = w.End(q);
+    if (__float_as_int(r.w) >= 0) trial(r, q);
+  }
+  int bi = -1, bside = 0, k = -1;
+  if (bq >= 0) {
+    bi = bq >> 1;
+    bside = bq & 1;
+    k = __float_as_int(w.End(bq).w);
   }
   L.draw = d;
   if (bi < 0 || best < M.lnTc) return GAPS_STATUS_DONE;
@@ -295,7 +437,6 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   const uint32_t ti = w.T(bi);
   const int fl_i = tag_fl(ti);
   const bool ini = pp && bi < 2;
-  const int k = __float_as_int(w.End(bside, bi).w);
   const bool ink = pp && k < 2;
   const int type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
   const int ch = (ini ? (fl_i == 21 ? 5 : 3) : (fl_i == 21 ? 1 : 0)) + bch;
@@ -403,104 +544,14 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   }
   if (L.n >= M.P.nmax) return GAPS_ERR_CAPACITY;
 
-  // ---- FP64 emission kinematics ----
-  const double t = (double)tw;
-  const double zd = (double)z, omzd = (double)omz;
-  double e1v[4], e2v[4];
-  transverse_basis(Pm, K, e1v, e2v);
-  double cph, sph;
-  gm_sincos2pi(Rphi, cph, sph);
-  const double st = sqrt(t);
-  double kt[4];
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu) kt[mu] = st * (cph * e1v[mu] + sph * e2v[mu]);
-  const int j = L.n;
-  double pj[4];
-  if (type == kFF) {
-    const double yd = t / (zd * omzd * sd);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      w.P(mu, bi) = zd * Pm[mu] + (yd * omzd) * K[mu] + kt[mu];
-      pj[mu] = omzd * Pm[mu] + (yd * zd) * K[mu] - kt[mu];
-      w.P(mu, k) = (1.0 - yd) * K[mu];
-    }
-  } else if (type == kFI) {
-    const double rhod = t / (zd * omzd * sd);
-    const double xinv = 1.0 + rhod;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      w.P(mu, bi) = zd * Pm[mu] + (omzd * rhod) * K[mu] + kt[mu];
-      pj[mu] = omzd * Pm[mu] + (zd * rhod) * K[mu] - kt[mu];
-      w.P(mu, k) = xinv * K[mu];
-    }
-    if (k == 0) L.eta0 *= xinv; else L.eta1 *= xinv;
-  } else if (type == kIF) {
-    double xd, omxd, ud, omud;
-    if (!if_map(t / sd, zd, omzd, xd, omxd, ud, omud)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      w.P(mu, bi) = Pm[mu] / xd;
-      pj[mu] = (omud * omxd / xd) * Pm[mu] + ud * K[mu] - kt[mu];
-      w.P(mu, k) = (ud * omxd / xd) * Pm[mu] + omud * K[mu] + kt[mu];
-    }
-    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
-  } else {
-    double xd, omxd, vd;
-    if (!ii_map(t / sd, zd, omzd, xd, omxd, vd)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
-    double pa[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      pa[mu] = Pm[mu] / xd;
-      w.P(mu, bi) = pa[mu];
-      pj[mu] = ((omxd - vd) / xd) * Pm[mu] + vd * K[mu] - kt[mu];
-    }
-    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
-    double Kp[4], Kn[4], KK[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      Kp[mu] = Pm[mu] + K[mu];
-      Kn[mu] = (pa[mu] + K[mu]) - pj[mu];
-      KK[mu] = Kp[mu] + Kn[mu];
-    }
-    const double KK2 = dot4(KK, KK), Kp2 = dot4(Kp, Kp);
-    for (int m = 2; m < L.n; ++m) {
-      double q[4];
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) q[mu] = w.P(mu, m);
-      const double a = 2.0 * dot4(KK, q) / KK2, b = 2.0 * dot4(Kp, q) / Kp2;
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) w.P(mu, m) = q[mu] - a * KK[mu] + b * Kn[mu];
-    }
-  }
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu) w.P(mu, j) = pj[mu];
-
-  // colours
-  const int T = 100 + L.n;
-  int ci = tag_col(ti), ai = tag_acol(ti), cj = 0, aj = 0;
-  if (ch == 0 || ch == 1 || ch == 3 || ch == 5) {
-    if (bside == 0) { cj = ci; aj = T; ci = T; }
-    else { aj = ai; cj = T; ai = T; }
-  } else if (ch == 2) {
-    aj = ai; cj = 0; ai = 0;
-  } else if (ch == 4) {
-    if (ai != 0) { ci = T; aj = T; cj = 0; }
-    else { ai = T; cj = T; aj = 0; }
-  } else {
-    int A = ci, Bt = ai;
-    if (new_fl_i > 0) { ci = 0; ai = Bt; cj = A; aj = 0; }
-    else { ci = A; ai = 0; cj = 0; aj = Bt; }
-  }
-  w.T(bi) = pack_tag(new_fl_i, ci, ai);
-  w.T(j) = pack_tag(fl_j, cj, aj);
-  L.n += 1;
-  L.n_emit += 1;
-  cnt.accepts += 1;
-  rebuild_ends(M, S, w, L);
+  // accepted: the emission is built later, together with the other parked
+  // lanes of the warp (see the kernel loop)
+  pend = Emission{bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, Rphi, ti};
+  parked = true;
   return GAPS_STATUS_ACTIVE;
 }
 
-__device__ void load_event(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L, uint64_t e) {
+__device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, Lane& L, uint64_t e) {
   const DevEvents& E = M.E;
   L.ev = e;
   L.status = E.status[e];
@@ -518,10 +569,9 @@ __device__ void load_event(const MixedCtx& M, const SmemPdf& S, const WS& w, Lan
     for (int mu = 0; mu < 4; ++mu) w.P(mu, s) = E.P(mu, s, e);
     w.T(s) = pack_tag(E.F(s, e), E.C(s, e), E.A(s, e));
   }
-  rebuild_ends(M, S, w, L);
 }
 
-__device__ void store_event(const MixedCtx& M, const WS& w, const Lane& L) {
+__device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const Lane& L) {
   const DevEvents& E = M.E;
   const uint64_t e = L.ev;
   if (L.n >= 2 && L.n <= M.P.nmax) {
@@ -543,7 +593,10 @@ __device__ void store_event(const MixedCtx& M, const WS& w, const Lane& L) {
   E.draw[e] = L.draw;
 }
 
-__global__ void __launch_bounds__(256) k_shower_mixed(MixedCtx M) {
+// MINB sets the register tier: 256-thread blocks x MINB per SM (128, 80 or
+// 64 registers per thread)
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   __shared__ SmemPdf S;
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
@@ -560,6 +613,7 @@ __global__ void __launch_bounds__(256) k_shower_mixed(MixedCtx M) {
 
   const int lane_id = threadIdx.x & 31;
   const int gl = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp_base = gl - lane_id;
   WS w{M.W, gl, M.P.nmax};
   Lane L;
   bool active = false;
@@ -568,6 +622,9 @@ __global__ void __launch_bounds__(256) k_shower_mixed(MixedCtx M) {
   unsigned long long finished = 0, err_cap = 0, err_iter = 0, err_num = 0;
   unsigned long long lane_steps = 0, warp_steps = 0;
   int since_refill = M.period;
+  bool parked = false;
+  Emission pend;
+  int since_flush = 0;
   while (true) {
     // warp-aggregated refill of idle lanes
     unsigned idle = __ballot_sync(0xffffffffu, !active);
@@ -578,15 +635,27 @@ __global__ void __launch_bounds__(256) k_shower_mixed(MixedCtx M) {
       if (lane_id == 0) base = atomicAdd(M.next, (unsigned long long)cnt_idle);
       base = __shfl_sync(0xffffffffu, base, 0);
       if (base >= M.n) exhausted = true;
+      bool loaded = false;
       if (!active) {
         int rank = __popc(idle & ((1u << lane_id) - 1u));
         uint64_t e = base + rank;
         if (e < M.n) {
-          load_event(M, S, w, L, e);
-          if (L.status == GAPS_STATUS_ACTIVE) active = true;
+          load_event(M, w, L, e);
+          if (L.status == GAPS_STATUS_ACTIVE) active = loaded = true;
           else { store_event(M, w, L); finished += 1; }
         }
       }
+      // cooperative end tables of the freshly loaded events
+      __syncwarp();  // the loads above are visible to the whole warp
+      unsigned todo = __ballot_sync(0xffffffffu, loaded);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int n_src = __shfl_sync(0xffffffffu, L.n, src);
+        const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
+        rebuild_coop(M, S, warp_base + src, n_src, e0, e1, lane_id);
+      }
+      __syncwarp();
     }
     unsigned act = __ballot_sync(0xffffffffu, active);
     if (act == 0) {
@@ -595,10 +664,34 @@ __global__ void __launch_bounds__(256) k_shower_mixed(MixedCtx M) {
       continue;
     }
     since_refill += 1;
-    lane_steps += __popc(act);
+    // build the parked emissions when enough lanes wait, when no active lane
+    // could take another step, or after the longest allowed wait
+    const unsigned pk = __ballot_sync(0xffffffffu, parked);
+    since_flush += 1;
+    if (pk && (__popc(pk) >= M.emit_batch || pk == act || since_flush >= M.emit_wait)) {
+      since_flush = 0;
+      bool done_emit = false;
+      if (parked) {
+        parked = false;
+        done_emit = emit(M, S, w, L, pend);
+        if (done_emit) cnt.accepts += 1;
+        else cnt.vetoes += 1;
+      }
+      __syncwarp();  // the emissions above are visible to the whole warp
+      unsigned todo = __ballot_sync(0xffffffffu, done_emit);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int n_src = __shfl_sync(0xffffffffu, L.n, src);
+        const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
+        rebuild_coop(M, S, warp_base + src, n_src, e0, e1, lane_id);
+      }
+      __syncwarp();
+    }
+    lane_steps += __popc(__ballot_sync(0xffffffffu, active && !parked));
     warp_steps += 32;
-    if (active) {
-      int st = step_mixed(M, S, w, L, M.first + L.ev, cnt);
+    if (active && !parked) {
+      int st = step_mixed(M, S, w, L, M.first + L.ev, cnt, pend, parked);
       if (++L.steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st != GAPS_STATUS_ACTIVE) {
         L.status = st;
@@ -642,19 +735,26 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
 }
 
 cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, uint64_t first,
-                                uint64_t n, int blocks, int block_size, int period, int q_independent,
-                                unsigned long long* next, cudaStream_t stream) {
+                                uint64_t n, int blocks, int block_size, int sm_count, int period,
+                                int emit_batch, int q_independent, unsigned long long* next,
+                                cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   MixedCtx M;
   M.P = P; M.E = E; M.W = W; M.first = first; M.n = n; M.next = next;
   M.q_independent = q_independent;
   M.period = period < 1 ? 1 : period;
+  M.emit_batch = emit_batch < 1 ? 1 : (emit_batch > 32 ? 32 : emit_batch);
+  M.emit_wait = 4 * M.emit_batch;
   M.lnTc = (float)gm_log(P.t_cut);
   M.asOver2pi = (float)(P.as_over / (2.0 * kPi));
   M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
   cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
   if (err != cudaSuccess) return err;
-  k_shower_mixed<<<blocks, block_size, 0, stream>>>(M);
+  // the register tier follows the resident threads the launch asks for
+  const int threads_per_sm = blocks * block_size / max(1, sm_count);
+  if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, 0, stream>>>(M);
+  else if (threads_per_sm <= 768) k_shower_mixed<3><<<blocks, block_size, 0, stream>>>(M);
+  else k_shower_mixed<4><<<blocks, block_size, 0, stream>>>(M);
   return cudaGetLastError();
 }
 

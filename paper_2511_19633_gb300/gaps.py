@@ -38,7 +38,7 @@ class GapsConfig(ctypes.Structure):
         ("alpha_s_mz", ctypes.c_double), ("t_cut", ctypes.c_double), ("p_s", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("pdf_grid", ctypes.c_void_p), ("block_size", ctypes.c_int),
         ("schedule", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-        ("refill_period", ctypes.c_int),
+        ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
     ]
 
 
@@ -230,9 +230,9 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 alpha_s_mz: float = 0.118, nf: int = 5, nmax: int = 128, seed: int = 1,
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
-                refill_period: int = 0) -> GapsConfig:
+                refill_period: int = 0, emit_batch: int = 0) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied)."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     return GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
-                      block_size, schedule, blocks_per_sm, refill_period)
+                      block_size, schedule, blocks_per_sm, refill_period, emit_batch)

@@ -15,11 +15,12 @@ def gaps():
 
 
 def run_gpu(G, process, sqrt_s, first, n, pdf, nmax=128, seed=1, schedule=0, block_size=0,
-            blocks_per_sm=0, precision=0, t_cut=1.0, obs=True):
+            blocks_per_sm=0, precision=0, t_cut=1.0, obs=True, refill_period=0, emit_batch=0):
     import torch
     cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=nmax, seed=seed,
                         schedule=schedule, block_size=block_size, blocks_per_sm=blocks_per_sm,
-                        precision=precision, t_cut=t_cut)
+                        precision=precision, t_cut=t_cut, refill_period=refill_period,
+                        emit_batch=emit_batch)
     ctx = G.gaps_init(cfg)
     try:
         buf = G.EventBuffers.allocate(max(n, 1), nmax)

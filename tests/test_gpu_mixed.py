@@ -1,0 +1,121 @@
+"""Mixed-precision persistent shower (GAPS_MIXED): agreement with the FP64
+path event by event where histories coincide, and with the FP64 oracle's
+histograms (chi^2/ndf < 1.2) at the workloads' full event counts."""
+import numpy as np
+import pytest
+
+from tests.gpu_common import PROCESS, gaps, run_gpu
+from tests.hist_common import chi2_per_hist, chi2_summary, load_golden
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+
+
+@pytest.fixture(scope="module")
+def G():
+    return gaps()
+
+
+def test_mixed_follows_fp64_histories(G, pdf):
+    """Same random streams: most events take the same branchings; where they
+    do, the momenta differ only by the FP32 rounding of t and z."""
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    n = 20011
+    a = run_gpu(G, proc, sqrt_s, 0, n, pdf)
+    b = run_gpu(G, proc, sqrt_s, 0, n, pdf, precision=MIXED, schedule=1, blocks_per_sm=4)
+    same = (a["npart"] == b["npart"]) & np.all(a["flav"] == b["flav"], axis=1)
+    frac = same.mean()
+    assert frac > 0.9, frac
+    rel = []
+    for e in np.nonzero(same)[0][:5000]:
+        m = a["npart"][e]
+        sc = np.abs(a["p"][e, :m, 0]).max()
+        rel.append(np.abs(a["p"][e, :m] - b["p"][e, :m]).max() / sc)
+    assert np.median(rel) < 1e-4, np.median(rel)
+    assert b["stats"]["violations"] == 0 and b["stats"]["events"] == n
+
+
+@pytest.mark.parametrize("name", ["ee91", "pp_nlo"])
+def test_mixed_conserves_momentum_and_colour(G, pdf, name):
+    proc, sqrt_s = PROCESS[name]
+    n = 10007
+    g = run_gpu(G, proc, sqrt_s, 77, n, pdf, precision=MIXED, schedule=1)
+    assert np.all(g["status"] == 1)
+    P = g["p"]
+    for e in range(0, n, 7):
+        m = g["npart"][e]
+        if proc:
+            pin = P[e, 0] + P[e, 1]
+            pout = P[e, 2:m].sum(0)
+        else:
+            pin = np.array([sqrt_s, 0, 0, 0])
+            pout = P[e, :m].sum(0)
+        assert np.abs(pout - pin).max() < 1e-11 * sqrt_s
+        col, acol = g["col"][e, :m], g["acol"][e, :m]
+        assert sorted(col[col != 0]) == sorted(acol[acol != 0])
+
+
+@pytest.mark.parametrize("period,block,bps,batch", [(1, 128, 4, 1), (8, 64, 8, 4), (32, 256, 2, 16)])
+def test_mixed_launch_shape_does_not_change_events(G, pdf, period, block, bps, batch):
+    proc, sqrt_s = PROCESS["pp_lo"]
+    n = 5003
+    ref = run_gpu(G, proc, sqrt_s, 9, n, pdf, precision=MIXED, schedule=1)
+    cfg_g = run_gpu(G, proc, sqrt_s, 9, n, pdf, precision=MIXED, schedule=1, block_size=block,
+                    blocks_per_sm=bps, refill_period=period, emit_batch=batch)
+    for k in ("p", "flav", "npart", "weight", "obs"):
+        assert np.array_equal(ref[k], cfg_g[k]), k
+
+
+def test_mixed_capacity_errors(G, pdf):
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    g = run_gpu(G, proc, sqrt_s, 0, 3001, pdf, nmax=6, precision=MIXED, schedule=1)
+    st = g["status"]
+    assert set(np.unique(st)) <= {1, -2} and (st == -2).sum() > 100
+    assert g["stats"]["err_capacity"] == (st == -2).sum()
+    assert np.all(g["npart"][st == -2] == 6)
+
+
+def _gpu_hists(G, name, pdf, precision, n, chunk=1 << 21):
+    import torch
+    proc, sqrt_s = PROCESS[name]
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf if proc else None, nmax=128, seed=1,
+                        precision=precision, schedule=1)
+    ctx = G.gaps_init(cfg)
+    try:
+        cap = min(chunk, n)
+        buf = G.EventBuffers.allocate(cap, 128)
+        ev = buf.view()
+        hw = torch.zeros((G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
+        hw2 = torch.zeros_like(hw)
+        hists = G.GapsHists(hw.data_ptr(), hw2.data_ptr())
+        for first in range(0, n, cap):
+            m = min(cap, n - first)
+            G.gaps_generate_hard(ctx, first, m, ev)
+            G.gaps_shower(ctx, first, m, ev)
+            G.gaps_observables(ctx, m, ev, None, hists)
+        torch.cuda.synchronize()
+        binning = [G.gaps_hist_binning(ctx, h) for h in range(G.GAPS_NHIST)]
+        stats = G.gaps_get_stats(ctx)
+    finally:
+        G.gaps_destroy(ctx)
+    return hw.cpu().numpy(), hw2.cpu().numpy(), binning, stats
+
+
+@pytest.mark.parametrize("name", ["ee91", "ee500", "pp_lo", "pp_nlo"])
+def test_mixed_histograms_match_oracle(G, pdf, name):
+    """chi^2/ndf < 1.2 against the FP64 oracle's histograms (independent seed)
+    at the full event count of each workload (1e7 for NLO pp -> Z)."""
+    import os
+    from tests.hist_common import GOLDEN
+    if not os.path.exists(os.path.join(GOLDEN, "oracle_hists_%s.json" % name)):
+        pytest.fail("reference histograms missing: run tests/golden/make_oracle_hists.py")
+    gold = load_golden(name)
+    n = gold["events"]
+    w, w2, binning, stats = _gpu_hists(G, name, pdf, MIXED, n)
+    for (lo, hi, nb, oi, lg), b in zip(gold["binning"], binning):
+        assert (b["lo"], b["hi"], b["nbins"], b["obs"], int(b["log10"])) == pytest.approx((lo, hi, nb, oi, lg))
+    per = chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"])
+    red, chi2, ndf = chi2_summary(per)
+    assert stats["violations"] == 0 and stats["events"] == n
+    assert red < 1.2, (red, per)
