@@ -175,6 +175,30 @@ int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
 int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
                 const gaps_events* ev, void* stream);
 
+/* Shower without any device allocation, for callers that cannot allocate
+ * device memory themselves (code embedded in a host application that owns all
+ * device allocations, or whose device footprint is fixed before it runs).
+ * The paper has no counterpart: it is the GAPS_MIXED persistent shower of
+ * gaps_shower, run with 64 blocks of 128 threads and emission batch 8, with
+ * every piece of scratch memory held in device arrays of the library itself:
+ * a working set for at most 32 partons per event (17.8 MB), the work counter,
+ * the statistics and copies of the PDF grid and its bound tables. Every GPU
+ * that loads the library keeps these arrays until the process exits.
+ * It needs no context: `cfg` is read as in gaps_init (its precision and launch
+ * fields are ignored) and the caller still passes the event records, written
+ * by gaps_generate_hard or an equivalent. Results are identical to
+ * gaps_shower with GAPS_MIXED for the same events.
+ *   - Rejects ev->nmax above 32 (or different from cfg->nmax_partons) and
+ *     any invalid configuration with GAPS_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the arrays' device addresses; make
+ *     that first call before any stream capture.
+ *   - All calls share the same arrays (the counters are cleared by each
+ *     call): calls that overlap on the GPU, from any stream or thread, race.
+ *   - When stats != NULL it synchronises `stream` and returns this call's
+ *     counters. */
+int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
+                       const gaps_events* ev, gaps_stats* stats, void* stream);
+
 /* Observables (Section 4.1): writes obs[GAPS_NOBS][capacity] (device) and,
  * when hists != NULL, adds every event with status DONE to the histograms.
  *   e+e-: 0 1-T, 1 y23, 2 y34 (Durham), 3 final partons, 4 emissions

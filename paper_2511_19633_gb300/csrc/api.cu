@@ -38,34 +38,15 @@ struct gaps_ctx {
   size_t work_bytes = 0;
 };
 
-namespace {
-
-int cuda_fail(cudaError_t e) { return e == cudaSuccess ? GAPS_OK : GAPS_ERR_CUDA; }
-
-bool events_ok(const gaps_ctx* c, const gaps_events* ev, uint64_t n) {
-  if (!ev || !ev->p || !ev->flav || !ev->col || !ev->acol || !ev->npart || !ev->status ||
-      !ev->n_emit || !ev->weight || !ev->t || !ev->eta || !ev->draw)
-    return false;
-  if (n > ev->capacity) return false;
-  if (ev->nmax != c->cfg.nmax_partons) return false;
-  return true;
-}
-
-DevEvents dev_events(const gaps_events* ev) {
-  DevEvents E;
-  E.cap = ev->capacity; E.nmax = ev->nmax; E.p = ev->p; E.flav = ev->flav; E.col = ev->col;
-  E.acol = ev->acol; E.npart = ev->npart; E.status = ev->status; E.n_emit = ev->n_emit;
-  E.weight = ev->weight; E.t = ev->t; E.eta = ev->eta; E.draw = ev->draw;
-  return E;
-}
+namespace gaps {
 
 // Per-node extrema of the grid over Q^2 and their suffix maxima in x: the
 // ingredients of the certified PDF-ratio bound (index 11 = sum of the ten
-// quark and antiquark densities).
-void build_bound_tables(const float* g, std::vector<double>& out) {
+// quark and antiquark densities). `out` holds kBoundTableDoubles values:
+// umax [12][NX], sufmax [12][NX+1], lmin [12][NX].
+void build_bound_tables(const float* g, double* out) {
   const int NX = GAPS_PDF_NX, NQ = GAPS_PDF_NQ;
-  out.assign(12 * NX + 12 * (NX + 1) + 12 * NX, 0.0);
-  double* umax = out.data();
+  double* umax = out;
   double* sufmax = umax + 12 * NX;
   double* lmin = sufmax + 12 * (NX + 1);
   auto node = [&](int f, int ix, int iq) -> double {
@@ -91,6 +72,92 @@ void build_bound_tables(const float* g, std::vector<double>& out) {
       sufmax[f * (NX + 1) + ix] = a > b ? a : b;
     }
   }
+}
+
+// GAPS_OK or GAPS_ERR_INVALID_ARG for a configuration (no device work)
+int validate_config(const gaps_config& c) {
+  if (c.process < GAPS_EE_QQ || c.process > GAPS_PP_Z_NLO) return GAPS_ERR_INVALID_ARG;
+  if (c.precision != GAPS_FP64 && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  if (!(c.sqrt_s > 0.0) || !std::isfinite(c.sqrt_s)) return GAPS_ERR_INVALID_ARG;
+  if (c.process != GAPS_EE_QQ && !(c.sqrt_s > 91.1876 && c.sqrt_s <= 13600.0)) return GAPS_ERR_INVALID_ARG;
+  if (!(c.t_cut >= GAPS_PDF_Q2MIN) || !std::isfinite(c.t_cut)) return GAPS_ERR_INVALID_ARG;
+  if (!(c.alpha_s_mz > 0.0 && c.alpha_s_mz < 1.0)) return GAPS_ERR_INVALID_ARG;
+  if (c.nf < 1 || c.nf > 5) return GAPS_ERR_INVALID_ARG;
+  if (c.nmax_partons < 4 || c.nmax_partons > 128) return GAPS_ERR_INVALID_ARG;
+  if (c.process == GAPS_PP_Z_NLO && !(c.p_s > 0.0 && c.p_s < 1.0)) return GAPS_ERR_INVALID_ARG;
+  if (c.process != GAPS_EE_QQ && !c.pdf_grid) return GAPS_ERR_INVALID_ARG;
+  if (c.block_size < 0 || c.block_size > 1024 || (c.block_size % 32) != 0) return GAPS_ERR_INVALID_ARG;
+  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT) return GAPS_ERR_INVALID_ARG;
+  if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
+  if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
+  if (c.emit_batch < 0 || c.emit_batch > 32) return GAPS_ERR_INVALID_ARG;
+  if (c.precision == GAPS_MIXED && c.block_size != 0 && c.block_size != 64 && c.block_size != 128 &&
+      c.block_size != 256)
+    return GAPS_ERR_INVALID_ARG;
+  // one-loop running must stay below its pole down to the cutoff
+  const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
+  double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
+  if (!(den > 0.0)) return GAPS_ERR_INVALID_ARG;
+  if (c.pdf_grid) {
+    const size_t gsz = (size_t)GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ;
+    for (size_t q = 0; q < gsz; ++q)
+      if (!std::isfinite(c.pdf_grid[q]) || c.pdf_grid[q] < 0.0f) return GAPS_ERR_INVALID_ARG;
+  }
+  return GAPS_OK;
+}
+
+// scalar parameters of a configuration (device pointers left unset)
+void fill_params(const gaps_config& c, DevParams& P) {
+  const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
+  double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
+  P.process = c.process;
+  P.nf = c.nf;
+  P.nmax = c.nmax_partons;
+  P.sqrt_s = c.sqrt_s;
+  P.s_had = c.sqrt_s * c.sqrt_s;
+  P.t_cut = c.t_cut;
+  P.as_mz = c.alpha_s_mz;
+  P.beta0 = beta0;
+  P.as_over = c.alpha_s_mz / den;  // alpha_s(t_cut), the overestimate of Appendix A.2
+  P.p_s = c.p_s;
+  P.seed = c.seed;
+  P.lxmin = gm_log(GAPS_PDF_XMIN);
+  P.dlx = (gm_log(GAPS_PDF_XMAX) - P.lxmin) / (GAPS_PDF_NX - 1);
+  P.lqmin = gm_log(GAPS_PDF_Q2MIN);
+  P.dlq = (gm_log(GAPS_PDF_Q2MAX) - P.lqmin) / (GAPS_PDF_NQ - 1);
+}
+
+// 1 when every Q^2 column of the grid is identical
+int grid_q_independent(const float* g) {
+  if (!g) return 1;
+  const size_t gsz = (size_t)GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ;
+  for (size_t q = 0; q < gsz; q += GAPS_PDF_NQ)
+    for (int iq = 1; iq < GAPS_PDF_NQ; ++iq)
+      if (g[q + iq] != g[q]) return 0;
+  return 1;
+}
+
+}  // namespace gaps
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? GAPS_OK : GAPS_ERR_CUDA; }
+
+bool events_ok(const gaps_ctx* c, const gaps_events* ev, uint64_t n) {
+  if (!ev || !ev->p || !ev->flav || !ev->col || !ev->acol || !ev->npart || !ev->status ||
+      !ev->n_emit || !ev->weight || !ev->t || !ev->eta || !ev->draw)
+    return false;
+  if (n > ev->capacity) return false;
+  if (ev->nmax != c->cfg.nmax_partons) return false;
+  return true;
+}
+
+DevEvents dev_events(const gaps_events* ev) {
+  DevEvents E;
+  E.cap = ev->capacity; E.nmax = ev->nmax; E.p = ev->p; E.flav = ev->flav; E.col = ev->col;
+  E.acol = ev->acol; E.npart = ev->npart; E.status = ev->status; E.n_emit = ev->n_emit;
+  E.weight = ev->weight; E.t = ev->t; E.eta = ev->eta; E.draw = ev->draw;
+  return E;
 }
 
 void set_hist_defs(int process, HistDef& H) {
@@ -130,28 +197,8 @@ const char* gaps_error_string(int code) {
 int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
   if (!out || !cfg) return GAPS_ERR_INVALID_ARG;
   const gaps_config& c = *cfg;
-  if (c.process < GAPS_EE_QQ || c.process > GAPS_PP_Z_NLO) return GAPS_ERR_INVALID_ARG;
-  if (c.precision != GAPS_FP64 && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
-  if (!(c.sqrt_s > 0.0) || !std::isfinite(c.sqrt_s)) return GAPS_ERR_INVALID_ARG;
-  if (c.process != GAPS_EE_QQ && !(c.sqrt_s > 91.1876 && c.sqrt_s <= 13600.0)) return GAPS_ERR_INVALID_ARG;
-  if (!(c.t_cut >= GAPS_PDF_Q2MIN) || !std::isfinite(c.t_cut)) return GAPS_ERR_INVALID_ARG;
-  if (!(c.alpha_s_mz > 0.0 && c.alpha_s_mz < 1.0)) return GAPS_ERR_INVALID_ARG;
-  if (c.nf < 1 || c.nf > 5) return GAPS_ERR_INVALID_ARG;
-  if (c.nmax_partons < 4 || c.nmax_partons > 128) return GAPS_ERR_INVALID_ARG;
-  if (c.process == GAPS_PP_Z_NLO && !(c.p_s > 0.0 && c.p_s < 1.0)) return GAPS_ERR_INVALID_ARG;
-  if (c.process != GAPS_EE_QQ && !c.pdf_grid) return GAPS_ERR_INVALID_ARG;
-  if (c.block_size < 0 || c.block_size > 1024 || (c.block_size % 32) != 0) return GAPS_ERR_INVALID_ARG;
-  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT) return GAPS_ERR_INVALID_ARG;
-  if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
-  if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
-  if (c.emit_batch < 0 || c.emit_batch > 32) return GAPS_ERR_INVALID_ARG;
-  if (c.precision == GAPS_MIXED && c.block_size != 0 && c.block_size != 64 && c.block_size != 128 &&
-      c.block_size != 256)
-    return GAPS_ERR_INVALID_ARG;
-  // one-loop running must stay below its pole down to the cutoff
-  const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
-  double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
-  if (!(den > 0.0)) return GAPS_ERR_INVALID_ARG;
+  int vrc = validate_config(c);
+  if (vrc != GAPS_OK) return vrc;
 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return GAPS_ERR_NO_DEVICE;
@@ -168,16 +215,10 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
     std::vector<float> zero;
     const float* g = c.pdf_grid;
     if (!g) { zero.assign(gsz, 0.0f); g = zero.data(); }
-    for (size_t q = 0; q < gsz; ++q)
-      if (!std::isfinite(g[q]) || g[q] < 0.0f) { rc = GAPS_ERR_INVALID_ARG; break; }
-    if (rc) break;
     if ((rc = cuda_fail(cudaMemcpy(ctx->d_grid, g, gsz * sizeof(float), cudaMemcpyHostToDevice)))) break;
-    ctx->q_independent = 1;
-    for (size_t q = 0; q < gsz && ctx->q_independent; q += GAPS_PDF_NQ)
-      for (int iq = 1; iq < GAPS_PDF_NQ; ++iq)
-        if (g[q + iq] != g[q]) { ctx->q_independent = 0; break; }
-    std::vector<double> tables;
-    build_bound_tables(g, tables);
+    ctx->q_independent = grid_q_independent(g);
+    std::vector<double> tables(kBoundTableDoubles);
+    build_bound_tables(g, tables.data());
     if ((rc = cuda_fail(cudaMalloc(&ctx->d_tables, tables.size() * sizeof(double))))) break;
     if ((rc = cuda_fail(cudaMemcpy(ctx->d_tables, tables.data(), tables.size() * sizeof(double),
                                    cudaMemcpyHostToDevice)))) break;
@@ -189,25 +230,11 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
     return rc;
   }
   DevParams& P = ctx->P;
-  P.process = c.process;
-  P.nf = c.nf;
-  P.nmax = c.nmax_partons;
-  P.sqrt_s = c.sqrt_s;
-  P.s_had = c.sqrt_s * c.sqrt_s;
-  P.t_cut = c.t_cut;
-  P.as_mz = c.alpha_s_mz;
-  P.beta0 = beta0;
-  P.as_over = c.alpha_s_mz / den;  // alpha_s(t_cut), the overestimate of Appendix A.2
-  P.p_s = c.p_s;
-  P.seed = c.seed;
+  fill_params(c, P);
   P.grid = ctx->d_grid;
   P.umax = ctx->d_tables;
   P.sufmax = ctx->d_tables + 12 * GAPS_PDF_NX;
   P.lmin = ctx->d_tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
-  P.lxmin = gm_log(GAPS_PDF_XMIN);
-  P.dlx = (gm_log(GAPS_PDF_XMAX) - P.lxmin) / (GAPS_PDF_NX - 1);
-  P.lqmin = gm_log(GAPS_PDF_Q2MIN);
-  P.dlq = (gm_log(GAPS_PDF_Q2MAX) - P.lqmin) / (GAPS_PDF_NQ - 1);
   P.counters = ctx->d_counters;
   set_hist_defs(c.process, ctx->H);
   *out = ctx;

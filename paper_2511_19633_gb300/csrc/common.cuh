@@ -47,6 +47,13 @@ struct WorkSet {
   int lanes;
 };
 
+// host helpers shared by the entry points (api.cu); none allocates memory
+constexpr int kBoundTableDoubles = 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1) + 12 * GAPS_PDF_NX;
+void build_bound_tables(const float* grid, double* out);
+int validate_config(const gaps_config& c);
+void fill_params(const gaps_config& c, DevParams& P);
+int grid_q_independent(const float* grid);
+
 // histogram binning of one process family
 struct HistDef {
   double lo[GAPS_NHIST], hi[GAPS_NHIST];

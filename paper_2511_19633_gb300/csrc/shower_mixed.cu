@@ -18,6 +18,8 @@
 // (< 0: channel absent, 0: no phase space) and is rebuilt after every
 // accepted emission. Lanes whose event has finished take new events in warp-aggregated
 // batches, at most every `period` cycles.
+#include <mutex>
+
 #include "physics_fp64.cuh"
 
 namespace gaps {
@@ -759,3 +761,120 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
 }
 
 }  // namespace gaps
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point. Some callers cannot allocate device memory:
+// code that runs inside a host that owns every allocation (an embedding
+// framework with its own pool, or a plugin that must not grow the process's
+// device footprint), or code whose memory is fixed before it starts. For them
+// the mixed-precision shower runs with every piece of its scratch memory in
+// file-scope device arrays: the per-lane working set of 64 blocks x 128 threads
+// for at most 32 partons per event (17.8 MB), the work counter, the
+// statistics, and copies of the PDF grid and its bound tables. Every GPU that
+// loads the library holds these arrays until the process exits.
+// ---------------------------------------------------------------------------
+namespace gaps {
+namespace {
+
+constexpr int kStaticBlocks = 64, kStaticThreads = 128;
+constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
+constexpr int kStaticMaxNmax = 32;
+constexpr size_t kStaticWorkBytes =
+    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+
+static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
+static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];
+static __device__ __align__(256) double g_static_tables[kBoundTableDoubles];
+static __device__ __align__(256) unsigned long long g_static_counters[C_NCOUNTERS + 1];
+
+// device addresses of the arrays, looked up once per device
+struct StaticAddrs {
+  void* work;
+  float* grid;
+  double* tables;
+  unsigned long long* counters;
+  bool ready;
+};
+constexpr int kStaticMaxDevices = 64;
+StaticAddrs g_static_addrs[kStaticMaxDevices];
+std::mutex g_static_mutex;
+
+int static_addresses(int dev, StaticAddrs& out) {
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  StaticAddrs& a = g_static_addrs[dev];
+  if (!a.ready) {
+    if (cudaGetSymbolAddress(&a.work, g_static_work) != cudaSuccess) return GAPS_ERR_CUDA;
+    if (cudaGetSymbolAddress((void**)&a.grid, g_static_grid) != cudaSuccess) return GAPS_ERR_CUDA;
+    if (cudaGetSymbolAddress((void**)&a.tables, g_static_tables) != cudaSuccess) return GAPS_ERR_CUDA;
+    if (cudaGetSymbolAddress((void**)&a.counters, g_static_counters) != cudaSuccess) return GAPS_ERR_CUDA;
+    a.ready = true;
+  }
+  out = a;
+  return GAPS_OK;
+}
+
+}  // namespace
+}  // namespace gaps
+
+extern "C" int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
+                                  const gaps_events* ev, gaps_stats* stats, void* stream) {
+  using namespace gaps;
+  if (!cfg || !ev) return GAPS_ERR_INVALID_ARG;
+  if (validate_config(*cfg) != GAPS_OK) return GAPS_ERR_INVALID_ARG;
+  if (!ev->p || !ev->flav || !ev->col || !ev->acol || !ev->npart || !ev->status || !ev->n_emit ||
+      !ev->weight || !ev->t || !ev->eta || !ev->draw)
+    return GAPS_ERR_INVALID_ARG;
+  if (n > ev->capacity || ev->nmax != cfg->nmax_partons) return GAPS_ERR_INVALID_ARG;
+  if (ev->nmax > kStaticMaxNmax) return GAPS_ERR_INVALID_ARG;  // beyond the static working set
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GAPS_ERR_NO_DEVICE;
+  if (dev < 0 || dev >= kStaticMaxDevices) return GAPS_ERR_INVALID_ARG;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GAPS_ERR_CUDA;
+  StaticAddrs a;
+  int rc = static_addresses(dev, a);
+  if (rc != GAPS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevParams P;
+  fill_params(*cfg, P);
+  int q_independent = 1;
+  if (cfg->pdf_grid) {
+    double tables[kBoundTableDoubles];
+    build_bound_tables(cfg->pdf_grid, tables);
+    q_independent = grid_q_independent(cfg->pdf_grid);
+    const size_t gbytes = sizeof(float) * GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ;
+    if (cudaMemcpyAsync(a.grid, cfg->pdf_grid, gbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return GAPS_ERR_CUDA;
+    if (cudaMemcpyAsync(a.tables, tables, sizeof tables, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return GAPS_ERR_CUDA;
+    // `tables` lives on this stack frame: wait for the copy before returning
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GAPS_ERR_CUDA;
+  }
+  // the counters keep the previous call's values: start from zero
+  if (cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * (C_NCOUNTERS + 1), st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  P.grid = a.grid;
+  P.umax = a.tables;
+  P.sufmax = a.tables + 12 * GAPS_PDF_NX;
+  P.lmin = a.tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
+  P.counters = a.counters;
+  DevEvents E;
+  E.cap = ev->capacity; E.nmax = ev->nmax; E.p = ev->p; E.flav = ev->flav; E.col = ev->col;
+  E.acol = ev->acol; E.npart = ev->npart; E.status = ev->status; E.n_emit = ev->n_emit;
+  E.weight = ev->weight; E.t = ev->t; E.eta = ev->eta; E.draw = ev->draw;
+  WorkSet W;
+  workset_carve(a.work, kStaticLanes, ev->nmax, W);
+  if (launch_shower_mixed(P, E, W, first_event, n, kStaticBlocks, kStaticThreads, n_sm, 1, 8,
+                          q_independent, a.counters + C_NCOUNTERS, st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  if (stats) {
+    unsigned long long h[C_NCOUNTERS];
+    if (cudaMemcpyAsync(h, a.counters, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GAPS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GAPS_ERR_CUDA;
+    stats->events = h[C_EVENTS]; stats->steps = h[C_STEPS]; stats->trials = h[C_TRIALS];
+    stats->isr_trials = h[C_ISR_TRIALS]; stats->vetoes = h[C_VETOES]; stats->accepts = h[C_ACCEPTS];
+    stats->violations = h[C_VIOLATIONS]; stats->err_capacity = h[C_ERR_CAP];
+    stats->err_iter_cap = h[C_ERR_ITER]; stats->err_numeric = h[C_ERR_NUM];
+    stats->lane_steps = h[C_LANE_STEPS]; stats->warp_steps = h[C_WARP_STEPS];
+  }
+  return GAPS_OK;
+}

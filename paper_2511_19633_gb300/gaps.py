@@ -66,7 +66,7 @@ class GapsStats(ctypes.Structure):
 
 EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
-           "gaps_destroy")
+           "gaps_destroy", "gaps_shower_static")
 
 
 class GapsError(RuntimeError):
@@ -94,6 +94,7 @@ def _load():
     lib.gaps_error_string.restype = ctypes.c_char_p
     lib.gaps_destroy.argtypes = [vp]
     lib.gaps_destroy.restype = None
+    lib.gaps_shower_static.argtypes = [P(GapsConfig), u64, u64, P(GapsEvents), P(GapsStats), vp]
     return lib
 
 
@@ -135,6 +136,17 @@ def gaps_generate_hard(ctx, first_event: int, n: int, ev: GapsEvents, stream=Non
 
 def gaps_shower(ctx, first_event: int, n: int, ev: GapsEvents, stream=None):
     _check(_lib.gaps_shower(ctx, first_event, n, ctypes.byref(ev), _stream_ptr(stream)), "gaps_shower")
+
+
+def gaps_shower_static(cfg: GapsConfig, first_event: int, n: int, ev: GapsEvents,
+                       stream=None) -> dict:
+    """The mixed-precision shower without any device allocation (its scratch is
+    in the library's own device arrays; at most 32 partons per event). Returns
+    the call's counters."""
+    st = GapsStats()
+    _check(_lib.gaps_shower_static(ctypes.byref(cfg), first_event, n, ctypes.byref(ev),
+                                   ctypes.byref(st), _stream_ptr(stream)), "gaps_shower_static")
+    return {name: int(getattr(st, name)) for name in STAT_FIELDS}
 
 
 def gaps_observables(ctx, n: int, ev: GapsEvents, obs: torch.Tensor | None,
