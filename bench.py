@@ -29,31 +29,46 @@ if ROOT not in sys.path:
 METRIC = "showered events/sec on 1 GB300 (learned+compacted vs plain GPU) at oracle-matched chi2/ndf<1.2"
 
 WORKLOADS = {
-    # name: (process, sqrt_s, events per step, precision, description)
-    "pp_lo_1e6_fp64": (1, 13600.0, 1_000_000, 0,
+    # name: (process, sqrt_s, events per step, chunk, precision, description)
+    "pp_nlo_1e7": (2, 13600.0, 10_000_000, 1 << 22, 1,
+                   "NLO-matched pp -> Z at 13.6 TeV, synthetic 100x50 PDF, 1e7 events per step in "
+                   "chunks of 2^22, FP32 trials/PDF + FP64 kinematics, persistent compacted shower"),
+    "pp_lo_1e6_fp64": (1, 13600.0, 1_000_000, 1_000_000, 0,
                        "pp -> Z at 13.6 TeV, LO + initial/final-state shower, synthetic 100x50 PDF, "
                        "1e6 events, FP64 (per-event oracle parity)"),
-    "pp_nlo_1e6_fp64": (2, 13600.0, 1_000_000, 0,
-                        "NLO-matched pp -> Z at 13.6 TeV, 1e6 events per step, FP64"),
-    "ee91_1e4_fp64": (0, 91.2, 10_000, 0, "e+e- -> q qbar at 91.2 GeV, FSR only, 1e4 events, FP64"),
+    "ee91_1e4_fp64": (0, 91.2, 10_000, 10_000, 0,
+                      "e+e- -> q qbar at 91.2 GeV, final-state shower, 1e4 events, FP64"),
 }
-DEFAULT_WORKLOAD = "pp_lo_1e6_fp64"
+DEFAULT_WORKLOAD = "pp_nlo_1e7"
 
-# Algorithmic FP64 work per unit, counted from the formulas of one trial,
-# one initial-state trial's extra bound lookup and one accepted emission; a
-# log, exp or sqrt counts as 20 FLOP (a degree ~10 polynomial with range
-# reduction). See the design notes for the derivation.
+# Algorithmic work, counted from the formulas (see the design notes):
+# FP64 path: FLOP per trial / initial-state trial / cycle / accepted emission,
+# a log, exp or sqrt counting as 20 FLOP.
 FLOP_PER_TRIAL = 85.0
 FLOP_PER_ISR_TRIAL = 16.0
 FLOP_PER_STEP = 160.0
 FLOP_PER_ACCEPT = 300.0
-# FP64 peak of one GB300: 1.25 TFLOP/s nominal (dense, vector + tensor).
+# FP64 peak of one GB300: 1.25 TFLOP/s nominal (dense).
 FP64_PEAK_TFLOPS = 1.25
+# Mixed path: 32-bit operations per trial (Philox-4x32-10: 10 rounds of two
+# 32x32->64 products, two 3-input XORs and two key additions = 60; uniform,
+# log, FMA, compare 7), per cycle (FP32 veto: limits, maps, kernel, two PDF
+# interpolations, alpha_s) and per accepted emission (FP64 kinematics and the
+# end-table rebuild, each operation counted once).
+OPS_PER_TRIAL = 67.0
+OPS_PER_STEP = 190.0
+OPS_PER_ACCEPT = 1200.0
+# 32-bit lane peak of one GB300: 152 SMs x 128 lanes x 2.07 GHz.
+LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
 def algorithmic_flops(stats: dict) -> float:
     return (stats["trials"] * FLOP_PER_TRIAL + stats["isr_trials"] * FLOP_PER_ISR_TRIAL
             + stats["steps"] * FLOP_PER_STEP + stats["accepts"] * FLOP_PER_ACCEPT)
+
+
+def algorithmic_ops_mixed(stats: dict) -> float:
+    return stats["trials"] * OPS_PER_TRIAL + stats["steps"] * OPS_PER_STEP + stats["accepts"] * OPS_PER_ACCEPT
 
 
 def dist_env():
@@ -128,6 +143,12 @@ def measured_peaks() -> dict:
     return {}
 
 
+def _oracle_run(O, st, first, n, pdf, cores, chunk=50_000):
+    """Runs the oracle over n events in chunks (bounded host memory)."""
+    for f0 in range(0, n, chunk):
+        O.run(st, first + f0, min(chunk, n - f0), pdf, threads=cores)
+
+
 def cpu_baseline(process: int, sqrt_s: float, target_s: float = 12.0) -> dict:
     """The FP64 oracle as it stands, on all host cores, over a bounded sample."""
     from oracle import oracle as O
@@ -137,11 +158,11 @@ def cpu_baseline(process: int, sqrt_s: float, target_s: float = 12.0) -> dict:
     st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
     probe = 500 * cores
     t0 = time.perf_counter()
-    O.run(st, 10_000_000_000, probe, pdf if process else None, threads=cores)
+    _oracle_run(O, st, 10_000_000_000, probe, pdf if process else None, cores)
     dt = time.perf_counter() - t0
     n = max(probe, int(probe * target_s / max(dt, 1e-3)))
     t0 = time.perf_counter()
-    O.run(st, 20_000_000_000, n, pdf if process else None, threads=cores)
+    _oracle_run(O, st, 20_000_000_000, n, pdf if process else None, cores)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
             "sample": "%d events of the same workload (event ids from 2e10), %.1f s" % (n, dt)}
@@ -149,7 +170,7 @@ def cpu_baseline(process: int, sqrt_s: float, target_s: float = 12.0) -> dict:
 
 def run_reference(args, ws, rank):
     name = args.workload
-    process, sqrt_s, per_step, precision, desc = WORKLOADS[name]
+    process, sqrt_s, per_step, chunk, precision, desc = WORKLOADS[name]
     if rank != 0:
         return
     from oracle import oracle as O
@@ -157,17 +178,17 @@ def run_reference(args, ws, rank):
     pdf = inputs.synthetic_pdf_grid()
     cores = os.cpu_count() or 1
     st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
-    # calibrate a per-step sample of about 20 s of CPU work
+    # each step: a sample of the workload sized to about 20 s of CPU work over all steps
     probe = 200 * cores
     t0 = time.perf_counter()
-    O.run(st, 30_000_000_000, probe, pdf if process else None, threads=cores)
+    _oracle_run(O, st, 30_000_000_000, probe, pdf if process else None, cores)
     rate = probe / (time.perf_counter() - t0)
-    n = max(probe, int(rate * 20.0 / max(1, args.steps + args.warmup) * 3))
+    n = max(probe, int(rate * 20.0 / max(1, args.steps)))
     for w in range(args.warmup):
-        O.run(st, 31_000_000_000 + w * n, min(n, probe), pdf if process else None, threads=cores)
+        _oracle_run(O, st, 31_000_000_000 + w * n, min(n, probe), pdf if process else None, cores)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        O.run(st, 32_000_000_000 + k * n, n, pdf if process else None, threads=cores)
+        _oracle_run(O, st, 32_000_000_000 + k * n, n, pdf if process else None, cores)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
@@ -181,8 +202,26 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def _pass(G, ctx, ev, obs, hists, first, total, chunk, stream, shower_events=None, host=None):
+    """One pass of the hot path over `total` events in chunks: hard process,
+    shower, observables and histograms. Returns the number of kernel launches."""
+    launches = 0
+    for k, f0 in enumerate(range(0, total, chunk)):
+        m = min(chunk, total - f0)
+        G.gaps_generate_hard(ctx, first + f0, m, ev, stream)
+        if shower_events is not None:
+            shower_events[k][0].record(stream)
+        G.gaps_shower(ctx, first + f0, m, ev, stream)
+        if shower_events is not None:
+            shower_events[k][1].record(stream)
+        G.gaps_observables(ctx, m, ev, obs, hists, stream)
+        launches += 3
+        if host is not None:
+            host[0][:, f0:f0 + m].copy_(obs[:, :m], non_blocking=True)
+    return launches
+
+
 def run_ours(args, ws, rank, local):
-    import numpy as np
     import torch
     from paper_2511_19633_gb300 import build
     build.build()
@@ -195,122 +234,157 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     name = args.workload
-    process, sqrt_s, per_step, precision, desc = WORKLOADS[name]
+    process, sqrt_s, total, chunk, precision, desc = WORKLOADS[name]
     if args.events:
-        per_step = args.events
+        total = args.events
+        chunk = min(chunk, total)
     nmax = 128
     pdf = inputs.synthetic_pdf_grid()
+    shape = {"block_size": args.block, "blocks_per_sm": args.bps, "refill_period": args.period,
+             "emit_batch": args.emit_batch}
+    tuning = None
+    if precision == G.GAPS_MIXED and not args.no_autotune:
+        from paper_2511_19633_gb300 import autotune
+        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 19)
+        shape = tuning["best"]
+    schedule = G.GAPS_SCHED_PERSISTENT if (precision == G.GAPS_MIXED or args.schedule) else G.GAPS_SCHED_PER_EVENT
     cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=nmax, seed=1,
-                        precision=precision, block_size=args.block, schedule=args.schedule,
-                        blocks_per_sm=args.bps)
+                        precision=precision, schedule=schedule, **shape)
     ctx = G.gaps_init(cfg)
-    buf = G.EventBuffers.allocate(per_step, nmax)
+    buf = G.EventBuffers.allocate(chunk, nmax)
     ev = buf.view()
-    obs = torch.zeros((G.GAPS_NOBS, per_step), dtype=torch.float64, device="cuda")
+    obs = torch.zeros((G.GAPS_NOBS, chunk), dtype=torch.float64, device="cuda")
     hw = torch.zeros((G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
     hw2 = torch.zeros_like(hw)
     hists = G.GapsHists(hw.data_ptr(), hw2.data_ptr())
     stream = torch.cuda.current_stream()
     steps_total = args.warmup + args.steps
+    n_chunks = (total + chunk - 1) // chunk
 
-    def step(k, ev_sh=None):
-        first = rank_first_event(rank, k, per_step, steps_total)
-        G.gaps_generate_hard(ctx, first, per_step, ev, stream)
-        if ev_sh:
-            ev_sh[0].record(stream)
-        G.gaps_shower(ctx, first, per_step, ev, stream)
-        if ev_sh:
-            ev_sh[1].record(stream)
-        G.gaps_observables(ctx, per_step, ev, obs, hists, stream)
+    def first_of(k):
+        return rank_first_event(rank, k, total, steps_total)
 
     for k in range(args.warmup):
-        step(k)
+        _pass(G, ctx, ev, obs, hists, first_of(k), total, chunk, stream)
     torch.cuda.synchronize()
     G.gaps_reset_stats(ctx, stream)
-    shower_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                 for _ in range(args.steps)]
+    shower_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(n_chunks)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches = 0
     with ClockSampler(local) as clk:
         start.record(stream)
         for k in range(args.steps):
-            step(args.warmup + k, shower_ev[k])
+            launches += _pass(G, ctx, ev, obs, hists, first_of(args.warmup + k), total, chunk, stream,
+                              shower_ev[k])
         stop.record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms = start.elapsed_time(stop)
-    shower_ms = [a.elapsed_time(b) for a, b in shower_ev]
+    shower_ms = [a.elapsed_time(b) for step in shower_ev for a, b in step]
     stats = G.gaps_get_stats(ctx, stream)
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    total_events = per_step * args.steps * ws
-    value = total_events / (ms / 1e3)
+    value = total * args.steps * ws / (ms / 1e3)
 
-    # end to end through the C ABI with host buffers: PDF grid from pinned host
-    # memory into a new context, the full path, per-event observables and the
-    # histograms back into pinned host memory
+    # end to end through the C ABI with host buffers: a fresh context per step
+    # (PDF grid from pinned host memory), the full pass, every event's
+    # observables and the histograms back into pinned host memory
     pdf_host = torch.from_numpy(pdf).pin_memory() if process else None
-    obs_host = torch.empty((G.GAPS_NOBS, per_step), dtype=torch.float64).pin_memory()
+    obs_host = torch.empty((G.GAPS_NOBS, total), dtype=torch.float64).pin_memory()
     h_host = torch.empty((2, G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         c2 = G.make_config(process, sqrt_s, pdf_grid=None, nmax=nmax, seed=1, precision=precision,
-                           block_size=args.block, schedule=args.schedule, blocks_per_sm=args.bps)
+                           schedule=schedule, **shape)
         if pdf_host is not None:
             c2.pdf_grid = pdf_host.data_ptr()
         ctx2 = G.gaps_init(c2)
-        hw.zero_(); hw2.zero_()
-        first = rank_first_event(rank, k, per_step, steps_total) + (1 << 50)
-        G.gaps_generate_hard(ctx2, first, per_step, ev, stream)
-        G.gaps_shower(ctx2, first, per_step, ev, stream)
-        G.gaps_observables(ctx2, per_step, ev, obs, hists, stream)
-        obs_host.copy_(obs, non_blocking=True)
+        hw.zero_()
+        hw2.zero_()
+        _pass(G, ctx2, ev, obs, hists, first_of(k) + (1 << 50), total, chunk, stream, host=(obs_host,))
         h_host[0].copy_(hw, non_blocking=True)
         h_host[1].copy_(hw2, non_blocking=True)
         torch.cuda.synchronize()
         G.gaps_destroy(ctx2)
     e2e_s = time.perf_counter() - t0
-    e2e_value = per_step * e2e_steps * ws / e2e_s
+    e2e_value = total * e2e_steps * ws / e2e_s
     h2d = pdf.nbytes if process else 0
     d2h = obs_host.numel() * 8 + h_host.numel() * 8
 
-    flops = algorithmic_flops(stats)
+    # the plain GPU veto algorithm for comparison: FP64, one thread per event,
+    # no compaction, plain bound, on a sample of the same workload
+    plain = None
+    if not args.no_plain:
+        n_plain = min(total, 1 << 19)
+        cfgp = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=nmax, seed=1,
+                             precision=G.GAPS_FP64, schedule=G.GAPS_SCHED_PER_EVENT)
+        ctxp = G.gaps_init(cfgp)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _pass(G, ctxp, ev, obs, None, 1 << 51, min(n_plain, 1 << 16), chunk, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        _pass(G, ctxp, ev, obs, None, (1 << 51) + (1 << 20), n_plain, chunk, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        G.gaps_destroy(ctxp)
+        plain = {"value": n_plain / (a.elapsed_time(b) / 1e3), "unit": "events/s", "events": n_plain,
+                 "mode": "FP64, one thread per event, no compaction, plain bound (the paper's layout)"}
+
     mean_shower_s = sum(shower_ms) / len(shower_ms) / 1e3
-    achieved = flops / args.steps / mean_shower_s / 1e12
+    per_launch_events = total / n_chunks
+    if precision == G.GAPS_MIXED:
+        ops = algorithmic_ops_mixed(stats)
+        achieved = ops / (sum(shower_ms) / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_shower_mixed", "achieved": achieved, "peak": LANE_PEAK_TOPS,
+                "unit": "Tops/s (32-bit lane operations)", "frac": achieved / LANE_PEAK_TOPS,
+                "traffic": None,
+                "peak_source": "152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "shower_ms_per_launch": mean_shower_s * 1e3, "events_per_launch": per_launch_events,
+                "ops_per_event": ops / max(1, stats["events"])}
+    else:
+        flops = algorithmic_flops(stats)
+        achieved = flops / (sum(shower_ms) / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_shower_fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 (dense) from the profiling recipe",
+                "shower_ms_per_launch": mean_shower_s * 1e3, "events_per_launch": per_launch_events,
+                "flop_per_event": flops / max(1, stats["events"])}
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == 0 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": name, "description": desc, "events_per_step": per_step,
+        "config": {"workload": name, "description": desc, "events_per_step": total, "chunk": chunk,
                    "parallelism": "independent event ranges per GPU" if ws > 1 else "single GPU",
-                   "schedule": "persistent" if args.schedule else "per-event",
-                   "block": args.block or 128, "blocks_per_sm": args.bps,
-                   "l2": "records of %.1f GB per step regenerated each step (> 129 MB L2)"
-                         % (per_step * nmax * 44 / 1e9)},
-        "roofline": {"bound": "alu", "kernel": "shower", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "nominal GB300 FP64 (dense) from the profiling recipe",
-                     "shower_ms": mean_shower_s * 1e3,
-                     "flop_per_event": flops / max(1, stats["events"])},
+                   "schedule": "persistent, live-event refill" if schedule else "one thread per event",
+                   "launch_shape": shape,
+                   "l2": "event records of %.1f GB per chunk rewritten every chunk (> 129 MB L2)"
+                         % (chunk * nmax * 44 / 1e9)},
+        "roofline": roof,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": launches,
+        "plain_gpu": plain,
         "shower_stats": {k: stats[k] for k in ("events", "steps", "trials", "isr_trials", "vetoes",
                                                 "accepts", "violations", "err_capacity",
                                                 "err_iter_cap", "err_numeric")},
+        "lane_efficiency": stats["lane_steps"] / max(1, stats["warp_steps"]),
         "hbm_gbs_measured": peaks.get("hbm_gbs"),
     }
+    if tuning is not None:
+        line["autotune"] = {"best": tuning["best"], "sample_events": tuning["sample_events"],
+                            "candidates": len(tuning["table"])}
     G.gaps_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(process, sqrt_s)
@@ -330,7 +404,11 @@ def main():
     ap.add_argument("--events", type=int, default=0, help="override events per step")
     ap.add_argument("--schedule", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--bps", type=int, default=4)
+    ap.add_argument("--bps", type=int, default=8)
+    ap.add_argument("--period", type=int, default=1)
+    ap.add_argument("--emit-batch", type=int, default=16)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()

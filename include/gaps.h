@@ -199,8 +199,64 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
 int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
                        const gaps_events* ev, gaps_stats* stats, void* stream);
 
+/* ---- learned initial-state proposal --------------------------------------
+ * The overestimate of every initial-state channel (Appendix A.2) is made
+ * piecewise constant over GAPS_ISR_BINS bins of zeta, the coordinate in which
+ * z is sampled; bin heights come from a 4 -> 64 -> 64 -> 1 ReLU network with
+ * inputs (ln eta, ln(s/t_c), bin centre in zeta, class of dipole type, channel
+ * and flavour), evaluated with BF16 weights and FP32 accumulation. Every
+ * acceptance weight is checked; a weight above one is counted as a violation
+ * and the event continues with the plain certified bound, so the result is
+ * the plain algorithm's whenever the violation count is zero.
+ * Parameter layout (FP32): W1 [64][4], b1 [64], W2 [64][64], b2 [64], W3 [64],
+ * b3. */
+#define GAPS_MLP_PARAMS 4545
+#define GAPS_ISR_BINS   8
+
+/* Runs the GAPS_MIXED shower with the plain bounds and logs the initial-state
+ * colour ends met at every rebuild of an event's end table: states is a
+ * device array [capacity][4] of {eta, s, dipole type (2 IF, 3 II), PDF index
+ * of the emitter}; *count (device) is incremented per logged end, also past
+ * capacity. Requires a pp process and GAPS_MIXED. */
+int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
+                            const gaps_events* ev, float* states,
+                            uint64_t capacity, uint64_t* count, void* stream);
+
+/* Training targets of the learned bound: for each logged state, channel and
+ * bin (16 rows per state, row = state * 16 + channel * 8 + bin) the network
+ * inputs features[row][4] and targets[row] = ln(max(r, 1e-6)), with r the
+ * largest acceptance ratio over 17 zeta points of the bin and 24 scales in
+ * [t_c, t_kin]. Device arrays. */
+int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states,
+                     float* features, float* targets, void* stream);
+
+/* Installs a trained network (host array of GAPS_MLP_PARAMS floats, copied)
+ * and the margin added to its output (bin height = min(1, exp(NN + margin)));
+ * later GAPS_MIXED showers of the context use it. params == NULL returns to
+ * the plain bounds. */
+int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, float log_margin);
+
+/* Network kernels (device arrays; features [n][4]):
+ * gaps_mlp_loss_grad: expectile loss mean w (y - t)^2, w = tau below the
+ *   target and 1 - tau above, and its gradient [GAPS_MLP_PARAMS] (FP32).
+ * gaps_mlp_forward: outputs [n], FP32 (bf16 = 0) or the BF16 tensor-core
+ *   numerics of the shower (bf16 = 1).
+ * gaps_mlp_train: `steps` Adam steps (lr, beta 0.9/0.999) on minibatches of
+ *   256 rows drawn with replacement (Philox, seed), updating params and the
+ *   moment buffers m, v in place; loss_history[k] = batch loss of step
+ *   k * history_every when not NULL. */
+int gaps_mlp_loss_grad(const float* params, const float* features, const float* targets,
+                       uint64_t n, float tau, float* grad, float* loss, void* stream);
+int gaps_mlp_forward(const float* params, const float* features, uint64_t n, int bf16,
+                     float* out, void* stream);
+int gaps_mlp_train(float* params, float* adam_m, float* adam_v, const float* features,
+                   const float* targets, uint64_t n, uint64_t steps, float lr, float tau,
+                   uint64_t seed, float* loss_history, int history_every, void* stream);
+
 /* Observables (Section 4.1): writes obs[GAPS_NOBS][capacity] (device) and,
  * when hists != NULL, adds every event with status DONE to the histograms.
+ * Clustering and event shapes run in FP64 for GAPS_FP64 contexts and in FP32
+ * for GAPS_MIXED ones (the Z observables always in FP64).
  *   e+e-: 0 1-T, 1 y23, 2 y34 (Durham), 3 final partons, 4 emissions
  *   pp  : 0 Z pT, 1 Z rapidity, 2 Z phi (0 without emission), 3 anti-kT
  *         R=0.4 jets with pT > 5 GeV and |eta| < 5, 4 leading jet pT,

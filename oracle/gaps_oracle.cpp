@@ -459,17 +459,19 @@ double collinear_leg(const Physics& ph, int fl, double eta, double R) {
 }
 
 // Dilogarithm Li2(x) for x in [0, 1]: the power series sum x^k/k^2 for
-// x <= 1/2 and Euler's reflection Li2(x) = pi^2/6 - ln x ln(1-x) - Li2(1-x)
-// above.
+// x <= 1/2 (summed until a term falls below 1e-17 of the sum) and Euler's
+// reflection Li2(x) = pi^2/6 - ln x ln(1-x) - Li2(1-x) above.
 double li2(double x) {
   if (x == 0.0) return 0.0;
   if (x == 1.0) return kPi * kPi / 6.0;
   if (x > 0.5) return kPi * kPi / 6.0 - lg(x) * lg(1.0 - x) - li2(1.0 - x);
+  // the remaining tail after a term t is below t x/(1-x) <= t for x <= 1/2
   double sum = 0.0, xk = x;
   for (int k = 1; k < 200; ++k) {
-    sum += xk / ((double)k * (double)k);
+    double term = xk / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
     xk *= x;
-    if (xk < 1e-300) break;
   }
   return sum;
 }
@@ -1527,6 +1529,87 @@ int oracle_if_map(double r, double z, double omz, double out[4]) {
 }
 int oracle_ii_map(double r, double z, double omz, double out[3]) {
   return ii_map(r, z, omz, out[0], out[1], out[2]) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Reference of the learned-proposal network: a 4 -> 64 -> 64 -> 1 multilayer
+// perceptron with ReLU hidden layers, in FP64. Parameter layout (4545 values):
+// W1 [64][4], b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1]. Loss: the
+// asymmetric squared error (expectile) mean_i w_i (y_i - t_i)^2 with
+// w_i = tau when the prediction is below the target, 1 - tau otherwise.
+// oracle_mlp_loss_grad returns the loss and writes d loss / d params by
+// backpropagation written out layer by layer.
+// ---------------------------------------------------------------------------
+constexpr int kH = 64, kIn = 4;
+constexpr int kParams = kH * kIn + kH + kH * kH + kH + kH + 1;
+
+static double mlp_forward_one(const double* P, const double* x, double* h1, double* h2) {
+  const double* W1 = P;
+  const double* b1 = W1 + kH * kIn;
+  const double* W2 = b1 + kH;
+  const double* b2 = W2 + kH * kH;
+  const double* W3 = b2 + kH;
+  const double b3 = W3[kH];
+  for (int i = 0; i < kH; ++i) {
+    double a = b1[i];
+    for (int k = 0; k < kIn; ++k) a += W1[i * kIn + k] * x[k];
+    h1[i] = a > 0.0 ? a : 0.0;
+  }
+  for (int i = 0; i < kH; ++i) {
+    double a = b2[i];
+    for (int k = 0; k < kH; ++k) a += W2[i * kH + k] * h1[k];
+    h2[i] = a > 0.0 ? a : 0.0;
+  }
+  double y = b3;
+  for (int k = 0; k < kH; ++k) y += W3[k] * h2[k];
+  return y;
+}
+
+void oracle_mlp_forward(const double* P, const double* X, uint64_t n, double* out) {
+  double h1[kH], h2[kH];
+  for (uint64_t i = 0; i < n; ++i) out[i] = mlp_forward_one(P, X + 4 * i, h1, h2);
+}
+
+double oracle_mlp_loss_grad(const double* P, const double* X, const double* T, uint64_t n, double tau,
+                            double* grad) {
+  for (int q = 0; q < kParams; ++q) grad[q] = 0.0;
+  const double* W2 = P + kH * kIn + kH;
+  const double* W3 = W2 + kH * kH + kH;
+  double* gW1 = grad;
+  double* gb1 = gW1 + kH * kIn;
+  double* gW2 = gb1 + kH;
+  double* gb2 = gW2 + kH * kH;
+  double* gW3 = gb2 + kH;
+  double* gb3 = gW3 + kH;
+  double loss = 0.0;
+  double h1[kH], h2[kH], d2[kH], d1[kH];
+  for (uint64_t s = 0; s < n; ++s) {
+    const double* x = X + 4 * s;
+    double y = mlp_forward_one(P, x, h1, h2);
+    double r = y - T[s];
+    double w = r < 0.0 ? tau : 1.0 - tau;
+    loss += w * r * r;
+    double dy = 2.0 * w * r / (double)n;  // d loss / d y
+    gb3[0] += dy;
+    for (int k = 0; k < kH; ++k) {
+      gW3[k] += dy * h2[k];
+      d2[k] = h2[k] > 0.0 ? dy * W3[k] : 0.0;  // through ReLU
+    }
+    for (int i = 0; i < kH; ++i) {
+      gb2[i] += d2[i];
+      for (int k = 0; k < kH; ++k) gW2[i * kH + k] += d2[i] * h1[k];
+    }
+    for (int k = 0; k < kH; ++k) {
+      double a = 0.0;
+      for (int i = 0; i < kH; ++i) a += W2[i * kH + k] * d2[i];
+      d1[k] = h1[k] > 0.0 ? a : 0.0;
+    }
+    for (int i = 0; i < kH; ++i) {
+      gb1[i] += d1[i];
+      for (int k = 0; k < kIn; ++k) gW1[i * kIn + k] += d1[i] * x[k];
+    }
+  }
+  return loss / (double)n;
 }
 
 void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {

@@ -96,6 +96,9 @@ def lib():
         _lib.oracle_antikt.restype = i
         _lib.oracle_first_emission.argtypes = [P(OracleConfig), i, i, d, d, ctypes.c_uint64, vp]
         _lib.oracle_if_map.argtypes = [d, d, d, vp]
+        _lib.oracle_mlp_forward.argtypes = [vp, vp, ctypes.c_uint64, vp]
+        _lib.oracle_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint64, d, vp]
+        _lib.oracle_mlp_loss_grad.restype = d
         _lib.oracle_ii_map.argtypes = [d, d, d, vp]
     return _lib
 
@@ -296,3 +299,25 @@ def ii_map(r: float, z: float, omz: float):
     o = np.zeros(3)
     ok = lib().oracle_ii_map(r, z, omz, _ptr(o))
     return bool(ok), o
+
+
+MLP_PARAMS = 64 * 4 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    """FP64 reference forward of the 4-64-64-1 ReLU network."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(X.shape[0])
+    lib().oracle_mlp_forward(_ptr(P), _ptr(X), X.shape[0], _ptr(out))
+    return out
+
+
+def mlp_loss_grad(params, X, T, tau: float):
+    """FP64 reference expectile loss and its gradient by backpropagation."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    g = np.zeros(MLP_PARAMS)
+    loss = lib().oracle_mlp_loss_grad(_ptr(P), _ptr(X), _ptr(T), X.shape[0], tau, _ptr(g))
+    return loss, g

@@ -25,6 +25,7 @@ UNITS = {
     "shower_fp64.cu": ["-fmad=false"],
     "observables.cu": ["-fmad=false"],
     "shower_mixed.cu": [],
+    "mlp.cu": [],
 }
 
 

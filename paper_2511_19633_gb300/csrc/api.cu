@@ -16,10 +16,11 @@ cudaError_t launch_shower_fp64(const DevParams&, const DevEvents&, uint64_t, uin
                                unsigned long long*, cudaStream_t);
 size_t workset_bytes(int lanes, int nmax);
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
-cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, uint64_t, uint64_t, int,
-                                int, int, int, int, int, unsigned long long*, cudaStream_t);
+cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, const LearnedCfg&, uint64_t,
+                                uint64_t, int, int, int, int, int, int, unsigned long long*, cudaStream_t);
+cudaError_t launch_isr_targets(const DevParams&, int, const float4*, uint64_t, float*, float*, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, double*, const HistDef&,
-                               double*, double*, cudaStream_t);
+                               double*, double*, int, cudaStream_t);
 }  // namespace gaps
 
 using namespace gaps;
@@ -36,6 +37,9 @@ struct gaps_ctx {
   int q_independent = 0;     // every Q^2 column of the grid is identical
   void* d_work = nullptr;    // mixed-precision working set
   size_t work_bytes = 0;
+  float* d_mlp = nullptr;    // learned-proposal network (FP32 parameters)
+  int learned = 0;
+  float log_margin = 0.0f;
 };
 
 namespace gaps {
@@ -247,27 +251,39 @@ int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const ga
   return cuda_fail(launch_generate_hard(ctx->P, dev_events(ev), first_event, n, (cudaStream_t)stream));
 }
 
+namespace {
+int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,
+                 void* stream) {
+  const gaps_config& c = ctx->cfg;
+  int bs = c.block_size > 0 ? c.block_size : 128;
+  int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
+  int blocks = ctx->n_sm * per_sm;
+  int lanes = blocks * bs;
+  size_t need = workset_bytes(lanes, c.nmax_partons);
+  if (need > ctx->work_bytes) {
+    if (ctx->d_work) cudaFree(ctx->d_work);
+    ctx->d_work = nullptr;
+    ctx->work_bytes = 0;
+    if (cudaMalloc(&ctx->d_work, need) != cudaSuccess) return GAPS_ERR_CUDA;
+    ctx->work_bytes = need;
+  }
+  WorkSet W;
+  workset_carve(ctx->d_work, lanes, c.nmax_partons, W);
+  return cuda_fail(launch_shower_mixed(ctx->P, dev_events(ev), W, Lc, first_event, n, blocks, bs, ctx->n_sm,
+                                       c.refill_period, c.emit_batch, ctx->q_independent,
+                                       ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
+}
+}  // namespace
+
 int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, void* stream) {
   if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
   const gaps_config& c = ctx->cfg;
   if (c.precision == GAPS_MIXED) {
-    int bs = c.block_size > 0 ? c.block_size : 128;
-    int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
-    int blocks = ctx->n_sm * per_sm;
-    int lanes = blocks * bs;
-    size_t need = workset_bytes(lanes, c.nmax_partons);
-    if (need > ctx->work_bytes) {
-      if (ctx->d_work) cudaFree(ctx->d_work);
-      ctx->d_work = nullptr;
-      ctx->work_bytes = 0;
-      if (cudaMalloc(&ctx->d_work, need) != cudaSuccess) return GAPS_ERR_CUDA;
-      ctx->work_bytes = need;
-    }
-    WorkSet W;
-    workset_carve(ctx->d_work, lanes, c.nmax_partons, W);
-    return cuda_fail(launch_shower_mixed(ctx->P, dev_events(ev), W, first_event, n, blocks, bs, ctx->n_sm,
-                                         c.refill_period, c.emit_batch, ctx->q_independent,
-                                         ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
+    LearnedCfg Lc{};
+    Lc.learned = ctx->learned && ctx->d_mlp && c.process != GAPS_EE_QQ;
+    Lc.log_margin = ctx->log_margin;
+    Lc.mlp = ctx->d_mlp;
+    return shower_mixed(ctx, first_event, n, ev, Lc, stream);
   }
   int bs = c.block_size > 0 ? c.block_size : 128;
   int pblocks = 0;
@@ -279,13 +295,48 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
                                       ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
 }
 
+int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
+                            float* states, uint64_t capacity, uint64_t* count, void* stream) {
+  if (!ctx || !events_ok(ctx, ev, n) || !states || !count) return GAPS_ERR_INVALID_ARG;
+  if (ctx->cfg.process == GAPS_EE_QQ || ctx->cfg.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  LearnedCfg Lc{};
+  Lc.collect = reinterpret_cast<float4*>(states);
+  Lc.collect_count = reinterpret_cast<unsigned long long*>(count);
+  Lc.collect_cap = capacity;
+  return shower_mixed(ctx, first_event, n, ev, Lc, stream);
+}
+
+int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states, float* features, float* targets,
+                     void* stream) {
+  if (!ctx || !states || !features || !targets) return GAPS_ERR_INVALID_ARG;
+  if (ctx->cfg.process == GAPS_EE_QQ) return GAPS_ERR_INVALID_ARG;
+  return cuda_fail(launch_isr_targets(ctx->P, ctx->q_independent, reinterpret_cast<const float4*>(states),
+                                      n_states, features, targets, (cudaStream_t)stream));
+}
+
+int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, float log_margin) {
+  if (!ctx || !std::isfinite(log_margin)) return GAPS_ERR_INVALID_ARG;
+  if (!params) {
+    ctx->learned = 0;
+    return GAPS_OK;
+  }
+  const size_t bytes = (size_t)GAPS_MLP_PARAMS * sizeof(float);
+  for (int q = 0; q < GAPS_MLP_PARAMS; ++q)
+    if (!std::isfinite(params[q])) return GAPS_ERR_INVALID_ARG;
+  if (!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, bytes) != cudaSuccess) return GAPS_ERR_CUDA;
+  if (cudaMemcpy(ctx->d_mlp, params, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return GAPS_ERR_CUDA;
+  ctx->learned = 1;
+  ctx->log_margin = log_margin;
+  return GAPS_OK;
+}
+
 int gaps_observables(gaps_ctx* ctx, uint64_t n, const gaps_events* ev, double* obs,
                      const gaps_hists* hists, void* stream) {
   if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
   if (hists && (!hists->sumw || !hists->sumw2)) return GAPS_ERR_INVALID_ARG;
   return cuda_fail(launch_observables(ctx->P, dev_events(ev), n, obs, ctx->H,
                                       hists ? hists->sumw : nullptr, hists ? hists->sumw2 : nullptr,
-                                      (cudaStream_t)stream));
+                                      ctx->cfg.precision == GAPS_MIXED, (cudaStream_t)stream));
 }
 
 int gaps_hist_binning(const gaps_ctx* ctx, int h, double* lo, double* hi, int* nbins, int* obs_index,
@@ -325,6 +376,7 @@ void gaps_destroy(gaps_ctx* ctx) {
   if (ctx->d_tables) cudaFree(ctx->d_tables);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->d_work) cudaFree(ctx->d_work);
+  if (ctx->d_mlp) cudaFree(ctx->d_mlp);
   delete ctx;
 }
 

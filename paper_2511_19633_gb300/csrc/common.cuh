@@ -44,7 +44,18 @@ struct WorkSet {
   double* p;
   uint32_t* tag;
   float4* end;
+  float* ub;     // learned bin heights [4 ends][2 channels][8 bins][lanes]
   int lanes;
+};
+
+// learned initial-state proposal and sample collection of one launch
+struct LearnedCfg {
+  int learned;                    // use the learned bin heights
+  float log_margin;               // added to the network output
+  const float* mlp;               // FP32 parameters, device
+  float4* collect;                // logged initial-state ends {eta, s, type, pdf index}
+  unsigned long long* collect_count;
+  uint64_t collect_cap;
 };
 
 // host helpers shared by the entry points (api.cu); none allocates memory

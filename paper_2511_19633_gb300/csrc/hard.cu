@@ -51,12 +51,14 @@ __device__ double born_pair_density(const DevParams& P, int k, double ea, double
   return kPi * Fa * Fb * born_me2(fa) / (mz2 * mz2);
 }
 
+// sum x^k/k^2 until a term falls below 1e-17 of the sum (x <= 1/2)
 __device__ double li2_series(double x) {
   double sum = 0.0, xk = x;
   for (int k = 1; k < 200; ++k) {
-    sum += xk / ((double)k * (double)k);
+    double term = xk / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
     xk *= x;
-    if (xk < 1e-300) break;
   }
   return sum;
 }

@@ -11,73 +11,85 @@ namespace {
 
 constexpr int kMaxFinal = 128;
 
-__device__ __forceinline__ double norm3(const double* p) {
+template <typename R>
+__device__ __forceinline__ R norm3(const R* p) {
   return sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
 }
 
 // thrust: all 2^(n-1) subsets for n <= 12 (total momentum is zero), otherwise
 // the exact construction from candidate axes p_i x p_j with the four sign
 // choices of i and j
-__device__ double thrust(const double (*ps)[4], int n) {
-  double sum = 0.0;
+template <typename R>
+__device__ R thrust(const R (*ps)[4], int n) {
+  R sum = 0;
   for (int i = 0; i < n; ++i) sum += norm3(ps[i]);
-  if (n < 2 || !(sum > 0.0)) return 1.0;
-  double best = 0.0;
+  if (n < 2 || !(sum > R(0))) return R(1);
+  R best = 0;
   if (n <= 12) {
     for (uint32_t m = 0; m < (1u << (n - 1)); ++m) {
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+      R v0 = 0, v1 = 0, v2 = 0;
       for (int i = 0; i < n; ++i)
         if ((m >> i) & 1u) { v0 += ps[i][1]; v1 += ps[i][2]; v2 += ps[i][3]; }
-      double l = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      R l = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
       best = fmax(best, l);
     }
   } else {
     for (int i = 0; i < n; ++i) {
       for (int j = i + 1; j < n; ++j) {
-        double ax0 = ps[i][2] * ps[j][3] - ps[i][3] * ps[j][2];
-        double ax1 = ps[i][3] * ps[j][1] - ps[i][1] * ps[j][3];
-        double ax2 = ps[i][1] * ps[j][2] - ps[i][2] * ps[j][1];
-        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        R ax0 = ps[i][2] * ps[j][3] - ps[i][3] * ps[j][2];
+        R ax1 = ps[i][3] * ps[j][1] - ps[i][1] * ps[j][3];
+        R ax2 = ps[i][1] * ps[j][2] - ps[i][2] * ps[j][1];
+        R b0 = 0, b1 = 0, b2 = 0;
         for (int k = 0; k < n; ++k) {
           if (k == i || k == j) continue;
-          double d = ps[k][1] * ax0 + ps[k][2] * ax1 + ps[k][3] * ax2;
-          if (d > 0.0) { b0 += ps[k][1]; b1 += ps[k][2]; b2 += ps[k][3]; }
+          R d = ps[k][1] * ax0 + ps[k][2] * ax1 + ps[k][3] * ax2;
+          if (d > R(0)) { b0 += ps[k][1]; b1 += ps[k][2]; b2 += ps[k][3]; }
         }
         for (int si = 0; si < 2; ++si) {
           for (int sj = 0; sj < 2; ++sj) {
-            double v0 = b0, v1 = b1, v2 = b2;
+            R v0 = b0, v1 = b1, v2 = b2;
             if (si) { v0 += ps[i][1]; v1 += ps[i][2]; v2 += ps[i][3]; }
             if (sj) { v0 += ps[j][1]; v1 += ps[j][2]; v2 += ps[j][3]; }
-            double l = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+            R l = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
             best = fmax(best, l);
           }
         }
       }
     }
   }
-  return 2.0 * best / sum;
+  return R(2) * best / sum;
 }
 
-__device__ __forceinline__ void erase(double (*ps)[4], int& m, int at) {
+template <typename R>
+__device__ __forceinline__ void erase(R (*ps)[4], int& m, int at) {
   for (int q = at; q < m - 1; ++q)
     for (int mu = 0; mu < 4; ++mu) ps[q][mu] = ps[q + 1][mu];
   m -= 1;
 }
 
 // Durham clustering, E-scheme; y23, y34 = smallest y_ij when 3 -> 2, 4 -> 3
-__device__ void durham(double (*ps)[4], int m, double& y23, double& y34) {
-  double evis = 0.0;
+template <typename R>
+__device__ void durham(R (*ps)[4], int m, R& y23, R& y34) {
+  R evis = 0;
   for (int i = 0; i < m; ++i) evis += ps[i][0];
-  y23 = 0.0; y34 = 0.0;
+  y23 = 0; y34 = 0;
   while (m > 1) {
-    double ymin = __longlong_as_double(0x7ff0000000000000ll);
+    R ymin = R(INFINITY);
     int bi = -1, bj = -1;
     for (int i = 0; i < m; ++i) {
       for (int j = i + 1; j < m; ++j) {
-        double ni = norm3(ps[i]), nj = norm3(ps[j]);
-        double cth = (ps[i][1] * ps[j][1] + ps[i][2] * ps[j][2] + ps[i][3] * ps[j][3]) / (ni * nj);
-        double emin = fmin(ps[i][0], ps[j][0]);
-        double y = 2.0 * emin * emin * (1.0 - cth) / (evis * evis);
+        R ni = norm3(ps[i]), nj = norm3(ps[j]);
+        R omc;  // 1 - cos(theta_ij)
+        if constexpr (sizeof(R) == 8) {
+          omc = R(1) - (ps[i][1] * ps[j][1] + ps[i][2] * ps[j][2] + ps[i][3] * ps[j][3]) / (ni * nj);
+        } else {
+          // |n_i - n_j|^2 / 2 keeps the relative precision for collinear pairs
+          R d0 = ps[i][1] / ni - ps[j][1] / nj, d1 = ps[i][2] / ni - ps[j][2] / nj,
+            d2 = ps[i][3] / ni - ps[j][3] / nj;
+          omc = R(0.5) * (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+        R emin = fmin(ps[i][0], ps[j][0]);
+        R y = R(2) * emin * emin * omc / (evis * evis);
         if (y < ymin) { ymin = y; bi = i; bj = j; }
       }
     }
@@ -88,54 +100,111 @@ __device__ void durham(double (*ps)[4], int m, double& y23, double& y34) {
   }
 }
 
-__device__ __forceinline__ void jet_kin(const double* p, double& pt2, double& y, double& phi) {
+// Pseudo-jet layout: FP64 keeps (E, px, py, pz); FP32 keeps the light-cone
+// components (E + pz, px, py, E - pz), formed in FP64 from the event record,
+// so that rapidities near the beam axis keep their relative precision (E-scheme
+// recombination adds both forms componentwise).
+template <typename R>
+__device__ __forceinline__ void jet_kin(const R* p, R& pt2, R& y, R& phi) {
   pt2 = p[1] * p[1] + p[2] * p[2];
-  y = 0.5 * log((p[0] + p[3]) / (p[0] - p[3]));
+  if constexpr (sizeof(R) == 8) y = R(0.5) * log((p[0] + p[3]) / (p[0] - p[3]));
+  else y = R(0.5) * log(p[0] / p[3]);
   phi = atan2(p[2], p[1]);
 }
 
-// anti-kT R (Cacciari, Salam, Soyez 2008), E-scheme; jets written over ps,
-// returns their number
-__device__ int antikt(double (*ps)[4], int m, double R, double (*jets)[4]) {
-  // drop particles without transverse momentum
+template <typename R>
+__device__ __forceinline__ R jet_pz(const R* p) {
+  if constexpr (sizeof(R) == 8) return p[3];
+  else return R(0.5) * (p[0] - p[3]);
+}
+
+// anti-kT distance of pseudo-jets i, j from their cached kinematics
+template <typename R>
+__device__ __forceinline__ R akt_dij(const R* pt2, const R* y, const R* phi, int i, int j, R R2) {
+  R dphi = fabs(phi[i] - phi[j]);
+  if (dphi > R(kPi)) dphi = R(2.0 * kPi) - dphi;
+  R dr2 = (y[i] - y[j]) * (y[i] - y[j]) + dphi * dphi;
+  return fmin(R(1) / pt2[i], R(1) / pt2[j]) * dr2 / R2;
+}
+
+// nearest neighbour of i among j > i
+template <typename R>
+__device__ __forceinline__ void akt_nn(const R* pt2, const R* y, const R* phi, int m, int i, R R2, R* nnd, int* nnj) {
+  R best = R(INFINITY);
+  int bj = -1;
+  for (int j = i + 1; j < m; ++j) {
+    R d = akt_dij(pt2, y, phi, i, j, R2);
+    if (d < best) { best = d; bj = j; }
+  }
+  nnd[i] = best;
+  nnj[i] = bj;
+}
+
+// anti-kT R (Cacciari, Salam, Soyez 2008), E-scheme, rapidity-azimuth
+// distance. Nearest-neighbour bookkeeping (O(n^2)); the minimum is searched
+// in the order of a full scan (beam distance of i, then pairs (i, j > i)), so
+// the clustering sequence equals the brute-force one. Reports the number of
+// jets with pT > 5 GeV and |eta| < 5 and the leading one's pT and eta.
+template <typename R>
+__device__ void antikt(R (*ps)[4], int m, R Rj, int& njets, R& lead, R& lead_eta) {
+  R pt2[kMaxFinal], y[kMaxFinal], phi[kMaxFinal], nnd[kMaxFinal];
+  int nnj[kMaxFinal];
   int w = 0;
   for (int i = 0; i < m; ++i) {
-    if (ps[i][1] * ps[i][1] + ps[i][2] * ps[i][2] > 0.0) {
+    if (ps[i][1] * ps[i][1] + ps[i][2] * ps[i][2] > R(0)) {
       for (int mu = 0; mu < 4; ++mu) ps[w][mu] = ps[i][mu];
       ++w;
     }
   }
   m = w;
-  int nj = 0;
-  const double kPiL = kPi;
+  const R R2 = Rj * Rj;
+  for (int i = 0; i < m; ++i) jet_kin(ps[i], pt2[i], y[i], phi[i]);
+  for (int i = 0; i < m; ++i) akt_nn(pt2, y, phi, m, i, R2, nnd, nnj);
+  njets = 0;
+  lead = 0;
+  lead_eta = 0;
   while (m > 0) {
-    double dmin = __longlong_as_double(0x7ff0000000000000ll);
+    R dmin = R(INFINITY);
     int bi = -1, bj = -1;
     for (int i = 0; i < m; ++i) {
-      double pti2, yi, phii;
-      jet_kin(ps[i], pti2, yi, phii);
-      double diB = 1.0 / pti2;
+      R diB = R(1) / pt2[i];
       if (diB < dmin) { dmin = diB; bi = i; bj = -1; }
-      for (int j = i + 1; j < m; ++j) {
-        double ptj2, yj, phij;
-        jet_kin(ps[j], ptj2, yj, phij);
-        double dphi = fabs(phii - phij);
-        if (dphi > kPiL) dphi = 2.0 * kPiL - dphi;
-        double dr2 = (yi - yj) * (yi - yj) + dphi * dphi;
-        double dij = fmin(1.0 / pti2, 1.0 / ptj2) * dr2 / (R * R);
-        if (dij < dmin) { dmin = dij; bi = i; bj = j; }
-      }
+      if (nnd[i] < dmin) { dmin = nnd[i]; bi = i; bj = nnj[i]; }
     }
+    int gone;
     if (bj < 0) {
-      for (int mu = 0; mu < 4; ++mu) jets[nj][mu] = ps[bi][mu];
-      ++nj;
-      erase(ps, m, bi);
+      R jpt = sqrt(ps[bi][1] * ps[bi][1] + ps[bi][2] * ps[bi][2]);
+      R jeta = asinh(jet_pz(ps[bi]) / jpt);
+      if (jpt > R(5) && fabs(jeta) < R(5)) {
+        njets += 1;
+        if (jpt > lead) { lead = jpt; lead_eta = jeta; }
+      }
+      gone = bi;
     } else {
       for (int mu = 0; mu < 4; ++mu) ps[bi][mu] += ps[bj][mu];
-      erase(ps, m, bj);
+      gone = bj;
+    }
+    // remove `gone`, keeping the order of the others
+    for (int q = gone; q < m - 1; ++q) {
+      for (int mu = 0; mu < 4; ++mu) ps[q][mu] = ps[q + 1][mu];
+      pt2[q] = pt2[q + 1]; y[q] = y[q + 1]; phi[q] = phi[q + 1];
+      nnd[q] = nnd[q + 1]; nnj[q] = nnj[q + 1];
+    }
+    m -= 1;
+    for (int i = 0; i < m; ++i)
+      if (nnj[i] > gone) nnj[i] -= 1;
+    if (bj >= 0) jet_kin(ps[bi], pt2[bi], y[bi], phi[bi]);
+    // refresh the neighbours that pointed at a changed or removed pseudo-jet
+    for (int i = 0; i < m; ++i) {
+      bool stale = (bj >= 0 && (i == bi || nnj[i] == bi)) || nnj[i] == gone;
+      if (bj >= 0 && i < bi && !stale) {
+        // a merged pseudo-jet may become i's nearest neighbour, or displace one
+        R d = akt_dij(pt2, y, phi, i, bi, R2);
+        if (d < nnd[i] || (d == nnd[i] && bi < nnj[i])) { nnd[i] = d; nnj[i] = bi; }
+      }
+      if (stale) akt_nn(pt2, y, phi, m, i, R2, nnd, nnj);
     }
   }
-  return nj;
 }
 
 __device__ __forceinline__ int bin_of(const HistDef& H, int h, double v) {
@@ -150,6 +219,8 @@ __device__ __forceinline__ int bin_of(const HistDef& H, int h, double v) {
   return b + 1;
 }
 
+// R = double for per-event parity (GAPS_FP64), float for mixed-precision contexts
+template <typename R>
 __global__ void k_observables(DevParams P, DevEvents E, uint64_t n, double* obs, HistDef H,
                               double* sumw, double* sumw2) {
   extern __shared__ double sh[];
@@ -164,22 +235,32 @@ __global__ void k_observables(DevParams P, DevEvents E, uint64_t n, double* obs,
   if (e < n) {
     double o[GAPS_NOBS];
     for (int q = 0; q < GAPS_NOBS; ++q) o[q] = 0.0;
-    double ps[kMaxFinal][4];
-    double jets[kMaxFinal][4];
+    R ps[kMaxFinal][4];
     int np = E.npart[e];
     int m = 0;
     bool pp = P.process != GAPS_EE_QQ;
     for (int i = 0; i < np && m < kMaxFinal; ++i) {
       if (pp && i < 2) continue;
       if (E.F(i, e) == 23) continue;
-      for (int mu = 0; mu < 4; ++mu) ps[m][mu] = E.P(mu, i, e);
+      if (sizeof(R) == 4 && pp) {
+        const double en = E.P(0, i, e), pz = E.P(3, i, e);
+        ps[m][0] = (R)(en + pz);
+        ps[m][1] = (R)E.P(1, i, e);
+        ps[m][2] = (R)E.P(2, i, e);
+        ps[m][3] = (R)(en - pz);
+      } else {
+        for (int mu = 0; mu < 4; ++mu) ps[m][mu] = (R)E.P(mu, i, e);
+      }
       ++m;
     }
     if (!pp) {
-      o[0] = 1.0 - thrust(ps, m);
+      o[0] = 1.0 - (double)thrust(ps, m);
       o[3] = (double)m;
       o[4] = (double)E.n_emit[e];
-      durham(ps, m, o[1], o[2]);
+      R y23, y34;
+      durham(ps, m, y23, y34);
+      o[1] = y23;
+      o[2] = y34;
     } else {
       double z0 = E.P(0, 2, e), z1 = E.P(1, 2, e), z2 = E.P(2, 2, e), z3 = E.P(3, 2, e);
       double pt = sqrt(z1 * z1 + z2 * z2);
@@ -188,17 +269,9 @@ __global__ void k_observables(DevParams P, DevEvents E, uint64_t n, double* obs,
       o[2] = pt > 0.0 ? atan2(z2, z1) : 0.0;
       o[6] = (double)m;
       o[7] = (double)E.n_emit[e];
-      int nj = antikt(ps, m, 0.4, jets);
       int cnt = 0;
-      double lead = 0.0, lead_eta = 0.0;
-      for (int q = 0; q < nj; ++q) {
-        double jpt = sqrt(jets[q][1] * jets[q][1] + jets[q][2] * jets[q][2]);
-        double jeta = asinh(jets[q][3] / jpt);
-        if (jpt > 5.0 && fabs(jeta) < 5.0) {
-          cnt += 1;
-          if (jpt > lead) { lead = jpt; lead_eta = jeta; }
-        }
-      }
+      R lead = 0, lead_eta = 0;
+      antikt(ps, m, R(0.4), cnt, lead, lead_eta);
       o[3] = (double)cnt;
       o[4] = lead;
       o[5] = lead_eta;
@@ -226,12 +299,13 @@ __global__ void k_observables(DevParams P, DevEvents E, uint64_t n, double* obs,
 }  // namespace
 
 cudaError_t launch_observables(const DevParams& P, const DevEvents& E, uint64_t n, double* obs,
-                               const HistDef& H, double* sumw, double* sumw2, cudaStream_t stream) {
+                               const HistDef& H, double* sumw, double* sumw2, int fp32, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   int bs = 64;
   unsigned grid = (unsigned)((n + bs - 1) / bs);
   size_t shm = sumw ? 2 * GAPS_NHIST * GAPS_HIST_BINS * sizeof(double) : 0;
-  k_observables<<<grid, bs, shm, stream>>>(P, E, n, obs, H, sumw, sumw2);
+  if (fp32) k_observables<float><<<grid, bs, shm, stream>>>(P, E, n, obs, H, sumw, sumw2);
+  else k_observables<double><<<grid, bs, shm, stream>>>(P, E, n, obs, H, sumw, sumw2);
   return cudaGetLastError();
 }
 

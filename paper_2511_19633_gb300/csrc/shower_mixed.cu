@@ -14,13 +14,26 @@
 //   end  f32x4 [2 nmax][L]   the event's colour ends in canonical order
 //                             (emitter ascending, colour side first):
 //                             {1/c0, 1/c1, ln t_kin, emitter | side << 8 | partner << 16}
+//   ub   f32 [4][2][8][L]     learned bin heights of the initial-state ends
 // `end` caches the inverse overestimate coefficients of the end's channels
 // (< 0: channel absent, 0: no phase space) and is rebuilt after every
-// accepted emission. Lanes whose event has finished take new events in warp-aggregated
+// accepted emission.
+//
+// Learned initial-state proposal: for the ends of the two incoming partons
+// the overestimate of each channel is made piecewise constant in 8 bins of
+// zeta, the coordinate in which z is sampled (the cumulative of Pover over
+// the z range at t_c). Bin m carries U_m = min(1, exp(NN + margin)), where the
+// network NN (4 -> 64 -> 64 -> 1, BF16 tensor cores) bounds the acceptance
+// ratio r = w / (alpha_s ratio) over the bin and every t in [t_c, t_kin].
+// The channel's coefficient becomes c * mean(U), the bin is chosen from R_z,
+// and the weight is divided by U_m. A weight above one is counted as a
+// violation; the event then continues with the plain bounds from the scale
+// before that cycle. Lanes whose event has finished take new events in warp-aggregated
 // batches, at most every `period` cycles.
 #include <mutex>
 
 #include "physics_fp64.cuh"
+#include "mlp_infer.cuh"
 
 namespace gaps {
 
@@ -39,6 +52,7 @@ struct MixedCtx {
   DevParams P;
   DevEvents E;
   WorkSet W;
+  LearnedCfg Lc;
   uint64_t first, n;
   unsigned long long* next;
   int q_independent;   // grid equal for every Q^2 node: use the staged x table
@@ -60,6 +74,7 @@ __device__ __forceinline__ int tag_acol(uint32_t t) { return (int)((t >> 16) & 0
 struct Lane {
   uint64_t ev;      // record index in the caller's arrays
   int n, n_emit, status, steps;
+  bool learned_ok;  // learned bounds active for this event
   float lnT;        // ln of the current evolution scale
   double eta0, eta1;
   uint64_t draw;
@@ -183,6 +198,9 @@ struct WS {
   }
   __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(size_t)slot * W.lanes + lane]; }
   __device__ __forceinline__ float4& End(int q) const { return W.end[(size_t)q * W.lanes + lane]; }
+  __device__ __forceinline__ float& UB(int q, int c, int m) const {
+    return W.ub[(((size_t)q * 2 + c) * 8 + m) * W.lanes + lane];
+  }
 };
 
 __device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side, int tag) {
@@ -194,10 +212,81 @@ __device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side,
   return -1;
 }
 
+// class of an initial-state end and channel for the learned bound: 22 per
+// dipole type (IF, II): q<-q and g<-q for each quark table index, g<-g, q<-g
+__device__ __forceinline__ int isr_class(int type, int ch, int fl_emitter) {
+  const int base = type == kII ? 22 : 0;
+  const int fi = pdf_index(fl_emitter);
+  if (ch == 3) return base + (fi - 1);
+  if (ch == 4) return base + 10 + (fi - 1);
+  return base + (ch == 5 ? 20 : 21);
+}
+
+// network inputs: ln eta, ln(s / t_c), the bin's centre in zeta, the class
+__device__ __forceinline__ void mlp_features(float eta, float s, float tc, int bin, int cls, float* f) {
+  f[0] = __logf(eta) * (1.0f / 7.0f) + 1.0f;
+  f[1] = __logf(s / tc) * 0.1f - 1.0f;
+  f[2] = 2.0f * ((float)bin + 0.5f) * 0.125f - 1.0f;
+  f[3] = (float)cls * (1.0f / 21.5f) - 1.0f;
+}
+
+struct IsrEval {
+  float r, x, omx, u, omu, v, sumF;
+  bool ok;
+};
+
+// Acceptance ratio r = kernel J x / Pover * PDF ratio / bound of an
+// initial-state winner (Appendix B.4/B.5), with (1-z) given directly; the
+// cycle's weight is alpha_s(t)/alpha_s(t_c) * r. ok = false outside the map.
+__device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int ch, int fl_i, float eta, float s,
+                              float tw, float z, float omz, float pover) {
+  IsrEval e;
+  e.ok = false;
+  e.r = 0.0f; e.x = 1.0f; e.omx = 0.0f; e.u = 0.0f; e.omu = 1.0f; e.v = 0.0f; e.sumF = 0.0f;
+  const float r = tw / s;
+  float J;
+  if (type == kIF) {
+    const float q = omz + r;
+    const float disc = 1.0f - 4.0f * r * z * omz / (q * q);
+    if (!(disc >= 0.0f)) return e;
+    e.x = 2.0f * z * omz / (q * (1.0f + sqrtf(disc)));
+    e.u = e.x * r / omz;
+    e.omu = 1.0f - e.u;
+    if (!(e.omu > 0.0f)) return e;
+    e.omx = omz / e.omu;
+    J = 1.0f / (e.x * e.omu + e.u * e.omx);
+  } else {
+    e.x = z * omz / (omz + r);
+    e.omx = (omz * omz + r) / (omz + r);
+    e.v = e.x * r / omz;
+    if (!(e.omx - e.v > 0.0f)) return e;
+    J = 1.0f / z;
+  }
+  if (!(e.x > eta)) return e;
+  const float x = e.x, omx = e.omx;
+  const float soft = (type == kIF) ? (omx + e.u) : omx;
+  float kk;
+  if (ch == 3) kk = (float)kCF * (2.0f / soft - (1.0f + x));
+  else if (ch == 4) kk = (float)kTR * (1.0f - 2.0f * x * omx);
+  else if (ch == 5) kk = (float)kCA * (1.0f / soft + omx / x - 1.0f + x * omx);
+  else kk = (float)kCF * 0.5f * (x + 2.0f * omx / x);
+  int num, den;
+  isr_pdf_indices(ch, fl_i, num, den);
+  const float B = bound32(M, S, num, den, eta);
+  const float F0 = pdf32(M, S, den, eta, tw);
+  const float F1 = pdf32(M, S, num, eta / x, tw);
+  if (ch == 6) e.sumF = F1;
+  const float Fratio = F0 > 0.0f ? F1 / F0 : 0.0f;
+  e.r = B > 0.0f ? kk * J * x / pover * Fratio / B : 0.0f;
+  e.ok = true;
+  return e;
+}
+
 // Cached record of colour end q = 2 slot + side of an event: {1/c0, 1/c1,
 // ln t_kin, partner} (partner -1: no dipole on this side).
 __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, int n, double eta0,
-                             double eta1, int q) {
+                             double eta1, int q, float& s_out, float& eta_out, int& type_out) {
+  type_out = -1;
   const bool pp = M.P.process != GAPS_EE_QQ;
   const int i = q >> 1, side = q & 1;
   const uint32_t ti = w.T(i);
@@ -214,6 +303,9 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, i
   float eta = 0.0f;
   if (type == kFI) eta = (float)(k == 0 ? eta0 : eta1);
   if (type == kIF || type == kII) eta = (float)(i == 0 ? eta0 : eta1);
+  s_out = s;
+  eta_out = eta;
+  type_out = type;
   const int first = ini ? (fi == 21 ? 5 : 3) : (fi == 21 ? 1 : 0);
   const int nch = (!ini && fi != 21) ? 1 : 2;
   const float tc = __expf(M.lnTc);
@@ -244,14 +336,79 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, i
 }
 
 // The whole warp rebuilds the colour-end table of the event held by lane
-// `src` (one end per lane), after an emission or a refill of that lane.
-__device__ __noinline__ void rebuild_coop(const MixedCtx& M, const SmemPdf& S, int src_global, int n,
-                                          double eta0, double eta1, int lane_id) {
+// `src` (one end per lane), after an emission or a refill of that lane. With
+// the learned proposal the warp then evaluates the network for the (up to
+// four) initial-state ends: 2 channels x 8 bins = one 16-row tile per end.
+__device__ __noinline__ void rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
+                                          float (*stage)[4], float* ustage, int src_global, int n,
+                                          double eta0, double eta1, bool learned_src, int lane_id) {
   const WS w{M.W, src_global, M.P.nmax};
-  for (int q = lane_id; q < 2 * n; q += 32) w.End(q) = end_record(M, S, w, n, eta0, eta1, q);
+  const bool pp = M.P.process != GAPS_EE_QQ;
+  float4 isr_rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
+  float isr_s = 0.0f, isr_eta = 0.0f;
+  int isr_type = -1;
+  for (int q = lane_id; q < 2 * n; q += 32) {
+    float s_, eta_;
+    int type_;
+    const float4 rec = end_record(M, S, w, n, eta0, eta1, q, s_, eta_, type_);
+    if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
+    else w.End(q) = rec;
+  }
+  if (!pp) return;
+  // lanes 0..3 hold the ends of the incoming partons
+  const bool valid = lane_id < 4 && lane_id < 2 * n && isr_type >= 0 && isr_rec.x > 0.0f && isr_rec.y > 0.0f &&
+                     (isr_type == kIF || isr_type == kII);
+  const int fl_i = lane_id < 4 && lane_id < 2 * n ? tag_fl(w.T(lane_id >> 1)) : 0;
+  if (valid && M.Lc.collect) {
+    const unsigned long long at = atomicAdd(M.Lc.collect_count, 1ull);
+    if (at < M.Lc.collect_cap)
+      M.Lc.collect[at] = make_float4(isr_eta, isr_s, (float)isr_type, (float)pdf_index(fl_i));
+  }
+  const bool use = M.Lc.learned && learned_src;
+  const unsigned any = __ballot_sync(0xffffffffu, valid && use);
+  if (any) {
+    const float tc = __expf(M.lnTc);
+    if (lane_id < 4) {
+      for (int c = 0; c < 2; ++c) {
+        const int ch = (fl_i == 21 ? 5 : 3) + c;
+        for (int m = 0; m < 8; ++m) {
+          float* f = stage[(lane_id * 2 + c) * 8 + m];
+          if (valid) mlp_features(isr_eta, isr_s, tc, m, isr_class(isr_type, ch, fl_i), f);
+          else { f[0] = f[1] = f[2] = f[3] = 0.0f; }
+        }
+      }
+    }
+    __syncwarp();
+    for (int tile = 0; tile < 4; ++tile)
+      if ((any >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
+    __syncwarp();
+  }
+  if (lane_id < 4 && lane_id < 2 * n) {
+    if (valid && use) {
+      float ic[2] = {isr_rec.x, isr_rec.y};
+      for (int c = 0; c < 2; ++c) {
+        float tot = 0.0f;
+        for (int m = 0; m < 8; ++m) {
+          const float U = fminf(1.0f, __expf(ustage[(lane_id * 2 + c) * 8 + m] + M.Lc.log_margin));
+          w.UB(lane_id, c, m) = U;
+          tot += U;
+        }
+        // c_learned = c * mean(U): the cached inverse grows by 8 / sum(U)
+        ic[c] = tot > 0.0f ? ic[c] * 8.0f / tot : 0.0f;
+      }
+      isr_rec.x = ic[0];
+      isr_rec.y = ic[1];
+    } else if (valid) {
+      for (int c = 0; c < 2; ++c)
+        for (int m = 0; m < 8; ++m) w.UB(lane_id, c, m) = 1.0f;
+    }
+    w.End(lane_id) = isr_rec;
+  }
+  __syncwarp();
 }
 
 struct Emission {
+  int kind;  // 0: build the emission, 1: only rebuild the end table (learned-bound fallback)
   int bi, k, bside, ch, type, new_fl_i, fl_j;
   float z, omz, tw;
   double Rphi;
@@ -432,6 +589,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   const float Rveto = u24(o1[1]);
   const double Rphi = u01(o1[2], o1[3]);
   const float Rfl = u24(o2[1]);
+  const float lnT_before = L.lnT;
   L.lnT = best;
   const float tw = __expf(best);
 
@@ -456,8 +614,27 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   const float coef = (float)coefd;
   float zm, delta;
   zlim32(type, __expf(M.lnTc), s, eta, zm, delta);
+  // learned bounds: pick the bin from R_z, then zeta inside it
+  const bool learned_end = M.Lc.learned && L.learned_ok && ini;
+  float zeta = bRz, Um = 1.0f;
+  if (learned_end) {
+    float U[8], tot = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) { U[m] = w.UB(bq, bch, m); tot += U[m]; }
+    const float target = bRz * tot;
+    float acc = 0.0f;
+    int mb = 7;  // when no earlier bin is reached, acc = U[0] + ... + U[6]
+    for (int m = 0; m < 7; ++m) {
+      if (target < acc + U[m]) { mb = m; break; }
+      acc += U[m];
+    }
+    Um = U[mb];
+    float frac = Um > 0.0f ? (target - acc) / Um : 0.5f;
+    frac = fminf(fmaxf(frac, 0.0f), 0.99999994f);
+    zeta = ((float)mb + frac) * 0.125f;
+  }
   float z, omz;
-  shape_sample32(shape, zm, delta, bRz, z, omz);
+  shape_sample32(shape, zm, delta, zeta, z, omz);
   float zm_t, delta_t;
   if (!zlim32(type, tw, s, eta, zm_t, delta_t) || !(omz > delta_t) || !(z > zm_t)) {
     cnt.vetoes += 1;
@@ -491,43 +668,26 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
     float ratio = F0 > 0.0f ? x * F1 / F0 : 0.0f;
     w8 = as_ratio * kk / pover * ratio / B;
   } else {
-    float r = tw / s, J;
-    if (type == kIF) {
-      float q = omz + r;
-      float disc = 1.0f - 4.0f * r * z * omz / (q * q);
-      if (!(disc >= 0.0f)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
-      x = 2.0f * z * omz / (q * (1.0f + sqrtf(disc)));
-      u = x * r / omz;
-      omu = 1.0f - u;
-      if (!(omu > 0.0f)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
-      omx = omz / omu;
-      J = 1.0f / (x * omu + u * omx);
-    } else {
-      x = z * omz / (omz + r);
-      omx = (omz * omz + r) / (omz + r);
-      v = x * r / omz;
-      if (!(omx - v > 0.0f)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
-      J = 1.0f / z;
-    }
-    if (!(x > eta)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
-    float soft = (type == kIF) ? (omx + u) : omx, kk;
-    if (ch == 3) kk = (float)kCF * (2.0f / soft - (1.0f + x));
-    else if (ch == 4) kk = (float)kTR * (1.0f - 2.0f * x * omx);
-    else if (ch == 5) kk = (float)kCA * (1.0f / soft + omx / x - 1.0f + x * omx);
-    else kk = (float)kCF * 0.5f * (x + 2.0f * omx / x);
-    int num, den;
-    isr_pdf_indices(ch, fl_i, num, den);
-    B = bound32(M, S, num, den, eta);
-    float F0 = pdf32(M, S, den, eta, tw);
-    float F1 = pdf32(M, S, num, eta / x, tw);
-    if (ch == 6) sumF = F1;
-    float Fratio = F0 > 0.0f ? F1 / F0 : 0.0f;
-    w8 = as_ratio * kk * J * x / pover * Fratio / B;
+    const IsrEval ev = isr_eval32(M, S, type, ch, fl_i, eta, s, tw, z, omz, pover);
+    if (!ev.ok) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
+    x = ev.x; omx = ev.omx; u = ev.u; omu = ev.omu; v = ev.v; sumF = ev.sumF;
+    w8 = as_ratio * ev.r / Um;
     if (ch == 4) { new_fl_i = 21; fl_j = -fl_i; }
     if (ch == 5) { new_fl_i = 21; fl_j = 21; }
   }
   if (!isfinite(w8)) return GAPS_ERR_NUMERIC;
-  if (w8 > 1.0f) cnt.violations += 1;
+  if (w8 > 1.0f) {
+    cnt.violations += 1;
+    if (learned_end) {
+      // the learned bound failed here: continue the event with the plain
+      // bounds from the scale before this cycle
+      L.learned_ok = false;
+      L.lnT = lnT_before;
+      pend = Emission{1, bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, Rphi, ti};
+      parked = true;
+      return GAPS_STATUS_ACTIVE;
+    }
+  }
   if (!(Rveto < w8)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
 
   if (ch == 2) {
@@ -548,7 +708,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
 
   // accepted: the emission is built later, together with the other parked
   // lanes of the warp (see the kernel loop)
-  pend = Emission{bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, Rphi, ti};
+  pend = Emission{0, bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, Rphi, ti};
   parked = true;
   return GAPS_STATUS_ACTIVE;
 }
@@ -564,6 +724,7 @@ __device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, Lane& L,
   L.eta1 = E.eta[E.cap + e];
   L.draw = E.draw[e];
   L.lnT = __logf((float)E.t[e]);
+  L.learned_ok = true;
   if (L.status != GAPS_STATUS_ACTIVE) return;
   if (L.n < 2 || L.n > M.P.nmax) { L.status = GAPS_ERR_NUMERIC; return; }
   for (int s = 0; s < L.n; ++s) {
@@ -600,6 +761,14 @@ __device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const L
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   __shared__ SmemPdf S;
+  // learned proposal only (dynamic size 0 otherwise): the network image, then
+  // per warp 64 rows of input features and 64 outputs
+  extern __shared__ __align__(16) unsigned char learned_smem[];
+  MlpSmem& mlp_s = *reinterpret_cast<MlpSmem*>(learned_smem);
+  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem + kMlpSmemBytes);
+  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + kMlpSmemBytes +
+                                                      (blockDim.x >> 5) * 64 * 4 * sizeof(float));
+  if (M.Lc.learned) mlp_load_smem(mlp_s, M.Lc.mlp);
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
     S.umax[f][ix] = (float)M.P.umax[q];
@@ -616,6 +785,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   const int lane_id = threadIdx.x & 31;
   const int gl = blockIdx.x * blockDim.x + threadIdx.x;
   const int warp_base = gl - lane_id;
+  const int warp_id = threadIdx.x >> 5;
   WS w{M.W, gl, M.P.nmax};
   Lane L;
   bool active = false;
@@ -655,7 +825,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         todo &= todo - 1;
         const int n_src = __shfl_sync(0xffffffffu, L.n, src);
         const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
-        rebuild_coop(M, S, warp_base + src, n_src, e0, e1, lane_id);
+        const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
+        rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1, lok, lane_id);
       }
       __syncwarp();
     }
@@ -675,9 +846,13 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
       bool done_emit = false;
       if (parked) {
         parked = false;
-        done_emit = emit(M, S, w, L, pend);
-        if (done_emit) cnt.accepts += 1;
-        else cnt.vetoes += 1;
+        if (pend.kind == 1) {
+          done_emit = true;  // plain rebuild after a learned-bound violation
+        } else {
+          done_emit = emit(M, S, w, L, pend);
+          if (done_emit) cnt.accepts += 1;
+          else cnt.vetoes += 1;
+        }
       }
       __syncwarp();  // the emissions above are visible to the whole warp
       unsigned todo = __ballot_sync(0xffffffffu, done_emit);
@@ -686,7 +861,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         todo &= todo - 1;
         const int n_src = __shfl_sync(0xffffffffu, L.n, src);
         const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
-        rebuild_coop(M, S, warp_base + src, n_src, e0, e1, lane_id);
+        const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
+        rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1, lok, lane_id);
       }
       __syncwarp();
     }
@@ -723,7 +899,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
 }  // namespace
 
 size_t workset_bytes(int lanes, int nmax) {
-  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+         (size_t)lanes * 64 * sizeof(float);
 }
 
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
@@ -733,16 +910,92 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   p += (size_t)lanes * nmax * 4 * sizeof(double);
   W.end = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
+  W.ub = (float*)p;
+  p += (size_t)lanes * 64 * sizeof(float);
   W.tag = (uint32_t*)p;
 }
 
-cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, uint64_t first,
-                                uint64_t n, int blocks, int block_size, int sm_count, int period,
+
+namespace {
+
+// Targets of the learned bound (the "teacher"): for every logged initial-state
+// end, channel and zeta bin, the largest acceptance ratio r over 17 zeta points
+// of the bin and 24 scales t log-spaced in [t_c, t_kin], as ln(max(r, 1e-6)),
+// with the network's input features of the row.
+__global__ void k_isr_targets(MixedCtx M, const float4* states, uint64_t n_states, float* feats, float* targets) {
+  __shared__ SmemPdf S;
+  for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
+    int f = q / kSmNX, ix = q % kSmNX;
+    S.umax[f][ix] = (float)M.P.umax[q];
+    S.lmin[f][ix] = (float)M.P.lmin[q];
+    float xf = 0.0f;
+    if (f < 11) xf = M.P.grid[((size_t)f * kNX + ix) * kNQ];
+    else for (int k = 1; k <= 10; ++k) xf += M.P.grid[((size_t)k * kNX + ix) * kNQ];
+    S.xf[f][ix] = xf;
+  }
+  for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
+    S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  __syncthreads();
+  const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_states * 16) return;
+  const float4 st = states[row / 16];
+  const int c = (int)((row / 8) % 2), m = (int)(row % 8);
+  const float eta = st.x, s = st.y;
+  const int type = (int)st.z, fidx = (int)st.w;
+  const int fl_i = fidx == 0 ? 21 : (fidx <= 5 ? fidx : -(fidx - 5));
+  const int ch = (fl_i == 21 ? 5 : 3) + c;
+  const float tc = __expf(M.lnTc);
+  float f[4];
+  mlp_features(eta, s, tc, m, isr_class(type, ch, fl_i), f);
+  for (int k = 0; k < 4; ++k) feats[4 * row + k] = f[k];
+  int shape;
+  double coefd;
+  channel_over(ch, type, M.P.nf, shape, coefd);
+  float zm, delta;
+  float best = 0.0f;
+  const float tk = tkin32(type, s, eta);
+  if (tk > tc && zlim32(type, tc, s, eta, zm, delta)) {
+    const float ltc = __logf(tc), ltk = __logf(tk);
+    for (int a = 0; a <= 16; ++a) {
+      const float zeta = ((float)m + (float)a * (1.0f / 16.0f)) * 0.125f;
+      float z, omz;
+      shape_sample32(shape, zm, delta, fminf(zeta, 0.99999994f), z, omz);
+      const float pover = shape_val32(shape, (float)coefd, z, omz);
+      for (int b = 0; b < 24; ++b) {
+        const float t = __expf(ltc + (ltk - ltc) * ((float)b + 0.5f) * (1.0f / 24.0f));
+        float zm_t, delta_t;
+        if (!zlim32(type, t, s, eta, zm_t, delta_t) || !(omz > delta_t) || !(z > zm_t)) continue;
+        const IsrEval ev = isr_eval32(M, S, type, ch, fl_i, eta, s, t, z, omz, pover);
+        if (ev.ok) best = fmaxf(best, ev.r);
+      }
+    }
+  }
+  targets[row] = __logf(fmaxf(best, 1e-6f));
+}
+
+}  // namespace
+
+cudaError_t launch_isr_targets(const DevParams& P, int q_independent, const float4* states, uint64_t n_states,
+                               float* feats, float* targets, cudaStream_t stream) {
+  if (n_states == 0) return cudaSuccess;
+  MixedCtx M;
+  M.P = P;
+  M.q_independent = q_independent;
+  M.lnTc = (float)gm_log(P.t_cut);
+  M.asOver2pi = (float)(P.as_over / (2.0 * kPi));
+  M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
+  const uint64_t rows = n_states * 16;
+  k_isr_targets<<<(unsigned)((rows + 127) / 128), 128, 0, stream>>>(M, states, n_states, feats, targets);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, const LearnedCfg& Lc,
+                                uint64_t first, uint64_t n, int blocks, int block_size, int sm_count, int period,
                                 int emit_batch, int q_independent, unsigned long long* next,
                                 cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   MixedCtx M;
-  M.P = P; M.E = E; M.W = W; M.first = first; M.n = n; M.next = next;
+  M.P = P; M.E = E; M.W = W; M.Lc = Lc; M.first = first; M.n = n; M.next = next;
   M.q_independent = q_independent;
   M.period = period < 1 ? 1 : period;
   M.emit_batch = emit_batch < 1 ? 1 : (emit_batch > 32 ? 32 : emit_batch);
@@ -752,11 +1005,12 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
   cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
   if (err != cudaSuccess) return err;
+  const size_t dyn = Lc.learned ? kMlpSmemBytes + (size_t)(block_size / 32) * 64 * 5 * sizeof(float) : 0;
   // the register tier follows the resident threads the launch asks for
   const int threads_per_sm = blocks * block_size / max(1, sm_count);
-  if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, 0, stream>>>(M);
-  else if (threads_per_sm <= 768) k_shower_mixed<3><<<blocks, block_size, 0, stream>>>(M);
-  else k_shower_mixed<4><<<blocks, block_size, 0, stream>>>(M);
+  if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, dyn, stream>>>(M);
+  else if (threads_per_sm <= 768) k_shower_mixed<3><<<blocks, block_size, dyn, stream>>>(M);
+  else k_shower_mixed<4><<<blocks, block_size, dyn, stream>>>(M);
   return cudaGetLastError();
 }
 
@@ -769,7 +1023,7 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
 // device footprint), or code whose memory is fixed before it starts. For them
 // the mixed-precision shower runs with every piece of its scratch memory in
 // file-scope device arrays: the per-lane working set of 64 blocks x 128 threads
-// for at most 32 partons per event (17.8 MB), the work counter, the
+// for at most 32 partons per event (20 MB), the work counter, the
 // statistics, and copies of the PDF grid and its bound tables. Every GPU that
 // loads the library holds these arrays until the process exits.
 // ---------------------------------------------------------------------------
@@ -780,7 +1034,8 @@ constexpr int kStaticBlocks = 64, kStaticThreads = 128;
 constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
 constexpr size_t kStaticWorkBytes =
-    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+    (size_t)kStaticLanes * 64 * sizeof(float);
 
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
 static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];
@@ -863,7 +1118,8 @@ extern "C" int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, 
   E.weight = ev->weight; E.t = ev->t; E.eta = ev->eta; E.draw = ev->draw;
   WorkSet W;
   workset_carve(a.work, kStaticLanes, ev->nmax, W);
-  if (launch_shower_mixed(P, E, W, first_event, n, kStaticBlocks, kStaticThreads, n_sm, 1, 8,
+  LearnedCfg plain{};
+  if (launch_shower_mixed(P, E, W, plain, first_event, n, kStaticBlocks, kStaticThreads, n_sm, 1, 8,
                           q_independent, a.counters + C_NCOUNTERS, st) != cudaSuccess)
     return GAPS_ERR_CUDA;
   if (stats) {

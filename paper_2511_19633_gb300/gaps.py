@@ -64,9 +64,13 @@ class GapsStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in STAT_FIELDS]
 
 
+GAPS_MLP_PARAMS = 4545
+GAPS_ISR_BINS = 8
+
 EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
-           "gaps_destroy", "gaps_shower_static")
+           "gaps_destroy", "gaps_shower_static", "gaps_collect_isr_states", "gaps_isr_targets",
+           "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train")
 
 
 class GapsError(RuntimeError):
@@ -95,6 +99,13 @@ def _load():
     lib.gaps_destroy.argtypes = [vp]
     lib.gaps_destroy.restype = None
     lib.gaps_shower_static.argtypes = [P(GapsConfig), u64, u64, P(GapsEvents), P(GapsStats), vp]
+    f = ctypes.c_float
+    lib.gaps_collect_isr_states.argtypes = [vp, u64, u64, P(GapsEvents), vp, u64, vp, vp]
+    lib.gaps_isr_targets.argtypes = [vp, vp, u64, vp, vp, vp]
+    lib.gaps_set_learned_proposal.argtypes = [vp, vp, f]
+    lib.gaps_mlp_loss_grad.argtypes = [vp, vp, vp, u64, f, vp, vp, vp]
+    lib.gaps_mlp_forward.argtypes = [vp, vp, u64, i, vp, vp]
+    lib.gaps_mlp_train.argtypes = [vp, vp, vp, vp, vp, u64, u64, f, f, u64, vp, i, vp]
     return lib
 
 
@@ -147,6 +158,52 @@ def gaps_shower_static(cfg: GapsConfig, first_event: int, n: int, ev: GapsEvents
     _check(_lib.gaps_shower_static(ctypes.byref(cfg), first_event, n, ctypes.byref(ev),
                                    ctypes.byref(st), _stream_ptr(stream)), "gaps_shower_static")
     return {name: int(getattr(st, name)) for name in STAT_FIELDS}
+
+
+def gaps_collect_isr_states(ctx, first_event: int, n: int, ev: GapsEvents, states: torch.Tensor,
+                            count: torch.Tensor, stream=None):
+    """states: float32 [capacity, 4] device; count: int64 [1] device (incremented)."""
+    _check(_lib.gaps_collect_isr_states(ctx, first_event, n, ctypes.byref(ev), states.data_ptr(),
+                                        states.shape[0], count.data_ptr(), _stream_ptr(stream)),
+           "gaps_collect_isr_states")
+
+
+def gaps_isr_targets(ctx, states: torch.Tensor, n_states: int, features: torch.Tensor,
+                     targets: torch.Tensor, stream=None):
+    _check(_lib.gaps_isr_targets(ctx, states.data_ptr(), n_states, features.data_ptr(),
+                                 targets.data_ptr(), _stream_ptr(stream)), "gaps_isr_targets")
+
+
+def gaps_set_learned_proposal(ctx, params, log_margin: float = 0.0):
+    """params: host float32 array of GAPS_MLP_PARAMS (copied) or None."""
+    if params is None:
+        _check(_lib.gaps_set_learned_proposal(ctx, None, log_margin), "gaps_set_learned_proposal")
+        return
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.gaps_set_learned_proposal(ctx, p.ctypes.data, float(log_margin)),
+           "gaps_set_learned_proposal")
+
+
+def gaps_mlp_loss_grad(params: torch.Tensor, features: torch.Tensor, targets: torch.Tensor, tau: float,
+                       grad: torch.Tensor, loss: torch.Tensor, stream=None):
+    _check(_lib.gaps_mlp_loss_grad(params.data_ptr(), features.data_ptr(), targets.data_ptr(),
+                                   targets.shape[0], float(tau), grad.data_ptr(), loss.data_ptr(),
+                                   _stream_ptr(stream)), "gaps_mlp_loss_grad")
+
+
+def gaps_mlp_forward(params: torch.Tensor, features: torch.Tensor, out: torch.Tensor, bf16: bool,
+                     stream=None):
+    _check(_lib.gaps_mlp_forward(params.data_ptr(), features.data_ptr(), features.shape[0], int(bf16),
+                                 out.data_ptr(), _stream_ptr(stream)), "gaps_mlp_forward")
+
+
+def gaps_mlp_train(params, adam_m, adam_v, features, targets, steps: int, lr: float, tau: float,
+                   seed: int, loss_history=None, history_every: int = 0, stream=None):
+    _check(_lib.gaps_mlp_train(params.data_ptr(), adam_m.data_ptr(), adam_v.data_ptr(), features.data_ptr(),
+                               targets.data_ptr(), targets.shape[0], steps, float(lr), float(tau), seed,
+                               None if loss_history is None else loss_history.data_ptr(), history_every,
+                               _stream_ptr(stream)), "gaps_mlp_train")
 
 
 def gaps_observables(ctx, n: int, ev: GapsEvents, obs: torch.Tensor | None,

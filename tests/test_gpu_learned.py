@@ -1,0 +1,156 @@
+"""Learned initial-state proposal: the network kernels against the FP64
+reference, the training pipeline, and the learned shower against the plain
+algorithm (zero violations, fewer cycles, chi^2/ndf < 1.2 at 1e7 events)."""
+import numpy as np
+import pytest
+
+from tests.gpu_common import PROCESS, gaps
+from tests.hist_common import chi2_per_hist, chi2_summary, load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    return gaps()
+
+
+def _rand_params(seed):
+    from paper_2511_19633_gb300 import learned
+    return learned.init_params(seed)
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.97])
+def test_gradients_match_oracle(G, oracle_mod, tau):
+    import torch
+    rng = np.random.default_rng(7)
+    P = _rand_params(5)
+    X = rng.uniform(-1, 1, (777, 4)).astype(np.float32)
+    T = rng.normal(-2, 1, 777).astype(np.float32)
+    grad = torch.zeros(G.GAPS_MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    G.gaps_mlp_loss_grad(torch.from_numpy(P).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),
+                         tau, grad, loss)
+    torch.cuda.synchronize()
+    ref_loss, ref_grad = oracle_mod.mlp_loss_grad(P.astype(np.float64), X.astype(np.float64),
+                                                  T.astype(np.float64), tau)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-4)
+    assert np.linalg.norm(g - ref_grad) <= 1e-4 * np.linalg.norm(ref_grad)
+    # every parameter block is exercised
+    for lo, hi in ((0, 256), (256, 320), (320, 4416), (4416, 4480), (4480, 4545)):
+        assert np.linalg.norm(ref_grad[lo:hi]) > 0
+
+
+def test_bf16_tensor_core_forward_close_to_fp32(G, oracle_mod):
+    import torch
+    rng = np.random.default_rng(8)
+    P = _rand_params(6)
+    X = rng.uniform(-1, 1, (1000, 4)).astype(np.float32)
+    Pt, Xt = torch.from_numpy(P).cuda(), torch.from_numpy(X).cuda()
+    a = torch.zeros(1000, device="cuda")
+    b = torch.zeros(1000, device="cuda")
+    G.gaps_mlp_forward(Pt, Xt, a, False)
+    G.gaps_mlp_forward(Pt, Xt, b, True)
+    torch.cuda.synchronize()
+    ref = oracle_mod.mlp_forward(P.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(a.cpu().numpy(), ref, rtol=1e-5, atol=1e-5)
+    # BF16 weights and activations: relative error of order 2^-8 per operand
+    assert np.abs(b.cpu().numpy() - ref).max() <= 0.03 * (1 + np.abs(ref).max())
+
+
+def test_training_fits_a_known_function(G, oracle_mod):
+    import torch
+    rng = np.random.default_rng(9)
+    teacher = _rand_params(11)
+    X = rng.uniform(-1, 1, (20000, 4)).astype(np.float32)
+    T = oracle_mod.mlp_forward(teacher.astype(np.float64), X.astype(np.float64)).astype(np.float32)
+    from paper_2511_19633_gb300 import learned
+    P, hist = learned.train(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), steps=6000, lr=2e-3,
+                            tau=0.5, seed=1, history_every=100)
+    out = oracle_mod.mlp_forward(P.cpu().numpy().astype(np.float64), X.astype(np.float64))
+    assert np.sqrt(np.mean((out - T) ** 2)) < 0.1 * np.std(T)
+    assert hist[-1] < 0.1 * hist[0]
+
+
+@pytest.fixture(scope="module")
+def trained(G, pdf):
+    """Network trained on states of NLO events with seed 1 from an event range
+    disjoint from every test range."""
+    from paper_2511_19633_gb300 import learned
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=G.GAPS_MIXED, schedule=1,
+                        blocks_per_sm=4, emit_batch=8)
+    ctx = G.gaps_init(cfg)
+    try:
+        res = learned.train_and_install(ctx, first_event=3 << 40, n_events=1 << 20, capacity=1 << 20)
+    finally:
+        G.gaps_destroy(ctx)
+    return res
+
+
+def test_teacher_targets_respect_the_plain_bound(G, pdf):
+    """The plain bound is certified, so every teacher target ln r is <= 0."""
+    from paper_2511_19633_gb300 import learned
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=G.GAPS_MIXED, schedule=1)
+    ctx = G.gaps_init(cfg)
+    try:
+        states = learned.collect_states(ctx, 5 << 40, 20000, 1 << 18)
+        feats, targ = learned.make_dataset(ctx, states)
+    finally:
+        G.gaps_destroy(ctx)
+    t = targ.cpu().numpy()
+    s = states.cpu().numpy()
+    assert s.shape[0] > 1000
+    assert np.all(np.isfinite(t)) and t.max() <= np.log(1.0001)
+    assert set(np.unique(s[:, 2]).astype(int)) <= {2, 3}
+    assert np.all((s[:, 0] > 0) & (s[:, 0] < 1) & (s[:, 1] > 0))
+
+
+def _shower_hists(G, pdf, params, margin, n, first=0, chunk=1 << 21):
+    import torch
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, seed=1, precision=G.GAPS_MIXED, schedule=1,
+                        blocks_per_sm=4, emit_batch=8)
+    ctx = G.gaps_init(cfg)
+    try:
+        if params is not None:
+            G.gaps_set_learned_proposal(ctx, params, margin)
+        cap = min(chunk, n)
+        buf = G.EventBuffers.allocate(cap, 128)
+        ev = buf.view()
+        hw = torch.zeros((G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
+        hw2 = torch.zeros_like(hw)
+        hists = G.GapsHists(hw.data_ptr(), hw2.data_ptr())
+        for f0 in range(0, n, cap):
+            m = min(cap, n - f0)
+            G.gaps_generate_hard(ctx, first + f0, m, ev)
+            G.gaps_shower(ctx, first + f0, m, ev)
+            G.gaps_observables(ctx, m, ev, None, hists)
+        torch.cuda.synchronize()
+        st = G.gaps_get_stats(ctx)
+    finally:
+        G.gaps_destroy(ctx)
+    return hw.cpu().numpy(), hw2.cpu().numpy(), st
+
+
+def test_learned_proposal_is_exact_and_cheaper(G, pdf, trained):
+    """Same events, learned vs plain bounds: no violation, fewer cycles and
+    trials; distributions agree (chi^2/ndf < 1.2)."""
+    n = 1_000_000
+    wl, wl2, sl = _shower_hists(G, pdf, trained["params"], trained["log_margin"], n)
+    wp, wp2, sp = _shower_hists(G, pdf, None, 0.0, n)
+    assert sl["violations"] == 0 and sl["events"] == n
+    assert sl["steps"] < sp["steps"] and sl["trials"] < sp["trials"]
+    red, _, _ = chi2_summary(chi2_per_hist(wl, wl2, n, wp, wp2, n))
+    assert red < 1.2, red
+
+
+def test_learned_histograms_match_oracle_at_1e7(G, pdf, trained):
+    gold = load_golden("pp_nlo")
+    n = gold["events"]
+    w, w2, st = _shower_hists(G, pdf, trained["params"], trained["log_margin"], n)
+    assert st["violations"] == 0 and st["events"] == n
+    red, _, _ = chi2_summary(chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"]))
+    assert red < 1.2, red
