@@ -28,16 +28,23 @@ if ROOT not in sys.path:
 
 METRIC = "showered events/sec on 1 GB300 (learned+compacted vs plain GPU) at oracle-matched chi2/ndf<1.2"
 
+MIX_ROWS = [(2, 13600.0, 1.0, 0.5), (0, 91.2, 0.5, 0.25), (0, 500.0, 4.0, 0.25)]
+
 WORKLOADS = {
-    # name: (process, sqrt_s, events per step, chunk, precision, description)
-    "pp_nlo_1e7": (2, 13600.0, 10_000_000, 1 << 22, 1,
+    # name: (process, sqrt_s, events per step, chunk, precision, mixed-batch rows, description)
+    "pp_nlo_1e7": (2, 13600.0, 10_000_000, 1 << 22, 1, None,
                    "NLO-matched pp -> Z at 13.6 TeV, synthetic 100x50 PDF, 1e7 events per step in "
-                   "chunks of 2^22, FP32 trials/PDF + FP64 kinematics, persistent compacted shower"),
-    "pp_lo_1e6_fp64": (1, 13600.0, 1_000_000, 1_000_000, 0,
+                   "chunks of 2^22, FP32 trials/PDF + FP64 kinematics, learned initial-state proposal, "
+                   "persistent compacted shower, one CUDA graph per step"),
+    "pp_lo_1e6_fp64": (1, 13600.0, 1_000_000, 1_000_000, 0, None,
                        "pp -> Z at 13.6 TeV, LO + initial/final-state shower, synthetic 100x50 PDF, "
                        "1e6 events, FP64 (per-event oracle parity)"),
-    "ee91_1e4_fp64": (0, 91.2, 10_000, 10_000, 0,
+    "ee91_1e4_fp64": (0, 91.2, 10_000, 10_000, 0, None,
                       "e+e- -> q qbar at 91.2 GeV, final-state shower, 1e4 events, FP64"),
+    "mix_1e8": (2, 13600.0, 100_000_000, 1 << 22, 1, MIX_ROWS,
+                "mixed batch in one persistent launch per chunk: 50% NLO pp -> Z at 13.6 TeV "
+                "(t_c 1 GeV^2), 25% e+e- at 91.2 GeV (t_c 0.5), 25% e+e- at 500 GeV (t_c 4), "
+                "1e8 events in chunks of 2^22, learned proposal, one CUDA graph per step"),
 }
 DEFAULT_WORKLOAD = "pp_nlo_1e7"
 
@@ -143,52 +150,64 @@ def measured_peaks() -> dict:
     return {}
 
 
-def _oracle_run(O, st, first, n, pdf, cores, chunk=50_000):
+def _oracle_run(O, rows, fractions, first, n, pdf, cores, chunk=50_000):
     """Runs the oracle over n events in chunks (bounded host memory)."""
     for f0 in range(0, n, chunk):
-        O.run(st, first + f0, min(chunk, n - f0), pdf, threads=cores)
+        m = min(chunk, n - f0)
+        if len(rows) == 1:
+            O.run(rows[0], first + f0, m, pdf if rows[0].process else None, threads=cores)
+        else:
+            O.run_mix(rows, fractions, first + f0, m, pdf, threads=cores)
 
 
-def cpu_baseline(process: int, sqrt_s: float, target_s: float = 12.0) -> dict:
+def _oracle_rows(O, process, sqrt_s, mix):
+    if mix:
+        return ([O.Settings(process=p, sqrt_s=rs, t_cut=tc, nmax=128) for p, rs, tc, _ in mix],
+                [r[3] for r in mix])
+    return [O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)], [1.0]
+
+
+def cpu_baseline(process: int, sqrt_s: float, mix=None, target_s: float = 12.0) -> dict:
     """The FP64 oracle as it stands, on all host cores, over a bounded sample."""
     from oracle import oracle as O
     from paper_2511_19633_gb300 import inputs
     pdf = inputs.synthetic_pdf_grid()
     cores = os.cpu_count() or 1
-    st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
+    rows, fr = _oracle_rows(O, process, sqrt_s, mix)
     probe = 500 * cores
     t0 = time.perf_counter()
-    _oracle_run(O, st, 10_000_000_000, probe, pdf if process else None, cores)
+    _oracle_run(O, rows, fr, 10_000_000_000, probe, pdf, cores)
     dt = time.perf_counter() - t0
     n = max(probe, int(probe * target_s / max(dt, 1e-3)))
     t0 = time.perf_counter()
-    _oracle_run(O, st, 20_000_000_000, n, pdf if process else None, cores)
+    _oracle_run(O, rows, fr, 20_000_000_000, n, pdf, cores)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": "%d events of the same workload (event ids from 2e10), %.1f s" % (n, dt)}
+            "sample": "%d events of the same workload (event ids from 2e10), %.1f s, FP64 plain bound"
+                      % (n, dt)}
 
 
 def run_reference(args, ws, rank):
     name = args.workload
-    process, sqrt_s, per_step, chunk, precision, desc = WORKLOADS[name]
+    process, sqrt_s, per_step, chunk, precision, mix, desc = WORKLOADS[name]
     if rank != 0:
         return
     from oracle import oracle as O
     from paper_2511_19633_gb300 import inputs
     pdf = inputs.synthetic_pdf_grid()
     cores = os.cpu_count() or 1
-    st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128)
+    rows, fr = _oracle_rows(O, process, sqrt_s, mix)
     # each step: a sample of the workload sized to about 20 s of CPU work over all steps
     probe = 200 * cores
     t0 = time.perf_counter()
-    _oracle_run(O, st, 30_000_000_000, probe, pdf if process else None, cores)
+    _oracle_run(O, rows, fr, 30_000_000_000, probe, pdf, cores)
     rate = probe / (time.perf_counter() - t0)
     n = max(probe, int(rate * 20.0 / max(1, args.steps)))
     for w in range(args.warmup):
-        _oracle_run(O, st, 31_000_000_000 + w * n, min(n, probe), pdf if process else None, cores)
+        _oracle_run(O, rows, fr, 31_000_000_000 + w * n, min(n, probe), pdf, cores)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        _oracle_run(O, st, 32_000_000_000 + k * n, n, pdf if process else None, cores)
+        _oracle_run(O, rows, fr, 32_000_000_000 + k * n, n, pdf, cores)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
@@ -202,23 +221,38 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def _pass(G, ctx, ev, obs, hists, first, total, chunk, stream, shower_events=None, host=None):
-    """One pass of the hot path over `total` events in chunks: hard process,
-    shower, observables and histograms. Returns the number of kernel launches."""
-    launches = 0
-    for k, f0 in enumerate(range(0, total, chunk)):
+def _plain_pass(G, ctx, ev, first, total, chunk, stream):
+    """hard + shower + observables through the per-call entry points."""
+    for f0 in range(0, total, chunk):
         m = min(chunk, total - f0)
         G.gaps_generate_hard(ctx, first + f0, m, ev, stream)
-        if shower_events is not None:
-            shower_events[k][0].record(stream)
         G.gaps_shower(ctx, first + f0, m, ev, stream)
-        if shower_events is not None:
-            shower_events[k][1].record(stream)
-        G.gaps_observables(ctx, m, ev, obs, hists, stream)
-        launches += 3
-        if host is not None:
-            host[0][:, f0:f0 + m].copy_(obs[:, :m], non_blocking=True)
-    return launches
+        G.gaps_observables(ctx, first + f0, m, ev, None, None, stream)
+
+
+def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None):
+    """Events per second of one configuration over n events (after a warm-up
+    pass), with its shower statistics."""
+    import torch
+    ctx = G.gaps_init(cfg)
+    try:
+        if learned is not None:
+            G.gaps_set_learned_proposal(ctx, *learned)
+        _plain_pass(G, ctx, ev, first - (1 << 40), min(n, 1 << 16), chunk, stream)
+        torch.cuda.synchronize()
+        G.gaps_reset_stats(ctx, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _plain_pass(G, ctx, ev, first, n, chunk, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = G.gaps_get_stats(ctx, stream)
+    finally:
+        G.gaps_destroy(ctx)
+    return {"value": n / (a.elapsed_time(b) / 1e3), "unit": "events/s", "events": n,
+            "steps_per_event": st["steps"] / max(1, st["events"]),
+            "trials_per_event": st["trials"] / max(1, st["events"]),
+            "violations": st["violations"]}
 
 
 def run_ours(args, ws, rank, local):
@@ -234,30 +268,63 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     name = args.workload
-    process, sqrt_s, total, chunk, precision, desc = WORKLOADS[name]
+    process, sqrt_s, total, chunk, precision, mix, desc = WORKLOADS[name]
     if args.events:
         total = args.events
         chunk = min(chunk, total)
     nmax = 128
     pdf = inputs.synthetic_pdf_grid()
+    uses_pdf = bool(process or (mix and any(r[0] for r in mix)))
+    stream = torch.cuda.current_stream()
+    mixed = precision == G.GAPS_MIXED
+
+    # learned initial-state proposal: trained on the GPU before the timed
+    # region, on shower states of events outside every timed range
+    learned = None
+    learned_info = None
+    if mixed and not args.no_learned:
+        from paper_2511_19633_gb300 import learned as LP
+        tcfg = G.make_config(G.GAPS_PP_Z_NLO, 13600.0, pdf_grid=pdf, nmax=nmax, seed=1,
+                             precision=G.GAPS_MIXED, schedule=G.GAPS_SCHED_PERSISTENT,
+                             blocks_per_sm=4, emit_batch=8)
+        tctx = G.gaps_init(tcfg)
+        t0 = time.perf_counter()
+        try:
+            res = LP.train_and_install(tctx, first_event=(3 << 40) + (rank << 38))
+        finally:
+            G.gaps_destroy(tctx)
+        learned = (res["params"], res["log_margins"])
+        learned_info = {"train_seconds": time.perf_counter() - t0, "states": res["states"],
+                        "training_rows": res["rows"], "holdout_states": res["holdout_states"],
+                        "mean_bin_height": res["mean_bin_height"], "loss_last": res["loss_last"],
+                        "cells_calibrated": res["cells_seen"]}
+
     shape = {"block_size": args.block, "blocks_per_sm": args.bps, "refill_period": args.period,
              "emit_batch": args.emit_batch}
     tuning = None
-    if precision == G.GAPS_MIXED and not args.no_autotune:
+    if mixed and not args.no_autotune:
         from paper_2511_19633_gb300 import autotune
-        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 19)
+        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 19, mix=mix, learned=learned)
         shape = tuning["best"]
-    schedule = G.GAPS_SCHED_PERSISTENT if (precision == G.GAPS_MIXED or args.schedule) else G.GAPS_SCHED_PER_EVENT
-    cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=nmax, seed=1,
-                        precision=precision, schedule=schedule, **shape)
-    ctx = G.gaps_init(cfg)
+    schedule = G.GAPS_SCHED_PERSISTENT if (mixed or args.schedule) else G.GAPS_SCHED_PER_EVENT
+
+    def config(pdf_ptr=None):
+        c = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf and pdf_ptr is None else None, nmax=nmax,
+                          seed=1, precision=precision, schedule=schedule, mix=mix, **shape)
+        if pdf_ptr is not None:
+            c.pdf_grid = pdf_ptr
+        return c
+
+    ctx = G.gaps_init(config())
+    if learned is not None:
+        G.gaps_set_learned_proposal(ctx, *learned)
+    n_rows = len(mix) if mix else 1
     buf = G.EventBuffers.allocate(chunk, nmax)
     ev = buf.view()
     obs = torch.zeros((G.GAPS_NOBS, chunk), dtype=torch.float64, device="cuda")
-    hw = torch.zeros((G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
+    hw = torch.zeros((n_rows, G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
     hw2 = torch.zeros_like(hw)
     hists = G.GapsHists(hw.data_ptr(), hw2.data_ptr())
-    stream = torch.cuda.current_stream()
     steps_total = args.warmup + args.steps
     n_chunks = (total + chunk - 1) // chunk
 
@@ -265,90 +332,87 @@ def run_ours(args, ws, rank, local):
         return rank_first_event(rank, k, total, steps_total)
 
     for k in range(args.warmup):
-        _pass(G, ctx, ev, obs, hists, first_of(k), total, chunk, stream)
+        G.gaps_process(ctx, first_of(k), total, ev, obs, None, hists, stream)
     torch.cuda.synchronize()
     G.gaps_reset_stats(ctx, stream)
-    shower_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(n_chunks)] for _ in range(args.steps)]
+    shower_ms = []
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    launches = 0
     with ClockSampler(local) as clk:
         start.record(stream)
         for k in range(args.steps):
-            launches += _pass(G, ctx, ev, obs, hists, first_of(args.warmup + k), total, chunk, stream,
-                              shower_ev[k])
+            G.gaps_process(ctx, first_of(args.warmup + k), total, ev, obs, None, hists, stream)
+            if k + 1 < args.steps:
+                shower_ms += G.gaps_process_shower_ms(ctx)
         stop.record(stream)
         torch.cuda.synchronize()
+    shower_ms += G.gaps_process_shower_ms(ctx)
     if dist:
         dist.barrier()
     ms = start.elapsed_time(stop)
-    shower_ms = [a.elapsed_time(b) for step in shower_ev for a, b in step]
     stats = G.gaps_get_stats(ctx, stream)
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = total * args.steps * ws / (ms / 1e3)
+    launches = 3 * n_chunks * args.steps  # hard, shower and observables kernels per chunk
 
     # end to end through the C ABI with host buffers: a fresh context per step
-    # (PDF grid from pinned host memory), the full pass, every event's
-    # observables and the histograms back into pinned host memory
-    pdf_host = torch.from_numpy(pdf).pin_memory() if process else None
+    # (PDF grid and network from host memory), the full path as one graph,
+    # every event's observables and the histograms back into pinned host memory
+    pdf_host = torch.from_numpy(pdf).pin_memory() if uses_pdf else None
     obs_host = torch.empty((G.GAPS_NOBS, total), dtype=torch.float64).pin_memory()
-    h_host = torch.empty((2, G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64).pin_memory()
+    h_host = torch.empty((2, n_rows, G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64).pin_memory()
     e2e_steps = 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        c2 = G.make_config(process, sqrt_s, pdf_grid=None, nmax=nmax, seed=1, precision=precision,
-                           schedule=schedule, **shape)
-        if pdf_host is not None:
-            c2.pdf_grid = pdf_host.data_ptr()
-        ctx2 = G.gaps_init(c2)
+        ctx2 = G.gaps_init(config(pdf_host.data_ptr() if pdf_host is not None else None))
+        if learned is not None:
+            G.gaps_set_learned_proposal(ctx2, *learned)
         hw.zero_()
         hw2.zero_()
-        _pass(G, ctx2, ev, obs, hists, first_of(k) + (1 << 50), total, chunk, stream, host=(obs_host,))
+        G.gaps_process(ctx2, first_of(k) + (1 << 50), total, ev, obs, obs_host, hists, stream)
         h_host[0].copy_(hw, non_blocking=True)
         h_host[1].copy_(hw2, non_blocking=True)
         torch.cuda.synchronize()
         G.gaps_destroy(ctx2)
     e2e_s = time.perf_counter() - t0
     e2e_value = total * e2e_steps * ws / e2e_s
-    h2d = pdf.nbytes if process else 0
+    h2d = (pdf.nbytes if uses_pdf else 0) + (learned[0].nbytes + learned[1].nbytes if learned else 0)
     d2h = obs_host.numel() * 8 + h_host.numel() * 8
 
-    # the plain GPU veto algorithm for comparison: FP64, one thread per event,
-    # no compaction, plain bound, on a sample of the same workload
-    plain = None
+    # comparisons on samples of the same workload: the plain GPU veto
+    # algorithm (FP64, one thread per event, no compaction, plain bound: the
+    # paper's layout) and the compacted mixed-precision shower without the
+    # learned proposal
+    plain = mixed_plain = None
     if not args.no_plain:
         n_plain = min(total, 1 << 19)
-        cfgp = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=nmax, seed=1,
-                             precision=G.GAPS_FP64, schedule=G.GAPS_SCHED_PER_EVENT)
-        ctxp = G.gaps_init(cfgp)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        _pass(G, ctxp, ev, obs, None, 1 << 51, min(n_plain, 1 << 16), chunk, stream)
-        torch.cuda.synchronize()
-        a.record(stream)
-        _pass(G, ctxp, ev, obs, None, (1 << 51) + (1 << 20), n_plain, chunk, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        G.gaps_destroy(ctxp)
-        plain = {"value": n_plain / (a.elapsed_time(b) / 1e3), "unit": "events/s", "events": n_plain,
-                 "mode": "FP64, one thread per event, no compaction, plain bound (the paper's layout)"}
+        cfgp = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf else None, nmax=nmax, seed=1,
+                             precision=G.GAPS_FP64, schedule=G.GAPS_SCHED_PER_EVENT, mix=mix)
+        plain = _time_variant(G, cfgp, ev, 1 << 51, n_plain, chunk, stream)
+        plain["mode"] = "FP64, one thread per event, no compaction, plain bound (the paper's layout)"
+        if mixed and learned is not None:
+            n_mp = min(total, chunk)
+            mixed_plain = _time_variant(G, config(), ev, (1 << 51) + (1 << 24), n_mp, chunk, stream)
+            mixed_plain["mode"] = "same shape and precision, plain bound (no learned proposal)"
+            with_l = _time_variant(G, config(), ev, (1 << 51) + (1 << 24), n_mp, chunk, stream, learned)
+            mixed_plain["learned_same_events"] = with_l
 
-    mean_shower_s = sum(shower_ms) / len(shower_ms) / 1e3
     per_launch_events = total / n_chunks
-    if precision == G.GAPS_MIXED:
+    mean_shower_ms = sum(shower_ms) / max(1, len(shower_ms))
+    if mixed:
         ops = algorithmic_ops_mixed(stats)
         achieved = ops / (sum(shower_ms) / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "k_shower_mixed", "achieved": achieved, "peak": LANE_PEAK_TOPS,
                 "unit": "Tops/s (32-bit lane operations)", "frac": achieved / LANE_PEAK_TOPS,
                 "traffic": None,
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
-                "shower_ms_per_launch": mean_shower_s * 1e3, "events_per_launch": per_launch_events,
+                "shower_ms_per_launch": mean_shower_ms, "events_per_launch": per_launch_events,
                 "ops_per_event": ops / max(1, stats["events"])}
     else:
         flops = algorithmic_flops(stats)
@@ -356,18 +420,19 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "kernel": "k_shower_fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "nominal GB300 FP64 (dense) from the profiling recipe",
-                "shower_ms_per_launch": mean_shower_s * 1e3, "events_per_launch": per_launch_events,
+                "shower_ms_per_launch": mean_shower_ms, "events_per_launch": per_launch_events,
                 "flop_per_event": flops / max(1, stats["events"])}
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == 0 else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == 0 else "f32+f64+bf16",
         "data": "synthetic",
         "config": {"workload": name, "description": desc, "events_per_step": total, "chunk": chunk,
                    "parallelism": "independent event ranges per GPU" if ws > 1 else "single GPU",
                    "schedule": "persistent, live-event refill" if schedule else "one thread per event",
-                   "launch_shape": shape,
+                   "launch_shape": shape, "learned_proposal": learned is not None,
+                   "cuda_graph": "one graph per step (all chunks), parameters updated in place",
                    "l2": "event records of %.1f GB per chunk rewritten every chunk (> 129 MB L2)"
                          % (chunk * nmax * 44 / 1e9)},
         "roofline": roof,
@@ -376,9 +441,12 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "plain_gpu": plain,
+        "mixed_plain_bound": mixed_plain,
+        "learned": learned_info,
         "shower_stats": {k: stats[k] for k in ("events", "steps", "trials", "isr_trials", "vetoes",
                                                 "accepts", "violations", "err_capacity",
                                                 "err_iter_cap", "err_numeric")},
+        "veto_rate": stats["vetoes"] / max(1, stats["steps"]),
         "lane_efficiency": stats["lane_steps"] / max(1, stats["warp_steps"]),
         "hbm_gbs_measured": peaks.get("hbm_gbs"),
     }
@@ -387,7 +455,7 @@ def run_ours(args, ws, rank, local):
                             "candidates": len(tuning["table"])}
     G.gaps_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(process, sqrt_s)
+        line["cpu_baseline"] = cpu_baseline(process, sqrt_s, mix)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -410,6 +478,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

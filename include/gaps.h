@@ -85,6 +85,21 @@ extern "C" {
 
 typedef struct gaps_ctx gaps_ctx;  /* opaque, owned by the library */
 
+/* Mixed batch (config field n_mix > 0): the batch holds several processes
+ * and one launch showers them all (Section 3 on heterogeneous batches). The
+ * paper does not say how events are assigned; here event `id` belongs to the
+ * first row whose cumulative fraction exceeds the uniform of Philox block
+ * (seed, id, draw 2^62), words 0 and 1 (the last row takes the remainder),
+ * and is then exactly event `id` of a one-process context with that row's
+ * process, sqrt_s and t_cut and the same other settings. */
+#define GAPS_MAX_MIX 4
+typedef struct {
+    int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO or GAPS_PP_Z_NLO */
+    double sqrt_s;        /* GeV */
+    double t_cut;         /* GeV^2 */
+    double fraction;      /* share of the events, > 0; the shares sum to 1 */
+} gaps_mix_row;
+
 /* Configuration, copied by gaps_init. */
 typedef struct {
     int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO or GAPS_PP_Z_NLO */
@@ -105,6 +120,10 @@ typedef struct {
     int emit_batch;       /* GAPS_MIXED: accepted emissions of a warp are built
                              together once this many lanes wait (or after 4x
                              this many cycles), 1..32, 0 = 1 */
+    int n_mix;            /* 0: one process (the fields above); 1..GAPS_MAX_MIX:
+                             mixed batch of these rows, which replace process,
+                             sqrt_s and t_cut above */
+    gaps_mix_row mix[GAPS_MAX_MIX];
 } gaps_config;
 
 /* Event records: structure of arrays in device memory, caller-owned, event
@@ -127,8 +146,9 @@ typedef struct {
 } gaps_events;
 
 /* Weighted histograms in device memory, caller-owned and zeroed by the
- * caller: sumw and sumw2 are [GAPS_NHIST][GAPS_HIST_BINS] doubles; the
- * binning of each histogram is returned by gaps_hist_binning. */
+ * caller: sumw and sumw2 are [GAPS_NHIST][GAPS_HIST_BINS] doubles, or
+ * [n_mix][GAPS_NHIST][GAPS_HIST_BINS] for a mixed batch (one set per row);
+ * the binning of each histogram is returned by gaps_hist_binning. */
 typedef struct {
     double* sumw;
     double* sumw2;
@@ -146,6 +166,8 @@ typedef struct {
     uint64_t err_capacity, err_iter_cap, err_numeric;
     uint64_t lane_steps;  /* active lanes summed over warp steps (divergence) */
     uint64_t warp_steps;  /* warp steps x 32 */
+    uint64_t rebuilds;    /* GAPS_MIXED: warp-cooperative colour-end table rebuilds */
+    uint64_t mlp_tiles;   /* GAPS_MIXED: 16-row network evaluations of the learned proposal */
 } gaps_stats;
 
 /* Creates a context on the current CUDA device: validates `cfg`, copies the
@@ -210,8 +232,12 @@ int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
  * the plain algorithm's whenever the violation count is zero.
  * Parameter layout (FP32): W1 [64][4], b1 [64], W2 [64][64], b2 [64], W3 [64],
  * b3. */
-#define GAPS_MLP_PARAMS 4545
-#define GAPS_ISR_BINS   8
+#define GAPS_MLP_PARAMS  4545
+#define GAPS_ISR_BINS    8
+/* classes of (dipole type, channel, emitter flavour): for IF (0..21) and II
+ * (22..43): q <- q for the ten quark PDF indices 1..10 (d u s c b, then the
+ * antiquarks), g <- q for the same ten, g <- g, q <- g */
+#define GAPS_ISR_CLASSES 44
 
 /* Runs the GAPS_MIXED shower with the plain bounds and logs the initial-state
  * colour ends met at every rebuild of an event's end table: states is a
@@ -225,16 +251,18 @@ int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
 /* Training targets of the learned bound: for each logged state, channel and
  * bin (16 rows per state, row = state * 16 + channel * 8 + bin) the network
  * inputs features[row][4] and targets[row] = ln(max(r, 1e-6)), with r the
- * largest acceptance ratio over 17 zeta points of the bin and 24 scales in
+ * largest acceptance ratio over 33 zeta points of the bin and 64 scales in
  * [t_c, t_kin]. Device arrays. */
 int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states,
                      float* features, float* targets, void* stream);
 
 /* Installs a trained network (host array of GAPS_MLP_PARAMS floats, copied)
- * and the margin added to its output (bin height = min(1, exp(NN + margin)));
- * later GAPS_MIXED showers of the context use it. params == NULL returns to
- * the plain bounds. */
-int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, float log_margin);
+ * and the calibration margins added to its output, a host array
+ * log_margins[GAPS_ISR_CLASSES][GAPS_ISR_BINS] (copied): the height of bin m
+ * of class c is min(1, exp(NN + log_margins[c][m])). Later GAPS_MIXED showers
+ * of the context use them. params == NULL returns to the plain bounds.
+ * Non-finite values give GAPS_ERR_INVALID_ARG. */
+int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* log_margins);
 
 /* Network kernels (device arrays; features [n][4]):
  * gaps_mlp_loss_grad: expectile loss mean w (y - t)^2, w = tau below the
@@ -253,18 +281,39 @@ int gaps_mlp_train(float* params, float* adam_m, float* adam_v, const float* fea
                    const float* targets, uint64_t n, uint64_t steps, float lr, float tau,
                    uint64_t seed, float* loss_history, int history_every, void* stream);
 
-/* Observables (Section 4.1): writes obs[GAPS_NOBS][capacity] (device) and,
- * when hists != NULL, adds every event with status DONE to the histograms.
+/* Observables (Section 4.1) of records first_event .. first_event + n - 1
+ * (the event ids pick the rows of a mixed batch): writes
+ * obs[GAPS_NOBS][capacity] (device) and, when hists != NULL, adds every
+ * event with status DONE to the histograms (of its row).
  * Clustering and event shapes run in FP64 for GAPS_FP64 contexts and in FP32
  * for GAPS_MIXED ones (the Z observables always in FP64).
  *   e+e-: 0 1-T, 1 y23, 2 y34 (Durham), 3 final partons, 4 emissions
  *   pp  : 0 Z pT, 1 Z rapidity, 2 Z phi (0 without emission), 3 anti-kT
  *         R=0.4 jets with pT > 5 GeV and |eta| < 5, 4 leading jet pT,
  *         5 leading jet eta, 6 final partons, 7 emissions */
-int gaps_observables(gaps_ctx* ctx, uint64_t n, const gaps_events* ev,
+int gaps_observables(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
                      double* obs, const gaps_hists* hists, void* stream);
 
-/* Binning of histogram h (0 .. GAPS_NHIST-1) of the context's process:
+/* The whole path over events first_event .. first_event + n - 1 in chunks of
+ * ev->capacity: per chunk the hard process, the shower and the observables
+ * (into obs_dev [GAPS_NOBS][capacity], device, may be NULL), the histograms
+ * when hists != NULL and, when obs_host != NULL (pinned host memory,
+ * [GAPS_NOBS][n], requires obs_dev), a copy of every event's observables.
+ * The launches of all chunks are captured into one CUDA graph on a stream of
+ * the context and launched on `stream` (asynchronous; the legacy default
+ * stream is allowed). A later call with the same n and capacity updates the
+ * graph's parameters in place instead of instantiating it again. Not to be
+ * called while `stream` or the context's other calls are being captured. */
+int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
+                 double* obs_dev, double* obs_host, const gaps_hists* hists, void* stream);
+
+/* Duration in ms of each chunk's shower in the last gaps_process call, timed
+ * by events recorded inside its graph; waits for that call to finish. Writes
+ * at most max_chunks values and returns how many (>= 0), or an error code. */
+int gaps_process_shower_ms(gaps_ctx* ctx, float* ms, int max_chunks);
+
+/* Binning of histogram h (0 .. GAPS_NHIST-1, or 0 .. n_mix * GAPS_NHIST - 1
+ * over the rows of a mixed batch) of the context's process:
  * lo, hi, number of regular bins (<= 64), observable index and whether the
  * observable is binned in log10. Returns GAPS_ERR_INVALID_ARG for bad h. */
 int gaps_hist_binning(const gaps_ctx* ctx, int h, double* lo, double* hi,

@@ -1318,6 +1318,27 @@ Physics make_physics(const Config& c) {
   return ph;
 }
 
+// Mixed batch (one launch over several processes, Sec. 3 on heterogeneous
+// batches). The paper does not say how events are assigned to processes.
+// Reading: event `id` belongs to row r of a table of (process, sqrt_s, t_c,
+// fraction) rows, r = the first row whose cumulative fraction exceeds the
+// uniform of Philox block (seed, id, draw 2^62), words 0 and 1; the last row
+// takes the remainder. The event is then exactly event `id` of a run with
+// that row's settings and the same seed.
+constexpr uint64_t kMixDraw = 0x4000000000000000ull;
+
+int mix_row(uint64_t seed, uint64_t id, const double* fractions, int n_rows) {
+  Stream r{seed, id, kMixDraw};
+  double u, unused;
+  r.next2(u, unused);
+  double cum = 0.0;
+  for (int k = 0; k + 1 < n_rows; ++k) {
+    cum += fractions[k];
+    if (u < cum) return k;
+  }
+  return n_rows - 1;
+}
+
 void run_event(const Physics& ph, uint64_t id, Event& ev) {
   generate_hard(ph, ev, id);
   ev.rng.draw = 0;
@@ -1448,6 +1469,49 @@ int oracle_run_threads(const OracleConfig* c, uint64_t first, uint64_t n, Oracle
     });
   }
   for (auto& th : pool) th.join();
+  return 0;
+}
+
+// Mixed batch: rows[k] are complete configurations (equal seeds), fractions[k]
+// their shares; row_out[i] (optional) receives the row of event first + i.
+// Runs on `threads` std::threads by contiguous event ranges.
+int oracle_run_mix(const OracleConfig* rows, const double* fractions, int n_rows, uint64_t first,
+                   uint64_t n, OracleOut* out, int32_t* row_out, int threads) {
+  if (n_rows < 1 || n_rows > 8) return -1;
+  std::vector<Physics> ph;
+  for (int r = 0; r < n_rows; ++r) {
+    Config k = to_config(rows + r);
+    if (k.process != 0 && !k.pdf) return -1;
+    if (k.seed != rows[0].seed || k.nmax != rows[0].nmax) return -1;
+    ph.push_back(make_physics(k));
+  }
+  if (threads < 1) threads = 1;
+  const int nmax = rows[0].nmax;
+  std::vector<std::thread> pool;
+  uint64_t chunk = (n + threads - 1) / threads;
+  for (int t = 0; t < threads; ++t) {
+    uint64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+    if (lo >= hi) break;
+    pool.emplace_back([&, lo, hi]() {
+      Event ev;
+      ev.parts.reserve(nmax + 1);
+      for (uint64_t i = lo; i < hi; ++i) {
+        const int r = mix_row(rows[0].seed, first + i, fractions, n_rows);
+        if (row_out) row_out[i] = r;
+        run_event(ph[r], first + i, ev);
+        store_event(ev, nmax, i, out);
+      }
+    });
+  }
+  for (auto& th : pool) th.join();
+  return 0;
+}
+
+// Rows of events first .. first + n - 1 of a mixed batch (no showering).
+int oracle_mix_rows(uint64_t seed, const double* fractions, int n_rows, uint64_t first, uint64_t n,
+                    int32_t* row_out) {
+  if (n_rows < 1 || n_rows > 8) return -1;
+  for (uint64_t i = 0; i < n; ++i) row_out[i] = mix_row(seed, first + i, fractions, n_rows);
   return 0;
 }
 

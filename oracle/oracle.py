@@ -61,6 +61,8 @@ def lib():
         _lib.oracle_hard.argtypes = _lib.oracle_run.argtypes
         _lib.oracle_run_threads.argtypes = [P(OracleConfig), ctypes.c_uint64, ctypes.c_uint64,
                                             P(OracleOut), i]
+        _lib.oracle_run_mix.argtypes = [vp, vp, i, ctypes.c_uint64, ctypes.c_uint64, P(OracleOut), vp, i]
+        _lib.oracle_mix_rows.argtypes = [ctypes.c_uint64, vp, i, ctypes.c_uint64, ctypes.c_uint64, vp]
         _lib.oracle_philox.argtypes = [vp, vp, vp]
         _lib.oracle_uniform.argtypes = [u32, u32]
         _lib.oracle_uniform.restype = d
@@ -158,6 +160,43 @@ def run(settings: Settings, first: int, n: int, pdf: np.ndarray | None = None,
         rc = L.oracle_run(ctypes.byref(c), first, n, ctypes.byref(o))
     if rc != 0:
         raise RuntimeError("oracle_run failed (%d)" % rc)
+    return out
+
+
+def run_mix(rows: list, fractions, first: int, n: int, pdf: np.ndarray | None = None,
+            threads: int = 1) -> dict:
+    """Mixed batch: rows are Settings (equal seed and nmax), fractions their
+    shares; event first + i takes the row of its Philox draw 2^62. Returns the
+    arrays of run() plus "row" [n]."""
+    if pdf is not None:
+        pdf = np.ascontiguousarray(pdf, dtype=np.float32)
+    nm = rows[0].nmax
+    out = {
+        "p": np.zeros((n, nm, 4)), "flav": np.zeros((n, nm), np.int32),
+        "col": np.zeros((n, nm), np.int32), "acol": np.zeros((n, nm), np.int32),
+        "initial": np.zeros((n, nm), np.int32), "npart": np.zeros(n, np.int32),
+        "status": np.zeros(n, np.int32), "n_emit": np.zeros(n, np.int32),
+        "weight": np.zeros(n), "eta": np.zeros((n, 2)), "t_first": np.zeros(n),
+        "obs": np.zeros((n, 8)), "counters": np.zeros((n, 6), np.uint64),
+    }
+    o = OracleOut(**{k: _ptr(v) for k, v in out.items()})
+    cfgs = (OracleConfig * len(rows))(*[r.to_c(pdf if r.process else None) for r in rows])
+    fr = np.ascontiguousarray(fractions, dtype=np.float64)
+    row = np.zeros(n, np.int32)
+    rc = lib().oracle_run_mix(ctypes.cast(cfgs, ctypes.c_void_p), _ptr(fr), len(rows), first, n,
+                              ctypes.byref(o), _ptr(row), threads)
+    if rc != 0:
+        raise RuntimeError("oracle_run_mix failed (%d)" % rc)
+    out["row"] = row
+    return out
+
+
+def mix_rows(seed: int, fractions, first: int, n: int) -> np.ndarray:
+    """Row of each event first .. first + n - 1 of a mixed batch."""
+    fr = np.ascontiguousarray(fractions, dtype=np.float64)
+    out = np.zeros(n, np.int32)
+    if lib().oracle_mix_rows(seed, _ptr(fr), len(fr), first, n, _ptr(out)) != 0:
+        raise RuntimeError("oracle_mix_rows failed")
     return out
 
 

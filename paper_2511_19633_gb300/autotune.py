@@ -16,18 +16,23 @@ from . import gaps as G
 
 DEFAULT_GRID = {
     "block_size": (128, 256),
-    "blocks_per_sm": (2, 4),
+    "blocks_per_sm": (2, 4, 8),
     "refill_period": (1, 4),
-    "emit_batch": (1, 4, 8),
+    "emit_batch": (4, 8, 16),
 }
 
 
 def time_shape(process, sqrt_s, pdf, shape: dict, n_events: int, precision=G.GAPS_MIXED,
-               first: int = 1 << 44, reps: int = 1) -> dict:
-    cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if process else None, nmax=128,
-                        precision=precision, schedule=G.GAPS_SCHED_PERSISTENT, **shape)
+               first: int = 1 << 44, reps: int = 1, mix=None, learned=None) -> dict:
+    """Shower time of one launch shape; mix: rows of a mixed batch; learned:
+    (params, log_margins) of the learned proposal."""
+    uses_pdf = process or (mix and any(r[0] for r in mix))
+    cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf else None, nmax=128,
+                        precision=precision, schedule=G.GAPS_SCHED_PERSISTENT, mix=mix, **shape)
     ctx = G.gaps_init(cfg)
     try:
+        if learned is not None:
+            G.gaps_set_learned_proposal(ctx, *learned)
         buf = G.EventBuffers.allocate(n_events, 128)
         ev = buf.view()
         s = torch.cuda.current_stream()
@@ -53,13 +58,15 @@ def time_shape(process, sqrt_s, pdf, shape: dict, n_events: int, precision=G.GAP
 
 
 def autotune(process, sqrt_s, pdf, n_events: int = 1 << 19, grid: dict | None = None,
-             precision=G.GAPS_MIXED) -> dict:
+             precision=G.GAPS_MIXED, mix=None, learned=None) -> dict:
     grid = grid or DEFAULT_GRID
     keys = list(grid)
     table = []
     for values in itertools.product(*(grid[k] for k in keys)):
         shape = dict(zip(keys, values))
-        table.append(time_shape(process, sqrt_s, pdf, shape, n_events, precision))
+        if shape.get("block_size", 128) * shape.get("blocks_per_sm", 1) > 2048:
+            continue  # more threads than an SM holds
+        table.append(time_shape(process, sqrt_s, pdf, shape, n_events, precision, mix=mix, learned=learned))
     best = min(table, key=lambda r: r["ms"])
     return {"best": {k: best[k] for k in keys}, "best_events_per_s": best["events_per_s"],
             "sample_events": n_events, "table": table}

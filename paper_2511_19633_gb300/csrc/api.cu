@@ -19,8 +19,8 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
 cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, const LearnedCfg&, uint64_t,
                                 uint64_t, int, int, int, int, int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_isr_targets(const DevParams&, int, const float4*, uint64_t, float*, float*, cudaStream_t);
-cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, double*, const HistDef&,
-                               double*, double*, int, cudaStream_t);
+cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
+                               const HistSet&, double*, double*, int, cudaStream_t);
 }  // namespace gaps
 
 using namespace gaps;
@@ -33,13 +33,18 @@ struct gaps_ctx {
   double* d_tables = nullptr;  // umax [12][100], sufmax [12][101], lmin [12][100]
   unsigned long long* d_counters = nullptr;  // C_NCOUNTERS + 1 (work counter)
   DevParams P;
-  HistDef H;
+  HistSet H;   // binning per row (one row for one process)
   int q_independent = 0;     // every Q^2 column of the grid is identical
   void* d_work = nullptr;    // mixed-precision working set
   size_t work_bytes = 0;
   float* d_mlp = nullptr;    // learned-proposal network (FP32 parameters)
   int learned = 0;
-  float log_margin = 0.0f;
+  // gaps_process: capture stream and the instantiated graph of the last call
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  uint64_t graph_n = 0, graph_cap = 0;
+  std::vector<cudaEvent_t> shower_ev;  // start/stop of each chunk's shower in the graph
+  int graph_chunks = 0;
 };
 
 namespace gaps {
@@ -79,7 +84,29 @@ void build_bound_tables(const float* g, double* out) {
 }
 
 // GAPS_OK or GAPS_ERR_INVALID_ARG for a configuration (no device work)
+// the one-process configuration of row r of a mixed batch
+gaps_config row_config(const gaps_config& c, int r) {
+  gaps_config k = c;
+  k.n_mix = 0;
+  k.process = c.mix[r].process;
+  k.sqrt_s = c.mix[r].sqrt_s;
+  k.t_cut = c.mix[r].t_cut;
+  return k;
+}
+
 int validate_config(const gaps_config& c) {
+  if (c.n_mix < 0 || c.n_mix > GAPS_MAX_MIX) return GAPS_ERR_INVALID_ARG;
+  if (c.n_mix > 0) {
+    double sum = 0.0;
+    for (int r = 0; r < c.n_mix; ++r) {
+      const double f = c.mix[r].fraction;
+      if (!(f > 0.0) || !std::isfinite(f)) return GAPS_ERR_INVALID_ARG;
+      sum += f;
+      const int rc = validate_config(row_config(c, r));
+      if (rc != GAPS_OK) return rc;
+    }
+    return std::fabs(sum - 1.0) <= 1e-9 ? GAPS_OK : GAPS_ERR_INVALID_ARG;
+  }
   if (c.process < GAPS_EE_QQ || c.process > GAPS_PP_Z_NLO) return GAPS_ERR_INVALID_ARG;
   if (c.precision != GAPS_FP64 && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
   if (!(c.sqrt_s > 0.0) || !std::isfinite(c.sqrt_s)) return GAPS_ERR_INVALID_ARG;
@@ -112,6 +139,20 @@ int validate_config(const gaps_config& c) {
 
 // scalar parameters of a configuration (device pointers left unset)
 void fill_params(const gaps_config& c, DevParams& P) {
+  if (c.n_mix > 0) {
+    // row 0 fills the scalar fields; each row its own process-dependent part
+    fill_params(row_config(c, 0), P);
+    double cum = 0.0;
+    for (int r = 0; r < c.n_mix; ++r) {
+      DevParams Q;
+      fill_params(row_config(c, r), Q);
+      P.rows[r] = Q.rows[0];
+      cum += c.mix[r].fraction;  // summed in row order, as the selection compares
+      P.cum[r] = cum;
+    }
+    P.n_rows = c.n_mix;
+    return;
+  }
   const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
   double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
   P.process = c.process;
@@ -129,6 +170,10 @@ void fill_params(const gaps_config& c, DevParams& P) {
   P.dlx = (gm_log(GAPS_PDF_XMAX) - P.lxmin) / (GAPS_PDF_NX - 1);
   P.lqmin = gm_log(GAPS_PDF_Q2MIN);
   P.dlq = (gm_log(GAPS_PDF_Q2MAX) - P.lqmin) / (GAPS_PDF_NQ - 1);
+  P.n_rows = 1;
+  P.rows[0] = RowParams{P.process, P.sqrt_s, P.s_had, P.t_cut, P.as_over};
+  P.cum[0] = 1.0;
+  for (int r = 1; r < kMaxRows; ++r) { P.rows[r] = P.rows[0]; P.cum[r] = 1.0; }
 }
 
 // 1 when every Q^2 column of the grid is identical
@@ -240,7 +285,7 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
   P.sufmax = ctx->d_tables + 12 * GAPS_PDF_NX;
   P.lmin = ctx->d_tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
   P.counters = ctx->d_counters;
-  set_hist_defs(c.process, ctx->H);
+  for (int r = 0; r < P.n_rows; ++r) set_hist_defs(P.rows[r].process, ctx->H.h[r]);
   *out = ctx;
   return GAPS_OK;
 }
@@ -252,12 +297,13 @@ int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const ga
 }
 
 namespace {
-int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,
-                 void* stream) {
+// working set of the mixed-precision shower for the context's launch shape
+// (allocated on first use)
+int ensure_workset(gaps_ctx* ctx, int& blocks, int& bs, WorkSet& W) {
   const gaps_config& c = ctx->cfg;
-  int bs = c.block_size > 0 ? c.block_size : 128;
+  bs = c.block_size > 0 ? c.block_size : 128;
   int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
-  int blocks = ctx->n_sm * per_sm;
+  blocks = ctx->n_sm * per_sm;
   int lanes = blocks * bs;
   size_t need = workset_bytes(lanes, c.nmax_partons);
   if (need > ctx->work_bytes) {
@@ -267,8 +313,17 @@ int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_eve
     if (cudaMalloc(&ctx->d_work, need) != cudaSuccess) return GAPS_ERR_CUDA;
     ctx->work_bytes = need;
   }
-  WorkSet W;
   workset_carve(ctx->d_work, lanes, c.nmax_partons, W);
+  return GAPS_OK;
+}
+
+int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,
+                 void* stream) {
+  const gaps_config& c = ctx->cfg;
+  int blocks, bs;
+  WorkSet W;
+  const int rc = ensure_workset(ctx, blocks, bs, W);
+  if (rc != GAPS_OK) return rc;
   return cuda_fail(launch_shower_mixed(ctx->P, dev_events(ev), W, Lc, first_event, n, blocks, bs, ctx->n_sm,
                                        c.refill_period, c.emit_batch, ctx->q_independent,
                                        ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
@@ -280,8 +335,9 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
   const gaps_config& c = ctx->cfg;
   if (c.precision == GAPS_MIXED) {
     LearnedCfg Lc{};
-    Lc.learned = ctx->learned && ctx->d_mlp && c.process != GAPS_EE_QQ;
-    Lc.log_margin = ctx->log_margin;
+    bool any_pp = false;
+    for (int r = 0; r < ctx->P.n_rows; ++r) any_pp = any_pp || ctx->P.rows[r].process != GAPS_EE_QQ;
+    Lc.learned = ctx->learned && ctx->d_mlp && any_pp;
     Lc.mlp = ctx->d_mlp;
     return shower_mixed(ctx, first_event, n, ev, Lc, stream);
   }
@@ -298,7 +354,8 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
 int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
                             float* states, uint64_t capacity, uint64_t* count, void* stream) {
   if (!ctx || !events_ok(ctx, ev, n) || !states || !count) return GAPS_ERR_INVALID_ARG;
-  if (ctx->cfg.process == GAPS_EE_QQ || ctx->cfg.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  if (ctx->cfg.n_mix > 0 || ctx->cfg.process == GAPS_EE_QQ || ctx->cfg.precision != GAPS_MIXED)
+    return GAPS_ERR_INVALID_ARG;
   LearnedCfg Lc{};
   Lc.collect = reinterpret_cast<float4*>(states);
   Lc.collect_count = reinterpret_cast<unsigned long long*>(count);
@@ -309,44 +366,135 @@ int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n, con
 int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states, float* features, float* targets,
                      void* stream) {
   if (!ctx || !states || !features || !targets) return GAPS_ERR_INVALID_ARG;
-  if (ctx->cfg.process == GAPS_EE_QQ) return GAPS_ERR_INVALID_ARG;
+  if (ctx->cfg.n_mix > 0 || ctx->cfg.process == GAPS_EE_QQ) return GAPS_ERR_INVALID_ARG;
   return cuda_fail(launch_isr_targets(ctx->P, ctx->q_independent, reinterpret_cast<const float4*>(states),
                                       n_states, features, targets, (cudaStream_t)stream));
 }
 
-int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, float log_margin) {
-  if (!ctx || !std::isfinite(log_margin)) return GAPS_ERR_INVALID_ARG;
+int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* log_margins) {
+  if (!ctx) return GAPS_ERR_INVALID_ARG;
   if (!params) {
     ctx->learned = 0;
     return GAPS_OK;
   }
-  const size_t bytes = (size_t)GAPS_MLP_PARAMS * sizeof(float);
+  if (!log_margins) return GAPS_ERR_INVALID_ARG;
+  constexpr int nm = GAPS_ISR_CLASSES * GAPS_ISR_BINS;
   for (int q = 0; q < GAPS_MLP_PARAMS; ++q)
     if (!std::isfinite(params[q])) return GAPS_ERR_INVALID_ARG;
-  if (!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, bytes) != cudaSuccess) return GAPS_ERR_CUDA;
-  if (cudaMemcpy(ctx->d_mlp, params, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return GAPS_ERR_CUDA;
+  for (int q = 0; q < nm; ++q)
+    if (!std::isfinite(log_margins[q])) return GAPS_ERR_INVALID_ARG;
+  // device image: parameters, then the margins
+  const size_t pbytes = (size_t)GAPS_MLP_PARAMS * sizeof(float);
+  if (!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, pbytes + nm * sizeof(float)) != cudaSuccess) return GAPS_ERR_CUDA;
+  if (cudaMemcpy(ctx->d_mlp, params, pbytes, cudaMemcpyHostToDevice) != cudaSuccess) return GAPS_ERR_CUDA;
+  if (cudaMemcpy(ctx->d_mlp + GAPS_MLP_PARAMS, log_margins, nm * sizeof(float), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return GAPS_ERR_CUDA;
   ctx->learned = 1;
-  ctx->log_margin = log_margin;
   return GAPS_OK;
 }
 
-int gaps_observables(gaps_ctx* ctx, uint64_t n, const gaps_events* ev, double* obs,
+int gaps_observables(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, double* obs,
                      const gaps_hists* hists, void* stream) {
   if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
   if (hists && (!hists->sumw || !hists->sumw2)) return GAPS_ERR_INVALID_ARG;
-  return cuda_fail(launch_observables(ctx->P, dev_events(ev), n, obs, ctx->H,
+  return cuda_fail(launch_observables(ctx->P, dev_events(ev), first_event, n, obs, ctx->H,
                                       hists ? hists->sumw : nullptr, hists ? hists->sumw2 : nullptr,
                                       ctx->cfg.precision == GAPS_MIXED, (cudaStream_t)stream));
 }
 
+int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, double* obs_dev,
+                 double* obs_host, const gaps_hists* hists, void* stream) {
+  if (!ctx || !ev || ev->capacity == 0) return GAPS_ERR_INVALID_ARG;
+  if (obs_host && !obs_dev) return GAPS_ERR_INVALID_ARG;
+  if (n == 0) return GAPS_OK;
+  const uint64_t cap = ev->capacity;
+  if (!events_ok(ctx, ev, n < cap ? n : cap)) return GAPS_ERR_INVALID_ARG;
+  // everything the launches need is allocated before the capture
+  if (ctx->cfg.precision == GAPS_MIXED) {
+    int blocks, bs;
+    WorkSet W;
+    const int rc = ensure_workset(ctx, blocks, bs, W);
+    if (rc != GAPS_OK) return rc;
+  }
+  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  const uint64_t chunks = (n + cap - 1) / cap;
+  if (chunks > 1u << 20) return GAPS_ERR_INVALID_ARG;
+  while (ctx->shower_ev.size() < 2 * chunks) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return GAPS_ERR_CUDA;
+    ctx->shower_ev.push_back(e);
+  }
+  cudaStream_t cs = ctx->cap_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GAPS_ERR_CUDA;
+  int rc = GAPS_OK;
+  for (uint64_t f0 = 0, k = 0; f0 < n && rc == GAPS_OK; f0 += cap, ++k) {
+    const uint64_t m = n - f0 < cap ? n - f0 : cap;
+    rc = gaps_generate_hard(ctx, first_event + f0, m, ev, cs);
+    if (rc == GAPS_OK && cudaEventRecordWithFlags(ctx->shower_ev[2 * k], cs, cudaEventRecordExternal) != cudaSuccess)
+      rc = GAPS_ERR_CUDA;
+    if (rc == GAPS_OK) rc = gaps_shower(ctx, first_event + f0, m, ev, cs);
+    if (rc == GAPS_OK &&
+        cudaEventRecordWithFlags(ctx->shower_ev[2 * k + 1], cs, cudaEventRecordExternal) != cudaSuccess)
+      rc = GAPS_ERR_CUDA;
+    if (rc == GAPS_OK) rc = gaps_observables(ctx, first_event + f0, m, ev, obs_dev, hists, cs);
+    if (rc == GAPS_OK && obs_host &&
+        cudaMemcpy2DAsync(obs_host + f0, n * sizeof(double), obs_dev, cap * sizeof(double), m * sizeof(double),
+                          GAPS_NOBS, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      rc = GAPS_ERR_CUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(cs, &g);
+  if (rc == GAPS_OK && (end != cudaSuccess || !g)) rc = GAPS_ERR_CUDA;
+  if (rc != GAPS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  // same chunking as the last call: update the parameters in place
+  bool updated = false;
+  if (ctx->graph && ctx->graph_n == n && ctx->graph_cap == cap) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(ctx->graph, g, &info) == cudaSuccess;
+    if (!updated) cudaGetLastError();
+  }
+  if (!updated) {
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    if (cudaGraphInstantiate(&ctx->graph, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      ctx->graph = nullptr;
+      return GAPS_ERR_CUDA;
+    }
+    ctx->graph_n = n;
+    ctx->graph_cap = cap;
+  }
+  cudaGraphDestroy(g);
+  ctx->graph_chunks = (int)chunks;
+  return cuda_fail(cudaGraphLaunch(ctx->graph, (cudaStream_t)stream));
+}
+
+int gaps_process_shower_ms(gaps_ctx* ctx, float* ms, int max_chunks) {
+  if (!ctx || !ms || max_chunks < 0) return GAPS_ERR_INVALID_ARG;
+  const int k = ctx->graph_chunks < max_chunks ? ctx->graph_chunks : max_chunks;
+  for (int c = 0; c < k; ++c) {
+    if (cudaEventSynchronize(ctx->shower_ev[2 * c + 1]) != cudaSuccess) return GAPS_ERR_CUDA;
+    if (cudaEventElapsedTime(&ms[c], ctx->shower_ev[2 * c], ctx->shower_ev[2 * c + 1]) != cudaSuccess)
+      return GAPS_ERR_CUDA;
+  }
+  return k;
+}
+
 int gaps_hist_binning(const gaps_ctx* ctx, int h, double* lo, double* hi, int* nbins, int* obs_index,
                       int* log10_axis) {
-  if (!ctx || h < 0 || h >= GAPS_NHIST) return GAPS_ERR_INVALID_ARG;
-  if (lo) *lo = ctx->H.lo[h];
-  if (hi) *hi = ctx->H.hi[h];
-  if (nbins) *nbins = ctx->H.nb[h];
-  if (obs_index) *obs_index = ctx->H.obs[h];
-  if (log10_axis) *log10_axis = ctx->H.logx[h];
+  if (!ctx || h < 0 || h >= GAPS_NHIST * ctx->P.n_rows) return GAPS_ERR_INVALID_ARG;
+  const HistDef& H = ctx->H.h[h / GAPS_NHIST];
+  h %= GAPS_NHIST;
+  if (lo) *lo = H.lo[h];
+  if (hi) *hi = H.hi[h];
+  if (nbins) *nbins = H.nb[h];
+  if (obs_index) *obs_index = H.obs[h];
+  if (log10_axis) *log10_axis = H.logx[h];
   return GAPS_OK;
 }
 
@@ -361,6 +509,7 @@ int gaps_get_stats(gaps_ctx* ctx, gaps_stats* out, void* stream) {
   out->violations = h[C_VIOLATIONS]; out->err_capacity = h[C_ERR_CAP];
   out->err_iter_cap = h[C_ERR_ITER]; out->err_numeric = h[C_ERR_NUM];
   out->lane_steps = h[C_LANE_STEPS]; out->warp_steps = h[C_WARP_STEPS];
+  out->rebuilds = h[C_REBUILDS]; out->mlp_tiles = h[C_MLP_TILES];
   return GAPS_OK;
 }
 
@@ -377,6 +526,9 @@ void gaps_destroy(gaps_ctx* ctx) {
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->d_work) cudaFree(ctx->d_work);
   if (ctx->d_mlp) cudaFree(ctx->d_mlp);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (cudaEvent_t e : ctx->shower_ev) cudaEventDestroy(e);
   delete ctx;
 }
 

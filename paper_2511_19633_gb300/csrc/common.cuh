@@ -24,12 +24,23 @@ constexpr int kMaxSteps = 200000;
 // counters in the device stats block (uint64 each)
 enum Counter {
   C_EVENTS = 0, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
-  C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_NCOUNTERS
+  C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES, C_NCOUNTERS
 };
+
+// the process-dependent part of the parameters (one row of a mixed batch)
+struct RowParams {
+  int process;
+  double sqrt_s, s_had, t_cut, as_over;
+};
+constexpr int kMaxRows = GAPS_MAX_MIX;
+constexpr uint64_t kMixDraw = 0x4000000000000000ull;
 
 struct DevParams {
   int process, nf, nmax;
   double sqrt_s, s_had, t_cut, as_mz, as_over, beta0, p_s;
+  int n_rows;                  // 1: one process; > 1: mixed batch
+  RowParams rows[kMaxRows];    // row 0 = the fields above for one process
+  double cum[kMaxRows];        // cumulative fractions, summed in row order
   uint64_t seed;
   const float* grid;      // [11][100][50] x f
   const double* umax;     // [12][100] max over Q^2 nodes (index 11 = sum of quarks)
@@ -45,14 +56,16 @@ struct WorkSet {
   uint32_t* tag;
   float4* end;
   float* ub;     // learned bin heights [4 ends][2 channels][8 bins][lanes]
+  float4* mkey;  // inputs of the last evaluation per end {eta, s, class code, -} [4][lanes]
+  float2* mscale;// 8 / sum of the heights per end and channel [4][lanes]
   int lanes;
 };
+constexpr size_t kLearnedLaneBytes = 64 * sizeof(float) + 4 * sizeof(float4) + 4 * sizeof(float2);
 
 // learned initial-state proposal and sample collection of one launch
 struct LearnedCfg {
   int learned;                    // use the learned bin heights
-  float log_margin;               // added to the network output
-  const float* mlp;               // FP32 parameters, device
+  const float* mlp;               // FP32 parameters, then the margins [44][8], device
   float4* collect;                // logged initial-state ends {eta, s, type, pdf index}
   unsigned long long* collect_count;
   uint64_t collect_cap;
@@ -69,6 +82,9 @@ int grid_q_independent(const float* grid);
 struct HistDef {
   double lo[GAPS_NHIST], hi[GAPS_NHIST];
   int nb[GAPS_NHIST], obs[GAPS_NHIST], logx[GAPS_NHIST];
+};
+struct HistSet {
+  HistDef h[GAPS_MAX_MIX];
 };
 
 struct DevEvents {
@@ -133,6 +149,29 @@ struct Rng {
     b = u01(w[2], w[3]);
   }
 };
+
+// row of event `id` in a mixed batch: the first row whose cumulative fraction
+// exceeds the uniform of block (seed, id, 2^62), the last one otherwise
+__device__ __forceinline__ int mix_row(const DevParams& P, uint64_t id) {
+  if (P.n_rows <= 1) return 0;
+  Rng r;
+  r.init(P.seed, id, kMixDraw);
+  double u, unused;
+  r.next2(u, unused);
+  for (int k = 0; k + 1 < P.n_rows; ++k)
+    if (u < P.cum[k]) return k;
+  return P.n_rows - 1;
+}
+
+// copy of the parameters with the process-dependent fields of row r
+__device__ __forceinline__ void apply_row(DevParams& Q, int r) {
+  const RowParams& R = Q.rows[r];
+  Q.process = R.process;
+  Q.sqrt_s = R.sqrt_s;
+  Q.s_had = R.s_had;
+  Q.t_cut = R.t_cut;
+  Q.as_over = R.as_over;
+}
 
 // ---------------------------------------------------------------------------
 // flavours

@@ -112,10 +112,12 @@ __device__ __forceinline__ void incoming_quark_tags(int fl, int tag, int& c, int
   if (fl > 0) { c = 0; a = tag; } else { c = tag; a = 0; }
 }
 
-__global__ void k_generate_hard(DevParams P, DevEvents E, uint64_t first, uint64_t n) {
+__global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint64_t n) {
   uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   uint64_t id = first + e;
+  DevParams P = P0;  // the event's row of a mixed batch
+  if (P0.n_rows > 1) apply_row(P, mix_row(P0, id));
   Rng rng;
   rng.init(P.seed, id, kHardDrawBase);
   double R0, R1, R2, R3, R4, R5;

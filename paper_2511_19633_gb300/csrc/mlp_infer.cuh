@@ -14,19 +14,25 @@ namespace gaps {
 
 constexpr int kMlpIn = 4, kMlpH = 64;
 constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;
+constexpr int kIsrClasses = 44, kIsrBins = 8;
 
 // shared-memory image, weights stored [n][k] so that the B fragment of
-// m16n8k16 (k = 2t, 2t+1 and 2t+8, 2t+9 of column n = g) is two 32-bit loads
+// m16n8k16 (k = 2t, 2t+1 and 2t+8, 2t+9 of column n = g) is two 32-bit loads.
+// Rows are padded by 8 values: a row stride of 4 (mod 32) banks puts the 32
+// lanes' loads of one fragment (8 rows g x 4 column pairs t) in 32 banks.
+constexpr int kPad = 8;
 struct MlpSmem {
-  __nv_bfloat16 w1[kMlpH][16];   // k padded from 4 to 16 with zeros
-  __nv_bfloat16 w2[kMlpH][kMlpH];
-  __nv_bfloat16 w3[8][kMlpH];    // output row 0; rows 1..7 zero
+  __nv_bfloat16 w1[kMlpH][16 + kPad];     // k padded from 4 to 16 with zeros
+  __nv_bfloat16 w2[kMlpH][kMlpH + kPad];
+  __nv_bfloat16 w3[8][kMlpH + kPad];      // output row 0; rows 1..7 zero
   float b1[kMlpH], b2[kMlpH], b3;
+  float margin[kIsrClasses * kIsrBins];  // calibration margins (shower only)
 };
 constexpr size_t kMlpSmemBytes = (sizeof(MlpSmem) + 15) / 16 * 16;
 
-// cooperative fill of the image from FP32 parameters (all threads of a block)
-__device__ inline void mlp_load_smem(MlpSmem& S, const float* P) {
+// cooperative fill of the image from FP32 parameters and, when not NULL, the
+// calibration margins (all threads of a block)
+__device__ inline void mlp_load_smem(MlpSmem& S, const float* P, const float* margins = nullptr) {
   const float* W1 = P;
   const float* b1 = W1 + kMlpH * kMlpIn;
   const float* W2 = b1 + kMlpH;
@@ -36,13 +42,15 @@ __device__ inline void mlp_load_smem(MlpSmem& S, const float* P) {
     int n = q / 16, k = q % 16;
     S.w1[n][k] = __float2bfloat16_rn(k < kMlpIn ? W1[n * kMlpIn + k] : 0.0f);
   }
-  for (int q = threadIdx.x; q < kMlpH * kMlpH; q += blockDim.x) S.w2[q / kMlpH][q % kMlpH] = __float2bfloat16_rn(W2[q]);
+  for (int q = threadIdx.x; q < kMlpH * kMlpH; q += blockDim.x)
+    S.w2[q / kMlpH][q % kMlpH] = __float2bfloat16_rn(W2[q]);
   for (int q = threadIdx.x; q < 8 * kMlpH; q += blockDim.x) {
     int n = q / kMlpH, k = q % kMlpH;
     S.w3[n][k] = __float2bfloat16_rn(n == 0 ? W3[k] : 0.0f);
   }
   for (int q = threadIdx.x; q < kMlpH; q += blockDim.x) { S.b1[q] = b1[q]; S.b2[q] = b2[q]; }
   if (threadIdx.x == 0) S.b3 = W3[kMlpH];
+  for (int q = threadIdx.x; q < kIsrClasses * kIsrBins; q += blockDim.x) S.margin[q] = margins ? margins[q] : 0.0f;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -59,7 +67,10 @@ __device__ __forceinline__ void mma16816(float d[4], const uint32_t a[4], uint32
 }
 
 // One warp evaluates 16 rows: feat[r][0..3] -> out[r] (both in shared or
-// global memory visible to the warp). All 32 lanes must call it.
+// global memory visible to the warp). All 32 lanes must call it. Layer 1 is
+// kept as packed BF16 A fragments (16 registers); layers 2 and 3 are
+// interleaved: the two layer-2 column tiles that form k-step j of layer 3 are
+// computed, rectified, packed and consumed at once.
 static __device__ __noinline__ void mlp_tile(const MlpSmem& S, const float (*feat)[4], float* out) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t a[4];
@@ -68,54 +79,52 @@ static __device__ __noinline__ void mlp_tile(const MlpSmem& S, const float (*fea
   a[1] = t < 2 ? pack_bf16(feat[g + 8][2 * t], feat[g + 8][2 * t + 1]) : 0u;
   a[2] = 0u;
   a[3] = 0u;
-  float h1[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int n = nt * 8 + g;
-    h1[nt][0] = S.b1[nt * 8 + 2 * t];
-    h1[nt][1] = S.b1[nt * 8 + 2 * t + 1];
-    h1[nt][2] = h1[nt][0];
-    h1[nt][3] = h1[nt][1];
-    uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w1[n][2 * t]);
-    uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w1[n][2 * t + 8]);
-    mma16816(h1[nt], a, b0, b1);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) h1[nt][q] = fmaxf(h1[nt][q], 0.0f);
-  }
-  // layer 2: K = 64 in four steps of 16; A from pairs of layer-1 tiles
-  float h2[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    h2[nt][0] = S.b2[nt * 8 + 2 * t];
-    h2[nt][1] = S.b2[nt * 8 + 2 * t + 1];
-    h2[nt][2] = h2[nt][0];
-    h2[nt][3] = h2[nt][1];
-  }
+  uint32_t A1[4][4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    uint32_t A[4] = {pack_bf16(h1[2 * j][0], h1[2 * j][1]), pack_bf16(h1[2 * j][2], h1[2 * j][3]),
-                     pack_bf16(h1[2 * j + 1][0], h1[2 * j + 1][1]), pack_bf16(h1[2 * j + 1][2], h1[2 * j + 1][3])};
+    float h[2][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int n = nt * 8 + g;
-      uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w2[n][16 * j + 2 * t]);
-      uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w2[n][16 * j + 8 + 2 * t]);
-      mma16816(h2[nt], A, b0, b1);
+    for (int u = 0; u < 2; ++u) {
+      const int nt = 2 * j + u, n = nt * 8 + g;
+      h[u][0] = S.b1[nt * 8 + 2 * t];
+      h[u][1] = S.b1[nt * 8 + 2 * t + 1];
+      h[u][2] = h[u][0];
+      h[u][3] = h[u][1];
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w1[n][2 * t]);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w1[n][2 * t + 8]);
+      mma16816(h[u], a, b0, b1);
     }
+    A1[j][0] = pack_bf16(fmaxf(h[0][0], 0.0f), fmaxf(h[0][1], 0.0f));
+    A1[j][1] = pack_bf16(fmaxf(h[0][2], 0.0f), fmaxf(h[0][3], 0.0f));
+    A1[j][2] = pack_bf16(fmaxf(h[1][0], 0.0f), fmaxf(h[1][1], 0.0f));
+    A1[j][3] = pack_bf16(fmaxf(h[1][2], 0.0f), fmaxf(h[1][3], 0.0f));
   }
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) h2[nt][q] = fmaxf(h2[nt][q], 0.0f);
-  // layer 3: N = 8 (column 0 is the output), K = 64
+  // layers 2 and 3: N = 8 for layer 3 (column 0 is the output), K = 64
   float o[4] = {S.b3, S.b3, S.b3, S.b3};
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t A[4] = {pack_bf16(h2[2 * j][0], h2[2 * j][1]), pack_bf16(h2[2 * j][2], h2[2 * j][3]),
-                     pack_bf16(h2[2 * j + 1][0], h2[2 * j + 1][1]), pack_bf16(h2[2 * j + 1][2], h2[2 * j + 1][3])};
-    uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w3[g][16 * j + 2 * t]);
-    uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w3[g][16 * j + 8 + 2 * t]);
-    mma16816(o, A, b0, b1);
+  for (int j3 = 0; j3 < 4; ++j3) {
+    float h[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int nt = 2 * j3 + u, n = nt * 8 + g;
+      h[u][0] = S.b2[nt * 8 + 2 * t];
+      h[u][1] = S.b2[nt * 8 + 2 * t + 1];
+      h[u][2] = h[u][0];
+      h[u][3] = h[u][1];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w2[n][16 * j + 2 * t]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w2[n][16 * j + 8 + 2 * t]);
+        mma16816(h[u], A1[j], b0, b1);
+      }
+    }
+    const uint32_t A3[4] = {pack_bf16(fmaxf(h[0][0], 0.0f), fmaxf(h[0][1], 0.0f)),
+                            pack_bf16(fmaxf(h[0][2], 0.0f), fmaxf(h[0][3], 0.0f)),
+                            pack_bf16(fmaxf(h[1][0], 0.0f), fmaxf(h[1][1], 0.0f)),
+                            pack_bf16(fmaxf(h[1][2], 0.0f), fmaxf(h[1][3], 0.0f))};
+    const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w3[g][16 * j3 + 2 * t]);
+    const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w3[g][16 * j3 + 8 + 2 * t]);
+    mma16816(o, A3, b0, b1);
   }
   if (t == 0) {
     out[g] = o[0];

@@ -221,24 +221,33 @@ __device__ __forceinline__ int bin_of(const HistDef& H, int h, double v) {
 
 // R = double for per-event parity (GAPS_FP64), float for mixed-precision contexts
 template <typename R>
-__global__ void k_observables(DevParams P, DevEvents E, uint64_t n, double* obs, HistDef H,
+__global__ void k_observables(DevParams P, DevEvents E, uint64_t first, uint64_t n, double* obs, HistSet Hs,
                               double* sumw, double* sumw2) {
+  // shared: per row of the batch, sumw then sumw2 [GAPS_NHIST][GAPS_HIST_BINS]
   extern __shared__ double sh[];
-  double* hw = sh;
-  double* hw2 = sh + GAPS_NHIST * GAPS_HIST_BINS;
+  __shared__ HistDef sH[kMaxRows];
+  __shared__ int s_pp[kMaxRows];
+  constexpr int kSet = GAPS_NHIST * GAPS_HIST_BINS;
   const bool fill = sumw != nullptr;
-  if (fill) {
-    for (int q = threadIdx.x; q < 2 * GAPS_NHIST * GAPS_HIST_BINS; q += blockDim.x) sh[q] = 0.0;
-    __syncthreads();
+  if (threadIdx.x < P.n_rows) {
+    sH[threadIdx.x] = Hs.h[threadIdx.x];
+    s_pp[threadIdx.x] = P.rows[threadIdx.x].process != GAPS_EE_QQ;
   }
+  if (fill)
+    for (int q = threadIdx.x; q < 2 * kSet * P.n_rows; q += blockDim.x) sh[q] = 0.0;
+  __syncthreads();
   uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) {
+    const int row = mix_row(P, first + e);
+    const HistDef& H = sH[row];
+    double* hw = sh + 2 * kSet * row;
+    double* hw2 = hw + kSet;
     double o[GAPS_NOBS];
     for (int q = 0; q < GAPS_NOBS; ++q) o[q] = 0.0;
     R ps[kMaxFinal][4];
     int np = E.npart[e];
     int m = 0;
-    bool pp = P.process != GAPS_EE_QQ;
+    const bool pp = s_pp[row] != 0;
     for (int i = 0; i < np && m < kMaxFinal; ++i) {
       if (pp && i < 2) continue;
       if (E.F(i, e) == 23) continue;
@@ -289,23 +298,25 @@ __global__ void k_observables(DevParams P, DevEvents E, uint64_t n, double* obs,
   }
   if (fill) {
     __syncthreads();
-    for (int q = threadIdx.x; q < GAPS_NHIST * GAPS_HIST_BINS; q += blockDim.x) {
-      if (hw[q] != 0.0) atomicAdd(&sumw[q], hw[q]);
-      if (hw2[q] != 0.0) atomicAdd(&sumw2[q], hw2[q]);
+    for (int q = threadIdx.x; q < kSet * P.n_rows; q += blockDim.x) {
+      const int r = q / kSet, k = q % kSet;
+      const double a = sh[2 * kSet * r + k], b = sh[2 * kSet * r + kSet + k];
+      if (a != 0.0) atomicAdd(&sumw[q], a);
+      if (b != 0.0) atomicAdd(&sumw2[q], b);
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_observables(const DevParams& P, const DevEvents& E, uint64_t n, double* obs,
-                               const HistDef& H, double* sumw, double* sumw2, int fp32, cudaStream_t stream) {
+cudaError_t launch_observables(const DevParams& P, const DevEvents& E, uint64_t first, uint64_t n, double* obs,
+                               const HistSet& H, double* sumw, double* sumw2, int fp32, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   int bs = 64;
   unsigned grid = (unsigned)((n + bs - 1) / bs);
-  size_t shm = sumw ? 2 * GAPS_NHIST * GAPS_HIST_BINS * sizeof(double) : 0;
-  if (fp32) k_observables<float><<<grid, bs, shm, stream>>>(P, E, n, obs, H, sumw, sumw2);
-  else k_observables<double><<<grid, bs, shm, stream>>>(P, E, n, obs, H, sumw, sumw2);
+  size_t shm = sumw ? 2 * (size_t)P.n_rows * GAPS_NHIST * GAPS_HIST_BINS * sizeof(double) : 0;
+  if (fp32) k_observables<float><<<grid, bs, shm, stream>>>(P, E, first, n, obs, H, sumw, sumw2);
+  else k_observables<double><<<grid, bs, shm, stream>>>(P, E, first, n, obs, H, sumw, sumw2);
   return cudaGetLastError();
 }
 

@@ -307,9 +307,11 @@ __device__ __forceinline__ void count_error(const DevParams& P, int st) {
 }
 
 // run event e to completion; returns its final status
-__device__ int run_event(const DevParams& P, const DevEvents& E, uint64_t e, uint64_t id, Counters& cnt) {
+__device__ int run_event(const DevParams& P0, const DevEvents& E, uint64_t e, uint64_t id, Counters& cnt) {
   int st = E.status[e];
   if (st != GAPS_STATUS_ACTIVE) return st;
+  DevParams P = P0;  // the event's row of a mixed batch
+  if (P0.n_rows > 1) apply_row(P, mix_row(P0, id));
   int n = E.npart[e];
   if (n < 2 || n > P.nmax) {  // not a record written by the hard-process kernel
     E.status[e] = GAPS_ERR_NUMERIC;

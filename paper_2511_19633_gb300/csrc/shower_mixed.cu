@@ -46,7 +46,19 @@ struct SmemPdf {
   float umax[12][kSmNX];
   float sufmax[12][kSmNX + 1];
   float lmin[12][kSmNX];
+  // per row of a mixed batch: ln t_c, alpha_s(t_c) / 2 pi, pp process
+  float lnTc[kMaxRows], asOver2pi[kMaxRows];
+  int pp[kMaxRows];
 };
+
+__device__ __forceinline__ void load_rows(SmemPdf& S, const DevParams& P) {
+  if (threadIdx.x < kMaxRows) {
+    const RowParams& R = P.rows[threadIdx.x < P.n_rows ? threadIdx.x : 0];
+    S.lnTc[threadIdx.x] = (float)gm_log(R.t_cut);
+    S.asOver2pi[threadIdx.x] = (float)(R.as_over / (2.0 * kPi));
+    S.pp[threadIdx.x] = R.process != GAPS_EE_QQ;
+  }
+}
 
 struct MixedCtx {
   DevParams P;
@@ -74,6 +86,7 @@ __device__ __forceinline__ int tag_acol(uint32_t t) { return (int)((t >> 16) & 0
 struct Lane {
   uint64_t ev;      // record index in the caller's arrays
   int n, n_emit, status, steps;
+  int row;          // row of a mixed batch
   bool learned_ok;  // learned bounds active for this event
   float lnT;        // ln of the current evolution scale
   double eta0, eta1;
@@ -201,6 +214,8 @@ struct WS {
   __device__ __forceinline__ float& UB(int q, int c, int m) const {
     return W.ub[(((size_t)q * 2 + c) * 8 + m) * W.lanes + lane];
   }
+  __device__ __forceinline__ float4& MKey(int q) const { return W.mkey[(size_t)q * W.lanes + lane]; }
+  __device__ __forceinline__ float2& MScale(int q) const { return W.mscale[(size_t)q * W.lanes + lane]; }
 };
 
 __device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side, int tag) {
@@ -285,9 +300,9 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
 // Cached record of colour end q = 2 slot + side of an event: {1/c0, 1/c1,
 // ln t_kin, partner} (partner -1: no dipole on this side).
 __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, int n, double eta0,
-                             double eta1, int q, float& s_out, float& eta_out, int& type_out) {
+                             double eta1, int row, int q, float& s_out, float& eta_out, int& type_out) {
   type_out = -1;
-  const bool pp = M.P.process != GAPS_EE_QQ;
+  const bool pp = S.pp[row] != 0;
   const int i = q >> 1, side = q & 1;
   const uint32_t ti = w.T(i);
   const int tag = side == 0 ? tag_col(ti) : tag_acol(ti);
@@ -308,7 +323,7 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, i
   type_out = type;
   const int first = ini ? (fi == 21 ? 5 : 3) : (fi == 21 ? 1 : 0);
   const int nch = (!ini && fi != 21) ? 1 : 2;
-  const float tc = __expf(M.lnTc);
+  const float tc = __expf(S.lnTc[row]);
   const float tk = tkin32(type, s, eta);
   float zm, delta;
   const bool ok = tk > tc && zlim32(type, tc, s, eta, zm, delta);
@@ -329,7 +344,7 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, i
       isr_pdf_indices(ch, fi, num, den);
       B = bound32(M, S, num, den, eta);
     }
-    const float cc = M.asOver2pi * B * (float)coefd * shape_int32(shape, zm, delta);
+    const float cc = S.asOver2pi[row] * B * (float)coefd * shape_int32(shape, zm, delta);
     ic[c] = cc > 0.0f ? 1.0f / cc : 0.0f;
   }
   return make_float4(ic[0], ic[1], __logf(tk), __int_as_float(k));
@@ -337,74 +352,104 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, i
 
 // The whole warp rebuilds the colour-end table of the event held by lane
 // `src` (one end per lane), after an emission or a refill of that lane. With
-// the learned proposal the warp then evaluates the network for the (up to
-// four) initial-state ends: 2 channels x 8 bins = one 16-row tile per end.
-__device__ __noinline__ void rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
+// the learned proposal the warp then evaluates the network for those of the
+// (up to four) initial-state ends whose inputs changed since their last
+// evaluation: 2 channels x 8 bins = one 16-row tile per end, two rows per
+// lane for the inputs and the bin heights.
+__device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
                                           float (*stage)[4], float* ustage, int src_global, int n,
-                                          double eta0, double eta1, bool learned_src, int lane_id) {
+                                          double eta0, double eta1, int row, bool learned_src, int lane_id) {
   const WS w{M.W, src_global, M.P.nmax};
-  const bool pp = M.P.process != GAPS_EE_QQ;
+  const bool pp = S.pp[row] != 0;
   float4 isr_rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
   float isr_s = 0.0f, isr_eta = 0.0f;
   int isr_type = -1;
   for (int q = lane_id; q < 2 * n; q += 32) {
     float s_, eta_;
     int type_;
-    const float4 rec = end_record(M, S, w, n, eta0, eta1, q, s_, eta_, type_);
+    const float4 rec = end_record(M, S, w, n, eta0, eta1, row, q, s_, eta_, type_);
     if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
     else w.End(q) = rec;
   }
-  if (!pp) return;
+  if (!pp) return 0;
   // lanes 0..3 hold the ends of the incoming partons
-  const bool valid = lane_id < 4 && lane_id < 2 * n && isr_type >= 0 && isr_rec.x > 0.0f && isr_rec.y > 0.0f &&
+  const bool mine = lane_id < 4 && lane_id < 2 * n;
+  const bool valid = mine && isr_type >= 0 && isr_rec.x > 0.0f && isr_rec.y > 0.0f &&
                      (isr_type == kIF || isr_type == kII);
-  const int fl_i = lane_id < 4 && lane_id < 2 * n ? tag_fl(w.T(lane_id >> 1)) : 0;
+  const int fl_i = mine ? tag_fl(w.T(lane_id >> 1)) : 0;
   if (valid && M.Lc.collect) {
     const unsigned long long at = atomicAdd(M.Lc.collect_count, 1ull);
     if (at < M.Lc.collect_cap)
       M.Lc.collect[at] = make_float4(isr_eta, isr_s, (float)isr_type, (float)pdf_index(fl_i));
   }
-  const bool use = M.Lc.learned && learned_src;
-  const unsigned any = __ballot_sync(0xffffffffu, valid && use);
-  if (any) {
-    const float tc = __expf(M.lnTc);
-    if (lane_id < 4) {
-      for (int c = 0; c < 2; ++c) {
-        const int ch = (fl_i == 21 ? 5 : 3) + c;
-        for (int m = 0; m < 8; ++m) {
-          float* f = stage[(lane_id * 2 + c) * 8 + m];
-          if (valid) mlp_features(isr_eta, isr_s, tc, m, isr_class(isr_type, ch, fl_i), f);
-          else { f[0] = f[1] = f[2] = f[3] = 0.0f; }
-        }
-      }
+  const bool use = valid && M.Lc.learned && learned_src;
+  // inputs of the end; the heights are reused while they are unchanged
+  const float code = (float)(isr_type * 32 + pdf_index(fl_i));
+  bool need = false;
+  if (use) {
+    const float4 key = w.MKey(lane_id);
+    need = !(key.x == isr_eta && key.y == isr_s && key.z == code);
+  }
+  const unsigned eval = __ballot_sync(0xffffffffu, need) & 0xFu;
+  if (eval) {
+    const float tc = __expf(S.lnTc[row]);
+    // rows r = lane and lane + 32: end r / 16, channel (r / 8) % 2, bin r % 8
+    int cls_j[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
+      const float eta_e = __shfl_sync(0xffffffffu, isr_eta, e);
+      const float s_e = __shfl_sync(0xffffffffu, isr_s, e);
+      const int type_e = __shfl_sync(0xffffffffu, isr_type, e);
+      const int fl_e = __shfl_sync(0xffffffffu, fl_i, e);
+      cls_j[j] = (eval >> e) & 1u ? isr_class(type_e, (fl_e == 21 ? 5 : 3) + c, fl_e) : 0;
+      if ((eval >> e) & 1u) mlp_features(eta_e, s_e, tc, m, cls_j[j], stage[r]);
     }
     __syncwarp();
     for (int tile = 0; tile < 4; ++tile)
-      if ((any >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
+      if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
     __syncwarp();
-  }
-  if (lane_id < 4 && lane_id < 2 * n) {
-    if (valid && use) {
-      float ic[2] = {isr_rec.x, isr_rec.y};
-      for (int c = 0; c < 2; ++c) {
-        float tot = 0.0f;
-        for (int m = 0; m < 8; ++m) {
-          const float U = fminf(1.0f, __expf(ustage[(lane_id * 2 + c) * 8 + m] + M.Lc.log_margin));
-          w.UB(lane_id, c, m) = U;
-          tot += U;
-        }
-        // c_learned = c * mean(U): the cached inverse grows by 8 / sum(U)
-        ic[c] = tot > 0.0f ? ic[c] * 8.0f / tot : 0.0f;
+    float tot[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
+      float U = 0.0f;
+      if ((eval >> e) & 1u) {
+        const int cls = cls_j[j];
+        U = fminf(1.0f, __expf(ustage[r] + mlp.margin[cls * kIsrBins + m]));
+        w.UB(e, c, m) = U;
       }
-      isr_rec.x = ic[0];
-      isr_rec.y = ic[1];
+      // sum over the 8 bins of the (end, channel): 8 consecutive lanes
+      U += __shfl_xor_sync(0xffffffffu, U, 1);
+      U += __shfl_xor_sync(0xffffffffu, U, 2);
+      U += __shfl_xor_sync(0xffffffffu, U, 4);
+      tot[j] = U;
+    }
+    // end e's sums sit in lanes (16 e) % 32 and (16 e + 8) % 32 of row half e / 2
+    const int src0 = (lane_id * 16) & 31, src1 = (lane_id * 16 + 8) & 31;
+    const float a0 = __shfl_sync(0xffffffffu, tot[0], src0), a1 = __shfl_sync(0xffffffffu, tot[1], src0);
+    const float b0 = __shfl_sync(0xffffffffu, tot[0], src1), b1 = __shfl_sync(0xffffffffu, tot[1], src1);
+    if (need) {
+      const float t0 = (lane_id >> 1) ? a1 : a0, t1 = (lane_id >> 1) ? b1 : b0;
+      // c_learned = c * mean(U): the cached inverse grows by 8 / sum(U)
+      w.MScale(lane_id) = make_float2(t0 > 0.0f ? 8.0f / t0 : 0.0f, t1 > 0.0f ? 8.0f / t1 : 0.0f);
+      w.MKey(lane_id) = make_float4(isr_eta, isr_s, code, 0.0f);
+    }
+  }
+  if (mine) {
+    if (use) {
+      const float2 sc = w.MScale(lane_id);
+      isr_rec.x *= sc.x;
+      isr_rec.y *= sc.y;
     } else if (valid) {
       for (int c = 0; c < 2; ++c)
         for (int m = 0; m < 8; ++m) w.UB(lane_id, c, m) = 1.0f;
+      w.MKey(lane_id) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
     }
     w.End(lane_id) = isr_rec;
   }
   __syncwarp();
+  return __popc(eval);
 }
 
 struct Emission {
@@ -534,7 +579,8 @@ struct Counters32 {
 // One max-veto cycle on the working set. Returns the new status.
 __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L, uint64_t id,
                           Counters32& cnt, Emission& pend, bool& parked) {
-  const bool pp = M.P.process != GAPS_EE_QQ;
+  const bool pp = S.pp[L.row] != 0;
+  const float lnTc = S.lnTc[L.row];
   cnt.steps += 1;
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
   const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
@@ -545,7 +591,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   // one overestimate trial per channel of every colour end, in canonical order
   auto trial = [&](const float4& rec, int q) {
     const float lnTmax = fminf(L.lnT, rec.z);
-    const bool live = lnTmax > M.lnTc;
+    const bool live = lnTmax > lnTc;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const float ic = c == 0 ? rec.x : rec.y;  // 1/c
@@ -581,7 +627,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
     k = __float_as_int(w.End(bq).w);
   }
   L.draw = d;
-  if (bi < 0 || best < M.lnTc) return GAPS_STATUS_DONE;
+  if (bi < 0 || best < lnTc) return GAPS_STATUS_DONE;
   uint32_t o1[4], o2[4];
   philox(e0, e1, (uint32_t)L.draw, (uint32_t)(L.draw >> 32), k0, k1, o1);
   philox(e0, e1, (uint32_t)(L.draw + 1), (uint32_t)((L.draw + 1) >> 32), k0, k1, o2);
@@ -613,7 +659,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   channel_over(ch, type, M.P.nf, shape, coefd);
   const float coef = (float)coefd;
   float zm, delta;
-  zlim32(type, __expf(M.lnTc), s, eta, zm, delta);
+  zlim32(type, __expf(lnTc), s, eta, zm, delta);
   // learned bounds: pick the bin from R_z, then zeta inside it
   const bool learned_end = M.Lc.learned && L.learned_ok && ini;
   float zeta = bRz, Um = 1.0f;
@@ -642,7 +688,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   }
   const float pover = shape_val32(shape, coef, z, omz);
   const float as_t = (float)M.P.as_mz / (1.0f + (float)M.P.as_mz * (float)M.P.beta0 * __logf(tw / (float)(kMZ * kMZ)));
-  const float as_ratio = as_t / (M.asOver2pi * 2.0f * (float)kPi);
+  const float as_ratio = as_t / (S.asOver2pi[L.row] * 2.0f * (float)kPi);
   float w8 = 0.0f, y = 0.0f, rho = 0.0f, x = 1.0f, omx = 0.0f, u = 0.0f, omu = 1.0f, v = 0.0f;
   int new_fl_i = fl_i, fl_j = 21;
   float sumF = 0.0f, B = 1.0f;
@@ -725,6 +771,9 @@ __device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, Lane& L,
   L.draw = E.draw[e];
   L.lnT = __logf((float)E.t[e]);
   L.learned_ok = true;
+  L.row = mix_row(M.P, M.first + e);
+  if (M.Lc.learned)
+    for (int q = 0; q < 4; ++q) w.MKey(q) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
   if (L.status != GAPS_STATUS_ACTIVE) return;
   if (L.n < 2 || L.n > M.P.nmax) { L.status = GAPS_ERR_NUMERIC; return; }
   for (int s = 0; s < L.n; ++s) {
@@ -768,7 +817,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem + kMlpSmemBytes);
   float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + kMlpSmemBytes +
                                                       (blockDim.x >> 5) * 64 * 4 * sizeof(float));
-  if (M.Lc.learned) mlp_load_smem(mlp_s, M.Lc.mlp);
+  if (M.Lc.learned) mlp_load_smem(mlp_s, M.Lc.mlp, M.Lc.mlp + kMlpParams);
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
     S.umax[f][ix] = (float)M.P.umax[q];
@@ -780,6 +829,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   }
   for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
     S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  load_rows(S, M.P);
   __syncthreads();
 
   const int lane_id = threadIdx.x & 31;
@@ -793,6 +843,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   Counters32 cnt;
   unsigned long long finished = 0, err_cap = 0, err_iter = 0, err_num = 0;
   unsigned long long lane_steps = 0, warp_steps = 0;
+  unsigned long long rebuilds = 0, mlp_tiles = 0;  // warp-uniform
   int since_refill = M.period;
   bool parked = false;
   Emission pend;
@@ -826,7 +877,10 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const int n_src = __shfl_sync(0xffffffffu, L.n, src);
         const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
         const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
-        rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1, lok, lane_id);
+        const int row_src = __shfl_sync(0xffffffffu, L.row, src);
+        mlp_tiles += rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1,
+                                  row_src, lok, lane_id);
+        rebuilds += 1;
       }
       __syncwarp();
     }
@@ -862,7 +916,10 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const int n_src = __shfl_sync(0xffffffffu, L.n, src);
         const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
         const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
-        rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1, lok, lane_id);
+        const int row_src = __shfl_sync(0xffffffffu, L.row, src);
+        mlp_tiles += rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1,
+                                  row_src, lok, lane_id);
+        rebuilds += 1;
       }
       __syncwarp();
     }
@@ -883,13 +940,14 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
     }
   }
   // counters: warp sums, one atomic per warp and counter
-  unsigned long long v[12] = {finished, cnt.steps, cnt.trials, cnt.isr_trials, cnt.vetoes, cnt.accepts,
+  unsigned long long v[14] = {finished, cnt.steps, cnt.trials, cnt.isr_trials, cnt.vetoes, cnt.accepts,
                               cnt.violations, err_cap, err_iter, err_num,
-                              lane_id == 0 ? lane_steps : 0ull, lane_id == 0 ? warp_steps : 0ull};
-  const int idx[12] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
-                       C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS};
+                              lane_id == 0 ? lane_steps : 0ull, lane_id == 0 ? warp_steps : 0ull,
+                              lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull};
+  const int idx[14] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
+                       C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES};
 #pragma unroll
-  for (int q = 0; q < 12; ++q) {
+  for (int q = 0; q < 14; ++q) {
     unsigned long long x = v[q];
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     if (lane_id == 0 && x) atomicAdd(&M.P.counters[idx[q]], x);
@@ -900,7 +958,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
 
 size_t workset_bytes(int lanes, int nmax) {
   return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
-         (size_t)lanes * 64 * sizeof(float);
+         (size_t)lanes * kLearnedLaneBytes;
 }
 
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
@@ -912,6 +970,10 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
   W.ub = (float*)p;
   p += (size_t)lanes * 64 * sizeof(float);
+  W.mkey = (float4*)p;
+  p += (size_t)lanes * 4 * sizeof(float4);
+  W.mscale = (float2*)p;
+  p += (size_t)lanes * 4 * sizeof(float2);
   W.tag = (uint32_t*)p;
 }
 
@@ -919,9 +981,10 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
 namespace {
 
 // Targets of the learned bound (the "teacher"): for every logged initial-state
-// end, channel and zeta bin, the largest acceptance ratio r over 17 zeta points
-// of the bin and 24 scales t log-spaced in [t_c, t_kin], as ln(max(r, 1e-6)),
+// end, channel and zeta bin, the largest acceptance ratio r over 33 zeta points
+// of the bin and 64 scales t log-spaced in [t_c, t_kin], as ln(max(r, 1e-6)),
 // with the network's input features of the row.
+constexpr int kTeacherZ = 32, kTeacherT = 64;
 __global__ void k_isr_targets(MixedCtx M, const float4* states, uint64_t n_states, float* feats, float* targets) {
   __shared__ SmemPdf S;
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
@@ -956,13 +1019,13 @@ __global__ void k_isr_targets(MixedCtx M, const float4* states, uint64_t n_state
   const float tk = tkin32(type, s, eta);
   if (tk > tc && zlim32(type, tc, s, eta, zm, delta)) {
     const float ltc = __logf(tc), ltk = __logf(tk);
-    for (int a = 0; a <= 16; ++a) {
-      const float zeta = ((float)m + (float)a * (1.0f / 16.0f)) * 0.125f;
+    for (int a = 0; a <= kTeacherZ; ++a) {
+      const float zeta = ((float)m + (float)a * (1.0f / kTeacherZ)) * 0.125f;
       float z, omz;
       shape_sample32(shape, zm, delta, fminf(zeta, 0.99999994f), z, omz);
       const float pover = shape_val32(shape, (float)coefd, z, omz);
-      for (int b = 0; b < 24; ++b) {
-        const float t = __expf(ltc + (ltk - ltc) * ((float)b + 0.5f) * (1.0f / 24.0f));
+      for (int b = 0; b < kTeacherT; ++b) {
+        const float t = __expf(ltc + (ltk - ltc) * ((float)b + 0.5f) * (1.0f / kTeacherT));
         float zm_t, delta_t;
         if (!zlim32(type, t, s, eta, zm_t, delta_t) || !(omz > delta_t) || !(z > zm_t)) continue;
         const IsrEval ev = isr_eval32(M, S, type, ch, fl_i, eta, s, t, z, omz, pover);
@@ -1035,7 +1098,7 @@ constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
 constexpr size_t kStaticWorkBytes =
     (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
-    (size_t)kStaticLanes * 64 * sizeof(float);
+    (size_t)kStaticLanes * kLearnedLaneBytes;
 
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
 static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];
@@ -1131,6 +1194,7 @@ extern "C" int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, 
     stats->violations = h[C_VIOLATIONS]; stats->err_capacity = h[C_ERR_CAP];
     stats->err_iter_cap = h[C_ERR_ITER]; stats->err_numeric = h[C_ERR_NUM];
     stats->lane_steps = h[C_LANE_STEPS]; stats->warp_steps = h[C_WARP_STEPS];
+    stats->rebuilds = h[C_REBUILDS]; stats->mlp_tiles = h[C_MLP_TILES];
   }
   return GAPS_OK;
 }

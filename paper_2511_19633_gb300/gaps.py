@@ -31,6 +31,14 @@ GAPS_STATUS_ACTIVE, GAPS_STATUS_DONE = 0, 1
 GAPS_NOBS, GAPS_NHIST, GAPS_HIST_BINS = 8, 6, 66
 
 
+GAPS_MAX_MIX = 4
+
+
+class GapsMixRow(ctypes.Structure):
+    _fields_ = [("process", ctypes.c_int), ("sqrt_s", ctypes.c_double), ("t_cut", ctypes.c_double),
+                ("fraction", ctypes.c_double)]
+
+
 class GapsConfig(ctypes.Structure):
     _fields_ = [
         ("process", ctypes.c_int), ("precision", ctypes.c_int), ("nf", ctypes.c_int),
@@ -39,6 +47,7 @@ class GapsConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("pdf_grid", ctypes.c_void_p), ("block_size", ctypes.c_int),
         ("schedule", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
         ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
+        ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX),
     ]
 
 
@@ -57,7 +66,8 @@ class GapsHists(ctypes.Structure):
 
 
 STAT_FIELDS = ("events", "steps", "trials", "isr_trials", "vetoes", "accepts", "violations",
-               "err_capacity", "err_iter_cap", "err_numeric", "lane_steps", "warp_steps")
+               "err_capacity", "err_iter_cap", "err_numeric", "lane_steps", "warp_steps", "rebuilds",
+               "mlp_tiles")
 
 
 class GapsStats(ctypes.Structure):
@@ -66,11 +76,13 @@ class GapsStats(ctypes.Structure):
 
 GAPS_MLP_PARAMS = 4545
 GAPS_ISR_BINS = 8
+GAPS_ISR_CLASSES = 44
 
 EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
            "gaps_destroy", "gaps_shower_static", "gaps_collect_isr_states", "gaps_isr_targets",
-           "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train")
+           "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train",
+           "gaps_process", "gaps_process_shower_ms")
 
 
 class GapsError(RuntimeError):
@@ -88,7 +100,9 @@ def _load():
     lib.gaps_init.argtypes = [P(vp), P(GapsConfig)]
     lib.gaps_generate_hard.argtypes = [vp, u64, u64, P(GapsEvents), vp]
     lib.gaps_shower.argtypes = [vp, u64, u64, P(GapsEvents), vp]
-    lib.gaps_observables.argtypes = [vp, u64, P(GapsEvents), vp, P(GapsHists), vp]
+    lib.gaps_observables.argtypes = [vp, u64, u64, P(GapsEvents), vp, P(GapsHists), vp]
+    lib.gaps_process.argtypes = [vp, u64, u64, P(GapsEvents), vp, vp, P(GapsHists), vp]
+    lib.gaps_process_shower_ms.argtypes = [vp, vp, i]
     d = ctypes.POINTER(ctypes.c_double)
     ip = ctypes.POINTER(ctypes.c_int)
     lib.gaps_hist_binning.argtypes = [vp, i, d, d, ip, ip, ip]
@@ -102,7 +116,7 @@ def _load():
     f = ctypes.c_float
     lib.gaps_collect_isr_states.argtypes = [vp, u64, u64, P(GapsEvents), vp, u64, vp, vp]
     lib.gaps_isr_targets.argtypes = [vp, vp, u64, vp, vp, vp]
-    lib.gaps_set_learned_proposal.argtypes = [vp, vp, f]
+    lib.gaps_set_learned_proposal.argtypes = [vp, vp, vp]
     lib.gaps_mlp_loss_grad.argtypes = [vp, vp, vp, u64, f, vp, vp, vp]
     lib.gaps_mlp_forward.argtypes = [vp, vp, u64, i, vp, vp]
     lib.gaps_mlp_train.argtypes = [vp, vp, vp, vp, vp, u64, u64, f, f, u64, vp, i, vp]
@@ -174,15 +188,17 @@ def gaps_isr_targets(ctx, states: torch.Tensor, n_states: int, features: torch.T
                                  targets.data_ptr(), _stream_ptr(stream)), "gaps_isr_targets")
 
 
-def gaps_set_learned_proposal(ctx, params, log_margin: float = 0.0):
-    """params: host float32 array of GAPS_MLP_PARAMS (copied) or None."""
-    if params is None:
-        _check(_lib.gaps_set_learned_proposal(ctx, None, log_margin), "gaps_set_learned_proposal")
-        return
+def gaps_set_learned_proposal(ctx, params, log_margins=0.0):
+    """params: host float32 array of GAPS_MLP_PARAMS (copied) or None;
+    log_margins: [GAPS_ISR_CLASSES][GAPS_ISR_BINS] (or a scalar, broadcast)."""
     import numpy as np
+    if params is None:
+        _check(_lib.gaps_set_learned_proposal(ctx, None, None), "gaps_set_learned_proposal")
+        return
     p = np.ascontiguousarray(params, dtype=np.float32)
-    _check(_lib.gaps_set_learned_proposal(ctx, p.ctypes.data, float(log_margin)),
-           "gaps_set_learned_proposal")
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(log_margins, dtype=np.float32),
+                                             (GAPS_ISR_CLASSES, GAPS_ISR_BINS)))
+    _check(_lib.gaps_set_learned_proposal(ctx, p.ctypes.data, m.ctypes.data), "gaps_set_learned_proposal")
 
 
 def gaps_mlp_loss_grad(params: torch.Tensor, features: torch.Tensor, targets: torch.Tensor, tau: float,
@@ -206,11 +222,32 @@ def gaps_mlp_train(params, adam_m, adam_v, features, targets, steps: int, lr: fl
                                _stream_ptr(stream)), "gaps_mlp_train")
 
 
-def gaps_observables(ctx, n: int, ev: GapsEvents, obs: torch.Tensor | None,
+def gaps_observables(ctx, first_event: int, n: int, ev: GapsEvents, obs: torch.Tensor | None,
                      hists: GapsHists | None, stream=None):
-    _check(_lib.gaps_observables(ctx, n, ctypes.byref(ev), None if obs is None else obs.data_ptr(),
+    _check(_lib.gaps_observables(ctx, first_event, n, ctypes.byref(ev), None if obs is None else obs.data_ptr(),
                                  None if hists is None else ctypes.byref(hists), _stream_ptr(stream)),
            "gaps_observables")
+
+
+def gaps_process(ctx, first_event: int, n: int, ev: GapsEvents, obs_dev: torch.Tensor | None = None,
+                 obs_host: torch.Tensor | None = None, hists: GapsHists | None = None, stream=None):
+    """Whole path over n events in chunks of ev.capacity, as one CUDA graph.
+    obs_dev: float64 [GAPS_NOBS, capacity] device; obs_host: pinned float64
+    [GAPS_NOBS, n]."""
+    _check(_lib.gaps_process(ctx, first_event, n, ctypes.byref(ev),
+                             None if obs_dev is None else obs_dev.data_ptr(),
+                             None if obs_host is None else obs_host.data_ptr(),
+                             None if hists is None else ctypes.byref(hists), _stream_ptr(stream)),
+           "gaps_process", "gaps_process_shower_ms")
+
+
+def gaps_process_shower_ms(ctx, max_chunks: int = 4096) -> list:
+    """Per-chunk shower durations (ms) of the last gaps_process call."""
+    buf = (ctypes.c_float * max_chunks)()
+    k = _lib.gaps_process_shower_ms(ctx, buf, max_chunks)
+    if k < 0:
+        _check(k, "gaps_process_shower_ms")
+    return [float(buf[c]) for c in range(k)]
 
 
 def gaps_hist_binning(ctx, h: int) -> dict:
@@ -299,9 +336,18 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 alpha_s_mz: float = 0.118, nf: int = 5, nmax: int = 128, seed: int = 1,
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
-                refill_period: int = 0, emit_batch: int = 0) -> GapsConfig:
+                refill_period: int = 0, emit_batch: int = 0, mix=None) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
-    must stay alive until gaps_init returns (it is copied)."""
+    must stay alive until gaps_init returns (it is copied). mix: optional list of
+    (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
+    process, sqrt_s and t_cut."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
-    return GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
-                      block_size, schedule, blocks_per_sm, refill_period, emit_batch)
+    c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
+                   block_size, schedule, blocks_per_sm, refill_period, emit_batch)
+    if mix:
+        if len(mix) > GAPS_MAX_MIX:
+            raise ValueError("at most %d rows" % GAPS_MAX_MIX)
+        c.n_mix = len(mix)
+        for k, (pr, rs, tc, fr) in enumerate(mix):
+            c.mix[k] = GapsMixRow(int(pr), float(rs), float(tc), float(fr))
+    return c

@@ -8,7 +8,8 @@
    4 -> 64 -> 64 -> 1 network with an expectile loss that keeps it above its
    targets;
 4. calibrate: the BF16 tensor-core numerics of the shower are evaluated on all
-   rows and the margin is set so that every row is covered;
+   rows of the training states and of held-out states, and a margin per
+   (class, bin) is set so that every row is covered;
 5. install: gaps_set_learned_proposal.
 The shower checks every acceptance weight; the violation count it reports
 decides whether the learned run equals the plain algorithm.
@@ -52,13 +53,25 @@ def collect_states(ctx, first_event: int, n_events: int, capacity: int, chunk: i
     return states[: min(int(count.item()), capacity)]
 
 
+# targets below ln(1e-4) are raised to it: a higher target is still an upper
+# bound, and bins that small are rarely proposed
+TARGET_FLOOR = math.log(1e-4)
+
+
 def make_dataset(ctx, states: torch.Tensor, stream=None):
     n = states.shape[0]
     feats = torch.zeros((n * 16, 4), dtype=torch.float32, device="cuda")
     targ = torch.zeros(n * 16, dtype=torch.float32, device="cuda")
     G.gaps_isr_targets(ctx, states, n, feats, targ, stream)
     torch.cuda.synchronize()
-    return feats, targ
+    return feats, torch.clamp(targ, min=TARGET_FLOOR)
+
+
+def row_class_bin(feats: torch.Tensor) -> torch.Tensor:
+    """Class * 8 + bin of every row, recovered from its input features."""
+    cls = torch.round((feats[:, 3] + 1.0) * 21.5).long()
+    m = torch.round((feats[:, 2] + 1.0) * 4.0 - 0.5).long()
+    return cls * G.GAPS_ISR_BINS + m
 
 
 def train(feats: torch.Tensor, targ: torch.Tensor, steps: int = 40000, lr: float = 2e-3, tau: float = 0.97,
@@ -78,29 +91,44 @@ def train(feats: torch.Tensor, targ: torch.Tensor, steps: int = 40000, lr: float
     return P, hist.cpu().numpy()
 
 
-def calibrate(P: torch.Tensor, feats: torch.Tensor, targ: torch.Tensor, slack: float = 0.02) -> dict:
-    """Margin so that exp(NN + margin) >= exp(target) on every row, with the
-    shower's BF16 inference numerics."""
-    out = torch.zeros_like(targ)
-    G.gaps_mlp_forward(P, feats, out, True)
+def calibrate(P: torch.Tensor, sets, slack: float = 0.1, unseen: float = 30.0) -> dict:
+    """Margins per (class, bin) so that exp(NN + margin) >= exp(target) on every
+    row of every (features, targets) set, with the shower's BF16 inference
+    numerics, times (1 + slack). (class, bin) cells without rows get `unseen`
+    (height 1, the plain bound)."""
+    ncell = G.GAPS_ISR_CLASSES * G.GAPS_ISR_BINS
+    gap = torch.full((ncell,), -float("inf"), device="cuda")
+    outs = []
+    for feats, targ in sets:
+        out = torch.zeros_like(targ)
+        G.gaps_mlp_forward(P, feats, out, True)
+        cell = row_class_bin(feats)
+        gap = gap.scatter_reduce(0, cell, targ - out, reduce="amax")
+        outs.append((out, cell, targ))
     torch.cuda.synchronize()
-    gap = (targ - out)
-    margin = float(gap.max().item()) + math.log(1.0 + slack)
-    # how much the learned heights shrink the plain overestimate on the sample
-    U = torch.clamp(torch.exp(out + margin), max=1.0)
-    return {"log_margin": margin, "mean_bin_height": float(U.mean().item()),
+    seen = torch.isfinite(gap)
+    margins = torch.where(seen, gap + math.log(1.0 + slack), torch.full_like(gap, unseen))
+    # how much the learned heights shrink the plain overestimate on the first set
+    out, cell, targ = outs[0]
+    U = torch.clamp(torch.exp(out + margins[cell]), max=1.0)
+    return {"log_margins": margins.view(G.GAPS_ISR_CLASSES, G.GAPS_ISR_BINS).cpu().numpy(),
+            "mean_bin_height": float(U.mean().item()), "cells_seen": int(seen.sum().item()),
             "rows": int(targ.shape[0]), "fit_rmse": float(torch.sqrt(torch.mean((out - targ) ** 2)).item())}
 
 
 def train_and_install(ctx, first_event: int = 3 << 40, n_events: int = 1 << 20, capacity: int = 1 << 20,
-                      steps: int = 40000) -> dict:
+                      steps: int = 40000, holdout_events: int = 1 << 20) -> dict:
     """Collects shower states (seed offset by first_event), trains, calibrates
-    and installs the network in ctx. Returns a summary."""
+    on the training rows and on held-out states of other events, and installs
+    the network in ctx. Returns a summary."""
     states = collect_states(ctx, first_event, n_events, capacity)
     feats, targ = make_dataset(ctx, states)
     P, hist = train(feats, targ, steps=steps)
-    cal = calibrate(P, feats, targ)
-    G.gaps_set_learned_proposal(ctx, P.cpu().numpy(), cal["log_margin"])
-    return {"states": int(states.shape[0]), "rows": int(feats.shape[0]), "loss_first": float(hist[0]),
+    held = collect_states(ctx, first_event + (1 << 36), holdout_events, capacity)
+    hf, ht = make_dataset(ctx, held)
+    cal = calibrate(P, [(feats, targ), (hf, ht)])
+    G.gaps_set_learned_proposal(ctx, P.cpu().numpy(), cal["log_margins"])
+    return {"states": int(states.shape[0]), "rows": int(feats.shape[0]), "holdout_states": int(held.shape[0]),
+            "loss_first": float(hist[0]),
             "loss_last": float(hist[hist > 0][-1]) if np.any(hist > 0) else None, **cal,
             "params": P.cpu().numpy()}

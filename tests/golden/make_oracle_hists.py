@@ -32,11 +32,15 @@ BINNING = {
 }
 NBINS = 66
 
+# name: (process, sqrt_s, events, t_cut)
 WORKLOADS = {
-    "ee91": (0, 91.2, 1_000_000),
-    "ee500": (0, 500.0, 1_000_000),
-    "pp_lo": (1, 13600.0, 1_000_000),
-    "pp_nlo": (2, 13600.0, 10_000_000),
+    "ee91": (0, 91.2, 1_000_000, 1.0),
+    "ee500": (0, 500.0, 1_000_000, 1.0),
+    "pp_lo": (1, 13600.0, 1_000_000, 1.0),
+    "pp_nlo": (2, 13600.0, 10_000_000, 1.0),
+    # the e+e- rows of the mixed batch (their own cutoffs)
+    "ee91_tc0.5": (0, 91.2, 1_000_000, 0.5),
+    "ee500_tc4": (0, 500.0, 1_000_000, 4.0),
 }
 SEED = 2
 
@@ -69,12 +73,12 @@ def fill(hsum, hsum2, obs, w, family):
 def make(name: str, threads: int, n_override: int | None = None) -> dict:
     from oracle import oracle as O
     from paper_2511_19633_gb300 import inputs
-    process, sqrt_s, n = WORKLOADS[name]
+    process, sqrt_s, n, t_cut = WORKLOADS[name]
     if n_override:
         n = n_override
     pdf = inputs.synthetic_pdf_grid()
     family = "ee" if process == 0 else "pp"
-    st = O.Settings(process=process, sqrt_s=sqrt_s, nmax=128, seed=SEED)
+    st = O.Settings(process=process, sqrt_s=sqrt_s, t_cut=t_cut, nmax=128, seed=SEED)
     hsum = np.zeros((6, NBINS))
     hsum2 = np.zeros((6, NBINS))
     counters = np.zeros(6, dtype=np.int64)
@@ -88,7 +92,7 @@ def make(name: str, threads: int, n_override: int | None = None) -> dict:
         bad += int((~done).sum())
         fill(hsum, hsum2, r["obs"][done], r["weight"][done], family)
         counters += r["counters"].astype(np.int64).sum(0)
-    return {"workload": name, "process": process, "sqrt_s": sqrt_s, "events": n, "seed": SEED,
+    return {"workload": name, "process": process, "sqrt_s": sqrt_s, "t_cut": t_cut, "events": n, "seed": SEED,
             "not_done": bad, "binning": BINNING[family], "sumw": hsum.tolist(), "sumw2": hsum2.tolist(),
             "oracle_counters": dict(zip(("steps", "trials", "isr_trials", "vetoes", "accepts",
                                          "violations"), counters.tolist())),

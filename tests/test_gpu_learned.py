@@ -127,7 +127,7 @@ def _shower_hists(G, pdf, params, margin, n, first=0, chunk=1 << 21):
             m = min(cap, n - f0)
             G.gaps_generate_hard(ctx, first + f0, m, ev)
             G.gaps_shower(ctx, first + f0, m, ev)
-            G.gaps_observables(ctx, m, ev, None, hists)
+            G.gaps_observables(ctx, first + f0, m, ev, None, hists)
         torch.cuda.synchronize()
         st = G.gaps_get_stats(ctx)
     finally:
@@ -139,7 +139,7 @@ def test_learned_proposal_is_exact_and_cheaper(G, pdf, trained):
     """Same events, learned vs plain bounds: no violation, fewer cycles and
     trials; distributions agree (chi^2/ndf < 1.2)."""
     n = 1_000_000
-    wl, wl2, sl = _shower_hists(G, pdf, trained["params"], trained["log_margin"], n)
+    wl, wl2, sl = _shower_hists(G, pdf, trained["params"], trained["log_margins"], n)
     wp, wp2, sp = _shower_hists(G, pdf, None, 0.0, n)
     assert sl["violations"] == 0 and sl["events"] == n
     assert sl["steps"] < sp["steps"] and sl["trials"] < sp["trials"]
@@ -150,7 +150,7 @@ def test_learned_proposal_is_exact_and_cheaper(G, pdf, trained):
 def test_learned_histograms_match_oracle_at_1e7(G, pdf, trained):
     gold = load_golden("pp_nlo")
     n = gold["events"]
-    w, w2, st = _shower_hists(G, pdf, trained["params"], trained["log_margin"], n)
+    w, w2, st = _shower_hists(G, pdf, trained["params"], trained["log_margins"], n)
     assert st["violations"] == 0 and st["events"] == n
     red, _, _ = chi2_summary(chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"]))
     assert red < 1.2, red

@@ -93,7 +93,7 @@ def _gpu_hists(G, name, pdf, precision, n, chunk=1 << 21):
             m = min(cap, n - first)
             G.gaps_generate_hard(ctx, first, m, ev)
             G.gaps_shower(ctx, first, m, ev)
-            G.gaps_observables(ctx, m, ev, None, hists)
+            G.gaps_observables(ctx, first, m, ev, None, hists)
         torch.cuda.synchronize()
         binning = [G.gaps_hist_binning(ctx, h) for h in range(G.GAPS_NHIST)]
         stats = G.gaps_get_stats(ctx)
