@@ -87,7 +87,8 @@ def dist_env():
 
 def rank_first_event(rank: int, step: int, events_per_step: int, steps_total: int) -> int:
     """Event range of (rank, step): ranks own disjoint contiguous blocks."""
-    return (rank * steps_total + step) * events_per_step
+    from paper_2511_19633_gb300.sharding import rank_first_event as first
+    return first(rank, step, events_per_step, steps_total)
 
 
 class ClockSampler:
@@ -354,9 +355,8 @@ def run_ours(args, ws, rank, local):
     ms = start.elapsed_time(stop)
     stats = G.gaps_get_stats(ctx, stream)
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2511_19633_gb300.sharding import max_over_ranks
+        ms = max_over_ranks(ms, dist, device="cuda")
     value = total * args.steps * ws / (ms / 1e3)
     launches = 3 * n_chunks * args.steps  # hard, shower and observables kernels per chunk
 
