@@ -99,9 +99,12 @@ static __device__ __noinline__ void mlp_tile(const MlpSmem& S, const float (*fea
     A1[j][2] = pack_bf16(fmaxf(h[1][0], 0.0f), fmaxf(h[1][1], 0.0f));
     A1[j][3] = pack_bf16(fmaxf(h[1][2], 0.0f), fmaxf(h[1][3], 0.0f));
   }
-  // layers 2 and 3: N = 8 for layer 3 (column 0 is the output), K = 64
+  // layers 2 and 3: N = 8 for layer 3 (column 0 is the output), K = 64. The
+  // k-step loop of layer 3 stays rolled: the tile runs inside the shower's
+  // warp-cooperative rebuild, where instruction-cache footprint costs more
+  // than the loop overhead.
   float o[4] = {S.b3, S.b3, S.b3, S.b3};
-#pragma unroll
+#pragma unroll 1
   for (int j3 = 0; j3 < 4; ++j3) {
     float h[2][4];
 #pragma unroll
