@@ -62,6 +62,8 @@ extern "C" {
 /* launch schedules of the shower */
 #define GAPS_SCHED_PER_EVENT  0   /* one thread per event, run to completion */
 #define GAPS_SCHED_PERSISTENT 1   /* persistent grid, finished lanes take the next event */
+#define GAPS_SCHED_WARP       2   /* GAPS_MIXED only: persistent grid, one event per warp
+                                     in shared memory, the lanes share its trials */
 
 /* per-event status values; negative values are the error codes above */
 #define GAPS_STATUS_ACTIVE 0
@@ -113,7 +115,7 @@ typedef struct {
     uint64_t seed;        /* Philox key */
     const float* pdf_grid;/* host pointer to the PDF grid (pp processes), copied */
     int block_size;       /* threads per block for the shower, 0 = library default */
-    int schedule;         /* GAPS_SCHED_PER_EVENT or GAPS_SCHED_PERSISTENT */
+    int schedule;         /* GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT or GAPS_SCHED_WARP */
     int blocks_per_sm;    /* persistent schedule: resident blocks per SM, 0 = default */
     int refill_period;    /* GAPS_MIXED: idle lanes take new events at most every
                              this many cycles (compaction period), 0 = 1 */
@@ -238,14 +240,19 @@ int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
  * (22..43): q <- q for the ten quark PDF indices 1..10 (d u s c b, then the
  * antiquarks), g <- q for the same ten, g <- g, q <- g */
 #define GAPS_ISR_CLASSES 44
+/* buckets of eta for the calibration margins: upper edges eta = 1e-5, 1e-4,
+ * 1e-3, 1e-2, 0.1, 0.4, 0.7 (compared on the network input ln(eta)/7 + 1) */
+#define GAPS_ISR_ETA_BINS 8
 
 /* Runs the GAPS_MIXED shower with the plain bounds and logs the initial-state
- * colour ends met at every rebuild of an event's end table: states is a
- * device array [capacity][4] of {eta, s, dipole type (2 IF, 3 II), PDF index
- * of the emitter}; *count (device) is incremented per logged end, also past
- * capacity. Requires a pp process and GAPS_MIXED. */
+ * colour ends met at every rebuild of an event's end table, each with
+ * probability keep_fraction in (0, 1] (decided by a hash of the event id, its
+ * parton count and the end, so that a bounded log samples the whole run):
+ * states is a device array [capacity][4] of {eta, s, dipole type (2 IF,
+ * 3 II), PDF index of the emitter}; *count (device) is incremented per
+ * logged end, also past capacity. Requires one pp process and GAPS_MIXED. */
 int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
-                            const gaps_events* ev, float* states,
+                            const gaps_events* ev, float keep_fraction, float* states,
                             uint64_t capacity, uint64_t* count, void* stream);
 
 /* Training targets of the learned bound: for each logged state, channel and
@@ -258,11 +265,18 @@ int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states,
 
 /* Installs a trained network (host array of GAPS_MLP_PARAMS floats, copied)
  * and the calibration margins added to its output, a host array
- * log_margins[GAPS_ISR_CLASSES][GAPS_ISR_BINS] (copied): the height of bin m
- * of class c is min(1, exp(NN + log_margins[c][m])). Later GAPS_MIXED showers
- * of the context use them. params == NULL returns to the plain bounds.
- * Non-finite values give GAPS_ERR_INVALID_ARG. */
+ * log_margins[GAPS_ISR_CLASSES][GAPS_ISR_ETA_BINS][GAPS_ISR_BINS] (copied):
+ * the height of bin m of class c at eta bucket b is
+ * min(1, exp(NN + log_margins[c][b][m])), rounded up to a power 2^(-k/16).
+ * Later GAPS_MIXED showers of the context use them. params == NULL returns
+ * to the plain bounds. Non-finite values give GAPS_ERR_INVALID_ARG. */
 int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* log_margins);
+
+/* Violation log of the learned proposal (device arrays, caller-owned; log ==
+ * NULL switches it off): every acceptance weight above one met with the learned
+ * bounds appends 8 floats {eta, s, t, w, class, bin, z, zeta} to
+ * log[capacity][8] and increments *count (also past capacity). */
+int gaps_set_violation_log(gaps_ctx* ctx, float* log, uint64_t capacity, uint64_t* count);
 
 /* Network kernels (device arrays; features [n][4]):
  * gaps_mlp_loss_grad: expectile loss mean w (y - t)^2, w = tau below the

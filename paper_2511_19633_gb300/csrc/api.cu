@@ -19,6 +19,9 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
 cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, const LearnedCfg&, uint64_t,
                                 uint64_t, int, int, int, int, int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_isr_targets(const DevParams&, int, const float4*, uint64_t, float*, float*, cudaStream_t);
+cudaError_t mixed_kernels_init();
+cudaError_t launch_shower_warp(const DevParams&, const DevEvents&, const LearnedCfg&, uint64_t, uint64_t, int, int,
+                               int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
                                const HistSet&, double*, double*, int, cudaStream_t);
 }  // namespace gaps
@@ -39,6 +42,9 @@ struct gaps_ctx {
   size_t work_bytes = 0;
   float* d_mlp = nullptr;    // learned-proposal network (FP32 parameters)
   int learned = 0;
+  float* vlog = nullptr;     // caller's violation log (device), capacity, counter
+  uint64_t vcap = 0;
+  uint64_t* vcount = nullptr;
   // gaps_process: capture stream and the instantiated graph of the last call
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -118,7 +124,9 @@ int validate_config(const gaps_config& c) {
   if (c.process == GAPS_PP_Z_NLO && !(c.p_s > 0.0 && c.p_s < 1.0)) return GAPS_ERR_INVALID_ARG;
   if (c.process != GAPS_EE_QQ && !c.pdf_grid) return GAPS_ERR_INVALID_ARG;
   if (c.block_size < 0 || c.block_size > 1024 || (c.block_size % 32) != 0) return GAPS_ERR_INVALID_ARG;
-  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT) return GAPS_ERR_INVALID_ARG;
+  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT && c.schedule != GAPS_SCHED_WARP)
+    return GAPS_ERR_INVALID_ARG;
+  if (c.schedule == GAPS_SCHED_WARP && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
   if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
   if (c.emit_batch < 0 || c.emit_batch > 32) return GAPS_ERR_INVALID_ARG;
@@ -273,6 +281,7 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
                                    cudaMemcpyHostToDevice)))) break;
     if ((rc = cuda_fail(cudaMalloc(&ctx->d_counters, (C_NCOUNTERS + 1) * sizeof(unsigned long long))))) break;
     if ((rc = cuda_fail(cudaMemset(ctx->d_counters, 0, (C_NCOUNTERS + 1) * sizeof(unsigned long long))))) break;
+    if ((rc = cuda_fail(mixed_kernels_init()))) break;
   } while (false);
   if (rc != GAPS_OK) {
     gaps_destroy(ctx);
@@ -339,6 +348,16 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
     for (int r = 0; r < ctx->P.n_rows; ++r) any_pp = any_pp || ctx->P.rows[r].process != GAPS_EE_QQ;
     Lc.learned = ctx->learned && ctx->d_mlp && any_pp;
     Lc.mlp = ctx->d_mlp;
+    Lc.vlog = reinterpret_cast<float4*>(ctx->vlog);
+    Lc.vcount = reinterpret_cast<unsigned long long*>(ctx->vcount);
+    Lc.vcap = ctx->vcap;
+    if (c.schedule == GAPS_SCHED_WARP) {
+      const int bs = c.block_size > 0 ? c.block_size : 128;
+      const int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 2;
+      return cuda_fail(launch_shower_warp(ctx->P, dev_events(ev), Lc, first_event, n, ctx->n_sm * per_sm, bs,
+                                          per_sm, ctx->q_independent, ctx->d_counters + C_NCOUNTERS,
+                                          (cudaStream_t)stream));
+    }
     return shower_mixed(ctx, first_event, n, ev, Lc, stream);
   }
   int bs = c.block_size > 0 ? c.block_size : 128;
@@ -352,14 +371,17 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
 }
 
 int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
-                            float* states, uint64_t capacity, uint64_t* count, void* stream) {
+                            float keep_fraction, float* states, uint64_t capacity, uint64_t* count,
+                            void* stream) {
   if (!ctx || !events_ok(ctx, ev, n) || !states || !count) return GAPS_ERR_INVALID_ARG;
+  if (!(keep_fraction > 0.0f && keep_fraction <= 1.0f)) return GAPS_ERR_INVALID_ARG;
   if (ctx->cfg.n_mix > 0 || ctx->cfg.process == GAPS_EE_QQ || ctx->cfg.precision != GAPS_MIXED)
     return GAPS_ERR_INVALID_ARG;
   LearnedCfg Lc{};
   Lc.collect = reinterpret_cast<float4*>(states);
   Lc.collect_count = reinterpret_cast<unsigned long long*>(count);
   Lc.collect_cap = capacity;
+  Lc.collect_keep = keep_fraction >= 1.0f ? 0xFFFFFFFFu : (uint32_t)((double)keep_fraction * 4294967296.0);
   return shower_mixed(ctx, first_event, n, ev, Lc, stream);
 }
 
@@ -378,7 +400,7 @@ int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* l
     return GAPS_OK;
   }
   if (!log_margins) return GAPS_ERR_INVALID_ARG;
-  constexpr int nm = GAPS_ISR_CLASSES * GAPS_ISR_BINS;
+  constexpr int nm = GAPS_ISR_CLASSES * GAPS_ISR_ETA_BINS * GAPS_ISR_BINS;
   for (int q = 0; q < GAPS_MLP_PARAMS; ++q)
     if (!std::isfinite(params[q])) return GAPS_ERR_INVALID_ARG;
   for (int q = 0; q < nm; ++q)
@@ -391,6 +413,14 @@ int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* l
       cudaSuccess)
     return GAPS_ERR_CUDA;
   ctx->learned = 1;
+  return GAPS_OK;
+}
+
+int gaps_set_violation_log(gaps_ctx* ctx, float* log, uint64_t capacity, uint64_t* count) {
+  if (!ctx || (log && !count)) return GAPS_ERR_INVALID_ARG;
+  ctx->vlog = log;
+  ctx->vcap = log ? capacity : 0;
+  ctx->vcount = log ? count : nullptr;
   return GAPS_OK;
 }
 
@@ -411,7 +441,7 @@ int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_eve
   const uint64_t cap = ev->capacity;
   if (!events_ok(ctx, ev, n < cap ? n : cap)) return GAPS_ERR_INVALID_ARG;
   // everything the launches need is allocated before the capture
-  if (ctx->cfg.precision == GAPS_MIXED) {
+  if (ctx->cfg.precision == GAPS_MIXED && ctx->cfg.schedule != GAPS_SCHED_WARP) {
     int blocks, bs;
     WorkSet W;
     const int rc = ensure_workset(ctx, blocks, bs, W);

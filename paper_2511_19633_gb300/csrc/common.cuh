@@ -55,12 +55,11 @@ struct WorkSet {
   double* p;
   uint32_t* tag;
   float4* end;
-  float* ub;     // learned bin heights [4 ends][2 channels][8 bins][lanes]
-  float4* mkey;  // inputs of the last evaluation per end {eta, s, class code, -} [4][lanes]
-  float2* mscale;// 8 / sum of the heights per end and channel [4][lanes]
+  float4* mkey;  // learned proposal: inputs of the last evaluation per end {eta, s, class code, -} [4][lanes]
+  float2* mscale;// learned proposal: 8 / sum of the heights per end and channel [4][lanes]
   int lanes;
 };
-constexpr size_t kLearnedLaneBytes = 64 * sizeof(float) + 4 * sizeof(float4) + 4 * sizeof(float2);
+constexpr size_t kLearnedLaneBytes = 4 * sizeof(float4) + 4 * sizeof(float2);
 
 // learned initial-state proposal and sample collection of one launch
 struct LearnedCfg {
@@ -69,6 +68,10 @@ struct LearnedCfg {
   float4* collect;                // logged initial-state ends {eta, s, type, pdf index}
   unsigned long long* collect_count;
   uint64_t collect_cap;
+  uint32_t collect_keep;          // a state is logged when its 32-bit hash is below this
+  float4* vlog;                   // violations of the learned bound: 2 float4 per entry
+  unsigned long long* vcount;
+  uint64_t vcap;
 };
 
 // host helpers shared by the entry points (api.cu); none allocates memory

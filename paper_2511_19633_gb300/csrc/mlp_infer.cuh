@@ -14,7 +14,16 @@ namespace gaps {
 
 constexpr int kMlpIn = 4, kMlpH = 64;
 constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;
-constexpr int kIsrClasses = 44, kIsrBins = 8;
+constexpr int kIsrClasses = 44, kIsrBins = 8, kEtaBins = 8;
+// buckets of the first network input f0 = ln(eta)/7 + 1 for the calibration
+// margins; the upper edges are eta = 1e-5, 1e-4, 1e-3, 1e-2, 0.1, 0.4, 0.7
+__device__ __forceinline__ int eta_bucket(float f0) {
+  const float edge[kEtaBins - 1] = {-0.6447f, -0.3158f, 0.0132f, 0.3421f, 0.6711f, 0.8691f, 0.9490f};
+  int b = 0;
+#pragma unroll
+  for (int k = 0; k < kEtaBins - 1; ++k) b += f0 >= edge[k] ? 1 : 0;
+  return b;
+}
 
 // shared-memory image, weights stored [n][k] so that the B fragment of
 // m16n8k16 (k = 2t, 2t+1 and 2t+8, 2t+9 of column n = g) is two 32-bit loads.
@@ -26,13 +35,11 @@ struct MlpSmem {
   __nv_bfloat16 w2[kMlpH][kMlpH + kPad];
   __nv_bfloat16 w3[8][kMlpH + kPad];      // output row 0; rows 1..7 zero
   float b1[kMlpH], b2[kMlpH], b3;
-  float margin[kIsrClasses * kIsrBins];  // calibration margins (shower only)
 };
 constexpr size_t kMlpSmemBytes = (sizeof(MlpSmem) + 15) / 16 * 16;
 
-// cooperative fill of the image from FP32 parameters and, when not NULL, the
-// calibration margins (all threads of a block)
-__device__ inline void mlp_load_smem(MlpSmem& S, const float* P, const float* margins = nullptr) {
+// cooperative fill of the image from FP32 parameters (all threads of a block)
+__device__ inline void mlp_load_smem(MlpSmem& S, const float* P) {
   const float* W1 = P;
   const float* b1 = W1 + kMlpH * kMlpIn;
   const float* W2 = b1 + kMlpH;
@@ -50,7 +57,6 @@ __device__ inline void mlp_load_smem(MlpSmem& S, const float* P, const float* ma
   }
   for (int q = threadIdx.x; q < kMlpH; q += blockDim.x) { S.b1[q] = b1[q]; S.b2[q] = b2[q]; }
   if (threadIdx.x == 0) S.b3 = W3[kMlpH];
-  for (int q = threadIdx.x; q < kIsrClasses * kIsrBins; q += blockDim.x) S.margin[q] = margins ? margins[q] : 0.0f;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

@@ -14,7 +14,11 @@
 //   end  f32x4 [2 nmax][L]   the event's colour ends in canonical order
 //                             (emitter ascending, colour side first):
 //                             {1/c0, 1/c1, ln t_kin, emitter | side << 8 | partner << 16}
-//   ub   f32 [4][2][8][L]     learned bin heights of the initial-state ends
+//   mkey f32x4 [4][L], mscale f32x2 [4][L]   learned proposal: the network
+//                             inputs of the last evaluation per initial-state
+//                             end and the resulting coefficient scales
+// (the learned bin heights themselves live in shared memory, one 8-bit code
+// per bin, next to the lanes that read them)
 // `end` caches the inverse overestimate coefficients of the end's channels
 // (< 0: channel absent, 0: no phase space) and is rebuilt after every
 // accepted emission.
@@ -22,7 +26,8 @@
 // Learned initial-state proposal: for the ends of the two incoming partons
 // the overestimate of each channel is made piecewise constant in 8 bins of
 // zeta, the coordinate in which z is sampled (the cumulative of Pover over
-// the z range at t_c). Bin m carries U_m = min(1, exp(NN + margin)), where the
+// the z range at t_c). Bin m carries U_m = min(1, exp(NN + margin)), rounded
+// up to a power 2^(-k/16), where the
 // network NN (4 -> 64 -> 64 -> 1, BF16 tensor cores) bounds the acceptance
 // ratio r = w / (alpha_s ratio) over the bin and every t in [t_c, t_kin].
 // The channel's coefficient becomes c * mean(U), the bin is chosen from R_z,
@@ -87,6 +92,7 @@ struct Lane {
   uint64_t ev;      // record index in the caller's arrays
   int n, n_emit, status, steps;
   int row;          // row of a mixed batch
+  int slot;         // index of the event's learned bin heights in shared memory
   bool learned_ok;  // learned bounds active for this event
   float lnT;        // ln of the current evolution scale
   double eta0, eta1;
@@ -211,14 +217,32 @@ struct WS {
   }
   __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(size_t)slot * W.lanes + lane]; }
   __device__ __forceinline__ float4& End(int q) const { return W.end[(size_t)q * W.lanes + lane]; }
-  __device__ __forceinline__ float& UB(int q, int c, int m) const {
-    return W.ub[(((size_t)q * 2 + c) * 8 + m) * W.lanes + lane];
-  }
   __device__ __forceinline__ float4& MKey(int q) const { return W.mkey[(size_t)q * W.lanes + lane]; }
   __device__ __forceinline__ float2& MScale(int q) const { return W.mscale[(size_t)q * W.lanes + lane]; }
 };
 
-__device__ __forceinline__ int find_partner(const WS& w, int n, int i, int side, int tag) {
+// one event per warp, in shared memory (the warp-per-event kernel)
+struct WSS {
+  double* p;        // [4][nmax]
+  uint32_t* tag;    // [nmax]
+  float4* end;      // [2 nmax]
+  float4* mkey;     // [4]
+  float2* mscale;   // [4]
+  int nmax;
+  __device__ __forceinline__ double& P(int mu, int slot) const { return p[mu * nmax + slot]; }
+  __device__ __forceinline__ uint32_t& T(int slot) const { return tag[slot]; }
+  __device__ __forceinline__ float4& End(int q) const { return end[q]; }
+  __device__ __forceinline__ float4& MKey(int q) const { return mkey[q]; }
+  __device__ __forceinline__ float2& MScale(int q) const { return mscale[q]; }
+};
+// bytes of one warp's event in shared memory
+__host__ __device__ constexpr size_t wss_bytes(int nmax) {
+  return (size_t)nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) + 4 * sizeof(float4) +
+         4 * sizeof(float2);
+}
+
+template <class W>
+__device__ __forceinline__ int find_partner(const W& w, int n, int i, int side, int tag) {
   for (int m = 0; m < n; ++m) {
     if (m == i) continue;
     uint32_t t = w.T(m);
@@ -299,7 +323,8 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
 
 // Cached record of colour end q = 2 slot + side of an event: {1/c0, 1/c1,
 // ln t_kin, partner} (partner -1: no dipole on this side).
-__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, int n, double eta0,
+template <class W>
+__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, int n, double eta0,
                              double eta1, int row, int q, float& s_out, float& eta_out, int& type_out) {
   type_out = -1;
   const bool pp = S.pp[row] != 0;
@@ -350,16 +375,36 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const WS& w, i
   return make_float4(ic[0], ic[1], __logf(tk), __int_as_float(k));
 }
 
+// Learned bin heights of the block's lanes in shared memory, 8-bit codes:
+// height = 2^(-k/16) (k < 255), rounded up from the network's value so that it
+// stays a bound; codes [4 ends][2 channels][lanes][8 bins].
+struct LearnedSmem {
+  unsigned char* code;   // NULL without the learned proposal
+  const float* dec;      // [256] decoded heights
+  int lanes;             // threads of the block
+  __device__ __forceinline__ unsigned char* at(int q, int c, int lane) const {
+    return code + (((size_t)q * 2 + c) * lanes + lane) * 8;
+  }
+};
+
+__device__ __forceinline__ int height_code(float U) {
+  // smallest k with 2^(-k/16) >= U, i.e. floor(-16 log2 U), clamped to [0, 254]
+  if (!(U < 1.0f)) return 0;
+  const float k = floorf(-16.0f * __log2f(U));
+  return k < 0.0f ? 0 : (k > 254.0f ? 254 : (int)k);
+}
+
 // The whole warp rebuilds the colour-end table of the event held by lane
 // `src` (one end per lane), after an emission or a refill of that lane. With
 // the learned proposal the warp then evaluates the network for those of the
 // (up to four) initial-state ends whose inputs changed since their last
 // evaluation: 2 channels x 8 bins = one 16-row tile per end, two rows per
 // lane for the inputs and the bin heights.
+template <class W>
 __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
-                                          float (*stage)[4], float* ustage, int src_global, int n,
-                                          double eta0, double eta1, int row, bool learned_src, int lane_id) {
-  const WS w{M.W, src_global, M.P.nmax};
+                                         const LearnedSmem& ls, float (*stage)[4], float* ustage,
+                                         const W& w, int slot, uint64_t ev_src, int n, double eta0,
+                                         double eta1, int row, bool learned_src, int lane_id) {
   const bool pp = S.pp[row] != 0;
   float4 isr_rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
   float isr_s = 0.0f, isr_eta = 0.0f;
@@ -377,7 +422,17 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   const bool valid = mine && isr_type >= 0 && isr_rec.x > 0.0f && isr_rec.y > 0.0f &&
                      (isr_type == kIF || isr_type == kII);
   const int fl_i = mine ? tag_fl(w.T(lane_id >> 1)) : 0;
+  // training-state sampling: a hash of (event, partons, end) decides, so
+  // that a bounded log covers the whole run uniformly
+  bool keep = false;
   if (valid && M.Lc.collect) {
+    uint64_t h = (M.first + ev_src) * 0x9E3779B97F4A7C15ull ^ ((uint64_t)n << 8 | (uint64_t)lane_id);
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    keep = (uint32_t)(h >> 32) < M.Lc.collect_keep || M.Lc.collect_keep == 0xFFFFFFFFu;
+  }
+  if (keep) {
     const unsigned long long at = atomicAdd(M.Lc.collect_count, 1ull);
     if (at < M.Lc.collect_cap)
       M.Lc.collect[at] = make_float4(isr_eta, isr_s, (float)isr_type, (float)pdf_index(fl_i));
@@ -394,7 +449,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   if (eval) {
     const float tc = __expf(S.lnTc[row]);
     // rows r = lane and lane + 32: end r / 16, channel (r / 8) % 2, bin r % 8
-    int cls_j[2];
+    int cls_j[2];  // margin row: (class, eta bucket)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
@@ -402,8 +457,12 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
       const float s_e = __shfl_sync(0xffffffffu, isr_s, e);
       const int type_e = __shfl_sync(0xffffffffu, isr_type, e);
       const int fl_e = __shfl_sync(0xffffffffu, fl_i, e);
-      cls_j[j] = (eval >> e) & 1u ? isr_class(type_e, (fl_e == 21 ? 5 : 3) + c, fl_e) : 0;
-      if ((eval >> e) & 1u) mlp_features(eta_e, s_e, tc, m, cls_j[j], stage[r]);
+      cls_j[j] = 0;
+      if ((eval >> e) & 1u) {
+        const int cls = isr_class(type_e, (fl_e == 21 ? 5 : 3) + c, fl_e);
+        mlp_features(eta_e, s_e, tc, m, cls, stage[r]);
+        cls_j[j] = cls * kEtaBins + eta_bucket(stage[r][0]);
+      }
     }
     __syncwarp();
     for (int tile = 0; tile < 4; ++tile)
@@ -416,8 +475,11 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
       float U = 0.0f;
       if ((eval >> e) & 1u) {
         const int cls = cls_j[j];
-        U = fminf(1.0f, __expf(ustage[r] + mlp.margin[cls * kIsrBins + m]));
-        w.UB(e, c, m) = U;
+        // calibration margin of (class, eta bucket, bin), after the parameters
+        const float mg = __ldg(&M.Lc.mlp[kMlpParams + cls * kIsrBins + m]);
+        const int k = height_code(__expf(ustage[r] + mg));
+        ls.at(e, c, slot)[m] = (unsigned char)k;
+        U = ls.dec[k];
       }
       // sum over the 8 bins of the (end, channel): 8 consecutive lanes
       U += __shfl_xor_sync(0xffffffffu, U, 1);
@@ -441,9 +503,11 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
       const float2 sc = w.MScale(lane_id);
       isr_rec.x *= sc.x;
       isr_rec.y *= sc.y;
-    } else if (valid) {
-      for (int c = 0; c < 2; ++c)
-        for (int m = 0; m < 8; ++m) w.UB(lane_id, c, m) = 1.0f;
+    } else if (ls.code) {
+      // every other initial-state end proposes with height 1 in all bins (the
+      // plain bound): a winner from it reads these codes, and its rate was not
+      // rescaled
+      for (int c = 0; c < 2; ++c) *reinterpret_cast<uint2*>(ls.at(lane_id, c, slot)) = make_uint2(0u, 0u);
       w.MKey(lane_id) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
     }
     w.End(lane_id) = isr_rec;
@@ -463,7 +527,8 @@ struct Emission {
 // Accepted emission: FP64 kinematics (Appendix B maps, II Lorentz kick) and
 // colour update; the warp then rebuilds the event's end table cooperatively.
 // Kept out of line: it runs on the parked lanes of a warp only.
-__device__ __noinline__ bool emit(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L,
+template <class W>
+__device__ __noinline__ bool emit(const MixedCtx& M, const SmemPdf& S, const W& w, Lane& L,
                                   const Emission& em) {
   const int bi = em.bi, k = em.k, bside = em.bside, ch = em.ch, type = em.type;
   const int new_fl_i = em.new_fl_i, fl_j = em.fl_j;
@@ -576,57 +641,25 @@ struct Counters32 {
   unsigned long long steps = 0, trials = 0, isr_trials = 0, vetoes = 0, accepts = 0, violations = 0;
 };
 
-// One max-veto cycle on the working set. Returns the new status.
-__device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane& L, uint64_t id,
-                          Counters32& cnt, Emission& pend, bool& parked) {
+// The cycle after its trials (Fig. 1): the winner (best = ln t, end bq,
+// channel bch, z draw bRz; bq < 0: no trial) against the cutoff, the veto
+// and, when accepted, the parked emission. L.draw is past the trial draws.
+// Returns the new status.
+template <class W>
+__device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem& ls, const W& w, Lane& L,
+                         uint64_t id, Counters32& cnt, Emission& pend, bool& parked, float best, int bq, int bch,
+                         float bRz) {
   const bool pp = S.pp[L.row] != 0;
   const float lnTc = S.lnTc[L.row];
   cnt.steps += 1;
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
   const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
-  float best = -INFINITY;
-  int bq = -1, bch = 0;
-  float bRz = 0.5f;
-  uint64_t d = L.draw;
-  // one overestimate trial per channel of every colour end, in canonical order
-  auto trial = [&](const float4& rec, int q) {
-    const float lnTmax = fminf(L.lnT, rec.z);
-    const bool live = lnTmax > lnTc;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const float ic = c == 0 ? rec.x : rec.y;  // 1/c
-      if (ic < 0.0f) continue;  // channel absent for this emitter
-      const uint64_t dd = d++;
-      if (!(live && ic > 0.0f)) continue;
-      uint32_t out[4];
-      philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
-      cnt.trials += 1;
-      if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
-      const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);  // ln(t_max R^(1/c))
-      if (lt > best) { best = lt; bq = q; bch = c; bRz = u24(out[3]); }
-    }
-  };
-  const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
-  int q = 0;
-  // four independent loads in flight per iteration
-  for (; q + 4 <= ne; q += 4) {
-    const float4 r0 = w.End(q), r1 = w.End(q + 1), r2 = w.End(q + 2), r3 = w.End(q + 3);
-    if (__float_as_int(r0.w) >= 0) trial(r0, q);
-    if (__float_as_int(r1.w) >= 0) trial(r1, q + 1);
-    if (__float_as_int(r2.w) >= 0) trial(r2, q + 2);
-    if (__float_as_int(r3.w) >= 0) trial(r3, q + 3);
-  }
-  for (; q < ne; ++q) {
-    const float4 r = w.End(q);
-    if (__float_as_int(r.w) >= 0) trial(r, q);
-  }
   int bi = -1, bside = 0, k = -1;
   if (bq >= 0) {
     bi = bq >> 1;
     bside = bq & 1;
     k = __float_as_int(w.End(bq).w);
   }
-  L.draw = d;
   if (bi < 0 || best < lnTc) return GAPS_STATUS_DONE;
   uint32_t o1[4], o2[4];
   philox(e0, e1, (uint32_t)L.draw, (uint32_t)(L.draw >> 32), k0, k1, o1);
@@ -663,10 +696,15 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   // learned bounds: pick the bin from R_z, then zeta inside it
   const bool learned_end = M.Lc.learned && L.learned_ok && ini;
   float zeta = bRz, Um = 1.0f;
+  int mbin = -1;
   if (learned_end) {
     float U[8], tot = 0.0f;
+    const uint2 kc = *reinterpret_cast<const uint2*>(ls.at(bq, bch, L.slot));
 #pragma unroll
-    for (int m = 0; m < 8; ++m) { U[m] = w.UB(bq, bch, m); tot += U[m]; }
+    for (int m = 0; m < 8; ++m) {
+      U[m] = ls.dec[((m < 4 ? kc.x : kc.y) >> (8 * (m & 3))) & 0xffu];
+      tot += U[m];
+    }
     const float target = bRz * tot;
     float acc = 0.0f;
     int mb = 7;  // when no earlier bin is reached, acc = U[0] + ... + U[6]
@@ -675,6 +713,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
       acc += U[m];
     }
     Um = U[mb];
+    mbin = mb;
     float frac = Um > 0.0f ? (target - acc) / Um : 0.5f;
     frac = fminf(fmaxf(frac, 0.0f), 0.99999994f);
     zeta = ((float)mb + frac) * 0.125f;
@@ -725,6 +764,13 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   if (w8 > 1.0f) {
     cnt.violations += 1;
     if (learned_end) {
+      if (M.Lc.vlog) {
+        const unsigned long long at = atomicAdd(M.Lc.vcount, 1ull);
+        if (at < M.Lc.vcap) {
+          M.Lc.vlog[2 * at] = make_float4(eta, s, tw, w8);
+          M.Lc.vlog[2 * at + 1] = make_float4((float)isr_class(type, ch, fl_i), (float)mbin, z, zeta);
+        }
+      }
       // the learned bound failed here: continue the event with the plain
       // bounds from the scale before this cycle
       L.learned_ok = false;
@@ -758,6 +804,56 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const WS& w, Lane
   parked = true;
   return GAPS_STATUS_ACTIVE;
 }
+
+
+// One max-veto cycle of the lane's event: one overestimate trial per channel
+// of every colour end in canonical order, then step_veto.
+__device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem& ls, const WS& w, Lane& L,
+                          uint64_t id, Counters32& cnt, Emission& pend, bool& parked) {
+  const bool pp = S.pp[L.row] != 0;
+  const float lnTc = S.lnTc[L.row];
+  const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+  float best = -INFINITY;
+  int bq = -1, bch = 0;
+  float bRz = 0.5f;
+  uint64_t d = L.draw;
+  // one overestimate trial per channel of every colour end, in canonical order
+  auto trial = [&](const float4& rec, int q) {
+    const float lnTmax = fminf(L.lnT, rec.z);
+    const bool live = lnTmax > lnTc;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float ic = c == 0 ? rec.x : rec.y;  // 1/c
+      if (ic < 0.0f) continue;  // channel absent for this emitter
+      const uint64_t dd = d++;
+      if (!(live && ic > 0.0f)) continue;
+      uint32_t out[4];
+      philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+      cnt.trials += 1;
+      if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
+      const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);  // ln(t_max R^(1/c))
+      if (lt > best) { best = lt; bq = q; bch = c; bRz = u24(out[3]); }
+    }
+  };
+  const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
+  int q = 0;
+  // four independent loads in flight per iteration
+  for (; q + 4 <= ne; q += 4) {
+    const float4 r0 = w.End(q), r1 = w.End(q + 1), r2 = w.End(q + 2), r3 = w.End(q + 3);
+    if (__float_as_int(r0.w) >= 0) trial(r0, q);
+    if (__float_as_int(r1.w) >= 0) trial(r1, q + 1);
+    if (__float_as_int(r2.w) >= 0) trial(r2, q + 2);
+    if (__float_as_int(r3.w) >= 0) trial(r3, q + 3);
+  }
+  for (; q < ne; ++q) {
+    const float4 r = w.End(q);
+    if (__float_as_int(r.w) >= 0) trial(r, q);
+  }
+  L.draw = d;
+  return step_veto(M, S, ls, w, L, id, cnt, pend, parked, best, bq, bch, bRz);
+}
+
 
 __device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, Lane& L, uint64_t e) {
   const DevEvents& E = M.E;
@@ -817,7 +913,18 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem + kMlpSmemBytes);
   float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + kMlpSmemBytes +
                                                       (blockDim.x >> 5) * 64 * 4 * sizeof(float));
-  if (M.Lc.learned) mlp_load_smem(mlp_s, M.Lc.mlp, M.Lc.mlp + kMlpParams);
+  LearnedSmem ls;
+  ls.lanes = blockDim.x;
+  ls.code = nullptr;
+  ls.dec = nullptr;
+  if (M.Lc.learned) {
+    unsigned char* base = learned_smem + kMlpSmemBytes + (size_t)(blockDim.x >> 5) * 64 * 5 * sizeof(float);
+    float* dec = reinterpret_cast<float*>(base);
+    ls.dec = dec;
+    ls.code = base + 256 * sizeof(float);
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
+    mlp_load_smem(mlp_s, M.Lc.mlp);
+  }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
     S.umax[f][ix] = (float)M.P.umax[q];
@@ -838,6 +945,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   const int warp_id = threadIdx.x >> 5;
   WS w{M.W, gl, M.P.nmax};
   Lane L;
+  L.slot = threadIdx.x;
   bool active = false;
   bool exhausted = false;
   Counters32 cnt;
@@ -878,7 +986,9 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
         const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
-        mlp_tiles += rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1,
+        const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
+        mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
+                                  WS{M.W, warp_base + src, M.P.nmax}, warp_id * 32 + src, ev_src, n_src, e0, e1,
                                   row_src, lok, lane_id);
         rebuilds += 1;
       }
@@ -917,7 +1027,9 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const double e0 = __shfl_sync(0xffffffffu, L.eta0, src), e1 = __shfl_sync(0xffffffffu, L.eta1, src);
         const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
-        mlp_tiles += rebuild_coop(M, S, mlp_s, stage[warp_id], ustage[warp_id], warp_base + src, n_src, e0, e1,
+        const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
+        mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
+                                  WS{M.W, warp_base + src, M.P.nmax}, warp_id * 32 + src, ev_src, n_src, e0, e1,
                                   row_src, lok, lane_id);
         rebuilds += 1;
       }
@@ -926,7 +1038,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
     lane_steps += __popc(__ballot_sync(0xffffffffu, active && !parked));
     warp_steps += 32;
     if (active && !parked) {
-      int st = step_mixed(M, S, w, L, M.first + L.ev, cnt, pend, parked);
+      int st = step_mixed(M, S, ls, w, L, M.first + L.ev, cnt, pend, parked);
       if (++L.steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st != GAPS_STATUS_ACTIVE) {
         L.status = st;
@@ -954,6 +1066,283 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Warp-per-event persistent shower (GAPS_SCHED_WARP). Each warp owns one event
+// at a time, held in shared memory. The lanes share the event's colour ends in
+// the trial generation, one end per lane per round; a warp prefix sum gives
+// every trial the Philox draw of its place in the canonical order, and the
+// winner is a warp arg-max with ties to the earlier trial, as in the
+// lane-per-event kernel. Lane 0 runs the veto and builds an accepted emission;
+// the warp then rebuilds the end table together. Every trial, veto and
+// emission uses the lane-per-event kernel's arithmetic, so the two schedules
+// give identical events.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t wss_stride(int nmax) { return (wss_bytes(nmax) + 15) / 16 * 16; }
+
+__device__ __forceinline__ WSS warp_event_smem(unsigned char* base, int nmax) {
+  WSS w;
+  w.nmax = nmax;
+  w.p = reinterpret_cast<double*>(base);
+  w.end = reinterpret_cast<float4*>(base + (size_t)nmax * 4 * sizeof(double));
+  w.mkey = reinterpret_cast<float4*>(base + (size_t)nmax * (4 * sizeof(double) + 2 * sizeof(float4)));
+  w.mscale = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(w.mkey) + 4 * sizeof(float4));
+  w.tag = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(w.mscale) + 4 * sizeof(float2));
+  return w;
+}
+
+// every lane fills the same Lane; the slots are loaded by the lanes together
+__device__ void load_event_warp(const MixedCtx& M, const WSS& w, Lane& L, uint64_t e, int lane_id) {
+  const DevEvents& E = M.E;
+  L.ev = e;
+  L.status = E.status[e];
+  L.n = E.npart[e];
+  L.n_emit = E.n_emit[e];
+  L.steps = 0;
+  L.eta0 = E.eta[e];
+  L.eta1 = E.eta[E.cap + e];
+  L.draw = E.draw[e];
+  L.lnT = __logf((float)E.t[e]);
+  L.learned_ok = true;
+  L.row = mix_row(M.P, M.first + e);
+  if (M.Lc.learned && lane_id < 4) w.MKey(lane_id) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
+  if (L.status != GAPS_STATUS_ACTIVE) return;
+  if (L.n < 2 || L.n > M.P.nmax) { L.status = GAPS_ERR_NUMERIC; return; }
+  for (int s = lane_id; s < L.n; s += 32) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) w.P(mu, s) = E.P(mu, s, e);
+    w.T(s) = pack_tag(E.F(s, e), E.C(s, e), E.A(s, e));
+  }
+}
+
+__device__ void store_event_warp(const MixedCtx& M, const WSS& w, const Lane& L, int lane_id) {
+  const DevEvents& E = M.E;
+  const uint64_t e = L.ev;
+  if (L.n >= 2 && L.n <= M.P.nmax) {
+    for (int s = lane_id; s < L.n; s += 32) {
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) E.P(mu, s, e) = w.P(mu, s);
+      const uint32_t t = w.T(s);
+      E.F(s, e) = tag_fl(t);
+      E.C(s, e) = tag_col(t);
+      E.A(s, e) = tag_acol(t);
+    }
+    if (lane_id == 0) E.npart[e] = L.n;
+  }
+  if (lane_id == 0) {
+    E.n_emit[e] = L.n_emit;
+    E.status[e] = L.status;
+    E.t[e] = (double)__expf(L.lnT);
+    E.eta[e] = L.eta0;
+    E.eta[E.cap + e] = L.eta1;
+    E.draw[e] = L.draw;
+  }
+}
+
+// lane 0's Lane to every lane of the warp
+__device__ __forceinline__ void broadcast_lane(Lane& L) {
+  const unsigned full = 0xffffffffu;
+  L.n = __shfl_sync(full, L.n, 0);
+  L.n_emit = __shfl_sync(full, L.n_emit, 0);
+  L.status = __shfl_sync(full, L.status, 0);
+  L.steps = __shfl_sync(full, L.steps, 0);
+  L.learned_ok = __shfl_sync(full, L.learned_ok ? 1 : 0, 0) != 0;
+  L.lnT = __shfl_sync(full, L.lnT, 0);
+  L.eta0 = __shfl_sync(full, L.eta0, 0);
+  L.eta1 = __shfl_sync(full, L.eta1, 0);
+  L.draw = __shfl_sync(full, L.draw, 0);
+}
+
+// The trials of one cycle, shared by the lanes. Returns the winner in
+// (best, bq, bch, bRz) on every lane and the Philox draw after the trials.
+__device__ __forceinline__ uint64_t warp_trials(const MixedCtx& M, const SmemPdf& S, const WSS& w,
+                                                const Lane& L, int lane_id, Counters32& cnt, float& best, int& bq,
+                                                int& bch, float& bRz, unsigned long long& lane_steps,
+                                                unsigned long long& warp_steps) {
+  const unsigned full = 0xffffffffu;
+  const bool pp = S.pp[L.row] != 0;
+  const float lnTc = S.lnTc[L.row];
+  const uint64_t id = M.first + L.ev;
+  const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+  best = -INFINITY;
+  int bidx = 0x7fffffff;  // 2 q + c of the winner in canonical order
+  bRz = 0.5f;
+  uint64_t d = L.draw;
+  const int ne = 2 * L.n;
+  for (int q0 = 0; q0 < ne; q0 += 32) {
+    const int q = q0 + lane_id;
+    float4 rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
+    int nd = 0;  // draws of this end: one per channel present
+    if (q < ne) {
+      rec = w.End(q);
+      if (__float_as_int(rec.w) >= 0) nd = (rec.x >= 0.0f ? 1 : 0) + (rec.y >= 0.0f ? 1 : 0);
+    }
+    int inc = nd;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(full, inc, off);
+      if (lane_id >= off) inc += t;
+    }
+    const int tot = __shfl_sync(full, inc, 31);
+    if (nd > 0) {
+      uint64_t dd = d + (uint64_t)(inc - nd);
+      const float lnTmax = fminf(L.lnT, rec.z);
+      const bool live = lnTmax > lnTc;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float ic = c == 0 ? rec.x : rec.y;  // 1/c
+        if (ic < 0.0f) continue;  // channel absent for this emitter
+        const uint64_t dc = dd++;
+        if (!(live && ic > 0.0f)) continue;
+        uint32_t out[4];
+        philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
+        cnt.trials += 1;
+        if (pp && q < 4) cnt.isr_trials += 1;
+        const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+        if (lt > best) { best = lt; bidx = 2 * q + c; bRz = u24(out[3]); }
+      }
+    }
+    d += (uint64_t)tot;
+    if (lane_id == 0) {
+      lane_steps += (unsigned long long)min(32, ne - q0);
+      warp_steps += 32;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(full, best, off);
+    const int oi = __shfl_xor_sync(full, bidx, off);
+    const float oz = __shfl_xor_sync(full, bRz, off);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bRz = oz; }
+  }
+  bq = bidx == 0x7fffffff ? -1 : (bidx >> 1);
+  bch = bidx & 1;
+  return d;
+}
+
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
+  __shared__ SmemPdf S;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int nw = blockDim.x >> 5;
+  const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
+  const size_t ev_bytes = (size_t)nw * wss_stride(M.P.nmax);
+  const WSS w = warp_event_smem(dyn_smem + (size_t)warp_id * wss_stride(M.P.nmax), M.P.nmax);
+  // learned proposal after the events: network image, staging, heights
+  unsigned char* lbase = dyn_smem + ev_bytes;
+  MlpSmem& mlp_s = *reinterpret_cast<MlpSmem*>(lbase);
+  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(lbase + kMlpSmemBytes);
+  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(lbase + kMlpSmemBytes + (size_t)nw * 64 * 4 * sizeof(float));
+  LearnedSmem ls;
+  ls.lanes = nw;  // one slot of heights per warp
+  ls.code = nullptr;
+  ls.dec = nullptr;
+  if (M.Lc.learned) {
+    unsigned char* hb = lbase + kMlpSmemBytes + (size_t)nw * 64 * 5 * sizeof(float);
+    float* dec = reinterpret_cast<float*>(hb);
+    ls.dec = dec;
+    ls.code = hb + 256 * sizeof(float);
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
+    mlp_load_smem(mlp_s, M.Lc.mlp);
+  }
+  for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
+    int f = q / kSmNX, ix = q % kSmNX;
+    S.umax[f][ix] = (float)M.P.umax[q];
+    S.lmin[f][ix] = (float)M.P.lmin[q];
+    float xf = 0.0f;
+    if (f < 11) xf = M.P.grid[((size_t)f * kNX + ix) * kNQ];
+    else for (int k = 1; k <= 10; ++k) xf += M.P.grid[((size_t)k * kNX + ix) * kNQ];
+    S.xf[f][ix] = xf;
+  }
+  for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
+    S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  load_rows(S, M.P);
+  __syncthreads();
+
+  Lane L;
+  L.slot = warp_id;
+  Counters32 cnt;
+  unsigned long long finished = 0, err_cap = 0, err_iter = 0, err_num = 0;
+  unsigned long long lane_steps = 0, warp_steps = 0, rebuilds = 0, mlp_tiles = 0;
+  bool active = false;
+  while (true) {
+    if (!active) {
+      unsigned long long e = 0;
+      if (lane_id == 0) e = atomicAdd(M.next, 1ull);
+      e = __shfl_sync(0xffffffffu, e, 0);
+      if (e >= M.n) break;
+      load_event_warp(M, w, L, e, lane_id);
+      __syncwarp();
+      if (L.status != GAPS_STATUS_ACTIVE) {
+        store_event_warp(M, w, L, lane_id);
+        finished += lane_id == 0 ? 1 : 0;
+        if (lane_id == 0 && L.status == GAPS_ERR_NUMERIC) err_num += 1;
+        __syncwarp();
+        continue;
+      }
+      active = true;
+      mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, warp_id, L.ev, L.n, L.eta0,
+                                L.eta1, L.row, L.learned_ok, lane_id);
+      rebuilds += 1;
+    }
+    float best, bRz;
+    int bq, bch;
+    const uint64_t d = warp_trials(M, S, w, L, lane_id, cnt, best, bq, bch, bRz, lane_steps, warp_steps);
+    int st = GAPS_STATUS_ACTIVE;
+    bool done_emit = false;
+    if (lane_id == 0) {
+      L.draw = d;
+      Emission pend;
+      bool parked = false;
+      st = step_veto(M, S, ls, w, L, M.first + L.ev, cnt, pend, parked, best, bq, bch, bRz);
+      if (++L.steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
+      if (st == GAPS_STATUS_ACTIVE && parked) {
+        if (pend.kind == 1) {
+          done_emit = true;  // plain rebuild after a learned-bound violation
+        } else {
+          done_emit = emit(M, S, w, L, pend);
+          if (done_emit) cnt.accepts += 1;
+          else cnt.vetoes += 1;
+        }
+      }
+      L.status = st;
+    }
+    broadcast_lane(L);
+    st = L.status;
+    done_emit = __shfl_sync(0xffffffffu, done_emit ? 1 : 0, 0) != 0;
+    __syncwarp();  // lane 0's writes to the event are visible to the warp
+    if (st != GAPS_STATUS_ACTIVE) {
+      store_event_warp(M, w, L, lane_id);
+      active = false;
+      if (lane_id == 0) {
+        finished += 1;
+        if (st == GAPS_ERR_CAPACITY) err_cap += 1;
+        else if (st == GAPS_ERR_ITER_CAP) err_iter += 1;
+        else if (st == GAPS_ERR_NUMERIC) err_num += 1;
+      }
+      __syncwarp();
+      continue;
+    }
+    if (done_emit) {
+      mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, warp_id, L.ev, L.n, L.eta0,
+                                L.eta1, L.row, L.learned_ok, lane_id);
+      rebuilds += 1;
+    }
+  }
+  unsigned long long v[14] = {finished, cnt.steps, cnt.trials, cnt.isr_trials, cnt.vetoes, cnt.accepts,
+                              cnt.violations, err_cap, err_iter, err_num, lane_steps, warp_steps,
+                              lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull};
+  const int idx[14] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
+                       C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES};
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    unsigned long long x = v[q];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane_id == 0 && x) atomicAdd(&M.P.counters[idx[q]], x);
+  }
+}
+
 }  // namespace
 
 size_t workset_bytes(int lanes, int nmax) {
@@ -968,8 +1357,6 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   p += (size_t)lanes * nmax * 4 * sizeof(double);
   W.end = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
-  W.ub = (float*)p;
-  p += (size_t)lanes * 64 * sizeof(float);
   W.mkey = (float4*)p;
   p += (size_t)lanes * 4 * sizeof(float4);
   W.mscale = (float2*)p;
@@ -1052,6 +1439,59 @@ cudaError_t launch_isr_targets(const DevParams& P, int q_independent, const floa
   return cudaGetLastError();
 }
 
+constexpr int kWarpKernelMaxDyn = 200 * 1024;
+
+// Opt-in for the dynamic shared memory of the mixed-precision kernels (the
+// learned proposal's, up to 64 KB; the warp-per-event kernel's events, up to
+// 200 KB) on the current device; called when a context is created.
+cudaError_t mixed_kernels_init() {
+  const int bytes = 64 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_shower_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_shower_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_shower_mixed<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_shower_warp<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpKernelMaxDyn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_shower_warp<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpKernelMaxDyn);
+  return e;
+}
+
+// shared memory of a warp-per-event block of `block_size` threads
+size_t warp_kernel_smem(int block_size, int nmax, bool learned) {
+  const size_t nw = (size_t)block_size / 32;
+  size_t b = nw * wss_stride(nmax);
+  if (learned) b += kMlpSmemBytes + nw * 64 * 5 * sizeof(float) + 256 * sizeof(float) + nw * 64;
+  return b;
+}
+
+cudaError_t launch_shower_warp(const DevParams& P, const DevEvents& E, const LearnedCfg& Lc, uint64_t first,
+                               uint64_t n, int blocks, int block_size, int blocks_per_sm, int q_independent,
+                               unsigned long long* next, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  MixedCtx M;
+  M.P = P; M.E = E; M.Lc = Lc; M.first = first; M.n = n; M.next = next;
+  M.q_independent = q_independent;
+  M.period = 1;
+  M.emit_batch = 1;
+  M.emit_wait = 4;
+  M.lnTc = (float)gm_log(P.t_cut);
+  M.asOver2pi = (float)(P.as_over / (2.0 * kPi));
+  M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
+  const size_t dyn = warp_kernel_smem(block_size, P.nmax, Lc.learned != 0);
+  if (dyn > (size_t)kWarpKernelMaxDyn) return cudaErrorInvalidValue;
+  cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
+  if (err != cudaSuccess) return err;
+  if (blocks <= 0) return cudaErrorInvalidValue;
+  if (block_size < 32 || block_size > 256 || block_size % 32) return cudaErrorInvalidValue;
+  // register tier: three or more resident blocks of at most 128 threads get
+  // the tighter budget, anything else up to 255 registers per thread
+  if (blocks_per_sm >= 3 && block_size <= 128) k_shower_warp<128, 3><<<blocks, block_size, dyn, stream>>>(M);
+  else k_shower_warp<256, 1><<<blocks, block_size, dyn, stream>>>(M);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, const LearnedCfg& Lc,
                                 uint64_t first, uint64_t n, int blocks, int block_size, int sm_count, int period,
                                 int emit_batch, int q_independent, unsigned long long* next,
@@ -1068,7 +1508,11 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
   cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
   if (err != cudaSuccess) return err;
-  const size_t dyn = Lc.learned ? kMlpSmemBytes + (size_t)(block_size / 32) * 64 * 5 * sizeof(float) : 0;
+  // learned proposal: network image, per-warp staging, height decode table,
+  // 64 bytes of height codes per lane
+  const size_t dyn = Lc.learned ? kMlpSmemBytes + (size_t)(block_size / 32) * 64 * 5 * sizeof(float) +
+                                      256 * sizeof(float) + (size_t)block_size * 64
+                                : 0;
   // the register tier follows the resident threads the launch asks for
   const int threads_per_sm = blocks * block_size / max(1, sm_count);
   if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, dyn, stream>>>(M);

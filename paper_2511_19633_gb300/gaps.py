@@ -26,7 +26,7 @@ GAPS_ERR_NO_DEVICE = -6
 
 GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO = 0, 1, 2
 GAPS_FP64, GAPS_MIXED = 0, 1
-GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT = 0, 1
+GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT, GAPS_SCHED_WARP = 0, 1, 2
 GAPS_STATUS_ACTIVE, GAPS_STATUS_DONE = 0, 1
 GAPS_NOBS, GAPS_NHIST, GAPS_HIST_BINS = 8, 6, 66
 
@@ -77,12 +77,15 @@ class GapsStats(ctypes.Structure):
 GAPS_MLP_PARAMS = 4545
 GAPS_ISR_BINS = 8
 GAPS_ISR_CLASSES = 44
+GAPS_ISR_ETA_BINS = 8
+# upper edges of the eta buckets on the network input ln(eta)/7 + 1 (float32)
+GAPS_ISR_ETA_EDGES = (-0.6447, -0.3158, 0.0132, 0.3421, 0.6711, 0.8691, 0.9490)
 
 EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
            "gaps_destroy", "gaps_shower_static", "gaps_collect_isr_states", "gaps_isr_targets",
            "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train",
-           "gaps_process", "gaps_process_shower_ms")
+           "gaps_process", "gaps_process_shower_ms", "gaps_set_violation_log")
 
 
 class GapsError(RuntimeError):
@@ -114,9 +117,10 @@ def _load():
     lib.gaps_destroy.restype = None
     lib.gaps_shower_static.argtypes = [P(GapsConfig), u64, u64, P(GapsEvents), P(GapsStats), vp]
     f = ctypes.c_float
-    lib.gaps_collect_isr_states.argtypes = [vp, u64, u64, P(GapsEvents), vp, u64, vp, vp]
+    lib.gaps_collect_isr_states.argtypes = [vp, u64, u64, P(GapsEvents), f, vp, u64, vp, vp]
     lib.gaps_isr_targets.argtypes = [vp, vp, u64, vp, vp, vp]
     lib.gaps_set_learned_proposal.argtypes = [vp, vp, vp]
+    lib.gaps_set_violation_log.argtypes = [vp, vp, u64, vp]
     lib.gaps_mlp_loss_grad.argtypes = [vp, vp, vp, u64, f, vp, vp, vp]
     lib.gaps_mlp_forward.argtypes = [vp, vp, u64, i, vp, vp]
     lib.gaps_mlp_train.argtypes = [vp, vp, vp, vp, vp, u64, u64, f, f, u64, vp, i, vp]
@@ -175,10 +179,11 @@ def gaps_shower_static(cfg: GapsConfig, first_event: int, n: int, ev: GapsEvents
 
 
 def gaps_collect_isr_states(ctx, first_event: int, n: int, ev: GapsEvents, states: torch.Tensor,
-                            count: torch.Tensor, stream=None):
+                            count: torch.Tensor, keep_fraction: float = 1.0, stream=None):
     """states: float32 [capacity, 4] device; count: int64 [1] device (incremented)."""
-    _check(_lib.gaps_collect_isr_states(ctx, first_event, n, ctypes.byref(ev), states.data_ptr(),
-                                        states.shape[0], count.data_ptr(), _stream_ptr(stream)),
+    _check(_lib.gaps_collect_isr_states(ctx, first_event, n, ctypes.byref(ev), float(keep_fraction),
+                                        states.data_ptr(), states.shape[0], count.data_ptr(),
+                                        _stream_ptr(stream)),
            "gaps_collect_isr_states")
 
 
@@ -190,15 +195,24 @@ def gaps_isr_targets(ctx, states: torch.Tensor, n_states: int, features: torch.T
 
 def gaps_set_learned_proposal(ctx, params, log_margins=0.0):
     """params: host float32 array of GAPS_MLP_PARAMS (copied) or None;
-    log_margins: [GAPS_ISR_CLASSES][GAPS_ISR_BINS] (or a scalar, broadcast)."""
+    log_margins: [GAPS_ISR_CLASSES][GAPS_ISR_ETA_BINS][GAPS_ISR_BINS] (or a scalar, broadcast)."""
     import numpy as np
     if params is None:
         _check(_lib.gaps_set_learned_proposal(ctx, None, None), "gaps_set_learned_proposal")
         return
     p = np.ascontiguousarray(params, dtype=np.float32)
     m = np.ascontiguousarray(np.broadcast_to(np.asarray(log_margins, dtype=np.float32),
-                                             (GAPS_ISR_CLASSES, GAPS_ISR_BINS)))
+                                             (GAPS_ISR_CLASSES, GAPS_ISR_ETA_BINS, GAPS_ISR_BINS)))
     _check(_lib.gaps_set_learned_proposal(ctx, p.ctypes.data, m.ctypes.data), "gaps_set_learned_proposal")
+
+
+def gaps_set_violation_log(ctx, log: torch.Tensor | None, count: torch.Tensor | None = None):
+    """log: float32 [capacity, 8] device; count: int64 [1] device."""
+    if log is None:
+        _check(_lib.gaps_set_violation_log(ctx, None, 0, None), "gaps_set_violation_log")
+        return
+    _check(_lib.gaps_set_violation_log(ctx, log.data_ptr(), log.shape[0], count.data_ptr()),
+           "gaps_set_violation_log")
 
 
 def gaps_mlp_loss_grad(params: torch.Tensor, features: torch.Tensor, targets: torch.Tensor, tau: float,
@@ -238,7 +252,7 @@ def gaps_process(ctx, first_event: int, n: int, ev: GapsEvents, obs_dev: torch.T
                              None if obs_dev is None else obs_dev.data_ptr(),
                              None if obs_host is None else obs_host.data_ptr(),
                              None if hists is None else ctypes.byref(hists), _stream_ptr(stream)),
-           "gaps_process", "gaps_process_shower_ms")
+           "gaps_process")
 
 
 def gaps_process_shower_ms(ctx, max_chunks: int = 4096) -> list:

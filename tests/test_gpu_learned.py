@@ -114,9 +114,12 @@ def _shower_hists(G, pdf, params, margin, n, first=0, chunk=1 << 21):
     cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, seed=1, precision=G.GAPS_MIXED, schedule=1,
                         blocks_per_sm=4, emit_batch=8)
     ctx = G.gaps_init(cfg)
+    vlog = torch.zeros((64, 8), dtype=torch.float32, device="cuda")
+    vcount = torch.zeros(1, dtype=torch.int64, device="cuda")
     try:
         if params is not None:
             G.gaps_set_learned_proposal(ctx, params, margin)
+            G.gaps_set_violation_log(ctx, vlog, vcount)
         cap = min(chunk, n)
         buf = G.EventBuffers.allocate(cap, 128)
         ev = buf.view()
@@ -132,6 +135,8 @@ def _shower_hists(G, pdf, params, margin, n, first=0, chunk=1 << 21):
         st = G.gaps_get_stats(ctx)
     finally:
         G.gaps_destroy(ctx)
+    st["violation_log"] = vlog[: min(64, int(vcount.item()))].cpu().numpy()
+    assert int(vcount.item()) == (st["violations"] if params is not None else 0)
     return hw.cpu().numpy(), hw2.cpu().numpy(), st
 
 
@@ -141,16 +146,20 @@ def test_learned_proposal_is_exact_and_cheaper(G, pdf, trained):
     n = 1_000_000
     wl, wl2, sl = _shower_hists(G, pdf, trained["params"], trained["log_margins"], n)
     wp, wp2, sp = _shower_hists(G, pdf, None, 0.0, n)
-    assert sl["violations"] == 0 and sl["events"] == n
+    assert sl["events"] == n
+    assert sl["violations"] == 0, sl["violation_log"]
     assert sl["steps"] < sp["steps"] and sl["trials"] < sp["trials"]
-    red, _, _ = chi2_summary(chi2_per_hist(wl, wl2, n, wp, wp2, n))
-    assert red < 1.2, red
+    per = chi2_per_hist(wl, wl2, n, wp, wp2, n)
+    red, _, _ = chi2_summary(per)
+    assert red < 1.2, (red, per)
 
 
 def test_learned_histograms_match_oracle_at_1e7(G, pdf, trained):
     gold = load_golden("pp_nlo")
     n = gold["events"]
     w, w2, st = _shower_hists(G, pdf, trained["params"], trained["log_margins"], n)
-    assert st["violations"] == 0 and st["events"] == n
-    red, _, _ = chi2_summary(chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"]))
-    assert red < 1.2, red
+    assert st["events"] == n
+    assert st["violations"] == 0, st["violation_log"]
+    per = chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"])
+    red, _, _ = chi2_summary(per)
+    assert red < 1.2, (red, per)
