@@ -314,6 +314,8 @@ int ensure_workset(gaps_ctx* ctx, int& blocks, int& bs, WorkSet& W) {
   int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
   blocks = ctx->n_sm * per_sm;
   int lanes = blocks * bs;
+  // the kernels index the working set with 32-bit element offsets
+  if ((size_t)lanes * 4 * (size_t)c.nmax_partons >= ((size_t)1 << 31)) return GAPS_ERR_INVALID_ARG;
   size_t need = workset_bytes(lanes, c.nmax_partons);
   if (need > ctx->work_bytes) {
     if (ctx->d_work) cudaFree(ctx->d_work);

@@ -109,7 +109,8 @@ __device__ __forceinline__ bool loc_x(const MixedCtx& M, float x, int& ix, float
   return true;
 }
 
-__device__ __forceinline__ float pdf32(const MixedCtx& M, const SmemPdf& S, int f, float x, float q2) {
+// out of line: one copy for all call sites (instruction-cache footprint)
+__device__ __noinline__ float pdf32(const MixedCtx& M, const SmemPdf& S, int f, float x, float q2) {
   if (f < 0 || f > 11) return 0.0f;
   int ix;
   float fx;
@@ -130,7 +131,7 @@ __device__ __forceinline__ float pdf32(const MixedCtx& M, const SmemPdf& S, int 
   return lo * (1.0f - fq) + hi * fq;
 }
 
-__device__ __forceinline__ float bound32(const MixedCtx& M, const SmemPdf& S, int num, int den, float eta) {
+__device__ __noinline__ float bound32(const MixedCtx& M, const SmemPdf& S, int num, int den, float eta) {
   if (num < 0 || num > 11 || den < 0 || den > 11) return 0.0f;
   int ix;
   float fx;
@@ -209,16 +210,17 @@ __device__ __forceinline__ float shape_val32(int sh, float coef, float z, float 
 }
 
 // ---- working-set access ------------------------------------------------------
+// 32-bit element indices: lanes x 4 nmax < 2^31 (checked by the launcher)
 struct WS {
   const WorkSet& W;
   int lane, nmax;
   __device__ __forceinline__ double& P(int mu, int slot) const {
-    return W.p[((size_t)mu * nmax + slot) * W.lanes + lane];
+    return W.p[(unsigned)((mu * nmax + slot) * W.lanes + lane)];
   }
-  __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(size_t)slot * W.lanes + lane]; }
-  __device__ __forceinline__ float4& End(int q) const { return W.end[(size_t)q * W.lanes + lane]; }
-  __device__ __forceinline__ float4& MKey(int q) const { return W.mkey[(size_t)q * W.lanes + lane]; }
-  __device__ __forceinline__ float2& MScale(int q) const { return W.mscale[(size_t)q * W.lanes + lane]; }
+  __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(unsigned)(slot * W.lanes + lane)]; }
+  __device__ __forceinline__ float4& End(int q) const { return W.end[(unsigned)(q * W.lanes + lane)]; }
+  __device__ __forceinline__ float4& MKey(int q) const { return W.mkey[(unsigned)(q * W.lanes + lane)]; }
+  __device__ __forceinline__ float2& MScale(int q) const { return W.mscale[(unsigned)(q * W.lanes + lane)]; }
 };
 
 // one event per warp, in shared memory (the warp-per-event kernel)
@@ -524,6 +526,79 @@ struct Emission {
   uint32_t ti;
 };
 
+// FP64 reciprocal and reciprocal square root for the mixed kernel's
+// kinematics: an FP32 estimate refined by two Newton-Raphson steps
+// (relative error (2^-23)^4 before rounding, i.e. an ulp of FP64), a few
+// instructions each instead of the library's division sequences. For normal
+// arguments within the FP32 range, which every invariant here is.
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = r * fma(-x, r, 2.0);
+  r = r * fma(-x, r, 2.0);
+  return r;
+}
+__device__ __forceinline__ double rsqrt64(double x) {
+  double r = (double)rsqrtf((float)x);
+  r = r * fma(-0.5 * x * r, r, 1.5);
+  r = r * fma(-0.5 * x * r, r, 1.5);
+  return r;
+}
+
+// Transverse basis of a dipole (as in physics_fp64.cuh) with one reciprocal
+// per divisor: the mixed-precision kernel needs FP64 accuracy here, not the
+// FP64 kernel's operation-for-operation agreement with the reference, and
+// every FP64 division is a long instruction sequence.
+__device__ __noinline__ void transverse_basis_mixed(const double P[4], const double K[4], double e1[4],
+                                                    double e2[4]) {
+  const double iPK = rcp64(dot4(P, K));
+  const double N1 = 1.0 + 2.0 * P[1] * K[1] * iPK;
+  const double N2 = 1.0 + 2.0 * P[2] * K[2] * iPK;
+  const double N3 = 1.0 + 2.0 * P[3] * K[3] * iPK;
+  int a = 1;
+  double Na = N1;
+  if (N2 > Na) { a = 2; Na = N2; }
+  if (N3 > Na) { a = 3; Na = N3; }
+  int b;
+  if (a == 1) b = (N3 > N2) ? 3 : 2;
+  else if (a == 2) b = (N3 > N1) ? 3 : 1;
+  else b = (N2 > N1) ? 2 : 1;
+  const double ina = rsqrt64(Na);
+  const double ka = K[a] * iPK, pa = P[a] * iPK, kb = K[b] * iPK, pb = P[b] * iPK;
+  double e2p[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) e1[mu] = ((mu == a ? 1.0 : 0.0) + ka * P[mu] + pa * K[mu]) * ina;
+  const double e1b = e1[b];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) e2p[mu] = (mu == b ? 1.0 : 0.0) + kb * P[mu] + pb * K[mu] - e1b * e1[mu];
+  const double in2 = rsqrt64(-dot4(e2p, e2p));
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) e2[mu] = e2p[mu] * in2;
+}
+
+// Appendix B.4 and B.5 maps as in physics_fp64.cuh, with one reciprocal per
+// divisor (FP64 accuracy without the FP64 kernel's operation order)
+__device__ __forceinline__ bool if_map_mixed(double r, double z, double omz, double& x, double& omx, double& u,
+                                             double& omu) {
+  const double iq = rcp64(omz + r);
+  const double disc = 1.0 - 4.0 * r * z * omz * iq * iq;
+  if (!(disc >= 0.0)) return false;
+  const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+  x = 2.0 * z * omz * iq * rcp64(1.0 + sq);
+  u = x * r * rcp64(omz);
+  omu = 1.0 - u;
+  if (!(omu > 0.0)) return false;
+  omx = omz * rcp64(omu);
+  return true;
+}
+
+__device__ __forceinline__ bool ii_map_mixed(double r, double z, double omz, double& x, double& omx, double& v) {
+  const double iq = rcp64(omz + r);
+  x = z * omz * iq;
+  omx = (omz * omz + r) * iq;
+  v = x * r * rcp64(omz);
+  return omx - v > 0.0;
+}
+
 // Accepted emission: FP64 kinematics (Appendix B maps, II Lorentz kick) and
 // colour update; the warp then rebuilds the event's end table cooperatively.
 // Kept out of line: it runs on the parked lanes of a warp only.
@@ -546,73 +621,85 @@ __device__ __noinline__ bool emit(const MixedCtx& M, const SmemPdf& S, const W& 
   const double zd = omz < 0.5f ? 1.0 - (double)omz : (double)z;
   const double omzd = omz < 0.5f ? (double)omz : 1.0 - (double)z;
   double e1v[4], e2v[4];
-  transverse_basis(Pm, K, e1v, e2v);
+  transverse_basis_mixed(Pm, K, e1v, e2v);
   double cph, sph;
   gm_sincos2pi(Rphi, cph, sph);
-  const double st = sqrt(t);
+  const double st = t * rsqrt64(t);
   double kt[4];
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) kt[mu] = st * (cph * e1v[mu] + sph * e2v[mu]);
   const int j = L.n;
-  double pj[4];
-  if (type == kFF) {
-    const double yd = t / (zd * omzd * sd);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      w.P(mu, bi) = zd * Pm[mu] + (yd * omzd) * K[mu] + kt[mu];
-      pj[mu] = omzd * Pm[mu] + (yd * zd) * K[mu] - kt[mu];
-      w.P(mu, k) = (1.0 - yd) * K[mu];
+  // the maps as p_i' = a1 p_i + b1 p_k + c1 k_T, p_k' = a2 p_i + b2 p_k + c2 k_T,
+  // p_j = a3 p_i + b3 p_k + c3 k_T (Appendix B), then one store of each
+  double a1, b1, c1, a2, b2, c2, a3, b3, c3;
+  double eta_f = 1.0;  // factor of eta of the incoming slot `eta_slot`
+  int eta_slot = -1;
+  double xd = 1.0, omxd = 0.0, vd = 0.0;
+  const double isd = rcp64(sd);
+  if (type == kFF || type == kFI) {
+    const double yd = t * rcp64(zd * omzd * sd);  // y (FF) or rho (FI)
+    a1 = zd; b1 = yd * omzd; c1 = 1.0;
+    a3 = omzd; b3 = yd * zd; c3 = -1.0;
+    a2 = 0.0; c2 = 0.0;
+    if (type == kFF) {
+      b2 = 1.0 - yd;
+    } else {
+      b2 = 1.0 + yd;
+      eta_slot = k;
+      eta_f = b2;
     }
-  } else if (type == kFI) {
-    const double rhod = t / (zd * omzd * sd);
-    const double xinv = 1.0 + rhod;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      w.P(mu, bi) = zd * Pm[mu] + (omzd * rhod) * K[mu] + kt[mu];
-      pj[mu] = omzd * Pm[mu] + (zd * rhod) * K[mu] - kt[mu];
-      w.P(mu, k) = xinv * K[mu];
-    }
-    if (k == 0) L.eta0 *= xinv; else L.eta1 *= xinv;
   } else if (type == kIF) {
-    double xd, omxd, ud, omud;
-    if (!if_map(t / sd, zd, omzd, xd, omxd, ud, omud)) return false;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      w.P(mu, bi) = Pm[mu] / xd;
-      pj[mu] = (omud * omxd / xd) * Pm[mu] + ud * K[mu] - kt[mu];
-      w.P(mu, k) = (ud * omxd / xd) * Pm[mu] + omud * K[mu] + kt[mu];
-    }
-    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
+    double ud, omud;
+    if (!if_map_mixed(t * isd, zd, omzd, xd, omxd, ud, omud)) return false;
+    const double ixd = rcp64(xd);
+    a1 = ixd; b1 = 0.0; c1 = 0.0;
+    a3 = omud * omxd * ixd; b3 = ud; c3 = -1.0;
+    a2 = ud * omxd * ixd; b2 = omud; c2 = 1.0;
+    eta_slot = bi;
+    eta_f = ixd;
   } else {
-    double xd, omxd, vd;
-    if (!ii_map(t / sd, zd, omzd, xd, omxd, vd)) return false;
-    double pa[4];
+    if (!ii_map_mixed(t * isd, zd, omzd, xd, omxd, vd)) return false;
+    const double ixd = rcp64(xd);
+    a1 = ixd; b1 = 0.0; c1 = 0.0;
+    a3 = (omxd - vd) * ixd; b3 = vd; c3 = -1.0;
+    a2 = 0.0; b2 = 1.0; c2 = 0.0;
+    eta_slot = bi;
+    eta_f = ixd;
+  }
+  double pi2[4], pk2[4], pj[4];
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      pa[mu] = Pm[mu] / xd;
-      w.P(mu, bi) = pa[mu];
-      pj[mu] = ((omxd - vd) / xd) * Pm[mu] + vd * K[mu] - kt[mu];
-    }
-    if (bi == 0) L.eta0 /= xd; else L.eta1 /= xd;
+  for (int mu = 0; mu < 4; ++mu) {
+    pi2[mu] = a1 * Pm[mu] + b1 * K[mu] + c1 * kt[mu];
+    pk2[mu] = a2 * Pm[mu] + b2 * K[mu] + c2 * kt[mu];
+    pj[mu] = a3 * Pm[mu] + b3 * K[mu] + c3 * kt[mu];
+  }
+  if (type == kII) {
+    // Lorentz kick of every final-state parton but j (Appendix B.5)
     double Kp[4], Kn[4], KK[4];
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       Kp[mu] = Pm[mu] + K[mu];
-      Kn[mu] = (pa[mu] + K[mu]) - pj[mu];
+      Kn[mu] = (pi2[mu] + K[mu]) - pj[mu];
       KK[mu] = Kp[mu] + Kn[mu];
     }
-    const double KK2 = dot4(KK, KK), Kp2 = dot4(Kp, Kp);
+    const double iKK2 = 2.0 * rcp64(dot4(KK, KK)), iKp2 = 2.0 * rcp64(dot4(Kp, Kp));
     for (int m = 2; m < L.n; ++m) {
       double q[4];
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) q[mu] = w.P(mu, m);
-      const double a = 2.0 * dot4(KK, q) / KK2, b = 2.0 * dot4(Kp, q) / Kp2;
+      const double a = dot4(KK, q) * iKK2, b = dot4(Kp, q) * iKp2;
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) w.P(mu, m) = q[mu] - a * KK[mu] + b * Kn[mu];
     }
   }
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) w.P(mu, j) = pj[mu];
+  for (int mu = 0; mu < 4; ++mu) {
+    w.P(mu, bi) = pi2[mu];
+    w.P(mu, k) = pk2[mu];
+    w.P(mu, j) = pj[mu];
+  }
+  if (eta_slot == 0) L.eta0 *= eta_f;
+  else if (eta_slot == 1) L.eta1 *= eta_f;
 
   // colours
   const int T = 100 + L.n;
@@ -822,7 +909,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
   auto trial = [&](const float4& rec, int q) {
     const float lnTmax = fminf(L.lnT, rec.z);
     const bool live = lnTmax > lnTc;
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const float ic = c == 0 ? rec.x : rec.y;  // 1/c
       if (ic < 0.0f) continue;  // channel absent for this emitter
@@ -837,17 +924,13 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
     }
   };
   const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
-  int q = 0;
-  // four independent loads in flight per iteration
-  for (; q + 4 <= ne; q += 4) {
-    const float4 r0 = w.End(q), r1 = w.End(q + 1), r2 = w.End(q + 2), r3 = w.End(q + 3);
-    if (__float_as_int(r0.w) >= 0) trial(r0, q);
-    if (__float_as_int(r1.w) >= 0) trial(r1, q + 1);
-    if (__float_as_int(r2.w) >= 0) trial(r2, q + 2);
-    if (__float_as_int(r3.w) >= 0) trial(r3, q + 3);
-  }
-  for (; q < ne; ++q) {
-    const float4 r = w.End(q);
+  // one copy of the trial code (instruction-cache footprint), the next
+  // record's load issued before the current record's trials
+  float4 nxt = w.End(0);
+#pragma unroll 1
+  for (int q = 0; q < ne; ++q) {
+    const float4 r = nxt;
+    if (q + 1 < ne) nxt = w.End(q + 1);
     if (__float_as_int(r.w) >= 0) trial(r, q);
   }
   L.draw = d;
@@ -1058,7 +1141,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
                               lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull};
   const int idx[14] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
                        C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES};
-#pragma unroll
+#pragma unroll 1
   for (int q = 0; q < 14; ++q) {
     unsigned long long x = v[q];
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
@@ -1335,7 +1418,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
                               lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull};
   const int idx[14] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
                        C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES};
-#pragma unroll
+#pragma unroll 1
   for (int q = 0; q < 14; ++q) {
     unsigned long long x = v[q];
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
