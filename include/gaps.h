@@ -258,7 +258,7 @@ int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
 /* Training targets of the learned bound: for each logged state, channel and
  * bin (16 rows per state, row = state * 16 + channel * 8 + bin) the network
  * inputs features[row][4] and targets[row] = ln(max(r, 1e-6)), with r the
- * largest acceptance ratio over 33 zeta points of the bin and 64 scales in
+ * largest acceptance ratio over 33 zeta points of the bin (its edges included) and 64 log-spaced scales in
  * [t_c, t_kin]. Device arrays. */
 int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states,
                      float* features, float* targets, void* stream);

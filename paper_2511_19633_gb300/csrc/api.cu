@@ -20,6 +20,8 @@ cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSe
                                 uint64_t, int, int, int, int, int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_isr_targets(const DevParams&, int, const float4*, uint64_t, float*, float*, cudaStream_t);
 cudaError_t mixed_kernels_init();
+cudaError_t launch_mlp_image(const float* params, void* image, cudaStream_t stream);
+size_t mlp_image_bytes();
 cudaError_t launch_shower_warp(const DevParams&, const DevEvents&, const LearnedCfg&, uint64_t, uint64_t, int, int,
                                int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
@@ -41,6 +43,7 @@ struct gaps_ctx {
   void* d_work = nullptr;    // mixed-precision working set
   size_t work_bytes = 0;
   float* d_mlp = nullptr;    // learned-proposal network (FP32 parameters)
+  void* d_mlp_image = nullptr;  // its BF16 weight image for the shower
   int learned = 0;
   float* vlog = nullptr;     // caller's violation log (device), capacity, counter
   uint64_t vcap = 0;
@@ -350,6 +353,7 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
     for (int r = 0; r < ctx->P.n_rows; ++r) any_pp = any_pp || ctx->P.rows[r].process != GAPS_EE_QQ;
     Lc.learned = ctx->learned && ctx->d_mlp && any_pp;
     Lc.mlp = ctx->d_mlp;
+    Lc.image = ctx->d_mlp_image;
     Lc.vlog = reinterpret_cast<float4*>(ctx->vlog);
     Lc.vcount = reinterpret_cast<unsigned long long*>(ctx->vcount);
     Lc.vcap = ctx->vcap;
@@ -414,6 +418,9 @@ int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* l
   if (cudaMemcpy(ctx->d_mlp + GAPS_MLP_PARAMS, log_margins, nm * sizeof(float), cudaMemcpyHostToDevice) !=
       cudaSuccess)
     return GAPS_ERR_CUDA;
+  if (!ctx->d_mlp_image && cudaMalloc(&ctx->d_mlp_image, mlp_image_bytes()) != cudaSuccess) return GAPS_ERR_CUDA;
+  if (launch_mlp_image(ctx->d_mlp, ctx->d_mlp_image, nullptr) != cudaSuccess) return GAPS_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GAPS_ERR_CUDA;
   ctx->learned = 1;
   return GAPS_OK;
 }
@@ -558,6 +565,7 @@ void gaps_destroy(gaps_ctx* ctx) {
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->d_work) cudaFree(ctx->d_work);
   if (ctx->d_mlp) cudaFree(ctx->d_mlp);
+  if (ctx->d_mlp_image) cudaFree(ctx->d_mlp_image);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (cudaEvent_t e : ctx->shower_ev) cudaEventDestroy(e);

@@ -64,7 +64,8 @@ constexpr size_t kLearnedLaneBytes = 4 * sizeof(float4) + 4 * sizeof(float2);
 // learned initial-state proposal and sample collection of one launch
 struct LearnedCfg {
   int learned;                    // use the learned bin heights
-  const float* mlp;               // FP32 parameters, then the margins [44][8], device
+  const float* mlp;               // FP32 parameters, then the margins [44][8][8], device
+  const void* image;              // BF16 weight image of the network (global memory, read through L1)
   float4* collect;                // logged initial-state ends {eta, s, type, pdf index}
   unsigned long long* collect_count;
   uint64_t collect_cap;

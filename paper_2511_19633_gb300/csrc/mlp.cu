@@ -117,6 +117,9 @@ __global__ void k_forward_bf16(const float* P, const float* X, uint64_t n, float
   }
 }
 
+// The network's BF16 image in global memory for the shower's inference
+__global__ void k_mlp_image(const float* P, MlpSmem* out) { mlp_load_smem(*out, P); }
+
 // Minibatch Adam training, one block of 256 threads looping over minibatches
 // of 256 rows drawn with replacement (Philox counter = step). Activations of
 // the batch live in shared memory; the small GEMMs of the backward pass are
@@ -246,6 +249,13 @@ __global__ void __launch_bounds__(kB) k_train(float* P, float* m1, float* m2, co
 }
 
 }  // namespace
+
+cudaError_t launch_mlp_image(const float* params, void* image, cudaStream_t stream) {
+  k_mlp_image<<<1, 256, 0, stream>>>(params, reinterpret_cast<MlpSmem*>(image));
+  return cudaGetLastError();
+}
+size_t mlp_image_bytes() { return sizeof(MlpSmem); }
+
 }  // namespace gaps
 
 using namespace gaps;

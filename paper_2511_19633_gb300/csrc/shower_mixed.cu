@@ -237,10 +237,25 @@ struct WSS {
   __device__ __forceinline__ float4& MKey(int q) const { return mkey[q]; }
   __device__ __forceinline__ float2& MScale(int q) const { return mscale[q]; }
 };
+// bytes of the lane kernel's per-warp tag staging (16-byte multiple)
+__host__ __device__ constexpr size_t tag_stage_bytes(int warps, int nmax) {
+  return ((size_t)warps * nmax * sizeof(uint32_t) + 15) / 16 * 16;
+}
+
 // bytes of one warp's event in shared memory
 __host__ __device__ constexpr size_t wss_bytes(int nmax) {
   return (size_t)nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) + 4 * sizeof(float4) +
          4 * sizeof(float2);
+}
+
+// colour partner of end (i, side) among the event's tags (shared memory)
+__device__ __forceinline__ int find_partner_tags(const uint32_t* tg, int n, int i, int side, int tag) {
+  for (int m = 0; m < n; ++m) {
+    if (m == i) continue;
+    const uint32_t t = tg[m];
+    if (side == 0 ? (tag_acol(t) == tag) : (tag_col(t) == tag)) return m;
+  }
+  return -1;
 }
 
 template <class W>
@@ -326,14 +341,15 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
 // Cached record of colour end q = 2 slot + side of an event: {1/c0, 1/c1,
 // ln t_kin, partner} (partner -1: no dipole on this side).
 template <class W>
-__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, int n, double eta0,
-                             double eta1, int row, int q, float& s_out, float& eta_out, int& type_out) {
+__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, const uint32_t* tg, int n,
+                             double eta0, double eta1, int row, int q, float& s_out, float& eta_out,
+                             int& type_out) {
   type_out = -1;
   const bool pp = S.pp[row] != 0;
   const int i = q >> 1, side = q & 1;
-  const uint32_t ti = w.T(i);
+  const uint32_t ti = tg[i];
   const int tag = side == 0 ? tag_col(ti) : tag_acol(ti);
-  const int k = tag ? find_partner(w, n, i, side, tag) : -1;
+  const int k = tag ? find_partner_tags(tg, n, i, side, tag) : -1;
   if (k < 0) return make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
   const int fi = tag_fl(ti);
   const bool ini = pp && i < 2, ink = pp && k < 2;
@@ -364,7 +380,7 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, in
     channel_over(ch, type, M.P.nf, shape, coefd);
     float B = 1.0f;
     if (type == kFI) {
-      const int f = pdf_index(tag_fl(w.T(k)));
+      const int f = pdf_index(tag_fl(tg[k]));
       B = bound32(M, S, f, f, eta);
     } else if (type == kIF || type == kII) {
       int num, den;
@@ -405,8 +421,14 @@ __device__ __forceinline__ int height_code(float U) {
 template <class W>
 __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
                                          const LearnedSmem& ls, float (*stage)[4], float* ustage,
-                                         const W& w, int slot, uint64_t ev_src, int n, double eta0,
-                                         double eta1, int row, bool learned_src, int lane_id) {
+                                         const W& w, uint32_t* tg, bool stage_tags, int slot, uint64_t ev_src,
+                                         int n, double eta0, double eta1, int row, bool learned_src,
+                                         int lane_id) {
+  // the event's tags in shared memory: every end scans them for its partner
+  if (stage_tags) {
+    for (int m = lane_id; m < n; m += 32) tg[m] = w.T(m);
+    __syncwarp();
+  }
   const bool pp = S.pp[row] != 0;
   float4 isr_rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
   float isr_s = 0.0f, isr_eta = 0.0f;
@@ -414,7 +436,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   for (int q = lane_id; q < 2 * n; q += 32) {
     float s_, eta_;
     int type_;
-    const float4 rec = end_record(M, S, w, n, eta0, eta1, row, q, s_, eta_, type_);
+    const float4 rec = end_record(M, S, w, tg, n, eta0, eta1, row, q, s_, eta_, type_);
     if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
     else w.End(q) = rec;
   }
@@ -423,7 +445,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   const bool mine = lane_id < 4 && lane_id < 2 * n;
   const bool valid = mine && isr_type >= 0 && isr_rec.x > 0.0f && isr_rec.y > 0.0f &&
                      (isr_type == kIF || isr_type == kII);
-  const int fl_i = mine ? tag_fl(w.T(lane_id >> 1)) : 0;
+  const int fl_i = mine ? tag_fl(tg[lane_id >> 1]) : 0;
   // training-state sampling: a hash of (event, partons, end) decides, so
   // that a bounded log covers the whole run uniformly
   bool keep = false;
@@ -989,24 +1011,27 @@ __device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const L
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   __shared__ SmemPdf S;
-  // learned proposal only (dynamic size 0 otherwise): the network image, then
-  // per warp 64 rows of input features and 64 outputs
-  extern __shared__ __align__(16) unsigned char learned_smem[];
-  MlpSmem& mlp_s = *reinterpret_cast<MlpSmem*>(learned_smem);
-  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem + kMlpSmemBytes);
-  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + kMlpSmemBytes +
-                                                      (blockDim.x >> 5) * 64 * 4 * sizeof(float));
+  // learned proposal only (dynamic size 0 otherwise): per warp 64 rows of
+  // input features and 64 outputs, the height decode table and the height
+  // codes; the network's weight image stays in global memory (read through L1)
+  extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
+  // per warp: the tags of the event being rebuilt, then (learned proposal)
+  // staging and heights
+  uint32_t* tag_stage = reinterpret_cast<uint32_t*>(dyn_lane_smem);
+  unsigned char* learned_smem = dyn_lane_smem + tag_stage_bytes(blockDim.x >> 5, M.P.nmax);
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem);
+  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + (blockDim.x >> 5) * 64 * 4 * sizeof(float));
   LearnedSmem ls;
   ls.lanes = blockDim.x;
   ls.code = nullptr;
   ls.dec = nullptr;
   if (M.Lc.learned) {
-    unsigned char* base = learned_smem + kMlpSmemBytes + (size_t)(blockDim.x >> 5) * 64 * 5 * sizeof(float);
+    unsigned char* base = learned_smem + (size_t)(blockDim.x >> 5) * 64 * 5 * sizeof(float);
     float* dec = reinterpret_cast<float*>(base);
     ls.dec = dec;
     ls.code = base + 256 * sizeof(float);
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
-    mlp_load_smem(mlp_s, M.Lc.mlp);
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
@@ -1071,8 +1096,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
-                                  WS{M.W, warp_base + src, M.P.nmax}, warp_id * 32 + src, ev_src, n_src, e0, e1,
-                                  row_src, lok, lane_id);
+                                  WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
+                                  warp_id * 32 + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1112,8 +1137,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
-                                  WS{M.W, warp_base + src, M.P.nmax}, warp_id * 32 + src, ev_src, n_src, e0, e1,
-                                  row_src, lok, lane_id);
+                                  WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
+                                  warp_id * 32 + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1312,22 +1337,22 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
   const size_t ev_bytes = (size_t)nw * wss_stride(M.P.nmax);
   const WSS w = warp_event_smem(dyn_smem + (size_t)warp_id * wss_stride(M.P.nmax), M.P.nmax);
-  // learned proposal after the events: network image, staging, heights
+  // learned proposal after the events: staging and heights (the network's
+  // weight image stays in global memory)
   unsigned char* lbase = dyn_smem + ev_bytes;
-  MlpSmem& mlp_s = *reinterpret_cast<MlpSmem*>(lbase);
-  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(lbase + kMlpSmemBytes);
-  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(lbase + kMlpSmemBytes + (size_t)nw * 64 * 4 * sizeof(float));
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(lbase);
+  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(lbase + (size_t)nw * 64 * 4 * sizeof(float));
   LearnedSmem ls;
   ls.lanes = nw;  // one slot of heights per warp
   ls.code = nullptr;
   ls.dec = nullptr;
   if (M.Lc.learned) {
-    unsigned char* hb = lbase + kMlpSmemBytes + (size_t)nw * 64 * 5 * sizeof(float);
+    unsigned char* hb = lbase + (size_t)nw * 64 * 5 * sizeof(float);
     float* dec = reinterpret_cast<float*>(hb);
     ls.dec = dec;
     ls.code = hb + 256 * sizeof(float);
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
-    mlp_load_smem(mlp_s, M.Lc.mlp);
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
@@ -1365,8 +1390,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
         continue;
       }
       active = true;
-      mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, warp_id, L.ev, L.n, L.eta0,
-                                L.eta1, L.row, L.learned_ok, lane_id);
+      mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, w.tag, false, warp_id, L.ev,
+                                L.n, L.eta0, L.eta1, L.row, L.learned_ok, lane_id);
       rebuilds += 1;
     }
     float best, bRz;
@@ -1408,8 +1433,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
       continue;
     }
     if (done_emit) {
-      mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, warp_id, L.ev, L.n, L.eta0,
-                                L.eta1, L.row, L.learned_ok, lane_id);
+      mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, w.tag, false, warp_id, L.ev,
+                                L.n, L.eta0, L.eta1, L.row, L.learned_ok, lane_id);
       rebuilds += 1;
     }
   }
@@ -1452,7 +1477,7 @@ namespace {
 
 // Targets of the learned bound (the "teacher"): for every logged initial-state
 // end, channel and zeta bin, the largest acceptance ratio r over 33 zeta points
-// of the bin and 64 scales t log-spaced in [t_c, t_kin], as ln(max(r, 1e-6)),
+// of the bin and 64 scales t log-spaced over [t_c, t_kin] (both ends), as ln(max(r, 1e-6)),
 // with the network's input features of the row.
 constexpr int kTeacherZ = 32, kTeacherT = 64;
 __global__ void k_isr_targets(MixedCtx M, const float4* states, uint64_t n_states, float* feats, float* targets) {
@@ -1495,7 +1520,8 @@ __global__ void k_isr_targets(MixedCtx M, const float4* states, uint64_t n_state
       shape_sample32(shape, zm, delta, fminf(zeta, 0.99999994f), z, omz);
       const float pover = shape_val32(shape, (float)coefd, z, omz);
       for (int b = 0; b < kTeacherT; ++b) {
-        const float t = __expf(ltc + (ltk - ltc) * ((float)b + 0.5f) * (1.0f / kTeacherT));
+        // log-spaced, both ends included: the ratio is often largest at t_c
+        const float t = __expf(ltc + (ltk - ltc) * (float)b * (1.0f / (kTeacherT - 1)));
         float zm_t, delta_t;
         if (!zlim32(type, t, s, eta, zm_t, delta_t) || !(omz > delta_t) || !(z > zm_t)) continue;
         const IsrEval ev = isr_eval32(M, S, type, ch, fl_i, eta, s, t, z, omz, pover);
@@ -1545,7 +1571,7 @@ cudaError_t mixed_kernels_init() {
 size_t warp_kernel_smem(int block_size, int nmax, bool learned) {
   const size_t nw = (size_t)block_size / 32;
   size_t b = nw * wss_stride(nmax);
-  if (learned) b += kMlpSmemBytes + nw * 64 * 5 * sizeof(float) + 256 * sizeof(float) + nw * 64;
+  if (learned) b += nw * 64 * 5 * sizeof(float) + 256 * sizeof(float) + nw * 64;
   return b;
 }
 
@@ -1591,11 +1617,12 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
   cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
   if (err != cudaSuccess) return err;
-  // learned proposal: network image, per-warp staging, height decode table,
-  // 64 bytes of height codes per lane
-  const size_t dyn = Lc.learned ? kMlpSmemBytes + (size_t)(block_size / 32) * 64 * 5 * sizeof(float) +
-                                      256 * sizeof(float) + (size_t)block_size * 64
-                                : 0;
+  // learned proposal: per-warp staging, height decode table, 64 bytes of
+  // height codes per lane
+  const size_t dyn = tag_stage_bytes(block_size / 32, P.nmax) +
+                     (Lc.learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) +
+                                       (size_t)block_size * 64
+                                 : 0);
   // the register tier follows the resident threads the launch asks for
   const int threads_per_sm = blocks * block_size / max(1, sm_count);
   if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, dyn, stream>>>(M);
