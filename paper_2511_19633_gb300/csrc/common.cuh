@@ -55,11 +55,8 @@ struct WorkSet {
   double* p;
   uint32_t* tag;
   float4* end;
-  float4* mkey;  // learned proposal: inputs of the last evaluation per end {eta, s, class code, -} [4][lanes]
-  float2* mscale;// learned proposal: 8 / sum of the heights per end and channel [4][lanes]
   int lanes;
 };
-constexpr size_t kLearnedLaneBytes = 4 * sizeof(float4) + 4 * sizeof(float2);
 
 // learned initial-state proposal and sample collection of one launch
 struct LearnedCfg {

@@ -14,11 +14,9 @@
 //   end  f32x4 [2 nmax][L]   the event's colour ends in canonical order
 //                             (emitter ascending, colour side first):
 //                             {1/c0, 1/c1, ln t_kin, emitter | side << 8 | partner << 16}
-//   mkey f32x4 [4][L], mscale f32x2 [4][L]   learned proposal: the network
-//                             inputs of the last evaluation per initial-state
-//                             end and the resulting coefficient scales
-// (the learned bin heights themselves live in shared memory, one 8-bit code
-// per bin, next to the lanes that read them)
+// (the learned proposal's bin heights, one 8-bit code per bin, and the network
+// inputs they were evaluated at live in shared memory next to the lanes that
+// read them)
 // `end` caches the inverse overestimate coefficients of the end's channels
 // (< 0: channel absent, 0: no phase space) and is rebuilt after every
 // accepted emission.
@@ -219,8 +217,6 @@ struct WS {
   }
   __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(unsigned)(slot * W.lanes + lane)]; }
   __device__ __forceinline__ float4& End(int q) const { return W.end[(unsigned)(q * W.lanes + lane)]; }
-  __device__ __forceinline__ float4& MKey(int q) const { return W.mkey[(unsigned)(q * W.lanes + lane)]; }
-  __device__ __forceinline__ float2& MScale(int q) const { return W.mscale[(unsigned)(q * W.lanes + lane)]; }
 };
 
 // one event per warp, in shared memory (the warp-per-event kernel)
@@ -228,14 +224,10 @@ struct WSS {
   double* p;        // [4][nmax]
   uint32_t* tag;    // [nmax]
   float4* end;      // [2 nmax]
-  float4* mkey;     // [4]
-  float2* mscale;   // [4]
   int nmax;
   __device__ __forceinline__ double& P(int mu, int slot) const { return p[mu * nmax + slot]; }
   __device__ __forceinline__ uint32_t& T(int slot) const { return tag[slot]; }
   __device__ __forceinline__ float4& End(int q) const { return end[q]; }
-  __device__ __forceinline__ float4& MKey(int q) const { return mkey[q]; }
-  __device__ __forceinline__ float2& MScale(int q) const { return mscale[q]; }
 };
 // bytes of the lane kernel's per-warp tag staging (16-byte multiple)
 __host__ __device__ constexpr size_t tag_stage_bytes(int warps, int nmax) {
@@ -244,8 +236,7 @@ __host__ __device__ constexpr size_t tag_stage_bytes(int warps, int nmax) {
 
 // bytes of one warp's event in shared memory
 __host__ __device__ constexpr size_t wss_bytes(int nmax) {
-  return (size_t)nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) + 4 * sizeof(float4) +
-         4 * sizeof(float2);
+  return (size_t)nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
 }
 
 // colour partner of end (i, side) among the event's tags (shared memory)
@@ -399,9 +390,19 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, co
 struct LearnedSmem {
   unsigned char* code;   // NULL without the learned proposal
   const float* dec;      // [256] decoded heights
-  int lanes;             // threads of the block
+  float4* key;           // [4 ends][slots]: {eta, s, class code, -} of the last evaluation
+  int lanes;             // event slots of the block (threads, or warps)
   __device__ __forceinline__ unsigned char* at(int q, int c, int lane) const {
     return code + (((size_t)q * 2 + c) * lanes + lane) * 8;
+  }
+  __device__ __forceinline__ float4& keyat(int q, int lane) const { return key[q * lanes + lane]; }
+  // c * mean(U) is the learned coefficient: the cached inverse grows by 8 / sum(U)
+  __device__ __forceinline__ float scale(int q, int c, int lane) const {
+    const uint2 kc = *reinterpret_cast<const uint2*>(at(q, c, lane));
+    float tot = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) tot += dec[((m < 4 ? kc.x : kc.y) >> (8 * (m & 3))) & 0xffu];
+    return tot > 0.0f ? 8.0f / tot : 0.0f;
   }
 };
 
@@ -466,7 +467,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   const float code = (float)(isr_type * 32 + pdf_index(fl_i));
   bool need = false;
   if (use) {
-    const float4 key = w.MKey(lane_id);
+    const float4 key = ls.keyat(lane_id, slot);
     need = !(key.x == isr_eta && key.y == isr_s && key.z == code);
   }
   const unsigned eval = __ballot_sync(0xffffffffu, need) & 0xFu;
@@ -492,47 +493,29 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
     for (int tile = 0; tile < 4; ++tile)
       if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
     __syncwarp();
-    float tot[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
-      float U = 0.0f;
       if ((eval >> e) & 1u) {
-        const int cls = cls_j[j];
         // calibration margin of (class, eta bucket, bin), after the parameters
-        const float mg = __ldg(&M.Lc.mlp[kMlpParams + cls * kIsrBins + m]);
-        const int k = height_code(__expf(ustage[r] + mg));
-        ls.at(e, c, slot)[m] = (unsigned char)k;
-        U = ls.dec[k];
+        const float mg = __ldg(&M.Lc.mlp[kMlpParams + cls_j[j] * kIsrBins + m]);
+        ls.at(e, c, slot)[m] = (unsigned char)height_code(__expf(ustage[r] + mg));
       }
-      // sum over the 8 bins of the (end, channel): 8 consecutive lanes
-      U += __shfl_xor_sync(0xffffffffu, U, 1);
-      U += __shfl_xor_sync(0xffffffffu, U, 2);
-      U += __shfl_xor_sync(0xffffffffu, U, 4);
-      tot[j] = U;
     }
-    // end e's sums sit in lanes (16 e) % 32 and (16 e + 8) % 32 of row half e / 2
-    const int src0 = (lane_id * 16) & 31, src1 = (lane_id * 16 + 8) & 31;
-    const float a0 = __shfl_sync(0xffffffffu, tot[0], src0), a1 = __shfl_sync(0xffffffffu, tot[1], src0);
-    const float b0 = __shfl_sync(0xffffffffu, tot[0], src1), b1 = __shfl_sync(0xffffffffu, tot[1], src1);
-    if (need) {
-      const float t0 = (lane_id >> 1) ? a1 : a0, t1 = (lane_id >> 1) ? b1 : b0;
-      // c_learned = c * mean(U): the cached inverse grows by 8 / sum(U)
-      w.MScale(lane_id) = make_float2(t0 > 0.0f ? 8.0f / t0 : 0.0f, t1 > 0.0f ? 8.0f / t1 : 0.0f);
-      w.MKey(lane_id) = make_float4(isr_eta, isr_s, code, 0.0f);
-    }
+    if (need) ls.keyat(lane_id, slot) = make_float4(isr_eta, isr_s, code, 0.0f);
+    __syncwarp();  // the codes are visible to the end's lane
   }
   if (mine) {
     if (use) {
-      const float2 sc = w.MScale(lane_id);
-      isr_rec.x *= sc.x;
-      isr_rec.y *= sc.y;
+      // the coefficient scale from the codes, summed in the order the veto sums them
+      isr_rec.x *= ls.scale(lane_id, 0, slot);
+      isr_rec.y *= ls.scale(lane_id, 1, slot);
     } else if (ls.code) {
       // every other initial-state end proposes with height 1 in all bins (the
       // plain bound): a winner from it reads these codes, and its rate was not
       // rescaled
       for (int c = 0; c < 2; ++c) *reinterpret_cast<uint2*>(ls.at(lane_id, c, slot)) = make_uint2(0u, 0u);
-      w.MKey(lane_id) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
+      ls.keyat(lane_id, slot) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
     }
     w.End(lane_id) = isr_rec;
   }
@@ -960,7 +943,8 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
 }
 
 
-__device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, Lane& L, uint64_t e) {
+__device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, const LearnedSmem& ls, Lane& L,
+                                       uint64_t e) {
   const DevEvents& E = M.E;
   L.ev = e;
   L.status = E.status[e];
@@ -973,8 +957,8 @@ __device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, Lane& L,
   L.lnT = __logf((float)E.t[e]);
   L.learned_ok = true;
   L.row = mix_row(M.P, M.first + e);
-  if (M.Lc.learned)
-    for (int q = 0; q < 4; ++q) w.MKey(q) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
+  if (ls.key)
+    for (int q = 0; q < 4; ++q) ls.keyat(q, L.slot) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
   if (L.status != GAPS_STATUS_ACTIVE) return;
   if (L.n < 2 || L.n > M.P.nmax) { L.status = GAPS_ERR_NUMERIC; return; }
   for (int s = 0; s < L.n; ++s) {
@@ -1026,11 +1010,13 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   ls.lanes = blockDim.x;
   ls.code = nullptr;
   ls.dec = nullptr;
+  ls.key = nullptr;
   if (M.Lc.learned) {
     unsigned char* base = learned_smem + (size_t)(blockDim.x >> 5) * 64 * 5 * sizeof(float);
     float* dec = reinterpret_cast<float*>(base);
     ls.dec = dec;
     ls.code = base + 256 * sizeof(float);
+    ls.key = reinterpret_cast<float4*>(ls.code + (size_t)blockDim.x * 64);
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
@@ -1079,7 +1065,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         int rank = __popc(idle & ((1u << lane_id) - 1u));
         uint64_t e = base + rank;
         if (e < M.n) {
-          load_event(M, w, L, e);
+          load_event(M, w, ls, L, e);
           if (L.status == GAPS_STATUS_ACTIVE) active = loaded = true;
           else { store_event(M, w, L); finished += 1; }
         }
@@ -1193,14 +1179,13 @@ __device__ __forceinline__ WSS warp_event_smem(unsigned char* base, int nmax) {
   w.nmax = nmax;
   w.p = reinterpret_cast<double*>(base);
   w.end = reinterpret_cast<float4*>(base + (size_t)nmax * 4 * sizeof(double));
-  w.mkey = reinterpret_cast<float4*>(base + (size_t)nmax * (4 * sizeof(double) + 2 * sizeof(float4)));
-  w.mscale = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(w.mkey) + 4 * sizeof(float4));
-  w.tag = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(w.mscale) + 4 * sizeof(float2));
+  w.tag = reinterpret_cast<uint32_t*>(base + (size_t)nmax * (4 * sizeof(double) + 2 * sizeof(float4)));
   return w;
 }
 
 // every lane fills the same Lane; the slots are loaded by the lanes together
-__device__ void load_event_warp(const MixedCtx& M, const WSS& w, Lane& L, uint64_t e, int lane_id) {
+__device__ void load_event_warp(const MixedCtx& M, const WSS& w, const LearnedSmem& ls, Lane& L, uint64_t e,
+                                int lane_id) {
   const DevEvents& E = M.E;
   L.ev = e;
   L.status = E.status[e];
@@ -1213,7 +1198,7 @@ __device__ void load_event_warp(const MixedCtx& M, const WSS& w, Lane& L, uint64
   L.lnT = __logf((float)E.t[e]);
   L.learned_ok = true;
   L.row = mix_row(M.P, M.first + e);
-  if (M.Lc.learned && lane_id < 4) w.MKey(lane_id) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
+  if (ls.key && lane_id < 4) ls.keyat(lane_id, L.slot) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
   if (L.status != GAPS_STATUS_ACTIVE) return;
   if (L.n < 2 || L.n > M.P.nmax) { L.status = GAPS_ERR_NUMERIC; return; }
   for (int s = lane_id; s < L.n; s += 32) {
@@ -1347,11 +1332,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
   ls.lanes = nw;  // one slot of heights per warp
   ls.code = nullptr;
   ls.dec = nullptr;
+  ls.key = nullptr;
   if (M.Lc.learned) {
     unsigned char* hb = lbase + (size_t)nw * 64 * 5 * sizeof(float);
     float* dec = reinterpret_cast<float*>(hb);
     ls.dec = dec;
     ls.code = hb + 256 * sizeof(float);
+    ls.key = reinterpret_cast<float4*>(ls.code + (size_t)nw * 64);
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
@@ -1380,7 +1367,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
       if (lane_id == 0) e = atomicAdd(M.next, 1ull);
       e = __shfl_sync(0xffffffffu, e, 0);
       if (e >= M.n) break;
-      load_event_warp(M, w, L, e, lane_id);
+      load_event_warp(M, w, ls, L, e, lane_id);
       __syncwarp();
       if (L.status != GAPS_STATUS_ACTIVE) {
         store_event_warp(M, w, L, lane_id);
@@ -1454,8 +1441,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
 }  // namespace
 
 size_t workset_bytes(int lanes, int nmax) {
-  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
-         (size_t)lanes * kLearnedLaneBytes;
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
 }
 
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
@@ -1465,10 +1451,6 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   p += (size_t)lanes * nmax * 4 * sizeof(double);
   W.end = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
-  W.mkey = (float4*)p;
-  p += (size_t)lanes * 4 * sizeof(float4);
-  W.mscale = (float2*)p;
-  p += (size_t)lanes * 4 * sizeof(float2);
   W.tag = (uint32_t*)p;
 }
 
@@ -1571,7 +1553,7 @@ cudaError_t mixed_kernels_init() {
 size_t warp_kernel_smem(int block_size, int nmax, bool learned) {
   const size_t nw = (size_t)block_size / 32;
   size_t b = nw * wss_stride(nmax);
-  if (learned) b += nw * 64 * 5 * sizeof(float) + 256 * sizeof(float) + nw * 64;
+  if (learned) b += nw * 64 * 5 * sizeof(float) + 256 * sizeof(float) + nw * 64 + nw * 4 * sizeof(float4);
   return b;
 }
 
@@ -1621,7 +1603,7 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   // height codes per lane
   const size_t dyn = tag_stage_bytes(block_size / 32, P.nmax) +
                      (Lc.learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) +
-                                       (size_t)block_size * 64
+                                       (size_t)block_size * 64 + (size_t)block_size * 4 * sizeof(float4)
                                  : 0);
   // the register tier follows the resident threads the launch asks for
   const int threads_per_sm = blocks * block_size / max(1, sm_count);
@@ -1640,7 +1622,7 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
 // device footprint), or code whose memory is fixed before it starts. For them
 // the mixed-precision shower runs with every piece of its scratch memory in
 // file-scope device arrays: the per-lane working set of 64 blocks x 128 threads
-// for at most 32 partons per event (20 MB), the work counter, the
+// for at most 32 partons per event (17.8 MB), the work counter, the
 // statistics, and copies of the PDF grid and its bound tables. Every GPU that
 // loads the library holds these arrays until the process exits.
 // ---------------------------------------------------------------------------
@@ -1651,8 +1633,7 @@ constexpr int kStaticBlocks = 64, kStaticThreads = 128;
 constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
 constexpr size_t kStaticWorkBytes =
-    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
-    (size_t)kStaticLanes * kLearnedLaneBytes;
+    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
 
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
 static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];
