@@ -305,7 +305,7 @@ def run_ours(args, ws, rank, local):
     tuning = None
     if mixed and not args.no_autotune:
         from paper_2511_19633_gb300 import autotune
-        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 19, mix=mix, learned=learned)
+        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 21, mix=mix, learned=learned)
         shape = tuning["best"]
     schedule = G.GAPS_SCHED_PERSISTENT if (mixed or args.schedule) else G.GAPS_SCHED_PER_EVENT
 

@@ -2,7 +2,9 @@
 
 Sweeps threads per block x resident blocks per SM x refill (compaction)
 period x emission batch on a sample of the workload, timing gaps_shower with
-CUDA events, and returns the fastest shape with the whole table. The paper
+CUDA events, and returns the fastest shape with the whole table. The sample
+must give every lane of the widest grid several events (2^21 events for up to
+155 648 lanes), or the tail of the launch decides. The paper
 tunes a single block size for all its kernels by hand (Section 3.2); here the
 persistent kernel's shape is tuned per workload.
 """
@@ -18,7 +20,7 @@ DEFAULT_GRID = {
     "block_size": (128, 256),
     "blocks_per_sm": (2, 4, 8),
     "refill_period": (1, 4),
-    "emit_batch": (4, 8, 16),
+    "emit_batch": (8, 16),
 }
 
 
@@ -57,7 +59,7 @@ def time_shape(process, sqrt_s, pdf, shape: dict, n_events: int, precision=G.GAP
             "lane_efficiency": st["lane_steps"] / max(1, st["warp_steps"])}
 
 
-def autotune(process, sqrt_s, pdf, n_events: int = 1 << 19, grid: dict | None = None,
+def autotune(process, sqrt_s, pdf, n_events: int = 1 << 21, grid: dict | None = None,
              precision=G.GAPS_MIXED, mix=None, learned=None) -> dict:
     grid = grid or DEFAULT_GRID
     keys = list(grid)

@@ -208,15 +208,19 @@ __device__ __forceinline__ float shape_val32(int sh, float coef, float z, float 
 }
 
 // ---- working-set access ------------------------------------------------------
-// 32-bit element indices: lanes x 4 nmax < 2^31 (checked by the launcher)
+// Lane-major: each lane's event is contiguous (a slot's four momentum
+// components in 32 bytes, the end table in 2 nmax x 16 bytes), so the trial
+// loop walks its own cache lines and the cooperative rebuild reads one
+// event's lines. 32-bit element indices: lanes x 4 nmax < 2^31 (checked by
+// the launcher).
 struct WS {
   const WorkSet& W;
   int lane, nmax;
   __device__ __forceinline__ double& P(int mu, int slot) const {
-    return W.p[(unsigned)((mu * nmax + slot) * W.lanes + lane)];
+    return W.p[(unsigned)((lane * nmax + slot) * 4 + mu)];
   }
-  __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(unsigned)(slot * W.lanes + lane)]; }
-  __device__ __forceinline__ float4& End(int q) const { return W.end[(unsigned)(q * W.lanes + lane)]; }
+  __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(unsigned)(lane * nmax + slot)]; }
+  __device__ __forceinline__ float4& End(int q) const { return W.end[(unsigned)(lane * 2 * nmax + q)]; }
 };
 
 // one event per warp, in shared memory (the warp-per-event kernel)
