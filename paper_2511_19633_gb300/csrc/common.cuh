@@ -55,6 +55,8 @@ struct WorkSet {
   double* p;
   uint32_t* tag;
   float4* end;
+  float4* lkey;          // learned proposal: network inputs of the last evaluation [lanes][4 ends]
+  unsigned char* lcode;  // learned proposal: 8-bit bin-height codes [lanes][4 ends][2][8]
   int lanes;
 };
 

@@ -388,18 +388,20 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, co
   return make_float4(ic[0], ic[1], __logf(tk), __int_as_float(k));
 }
 
-// Learned bin heights of the block's lanes in shared memory, 8-bit codes:
-// height = 2^(-k/16) (k < 255), rounded up from the network's value so that it
-// stays a bound; codes [4 ends][2 channels][lanes][8 bins].
+// Learned bin heights of an event slot, 8-bit codes: height = 2^(-k/16)
+// (k < 255), rounded up from the network's value so that it stays a bound.
+// Slot-major, [slot][4 ends][2 channels][8 bins] bytes and [slot][4 ends]
+// keys: in the lane kernel the slots are the global lanes (working set in
+// global memory, read through L1), in the warp kernel the block's warps
+// (shared memory).
 struct LearnedSmem {
   unsigned char* code;   // NULL without the learned proposal
-  const float* dec;      // [256] decoded heights
-  float4* key;           // [4 ends][slots]: {eta, s, class code, -} of the last evaluation
-  int lanes;             // event slots of the block (threads, or warps)
-  __device__ __forceinline__ unsigned char* at(int q, int c, int lane) const {
-    return code + (((size_t)q * 2 + c) * lanes + lane) * 8;
+  const float* dec;      // [256] decoded heights (shared memory)
+  float4* key;           // {eta, s, class code, -} of the last evaluation per end
+  __device__ __forceinline__ unsigned char* at(int q, int c, int slot) const {
+    return code + (size_t)slot * 64 + (q * 2 + c) * 8;
   }
-  __device__ __forceinline__ float4& keyat(int q, int lane) const { return key[q * lanes + lane]; }
+  __device__ __forceinline__ float4& keyat(int q, int slot) const { return key[(size_t)slot * 4 + q]; }
   // c * mean(U) is the learned coefficient: the cached inverse grows by 8 / sum(U)
   __device__ __forceinline__ float scale(int q, int c, int lane) const {
     const uint2 kc = *reinterpret_cast<const uint2*>(at(q, c, lane));
@@ -1011,7 +1013,6 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem);
   float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + (blockDim.x >> 5) * 64 * 4 * sizeof(float));
   LearnedSmem ls;
-  ls.lanes = blockDim.x;
   ls.code = nullptr;
   ls.dec = nullptr;
   ls.key = nullptr;
@@ -1019,8 +1020,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
     unsigned char* base = learned_smem + (size_t)(blockDim.x >> 5) * 64 * 5 * sizeof(float);
     float* dec = reinterpret_cast<float*>(base);
     ls.dec = dec;
-    ls.code = base + 256 * sizeof(float);
-    ls.key = reinterpret_cast<float4*>(ls.code + (size_t)blockDim.x * 64);
+    ls.code = M.W.lcode;
+    ls.key = M.W.lkey;
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
@@ -1043,7 +1044,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   const int warp_id = threadIdx.x >> 5;
   WS w{M.W, gl, M.P.nmax};
   Lane L;
-  L.slot = threadIdx.x;
+  L.slot = gl;
   bool active = false;
   bool exhausted = false;
   Counters32 cnt;
@@ -1087,7 +1088,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
                                   WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
-                                  warp_id * 32 + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
+                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1128,7 +1129,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
                                   WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
-                                  warp_id * 32 + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
+                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1332,8 +1333,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
   const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
   float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(lbase);
   float(*ustage)[64] = reinterpret_cast<float(*)[64]>(lbase + (size_t)nw * 64 * 4 * sizeof(float));
-  LearnedSmem ls;
-  ls.lanes = nw;  // one slot of heights per warp
+  LearnedSmem ls;  // one slot of heights per warp, in shared memory
   ls.code = nullptr;
   ls.dec = nullptr;
   ls.key = nullptr;
@@ -1445,7 +1445,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
 }  // namespace
 
 size_t workset_bytes(int lanes, int nmax) {
-  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+         (size_t)lanes * (64 + 4 * sizeof(float4));
 }
 
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
@@ -1455,6 +1456,10 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   p += (size_t)lanes * nmax * 4 * sizeof(double);
   W.end = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
+  W.lkey = (float4*)p;
+  p += (size_t)lanes * 4 * sizeof(float4);
+  W.lcode = (unsigned char*)p;
+  p += (size_t)lanes * 64;
   W.tag = (uint32_t*)p;
 }
 
@@ -1606,9 +1611,7 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   // learned proposal: per-warp staging, height decode table, 64 bytes of
   // height codes per lane
   const size_t dyn = tag_stage_bytes(block_size / 32, P.nmax) +
-                     (Lc.learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) +
-                                       (size_t)block_size * 64 + (size_t)block_size * 4 * sizeof(float4)
-                                 : 0);
+                     (Lc.learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) : 0);
   // the register tier follows the resident threads the launch asks for
   const int threads_per_sm = blocks * block_size / max(1, sm_count);
   if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, dyn, stream>>>(M);
@@ -1637,7 +1640,8 @@ constexpr int kStaticBlocks = 64, kStaticThreads = 128;
 constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
 constexpr size_t kStaticWorkBytes =
-    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+    (size_t)kStaticLanes * (64 + 4 * sizeof(float4));
 
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
 static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];

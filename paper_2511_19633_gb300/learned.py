@@ -59,7 +59,18 @@ def collect_states(ctx, first_event: int, n_events: int, capacity: int, chunk: i
         G.gaps_generate_hard(ctx, first_event + f0, m, ev, stream)
         G.gaps_collect_isr_states(ctx, first_event + f0, m, ev, states, count, keep, stream)
     torch.cuda.synchronize()
-    return states[: min(int(count.item()), capacity)]
+    return _canonical_order(states[: min(int(count.item()), capacity)])
+
+
+def _canonical_order(states: torch.Tensor) -> torch.Tensor:
+    """The logged states in a fixed order (the shower logs them in the order of
+    its atomic counter): with it the training, and so the network, is the same
+    on every run."""
+    if states.shape[0] == 0:
+        return states
+    h = states.cpu().numpy()
+    order = np.lexsort((h[:, 1], h[:, 0], h[:, 3], h[:, 2]))
+    return torch.from_numpy(np.ascontiguousarray(h[order])).to(states.device)
 
 
 # targets below ln(1e-4) are raised to it: a higher target is still an upper
