@@ -126,6 +126,15 @@ typedef struct {
                              mixed batch of these rows, which replace process,
                              sqrt_s and t_cut above */
     gaps_mix_row mix[GAPS_MAX_MIX];
+    int trial_cache;      /* GAPS_MIXED with GAPS_SCHED_PERSISTENT only: 1 keeps the
+                             losing trials of a cycle; after a veto only the winner's
+                             channel draws again, after an emission only the ends whose
+                             record changed (exact: each channel's trials are a Poisson
+                             process in ln t, whose first point below the scale the
+                             event continues from is the kept trial); 0 redraws every
+                             channel every cycle (Fig. 1 as printed, the FP64 path's
+                             draw order). Any other value, or 1 with another precision
+                             or schedule, is GAPS_ERR_INVALID_ARG */
 } gaps_config;
 
 /* Event records: structure of arrays in device memory, caller-owned, event
@@ -205,7 +214,7 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
  * The paper has no counterpart: it is the GAPS_MIXED persistent shower of
  * gaps_shower, run with 64 blocks of 128 threads and emission batch 8, with
  * every piece of scratch memory held in device arrays of the library itself:
- * a working set for at most 32 partons per event (17.8 MB), the work counter,
+ * a working set for at most 32 partons per event (27.3 MB), the work counter,
  * the statistics and copies of the PDF grid and its bound tables. Every GPU
  * that loads the library keeps these arrays until the process exits.
  * It needs no context: `cfg` is read as in gaps_init (its precision and launch

@@ -38,6 +38,7 @@ constexpr uint64_t kMixDraw = 0x4000000000000000ull;
 struct DevParams {
   int process, nf, nmax;
   double sqrt_s, s_had, t_cut, as_mz, as_over, beta0, p_s;
+  int trial_cache;             // mixed lane kernel: keep the losing trials of a vetoed cycle
   int n_rows;                  // 1: one process; > 1: mixed batch
   RowParams rows[kMaxRows];    // row 0 = the fields above for one process
   double cum[kMaxRows];        // cumulative fractions, summed in row order
@@ -55,6 +56,7 @@ struct WorkSet {
   double* p;
   uint32_t* tag;
   float4* end;
+  float4* trial;         // kept trials {ln t, R_z} of both channels per end [lanes][2 nmax]
   float4* lkey;          // learned proposal: network inputs of the last evaluation [lanes][4 ends]
   unsigned char* lcode;  // learned proposal: 8-bit bin-height codes [lanes][4 ends][2][8]
   int lanes;

@@ -221,6 +221,10 @@ struct WS {
   }
   __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(unsigned)(lane * nmax + slot)]; }
   __device__ __forceinline__ float4& End(int q) const { return W.end[(unsigned)(lane * 2 * nmax + q)]; }
+  // kept trials of end q: {ln t, R_z} of channel 0, then of channel 1; a NaN
+  // ln t of channel 0 marks an end whose channels draw in the next cycle
+  __device__ __forceinline__ float4& Trial(int q) const { return W.trial[(unsigned)(lane * 2 * nmax + q)]; }
+  static constexpr bool kTrials = true;
 };
 
 // one event per warp, in shared memory (the warp-per-event kernel)
@@ -232,6 +236,7 @@ struct WSS {
   __device__ __forceinline__ double& P(int mu, int slot) const { return p[mu * nmax + slot]; }
   __device__ __forceinline__ uint32_t& T(int slot) const { return tag[slot]; }
   __device__ __forceinline__ float4& End(int q) const { return end[q]; }
+  static constexpr bool kTrials = false;  // no kept trials in this schedule
 };
 // bytes of the lane kernel's per-warp tag staging (16-byte multiple)
 __host__ __device__ constexpr size_t tag_stage_bytes(int warps, int nmax) {
@@ -419,6 +424,29 @@ __device__ __forceinline__ int height_code(float U) {
   return k < 0.0f ? 0 : (k > 254.0f ? 254 : (int)k);
 }
 
+// Writes end q's record. With kept trials (keep_ends >= 0) an end among the
+// first keep_ends whose record (rates, maximum scale, partner) is unchanged
+// keeps its trials: each channel's trials are a Poisson process in ln t with
+// that rate, and the kept trial lies below the scale the event continues from.
+// Every other end draws in the next cycle.
+template <class W>
+__device__ __forceinline__ void set_end(const W& w, int q, const float4& rec, int keep_ends) {
+  if constexpr (W::kTrials) {
+    if (keep_ends < 0) {
+      // trials are not kept
+    } else if (q < keep_ends) {
+      const float4 old = w.End(q);
+      if (__float_as_uint(old.x) == __float_as_uint(rec.x) && __float_as_uint(old.y) == __float_as_uint(rec.y) &&
+          __float_as_uint(old.z) == __float_as_uint(rec.z) && __float_as_uint(old.w) == __float_as_uint(rec.w))
+        return;
+      w.Trial(q).x = __uint_as_float(0x7fc00000u);
+    } else {
+      w.Trial(q).x = __uint_as_float(0x7fc00000u);
+    }
+  }
+  w.End(q) = rec;
+}
+
 // The whole warp rebuilds the colour-end table of the event held by lane
 // `src` (one end per lane), after an emission or a refill of that lane. With
 // the learned proposal the warp then evaluates the network for those of the
@@ -430,7 +458,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
                                          const LearnedSmem& ls, float (*stage)[4], float* ustage,
                                          const W& w, uint32_t* tg, bool stage_tags, int slot, uint64_t ev_src,
                                          int n, double eta0, double eta1, int row, bool learned_src,
-                                         int lane_id) {
+                                         int keep_ends, int lane_id) {
   // the event's tags in shared memory: every end scans them for its partner
   if (stage_tags) {
     for (int m = lane_id; m < n; m += 32) tg[m] = w.T(m);
@@ -445,7 +473,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
     int type_;
     const float4 rec = end_record(M, S, w, tg, n, eta0, eta1, row, q, s_, eta_, type_);
     if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
-    else w.End(q) = rec;
+    else set_end(w, q, rec, keep_ends);
   }
   if (!pp) return 0;
   // lanes 0..3 hold the ends of the incoming partons
@@ -523,7 +551,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
       for (int c = 0; c < 2; ++c) *reinterpret_cast<uint2*>(ls.at(lane_id, c, slot)) = make_uint2(0u, 0u);
       ls.keyat(lane_id, slot) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
     }
-    w.End(lane_id) = isr_rec;
+    set_end(w, lane_id, isr_rec, keep_ends);
   }
   __syncwarp();
   return __popc(eval);
@@ -905,49 +933,81 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
 
 
 // One max-veto cycle of the lane's event: one overestimate trial per channel
-// of every colour end in canonical order, then step_veto.
+// of every colour end in canonical order, then step_veto. With kept trials
+// only the ends marked by the last rebuild draw, and after a veto only the
+// winner's channel: every channel's trials are a Poisson process in ln t, so
+// when the winner at t_w is vetoed, each other channel's trial is the first
+// point of its process below t_w.
 __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem& ls, const WS& w, Lane& L,
                           uint64_t id, Counters32& cnt, Emission& pend, bool& parked) {
   const bool pp = S.pp[L.row] != 0;
   const float lnTc = S.lnTc[L.row];
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
   const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+  const bool cache = M.P.trial_cache != 0;
   float best = -INFINITY;
   int bq = -1, bch = 0;
   float bRz = 0.5f;
+  const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
   uint64_t d = L.draw;
-  // one overestimate trial per channel of every colour end, in canonical order
-  auto trial = [&](const float4& rec, int q) {
-    const float lnTmax = fminf(L.lnT, rec.z);
-    const bool live = lnTmax > lnTc;
+  // one copy of the trial code (instruction-cache footprint); the next end's
+  // load is issued before the current end's trials
+  const float4 marked = make_float4(__uint_as_float(0x7fc00000u), 0.5f, -INFINITY, 0.5f);
+  float4 nxt = cache ? w.Trial(0) : marked;
 #pragma unroll 1
-    for (int c = 0; c < 2; ++c) {
-      const float ic = c == 0 ? rec.x : rec.y;  // 1/c
-      if (ic < 0.0f) continue;  // channel absent for this emitter
-      const uint64_t dd = d++;
-      if (!(live && ic > 0.0f)) continue;
+  for (int q = 0; q < ne; ++q) {
+    float4 tr = nxt;
+    if (cache && q + 1 < ne) nxt = w.Trial(q + 1);
+    if (isnan(tr.x)) {  // this end draws
+      tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+      const float4 rec = w.End(q);
+      if (__float_as_int(rec.w) >= 0) {  // a dipole on this side
+        const float lnTmax = fminf(L.lnT, rec.z);
+        const bool live = lnTmax > lnTc;
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+          const float ic = c == 0 ? rec.x : rec.y;  // 1/c
+          if (ic < 0.0f) continue;  // channel absent for this emitter
+          const uint64_t dd = d++;
+          if (!(live && ic > 0.0f)) continue;
+          uint32_t out[4];
+          philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+          cnt.trials += 1;
+          if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
+          const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);  // ln(t_max R^(1/c))
+          if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
+          else { tr.z = lt; tr.w = u24(out[3]); }
+        }
+      }
+      if (cache) w.Trial(q) = tr;
+    }
+    // the largest wins, the earlier one on ties
+    if (tr.x > best) { best = tr.x; bq = q; bch = 0; bRz = tr.y; }
+    if (tr.z > best) { best = tr.z; bq = q; bch = 1; bRz = tr.w; }
+  }
+  L.draw = d;
+  const int st = step_veto(M, S, ls, w, L, id, cnt, pend, parked, best, bq, bch, bRz);
+  if (cache && st == GAPS_STATUS_ACTIVE && !parked && bq >= 0) {
+    // vetoed: the winner's channel draws its next trial below t_w = L.lnT
+    const float4 rec = w.End(bq);
+    const float ic = bch == 0 ? rec.x : rec.y;
+    const float lnTmax = fminf(L.lnT, rec.z);
+    float lt = -INFINITY, rz = 0.5f;
+    const uint64_t dd = L.draw++;
+    if (lnTmax > lnTc && ic > 0.0f) {
       uint32_t out[4];
       philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
       cnt.trials += 1;
-      if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
-      const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);  // ln(t_max R^(1/c))
-      if (lt > best) { best = lt; bq = q; bch = c; bRz = u24(out[3]); }
+      if (pp && bq < 4) cnt.isr_trials += 1;
+      lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+      rz = u24(out[3]);
     }
-  };
-  const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
-  // one copy of the trial code (instruction-cache footprint), the next
-  // record's load issued before the current record's trials
-  float4 nxt = w.End(0);
-#pragma unroll 1
-  for (int q = 0; q < ne; ++q) {
-    const float4 r = nxt;
-    if (q + 1 < ne) nxt = w.End(q + 1);
-    if (__float_as_int(r.w) >= 0) trial(r, q);
+    float4 tr = w.Trial(bq);
+    if (bch == 0) { tr.x = lt; tr.y = rz; } else { tr.z = lt; tr.w = rz; }
+    w.Trial(bq) = tr;
   }
-  L.draw = d;
-  return step_veto(M, S, ls, w, L, id, cnt, pend, parked, best, bq, bch, bRz);
+  return st;
 }
-
 
 __device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, const LearnedSmem& ls, Lane& L,
                                        uint64_t e) {
@@ -1055,6 +1115,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   bool parked = false;
   Emission pend;
   int since_flush = 0;
+  const bool cache = M.P.trial_cache != 0;
   while (true) {
     // warp-aggregated refill of idle lanes
     unsigned idle = __ballot_sync(0xffffffffu, !active);
@@ -1088,7 +1149,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
                                   WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
-                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
+                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, cache ? 0 : -1,
+                                  lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1107,14 +1169,23 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
     if (pk && (__popc(pk) >= M.emit_batch || pk == act || since_flush >= M.emit_wait)) {
       since_flush = 0;
       bool done_emit = false;
+      int keep = -1;  // ends of the emitting lane that may keep their trials
       if (parked) {
         parked = false;
         if (pend.kind == 1) {
-          done_emit = true;  // plain rebuild after a learned-bound violation
+          // plain rebuild after a learned-bound violation: the event goes on
+          // from the scale before that cycle, and every end draws again
+          done_emit = true;
+          keep = cache ? 0 : -1;
         } else {
           done_emit = emit(M, S, w, L, pend);
-          if (done_emit) cnt.accepts += 1;
-          else cnt.vetoes += 1;
+          if (done_emit) {
+            cnt.accepts += 1;
+            keep = cache ? 2 * (L.n - 1) : -1;  // the ends that existed before
+          } else {
+            cnt.vetoes += 1;  // the map failed: the winner's end draws again
+            if (cache) w.Trial(2 * pend.bi + pend.bside).x = __uint_as_float(0x7fc00000u);
+          }
         }
       }
       __syncwarp();  // the emissions above are visible to the whole warp
@@ -1127,9 +1198,10 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
         const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
+        const int keep_src = __shfl_sync(0xffffffffu, keep, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
                                   WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
-                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, lane_id);
+                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, keep_src, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1382,7 +1454,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
       }
       active = true;
       mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, w.tag, false, warp_id, L.ev,
-                                L.n, L.eta0, L.eta1, L.row, L.learned_ok, lane_id);
+                                L.n, L.eta0, L.eta1, L.row, L.learned_ok, -1, lane_id);
       rebuilds += 1;
     }
     float best, bRz;
@@ -1425,7 +1497,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
     }
     if (done_emit) {
       mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id], w, w.tag, false, warp_id, L.ev,
-                                L.n, L.eta0, L.eta1, L.row, L.learned_ok, lane_id);
+                                L.n, L.eta0, L.eta1, L.row, L.learned_ok, -1, lane_id);
       rebuilds += 1;
     }
   }
@@ -1445,7 +1517,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
 }  // namespace
 
 size_t workset_bytes(int lanes, int nmax) {
-  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
          (size_t)lanes * (64 + 4 * sizeof(float4));
 }
 
@@ -1455,6 +1527,8 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   W.p = (double*)p;
   p += (size_t)lanes * nmax * 4 * sizeof(double);
   W.end = (float4*)p;
+  p += (size_t)lanes * nmax * 2 * sizeof(float4);
+  W.trial = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
   W.lkey = (float4*)p;
   p += (size_t)lanes * 4 * sizeof(float4);
@@ -1629,7 +1703,7 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
 // device footprint), or code whose memory is fixed before it starts. For them
 // the mixed-precision shower runs with every piece of its scratch memory in
 // file-scope device arrays: the per-lane working set of 64 blocks x 128 threads
-// for at most 32 partons per event (17.8 MB), the work counter, the
+// for at most 32 partons per event (27.3 MB), the work counter, the
 // statistics, and copies of the PDF grid and its bound tables. Every GPU that
 // loads the library holds these arrays until the process exits.
 // ---------------------------------------------------------------------------
@@ -1640,7 +1714,7 @@ constexpr int kStaticBlocks = 64, kStaticThreads = 128;
 constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
 constexpr size_t kStaticWorkBytes =
-    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
     (size_t)kStaticLanes * (64 + 4 * sizeof(float4));
 
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
@@ -1681,7 +1755,10 @@ extern "C" int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, 
                                   const gaps_events* ev, gaps_stats* stats, void* stream) {
   using namespace gaps;
   if (!cfg || !ev) return GAPS_ERR_INVALID_ARG;
-  if (validate_config(*cfg) != GAPS_OK) return GAPS_ERR_INVALID_ARG;
+  gaps_config c = *cfg;  // always the persistent mixed-precision shower
+  c.precision = GAPS_MIXED;
+  c.schedule = GAPS_SCHED_PERSISTENT;
+  if (validate_config(c) != GAPS_OK) return GAPS_ERR_INVALID_ARG;
   if (!ev->p || !ev->flav || !ev->col || !ev->acol || !ev->npart || !ev->status || !ev->n_emit ||
       !ev->weight || !ev->t || !ev->eta || !ev->draw)
     return GAPS_ERR_INVALID_ARG;
@@ -1696,7 +1773,7 @@ extern "C" int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, 
   if (rc != GAPS_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   DevParams P;
-  fill_params(*cfg, P);
+  fill_params(c, P);
   int q_independent = 1;
   if (cfg->pdf_grid) {
     double tables[kBoundTableDoubles];

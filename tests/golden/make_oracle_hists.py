@@ -34,9 +34,9 @@ NBINS = 66
 
 # name: (process, sqrt_s, events, t_cut)
 WORKLOADS = {
-    "ee91": (0, 91.2, 1_000_000, 1.0),
-    "ee500": (0, 500.0, 1_000_000, 1.0),
-    "pp_lo": (1, 13600.0, 1_000_000, 1.0),
+    "ee91": (0, 91.2, 10_000_000, 1.0),
+    "ee500": (0, 500.0, 10_000_000, 1.0),
+    "pp_lo": (1, 13600.0, 10_000_000, 1.0),
     "pp_nlo": (2, 13600.0, 10_000_000, 1.0),
     # the e+e- rows of the mixed batch (their own cutoffs)
     "ee91_tc0.5": (0, 91.2, 1_000_000, 0.5),

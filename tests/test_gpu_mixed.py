@@ -23,7 +23,7 @@ def test_mixed_follows_fp64_histories(G, pdf):
     proc, sqrt_s = PROCESS["pp_nlo"]
     n = 20011
     a = run_gpu(G, proc, sqrt_s, 0, n, pdf)
-    b = run_gpu(G, proc, sqrt_s, 0, n, pdf, precision=MIXED, schedule=1, blocks_per_sm=4)
+    b = run_gpu(G, proc, sqrt_s, 0, n, pdf, precision=MIXED, schedule=1, blocks_per_sm=4, trial_cache=False)
     same = (a["npart"] == b["npart"]) & np.all(a["flav"] == b["flav"], axis=1)
     frac = same.mean()
     assert frac > 0.9, frac
@@ -76,7 +76,7 @@ def test_mixed_capacity_errors(G, pdf):
     assert np.all(g["npart"][st == -2] == 6)
 
 
-def _gpu_hists(G, name, pdf, precision, n, chunk=1 << 21):
+def _gpu_hists(G, name, pdf, precision, n, first0=0, chunk=1 << 21):
     import torch
     proc, sqrt_s = PROCESS[name]
     cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf if proc else None, nmax=128, seed=1,
@@ -89,8 +89,8 @@ def _gpu_hists(G, name, pdf, precision, n, chunk=1 << 21):
         hw = torch.zeros((G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64, device="cuda")
         hw2 = torch.zeros_like(hw)
         hists = G.GapsHists(hw.data_ptr(), hw2.data_ptr())
-        for first in range(0, n, cap):
-            m = min(cap, n - first)
+        for first in range(first0, first0 + n, cap):
+            m = min(cap, first0 + n - first)
             G.gaps_generate_hard(ctx, first, m, ev)
             G.gaps_shower(ctx, first, m, ev)
             G.gaps_observables(ctx, first, m, ev, None, hists)
@@ -104,18 +104,56 @@ def _gpu_hists(G, name, pdf, precision, n, chunk=1 << 21):
 
 @pytest.mark.parametrize("name", ["ee91", "ee500", "pp_lo", "pp_nlo"])
 def test_mixed_histograms_match_oracle(G, pdf, name):
-    """chi^2/ndf < 1.2 against the FP64 oracle's histograms (independent seed)
-    at the full event count of each workload (1e7 for NLO pp -> Z)."""
+    """chi^2/ndf < 1.2 against the FP64 oracle's histograms (independent seed,
+    1e7 events) for samples of 1e7 events. With about 200 degrees of freedom a
+    correct generator exceeds 1.2 on about 2.6% of samples, so the bar is put
+    on the median of three independent event ranges (at least two of three
+    samples pass), with 1.5 as the limit for every sample."""
     import os
     from tests.hist_common import GOLDEN
     if not os.path.exists(os.path.join(GOLDEN, "oracle_hists_%s.json" % name)):
         pytest.fail("reference histograms missing: run tests/golden/make_oracle_hists.py")
     gold = load_golden(name)
     n = gold["events"]
-    w, w2, binning, stats = _gpu_hists(G, name, pdf, MIXED, n)
-    for (lo, hi, nb, oi, lg), b in zip(gold["binning"], binning):
-        assert (b["lo"], b["hi"], b["nbins"], b["obs"], int(b["log10"])) == pytest.approx((lo, hi, nb, oi, lg))
-    per = chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"])
-    red, chi2, ndf = chi2_summary(per)
-    assert stats["violations"] == 0 and stats["events"] == n
-    assert red < 1.2, (red, per)
+    reds = []
+    for r in range(3):
+        w, w2, binning, stats = _gpu_hists(G, name, pdf, MIXED, n, first0=r << 40)
+        for (lo, hi, nb, oi, lg), b in zip(gold["binning"], binning):
+            assert (b["lo"], b["hi"], b["nbins"], b["obs"], int(b["log10"])) == pytest.approx((lo, hi, nb, oi, lg))
+        per = chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"])
+        red, chi2, ndf = chi2_summary(per)
+        assert stats["violations"] == 0 and stats["events"] == n
+        reds.append(red)
+    assert float(np.median(reds)) < 1.2 and max(reds) < 1.5, reds
+
+def test_trial_cache_needs_persistent_mixed(G, pdf):
+    for prec, sched in ((0, 0), (0, 1), (MIXED, 2)):
+        with pytest.raises(G.GapsError) as e:
+            G.gaps_init(G.make_config(0, 91.2, precision=prec, schedule=sched, trial_cache=True))
+        assert e.value.code == G.GAPS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["ee500", "pp_nlo"])
+def test_trial_cache_keeps_distributions_and_cuts_trials(G, pdf, name):
+    """Kept trials are exact (each channel's trials are a Poisson process in
+    ln t): the same events, shower for shower, come out with different random
+    histories but the same distributions, from fewer overestimate trials."""
+    proc, sqrt_s = PROCESS[name]
+    n = 200003
+    on = run_gpu(G, proc, sqrt_s, 31, n, pdf, precision=MIXED, schedule=1, trial_cache=True)
+    off = run_gpu(G, proc, sqrt_s, 31, n, pdf, precision=MIXED, schedule=1, trial_cache=False)
+    for g in (on, off):
+        assert np.all(g["status"] == 1) and g["stats"]["events"] == n and g["stats"]["violations"] == 0
+    # the hard process is drawn before the shower: identical in both
+    assert np.array_equal(on["weight"], off["weight"])
+    assert on["stats"]["trials"] < 0.8 * off["stats"]["trials"], (on["stats"]["trials"], off["stats"]["trials"])
+    # emission multiplicity and per-event observables agree within 5 sigma
+    for a, b in ((on["n_emit"].astype(float), off["n_emit"].astype(float)),) + tuple(
+            (on["obs"][:, j], off["obs"][:, j]) for j in range(on["obs"].shape[1])):
+        ok = np.isfinite(a) & np.isfinite(b)
+        a, b = a[ok], b[ok]
+        if a.size < 1000 or a.std() == 0:
+            continue
+        err = np.hypot(a.std() / np.sqrt(a.size), b.std() / np.sqrt(b.size))
+        assert abs(a.mean() - b.mean()) < 5 * err, (a.mean(), b.mean(), err)
+    assert abs(on["stats"]["accepts"] - off["stats"]["accepts"]) < 5 * np.sqrt(2 * off["stats"]["accepts"])
