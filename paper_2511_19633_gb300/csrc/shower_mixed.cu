@@ -407,14 +407,6 @@ struct LearnedSmem {
     return code + (size_t)slot * 64 + (q * 2 + c) * 8;
   }
   __device__ __forceinline__ float4& keyat(int q, int slot) const { return key[(size_t)slot * 4 + q]; }
-  // c * mean(U) is the learned coefficient: the cached inverse grows by 8 / sum(U)
-  __device__ __forceinline__ float scale(int q, int c, int lane) const {
-    const uint2 kc = *reinterpret_cast<const uint2*>(at(q, c, lane));
-    float tot = 0.0f;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) tot += dec[((m < 4 ? kc.x : kc.y) >> (8 * (m & 3))) & 0xffu];
-    return tot > 0.0f ? 8.0f / tot : 0.0f;
-  }
 };
 
 __device__ __forceinline__ int height_code(float U) {
@@ -465,6 +457,13 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
     __syncwarp();
   }
   const bool pp = S.pp[row] != 0;
+  // the learned state of the initial-state ends, loaded before the records
+  // are built: the inputs of the last evaluation and the record it gave
+  float4 key = make_float4(-1.0f, -1.0f, -1.0f, 0.0f), old_isr = key;
+  if (pp && lane_id < 4 && lane_id < 2 * n && M.Lc.learned && learned_src) {
+    key = ls.keyat(lane_id, slot);
+    old_isr = w.End(lane_id);
+  }
   float4 isr_rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
   float isr_s = 0.0f, isr_eta = 0.0f;
   int isr_type = -1;
@@ -499,12 +498,9 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   const bool use = valid && M.Lc.learned && learned_src;
   // inputs of the end; the heights are reused while they are unchanged
   const float code = (float)(isr_type * 32 + pdf_index(fl_i));
-  bool need = false;
-  if (use) {
-    const float4 key = ls.keyat(lane_id, slot);
-    need = !(key.x == isr_eta && key.y == isr_s && key.z == code);
-  }
+  const bool need = use && !(key.x == isr_eta && key.y == isr_s && key.z == code);
   const unsigned eval = __ballot_sync(0xffffffffu, need) & 0xFu;
+  float scale0 = 0.0f, scale1 = 0.0f;  // 8 / sum of the new heights (lanes 0..3)
   if (eval) {
     const float tc = __expf(S.lnTc[row]);
     // rows r = lane and lane + 32: end r / 16, channel (r / 8) % 2, bin r % 8
@@ -523,27 +519,54 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
         cls_j[j] = cls * kEtaBins + eta_bucket(stage[r][0]);
       }
     }
+    // calibration margins of (class, eta bucket, bin), after the parameters,
+    // loaded before the tiles
+    float mg[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = lane_id + 32 * j;
+      if ((eval >> (r >> 4)) & 1u) mg[j] = __ldg(&M.Lc.mlp[kMlpParams + cls_j[j] * kIsrBins + (r & 7)]);
+    }
     __syncwarp();
     for (int tile = 0; tile < 4; ++tile)
       if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
     __syncwarp();
+    float tot[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
+      float U = 0.0f;
       if ((eval >> e) & 1u) {
-        // calibration margin of (class, eta bucket, bin), after the parameters
-        const float mg = __ldg(&M.Lc.mlp[kMlpParams + cls_j[j] * kIsrBins + m]);
-        ls.at(e, c, slot)[m] = (unsigned char)height_code(__expf(ustage[r] + mg));
+        const int hc = height_code(__expf(ustage[r] + mg[j]));
+        ls.at(e, c, slot)[m] = (unsigned char)hc;
+        U = ls.dec[hc];
       }
+      // the channel's sum over its 8 bins, in bin order (the order the veto sums them)
+      float t = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) t += __shfl_sync(0xffffffffu, U, (lane_id & ~7) + b);
+      tot[j] = t;
     }
+    // end e = lane (0..3): rows 16 e + 8 c + m, held by lanes 16 (e % 2) + 8 c + m in row set e / 2
+    const int base = (lane_id & 1) * 16;
+    const float t00 = __shfl_sync(0xffffffffu, tot[0], base), t01 = __shfl_sync(0xffffffffu, tot[1], base);
+    const float t10 = __shfl_sync(0xffffffffu, tot[0], base + 8), t11 = __shfl_sync(0xffffffffu, tot[1], base + 8);
+    const float tc0 = (lane_id & 2) ? t01 : t00, tc1 = (lane_id & 2) ? t11 : t10;
+    scale0 = tc0 > 0.0f ? 8.0f / tc0 : 0.0f;
+    scale1 = tc1 > 0.0f ? 8.0f / tc1 : 0.0f;
     if (need) ls.keyat(lane_id, slot) = make_float4(isr_eta, isr_s, code, 0.0f);
-    __syncwarp();  // the codes are visible to the end's lane
   }
   if (mine) {
     if (use) {
-      // the coefficient scale from the codes, summed in the order the veto sums them
-      isr_rec.x *= ls.scale(lane_id, 0, slot);
-      isr_rec.y *= ls.scale(lane_id, 1, slot);
+      // the coefficient scale c * mean(U): new heights, or the unchanged
+      // inputs' record of the last evaluation (the same product)
+      if (need) {
+        isr_rec.x *= scale0;
+        isr_rec.y *= scale1;
+      } else {
+        isr_rec.x = old_isr.x;
+        isr_rec.y = old_isr.y;
+      }
     } else if (ls.code) {
       // every other initial-state end proposes with height 1 in all bins (the
       // plain bound): a winner from it reads these codes, and its rate was not
@@ -1105,6 +1128,11 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   WS w{M.W, gl, M.P.nmax};
   Lane L;
   L.slot = gl;
+  L.ev = 0;
+  L.n = 0;
+  L.row = 0;
+  L.learned_ok = false;
+  L.eta0 = L.eta1 = 0.0;
   bool active = false;
   bool exhausted = false;
   Counters32 cnt;
