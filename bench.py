@@ -309,9 +309,10 @@ def run_ours(args, ws, rank, local):
         shape = tuning["best"]
     schedule = G.GAPS_SCHED_PERSISTENT if (mixed or args.schedule) else G.GAPS_SCHED_PER_EVENT
 
-    def config(pdf_ptr=None):
+    def config(pdf_ptr=None, trial_mode=None):
         c = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf and pdf_ptr is None else None, nmax=nmax,
-                          seed=1, precision=precision, schedule=schedule, mix=mix, **shape)
+                          seed=1, precision=precision, schedule=schedule, mix=mix, trial_mode=trial_mode,
+                          **shape)
         if pdf_ptr is not None:
             c.pdf_grid = pdf_ptr
         return c
@@ -389,7 +390,7 @@ def run_ours(args, ws, rank, local):
     # algorithm (FP64, one thread per event, no compaction, plain bound: the
     # paper's layout) and the compacted mixed-precision shower without the
     # learned proposal
-    plain = mixed_plain = None
+    plain = mixed_plain = trial_modes = None
     if not args.no_plain:
         n_plain = min(total, 1 << 19)
         cfgp = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf else None, nmax=nmax, seed=1,
@@ -402,6 +403,15 @@ def run_ours(args, ws, rank, local):
             mixed_plain["mode"] = "same shape and precision, plain bound (no learned proposal)"
             with_l = _time_variant(G, config(), ev, (1 << 51) + (1 << 24), n_mp, chunk, stream, learned)
             mixed_plain["learned_same_events"] = with_l
+        if mixed and schedule == G.GAPS_SCHED_PERSISTENT:
+            # the three trial schemes on the same events (max-veto redrawing
+            # every channel, max-veto keeping the losing trials, generate-select)
+            n_tm = min(total, chunk)
+            trial_modes = {}
+            for name, mode in (("redraw", G.GAPS_TRIALS_REDRAW), ("keep", G.GAPS_TRIALS_KEEP),
+                               ("select", G.GAPS_TRIALS_SELECT)):
+                trial_modes[name] = _time_variant(G, config(trial_mode=mode), ev, (1 << 51) + (2 << 24), n_tm,
+                                                  chunk, stream, learned)
 
     per_launch_events = total / n_chunks
     mean_shower_ms = sum(shower_ms) / max(1, len(shower_ms))
@@ -442,6 +452,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "plain_gpu": plain,
         "mixed_plain_bound": mixed_plain,
+        "trial_modes": trial_modes,
         "learned": learned_info,
         "shower_stats": {k: stats[k] for k in ("events", "steps", "trials", "isr_trials", "vetoes",
                                                 "accepts", "violations", "err_capacity",

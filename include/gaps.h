@@ -126,16 +126,28 @@ typedef struct {
                              mixed batch of these rows, which replace process,
                              sqrt_s and t_cut above */
     gaps_mix_row mix[GAPS_MAX_MIX];
-    int trial_cache;      /* GAPS_MIXED with GAPS_SCHED_PERSISTENT only: 1 keeps the
-                             losing trials of a cycle; after a veto only the winner's
-                             channel draws again, after an emission only the ends whose
-                             record changed (exact: each channel's trials are a Poisson
-                             process in ln t, whose first point below the scale the
-                             event continues from is the kept trial); 0 redraws every
-                             channel every cycle (Fig. 1 as printed, the FP64 path's
-                             draw order). Any other value, or 1 with another precision
-                             or schedule, is GAPS_ERR_INVALID_ARG */
+    int trial_mode;       /* GAPS_TRIALS_*: how the overestimate trials of a cycle are
+                             drawn; KEEP and SELECT only with GAPS_MIXED and
+                             GAPS_SCHED_PERSISTENT, any other combination or value is
+                             GAPS_ERR_INVALID_ARG */
 } gaps_config;
+
+/* Trial schemes (gaps_config.trial_mode). All three give the same
+ * distributions (Sec. 2): every channel's overestimate is a Poisson process
+ * in ln t with a constant rate while its dipole end's record is unchanged.
+ *   REDRAW  every channel of every end draws a trial each cycle and the
+ *           largest wins (max-veto, Fig. 1 as printed; the FP64 path's order)
+ *   KEEP    max-veto keeping the losing trials: after a veto only the
+ *           winner's channel draws again, after an emission only the ends
+ *           whose record changed (the kept trial is the channel's first point
+ *           below the scale the event continues from)
+ *   SELECT  generate-select (the alternative named in Sec. 2's footnote):
+ *           one trial from the summed rate of the channels active at the
+ *           current scale, restarted at each channel's maximum scale as it
+ *           is passed, and the channel chosen with probability rate / sum */
+#define GAPS_TRIALS_REDRAW 0
+#define GAPS_TRIALS_KEEP 1
+#define GAPS_TRIALS_SELECT 2
 
 /* Event records: structure of arrays in device memory, caller-owned, event
  * index fastest so that a warp's loads are coalesced. `capacity` is the

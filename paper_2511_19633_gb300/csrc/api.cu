@@ -130,8 +130,10 @@ int validate_config(const gaps_config& c) {
   if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT && c.schedule != GAPS_SCHED_WARP)
     return GAPS_ERR_INVALID_ARG;
   if (c.schedule == GAPS_SCHED_WARP && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
-  if (c.trial_cache != 0 && c.trial_cache != 1) return GAPS_ERR_INVALID_ARG;
-  if (c.trial_cache && (c.precision != GAPS_MIXED || c.schedule != GAPS_SCHED_PERSISTENT)) return GAPS_ERR_INVALID_ARG;
+  if (c.trial_mode != GAPS_TRIALS_REDRAW && c.trial_mode != GAPS_TRIALS_KEEP && c.trial_mode != GAPS_TRIALS_SELECT)
+    return GAPS_ERR_INVALID_ARG;
+  if (c.trial_mode != GAPS_TRIALS_REDRAW && (c.precision != GAPS_MIXED || c.schedule != GAPS_SCHED_PERSISTENT))
+    return GAPS_ERR_INVALID_ARG;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
   if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
   if (c.emit_batch < 0 || c.emit_batch > 32) return GAPS_ERR_INVALID_ARG;
@@ -169,7 +171,7 @@ void fill_params(const gaps_config& c, DevParams& P) {
   const double beta0 = (33.0 - 2.0 * 5.0) / (12.0 * 3.14159265358979323846);
   double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
   P.process = c.process;
-  P.trial_cache = c.trial_cache;
+  P.trial_mode = c.trial_mode;
   P.nf = c.nf;
   P.nmax = c.nmax_partons;
   P.sqrt_s = c.sqrt_s;

@@ -38,7 +38,7 @@ constexpr uint64_t kMixDraw = 0x4000000000000000ull;
 struct DevParams {
   int process, nf, nmax;
   double sqrt_s, s_had, t_cut, as_mz, as_over, beta0, p_s;
-  int trial_cache;             // mixed lane kernel: keep the losing trials of a vetoed cycle
+  int trial_mode;              // GAPS_TRIALS_* (KEEP and SELECT: mixed lane kernel only)
   int n_rows;                  // 1: one process; > 1: mixed batch
   RowParams rows[kMaxRows];    // row 0 = the fields above for one process
   double cum[kMaxRows];        // cumulative fractions, summed in row order

@@ -955,6 +955,70 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
 }
 
 
+// Generate-select (the alternative to max-veto in Sec. 2's footnote): the
+// superposition of every channel's overestimate process is a Poisson process
+// in ln t whose rate is the sum R of the rates of the channels active at that
+// scale (a channel is active below its end's maximum scale); a point of it
+// belongs to a channel with probability rate / R. One trial is drawn from R
+// at the current scale; when it falls below the next maximum scale of an
+// inactive channel, the process restarts there with that channel added (no
+// memory). Out of line: not on the default path.
+__device__ __noinline__ void select_trial(const WS& w, int ne, float lnT, float lnTc, bool pp, uint32_t e0,
+                                          uint32_t e1, uint32_t k0, uint32_t k1, uint64_t& d, Counters32& cnt,
+                                          float& best, int& bq, int& bch, float& bRz) {
+  float t0 = lnT;
+  // every pass either gives the trial or moves t0 down to the next distinct
+  // maximum scale: at most 2 ne + 1 passes
+  for (int pass = 0; pass <= 2 * ne && t0 > lnTc; ++pass) {
+    float R = 0.0f, t1 = -INFINITY;
+#pragma unroll 1
+    for (int q = 0; q < ne; ++q) {
+      const float4 rec = w.End(q);
+      if (__float_as_int(rec.w) < 0) continue;  // no dipole on this side
+      if (rec.z >= t0) {
+        if (rec.x > 0.0f) R += __frcp_rn(rec.x);
+        if (rec.y > 0.0f) R += __frcp_rn(rec.y);
+      } else if (rec.x > 0.0f || rec.y > 0.0f) {
+        t1 = fmaxf(t1, rec.z);
+      }
+    }
+    if (R > 0.0f) {
+      const uint64_t dd = d++;
+      uint32_t out[4];
+      philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+      cnt.trials += 1;
+      const float lt = t0 + __logf(u24(out[1])) / R;
+      if (lt >= t1) {
+        // the channel, in canonical order, with the same partial sums as R
+        const float target = u24(out[2]) * R;
+        float acc = 0.0f;
+        int sq = -1, sc = 0;
+#pragma unroll 1
+        for (int q = 0; q < ne && sq < 0; ++q) {
+          const float4 rec = w.End(q);
+          if (__float_as_int(rec.w) < 0 || rec.z < t0) continue;
+          if (rec.x > 0.0f) {
+            acc += __frcp_rn(rec.x);
+            bq = q; bch = 0;  // the last active channel, should rounding leave target >= acc
+            if (target < acc) { sq = q; sc = 0; continue; }
+          }
+          if (rec.y > 0.0f) {
+            acc += __frcp_rn(rec.y);
+            bq = q; bch = 1;
+            if (target < acc) { sq = q; sc = 1; }
+          }
+        }
+        if (sq >= 0) { bq = sq; bch = sc; }
+        if (pp && bq < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
+        best = lt;
+        bRz = u24(out[3]);
+        return;
+      }
+    }
+    t0 = t1;  // nothing above the next maximum scale: continue from there
+  }
+}
+
 // One max-veto cycle of the lane's event: one overestimate trial per channel
 // of every colour end in canonical order, then step_veto. With kept trials
 // only the ends marked by the last rebuild draw, and after a veto only the
@@ -967,18 +1031,20 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
   const float lnTc = S.lnTc[L.row];
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
   const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
-  const bool cache = M.P.trial_cache != 0;
+  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
   float best = -INFINITY;
   int bq = -1, bch = 0;
   float bRz = 0.5f;
   const int ne = 2 * L.n;  // ends q = 2 slot + side, canonical order
   uint64_t d = L.draw;
+  const bool select = M.P.trial_mode == GAPS_TRIALS_SELECT;
+  if (select) select_trial(w, ne, L.lnT, lnTc, pp, e0, e1, k0, k1, d, cnt, best, bq, bch, bRz);
   // one copy of the trial code (instruction-cache footprint); the next end's
   // load is issued before the current end's trials
   const float4 marked = make_float4(__uint_as_float(0x7fc00000u), 0.5f, -INFINITY, 0.5f);
   float4 nxt = cache ? w.Trial(0) : marked;
 #pragma unroll 1
-  for (int q = 0; q < ne; ++q) {
+  for (int q = 0; q < (select ? 0 : ne); ++q) {
     float4 tr = nxt;
     if (cache && q + 1 < ne) nxt = w.Trial(q + 1);
     if (isnan(tr.x)) {  // this end draws
@@ -1143,7 +1209,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
   bool parked = false;
   Emission pend;
   int since_flush = 0;
-  const bool cache = M.P.trial_cache != 0;
+  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
   while (true) {
     // warp-aggregated refill of idle lanes
     unsigned idle = __ballot_sync(0xffffffffu, !active);

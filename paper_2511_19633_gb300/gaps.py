@@ -27,6 +27,7 @@ GAPS_ERR_NO_DEVICE = -6
 GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO = 0, 1, 2
 GAPS_FP64, GAPS_MIXED = 0, 1
 GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT, GAPS_SCHED_WARP = 0, 1, 2
+GAPS_TRIALS_REDRAW, GAPS_TRIALS_KEEP, GAPS_TRIALS_SELECT = 0, 1, 2
 GAPS_STATUS_ACTIVE, GAPS_STATUS_DONE = 0, 1
 GAPS_NOBS, GAPS_NHIST, GAPS_HIST_BINS = 8, 6, 66
 
@@ -47,7 +48,7 @@ class GapsConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("pdf_grid", ctypes.c_void_p), ("block_size", ctypes.c_int),
         ("schedule", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
         ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
-        ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_cache", ctypes.c_int),
+        ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_mode", ctypes.c_int),
     ]
 
 
@@ -350,19 +351,20 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 alpha_s_mz: float = 0.118, nf: int = 5, nmax: int = 128, seed: int = 1,
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
-                refill_period: int = 0, emit_batch: int = 0, mix=None, trial_cache=None) -> GapsConfig:
+                refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied). mix: optional list of
     (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
-    process, sqrt_s and t_cut. trial_cache: None = on for GAPS_MIXED with the
-    persistent lane schedule."""
+    process, sqrt_s and t_cut. trial_mode: GAPS_TRIALS_*; None = KEEP for
+    GAPS_MIXED with the persistent lane schedule, REDRAW otherwise."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
                    block_size, schedule, blocks_per_sm, refill_period, emit_batch)
-    # trial caching: on by default where it applies (mixed precision, lane schedule)
-    if trial_cache is None:
-        trial_cache = precision == GAPS_MIXED and schedule == GAPS_SCHED_PERSISTENT
-    c.trial_cache = int(bool(trial_cache))
+    # kept trials by default where they apply (mixed precision, lane schedule)
+    if trial_mode is None:
+        trial_mode = (GAPS_TRIALS_KEEP if precision == GAPS_MIXED and schedule == GAPS_SCHED_PERSISTENT
+                      else GAPS_TRIALS_REDRAW)
+    c.trial_mode = int(trial_mode)
     if mix:
         if len(mix) > GAPS_MAX_MIX:
             raise ValueError("at most %d rows" % GAPS_MAX_MIX)

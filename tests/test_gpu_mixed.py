@@ -23,7 +23,8 @@ def test_mixed_follows_fp64_histories(G, pdf):
     proc, sqrt_s = PROCESS["pp_nlo"]
     n = 20011
     a = run_gpu(G, proc, sqrt_s, 0, n, pdf)
-    b = run_gpu(G, proc, sqrt_s, 0, n, pdf, precision=MIXED, schedule=1, blocks_per_sm=4, trial_cache=False)
+    b = run_gpu(G, proc, sqrt_s, 0, n, pdf, precision=MIXED, schedule=1, blocks_per_sm=4,
+                trial_mode=G.GAPS_TRIALS_REDRAW)
     same = (a["npart"] == b["npart"]) & np.all(a["flav"] == b["flav"], axis=1)
     frac = same.mean()
     assert frac > 0.9, frac
@@ -76,11 +77,11 @@ def test_mixed_capacity_errors(G, pdf):
     assert np.all(g["npart"][st == -2] == 6)
 
 
-def _gpu_hists(G, name, pdf, precision, n, first0=0, chunk=1 << 21):
+def _gpu_hists(G, name, pdf, precision, n, first0=0, chunk=1 << 21, trial_mode=None):
     import torch
     proc, sqrt_s = PROCESS[name]
     cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf if proc else None, nmax=128, seed=1,
-                        precision=precision, schedule=1)
+                        precision=precision, schedule=1, trial_mode=trial_mode)
     ctx = G.gaps_init(cfg)
     try:
         cap = min(chunk, n)
@@ -102,13 +103,15 @@ def _gpu_hists(G, name, pdf, precision, n, first0=0, chunk=1 << 21):
     return hw.cpu().numpy(), hw2.cpu().numpy(), binning, stats
 
 
-@pytest.mark.parametrize("name", ["ee91", "ee500", "pp_lo", "pp_nlo"])
-def test_mixed_histograms_match_oracle(G, pdf, name):
+@pytest.mark.parametrize("name,mode", [("ee91", 1), ("ee500", 1), ("pp_lo", 1), ("pp_nlo", 1),
+                                       ("ee91", 2), ("pp_nlo", 2)])
+def test_mixed_histograms_match_oracle(G, pdf, name, mode):
     """chi^2/ndf < 1.2 against the FP64 oracle's histograms (independent seed,
     1e7 events) for samples of 1e7 events. With about 200 degrees of freedom a
     correct generator exceeds 1.2 on about 2.6% of samples, so the bar is put
     on the median of three independent event ranges (at least two of three
-    samples pass), with 1.5 as the limit for every sample."""
+    samples pass), with 1.5 as the limit for every sample. Mode 1 keeps the
+    losing trials (the default), mode 2 is generate-select."""
     import os
     from tests.hist_common import GOLDEN
     if not os.path.exists(os.path.join(GOLDEN, "oracle_hists_%s.json" % name)):
@@ -117,7 +120,7 @@ def test_mixed_histograms_match_oracle(G, pdf, name):
     n = gold["events"]
     reds = []
     for r in range(3):
-        w, w2, binning, stats = _gpu_hists(G, name, pdf, MIXED, n, first0=r << 40)
+        w, w2, binning, stats = _gpu_hists(G, name, pdf, MIXED, n, first0=r << 40, trial_mode=mode)
         for (lo, hi, nb, oi, lg), b in zip(gold["binning"], binning):
             assert (b["lo"], b["hi"], b["nbins"], b["obs"], int(b["log10"])) == pytest.approx((lo, hi, nb, oi, lg))
         per = chi2_per_hist(w, w2, n, gold["sumw"], gold["sumw2"], gold["events"])
@@ -126,34 +129,43 @@ def test_mixed_histograms_match_oracle(G, pdf, name):
         reds.append(red)
     assert float(np.median(reds)) < 1.2 and max(reds) < 1.5, reds
 
-def test_trial_cache_needs_persistent_mixed(G, pdf):
-    for prec, sched in ((0, 0), (0, 1), (MIXED, 2)):
-        with pytest.raises(G.GapsError) as e:
-            G.gaps_init(G.make_config(0, 91.2, precision=prec, schedule=sched, trial_cache=True))
-        assert e.value.code == G.GAPS_ERR_INVALID_ARG
+def test_trial_modes_need_persistent_mixed(G, pdf):
+    for mode in (G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT):
+        for prec, sched in ((0, 0), (0, 1), (MIXED, 2)):
+            with pytest.raises(G.GapsError) as e:
+                G.gaps_init(G.make_config(0, 91.2, precision=prec, schedule=sched, trial_mode=mode))
+            assert e.value.code == G.GAPS_ERR_INVALID_ARG
+    with pytest.raises(G.GapsError):
+        G.gaps_init(G.make_config(0, 91.2, precision=MIXED, schedule=1, trial_mode=3))
 
 
 @pytest.mark.parametrize("name", ["ee500", "pp_nlo"])
-def test_trial_cache_keeps_distributions_and_cuts_trials(G, pdf, name):
-    """Kept trials are exact (each channel's trials are a Poisson process in
-    ln t): the same events, shower for shower, come out with different random
-    histories but the same distributions, from fewer overestimate trials."""
+def test_trial_modes_keep_distributions(G, pdf, name):
+    """The three trial schemes are exact (each channel's trials are a Poisson
+    process in ln t): the same events come out with different random
+    histories but the same distributions; kept trials and generate-select
+    need far fewer overestimate trials than the full redraw."""
     proc, sqrt_s = PROCESS[name]
     n = 200003
-    on = run_gpu(G, proc, sqrt_s, 31, n, pdf, precision=MIXED, schedule=1, trial_cache=True)
-    off = run_gpu(G, proc, sqrt_s, 31, n, pdf, precision=MIXED, schedule=1, trial_cache=False)
-    for g in (on, off):
+    runs = {m: run_gpu(G, proc, sqrt_s, 31, n, pdf, precision=MIXED, schedule=1, trial_mode=m)
+            for m in (G.GAPS_TRIALS_REDRAW, G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT)}
+    for g in runs.values():
         assert np.all(g["status"] == 1) and g["stats"]["events"] == n and g["stats"]["violations"] == 0
-    # the hard process is drawn before the shower: identical in both
-    assert np.array_equal(on["weight"], off["weight"])
-    assert on["stats"]["trials"] < 0.8 * off["stats"]["trials"], (on["stats"]["trials"], off["stats"]["trials"])
-    # emission multiplicity and per-event observables agree within 5 sigma
-    for a, b in ((on["n_emit"].astype(float), off["n_emit"].astype(float)),) + tuple(
-            (on["obs"][:, j], off["obs"][:, j]) for j in range(on["obs"].shape[1])):
-        ok = np.isfinite(a) & np.isfinite(b)
-        a, b = a[ok], b[ok]
-        if a.size < 1000 or a.std() == 0:
-            continue
-        err = np.hypot(a.std() / np.sqrt(a.size), b.std() / np.sqrt(b.size))
-        assert abs(a.mean() - b.mean()) < 5 * err, (a.mean(), b.mean(), err)
-    assert abs(on["stats"]["accepts"] - off["stats"]["accepts"]) < 5 * np.sqrt(2 * off["stats"]["accepts"])
+    off = runs[G.GAPS_TRIALS_REDRAW]
+    tr = {m: g["stats"]["trials"] for m, g in runs.items()}
+    assert tr[G.GAPS_TRIALS_KEEP] < 0.8 * tr[G.GAPS_TRIALS_REDRAW], tr
+    assert tr[G.GAPS_TRIALS_SELECT] < 0.8 * tr[G.GAPS_TRIALS_REDRAW], tr
+    for m in (G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT):
+        on = runs[m]
+        # the hard process is drawn before the shower: identical in all
+        assert np.array_equal(on["weight"], off["weight"])
+        # emission multiplicity and per-event observables agree within 5 sigma
+        for a, b in ((on["n_emit"].astype(float), off["n_emit"].astype(float)),) + tuple(
+                (on["obs"][:, j], off["obs"][:, j]) for j in range(on["obs"].shape[1])):
+            ok = np.isfinite(a) & np.isfinite(b)
+            a, b = a[ok], b[ok]
+            if a.size < 1000 or a.std() == 0:
+                continue
+            err = np.hypot(a.std() / np.sqrt(a.size), b.std() / np.sqrt(b.size))
+            assert abs(a.mean() - b.mean()) < 5 * err, (m, a.mean(), b.mean(), err)
+        assert abs(on["stats"]["accepts"] - off["stats"]["accepts"]) < 5 * np.sqrt(2 * off["stats"]["accepts"])

@@ -29,20 +29,20 @@ def _same(a, b, keys=("p", "flav", "col", "acol", "npart", "status", "n_emit", "
 def test_warp_schedule_equals_lane_schedule(G, pdf, name, block, bps):
     proc, sqrt_s = PROCESS[name]
     n = 6007
-    a = run_gpu(G, proc, sqrt_s, 1234, n, pdf, precision=1, schedule=1, trial_cache=False)
+    a = run_gpu(G, proc, sqrt_s, 1234, n, pdf, precision=1, schedule=1, trial_mode=G.GAPS_TRIALS_REDRAW)
     b = run_gpu(G, proc, sqrt_s, 1234, n, pdf, precision=1, schedule=2, block_size=block, blocks_per_sm=bps)
     _same(a, b)
 
 
 def test_warp_schedule_mixed_batch(G, pdf):
-    a = run_gpu(G, 0, 91.2, 99, 5003, pdf, precision=1, schedule=1, mix=MIX, trial_cache=False)
+    a = run_gpu(G, 0, 91.2, 99, 5003, pdf, precision=1, schedule=1, mix=MIX, trial_mode=G.GAPS_TRIALS_REDRAW)
     b = run_gpu(G, 0, 91.2, 99, 5003, pdf, precision=1, schedule=2, mix=MIX)
     _same(a, b)
 
 
 def test_warp_schedule_capacity_errors(G, pdf):
     proc, sqrt_s = PROCESS["pp_nlo"]
-    a = run_gpu(G, proc, sqrt_s, 0, 3001, pdf, nmax=6, precision=1, schedule=1, trial_cache=False)
+    a = run_gpu(G, proc, sqrt_s, 0, 3001, pdf, nmax=6, precision=1, schedule=1, trial_mode=G.GAPS_TRIALS_REDRAW)
     b = run_gpu(G, proc, sqrt_s, 0, 3001, pdf, nmax=6, precision=1, schedule=2)
     assert (b["status"] == -2).sum() > 100
     _same(a, b)
@@ -60,7 +60,7 @@ def test_warp_schedule_learned(G, pdf):
     import torch
     from paper_2511_19633_gb300 import learned
     proc, sqrt_s = PROCESS["pp_nlo"]
-    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=1, schedule=1, trial_cache=False)
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=1, schedule=1, trial_mode=G.GAPS_TRIALS_REDRAW)
     ctx = G.gaps_init(cfg)
     try:
         res = learned.train_and_install(ctx, first_event=7 << 40, n_events=1 << 18, capacity=1 << 18,
@@ -70,7 +70,7 @@ def test_warp_schedule_learned(G, pdf):
     out = []
     for sched in (1, 2):
         cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=1, schedule=sched,
-                            trial_cache=False)
+                            trial_mode=G.GAPS_TRIALS_REDRAW)
         ctx = G.gaps_init(cfg)
         try:
             G.gaps_set_learned_proposal(ctx, res["params"], res["log_margins"])
