@@ -297,7 +297,8 @@ struct Pdf {
 // one-loop running with n_f = 5 from alpha_s(m_Z^2).
 // ---------------------------------------------------------------------------
 struct Config {
-  int process;           // 0 = e+e- -> q qbar, 1 = pp -> Z LO, 2 = pp -> Z NLO
+  int process;           // 0 = e+e- -> q qbar, 1 = pp -> Z LO, 2 = pp -> Z NLO,
+                         // 3 = pp -> gamma*/Z -> e- e+ LO
   int nf;
   int nmax;
   int fixed_alpha;       // test switch: alpha_s(t) = alpha_s(m_Z) everywhere
@@ -308,6 +309,7 @@ struct Config {
   double y_fixed;        // test switch: finite forces the Born rapidity
   uint64_t seed;
   const float* pdf;
+  double mll_lo, mll_hi; // process 3: dilepton mass window (GeV)
 };
 
 struct Physics {
@@ -385,6 +387,23 @@ double ee_dsigma_dcos(double s, int f, double c) {
   double a = q.Q * q.Q - 2.0 * q.Q * Ve * Vf * chi1 + (Ae * Ae + Ve * Ve) * (Af * Af + Vf * Vf) * chi2;
   double b = -2.0 * q.Q * Ae * Af * chi1 + 4.0 * Ae * Ve * Af * Vf * chi2;
   return kNc * kPi * kAlphaEM * kAlphaEM / (2.0 * s) * ((1.0 + c * c) * a + 2.0 * c * b);
+}
+
+// q qbar -> gamma*/Z -> e- e+ (the process GAPS 2 provides besides on-shell Z
+// production, Sec. 4.1): the e+e- -> q qbar expression above read backwards
+// in time, with the average 1/N_c over the incoming colours in place of the
+// sum N_c over the outgoing ones. c = cosine of the angle between the
+// incoming quark and the electron in their centre-of-mass frame.
+double ll_dsigma_dcos(double s, int f, double c) {
+  return ee_dsigma_dcos(s, f, c) / (kNc * kNc);
+}
+
+// Breit-Wigner map of the dilepton mass: m^2 = m_Z^2 + m_Z Gamma_Z tan(2 pi r),
+// r uniform between the window's images (computed once per configuration)
+void ll_window(double mll_lo, double mll_hi, double& r_lo, double& r_hi) {
+  double mg = kMZ * kGZ, mz2 = kMZ * kMZ;
+  r_lo = std::atan((mll_lo * mll_lo - mz2) / mg) / kTwoPi;
+  r_hi = std::atan((mll_hi * mll_hi - mz2) / mg) / kTwoPi;
 }
 
 void set_beam_parton(Event& ev, int slot, double eta, double sqrt_s) {
@@ -1000,6 +1019,59 @@ void generate_hard(const Physics& ph, Event& ev, uint64_t event_id) {
     return;
   }
   ev.pp = true;
+  if (cf.process == 3) {
+    // m^2 by the Breit-Wigner map, y uniform in [-Y, Y], cos(theta*) and phi
+    // of the electron uniform in the dilepton rest frame (quark along +z if
+    // it comes from beam 1); flavour pair by its share of the density
+    double r_lo, r_hi;
+    ll_window(cf.mll_lo, cf.mll_hi, r_lo, r_hi);
+    double r = r_lo + R0 * (r_hi - r_lo);
+    double cr, sr;
+    sincos2pi(r, cr, sr);
+    double mg = kMZ * kGZ;
+    double m2 = kMZ * kMZ + mg * (sr / cr);
+    double m = std::sqrt(m2);
+    double Y = lg(cf.sqrt_s / m);
+    double y = (2.0 * R1 - 1.0) * Y;
+    double tau = m / cf.sqrt_s;
+    double ey = ex(y), iey = ex(-y);
+    double ea = ey * tau, eb = iey * tau;
+    double c = 2.0 * R3 - 1.0;
+    double dens[10], tot = 0.0;
+    for (int k = 0; k < 10; ++k) {
+      int fa, fb;
+      born_pair(k, fa, fb);
+      double Fa = ph.pdf.xf(pdf_index(fa), ea, m2), Fb = ph.pdf.xf(pdf_index(fb), eb, m2);
+      dens[k] = Fa * Fb * ll_dsigma_dcos(m2, fa > 0 ? fa : fb, fa > 0 ? c : -c);
+      tot += dens[k];
+    }
+    int pick = 9;
+    double target = R2 * tot, acc = 0.0;
+    for (int k = 0; k < 10; ++k) { acc += dens[k]; if (target < acc) { pick = k; break; } }
+    int fa, fb;
+    born_pair(pick, fa, fb);
+    ev.parts.resize(4);
+    ev.parts[0].fl = fa; ev.parts[1].fl = fb;
+    set_beam_parton(ev, 0, ea, cf.sqrt_s);
+    set_beam_parton(ev, 1, eb, cf.sqrt_s);
+    set_incoming_quark_colour(ev.parts[0], 1);
+    set_incoming_quark_colour(ev.parts[1], 1);
+    double cph, sph;
+    sincos2pi(R4, cph, sph);  // phi = 2 pi R4
+    double st = std::sqrt((1.0 - c) * (1.0 + c));
+    double ch = 0.5 * (ey + iey), sh = 0.5 * (ey - iey);
+    double hm = 0.5 * m;
+    Parton& el = ev.parts[2];
+    Parton& po = ev.parts[3];
+    el.p[0] = hm * (ch + c * sh); el.p[1] = hm * (st * cph); el.p[2] = hm * (st * sph); el.p[3] = hm * (sh + c * ch);
+    po.p[0] = hm * (ch - c * sh); po.p[1] = -(hm * (st * cph)); po.p[2] = -(hm * (st * sph)); po.p[3] = hm * (sh - c * ch);
+    el.fl = 11; po.fl = -11;
+    el.col = el.acol = po.col = po.acol = 0;
+    el.initial = po.initial = false;
+    // dsigma = sum_k F_a F_b / m^2 dsigma_k/dc dm^2 dy dc, with dm^2 = 2 pi m_Z Gamma_Z / cos^2 dr
+    ev.weight = tot / m2 * (kTwoPi * mg / (cr * cr)) * (r_hi - r_lo) * (2.0 * Y) * 2.0 * kGeV2pb;
+    return;
+  }
   double mz2 = kMZ * kMZ;
   bool hevent = false;
   double wsel = 1.0;
@@ -1270,8 +1342,13 @@ constexpr int kNObs = 8;
 void observables(const Event& ev, double obs[kNObs]) {
   for (int i = 0; i < kNObs; ++i) obs[i] = 0.0;
   std::vector<std::array<double, 4>> fin;
+  double Z[4] = {0.0, 0.0, 0.0, 0.0};  // the colourless final state: Z, or the lepton pair
   for (auto& P : ev.parts) {
-    if (P.initial || P.fl == 23) continue;
+    if (P.initial) continue;
+    if (P.fl == 23 || P.fl == 11 || P.fl == -11) {
+      for (int mu = 0; mu < 4; ++mu) Z[mu] += P.p[mu];
+      continue;
+    }
     fin.push_back({P.p[0], P.p[1], P.p[2], P.p[3]});
   }
   if (!ev.pp) {
@@ -1281,11 +1358,10 @@ void observables(const Event& ev, double obs[kNObs]) {
     obs[4] = (double)ev.n_emit;
     return;
   }
-  const Parton& Z = ev.parts[2];
-  double pt = std::sqrt(Z.p[1] * Z.p[1] + Z.p[2] * Z.p[2]);
+  double pt = std::sqrt(Z[1] * Z[1] + Z[2] * Z[2]);
   obs[0] = pt;
-  obs[1] = 0.5 * std::log((Z.p[0] + Z.p[3]) / (Z.p[0] - Z.p[3]));
-  obs[2] = pt > 0.0 ? std::atan2(Z.p[2], Z.p[1]) : 0.0;
+  obs[1] = 0.5 * std::log((Z[0] + Z[3]) / (Z[0] - Z[3]));
+  obs[2] = pt > 0.0 ? std::atan2(Z[2], Z[1]) : 0.0;
   std::vector<Jet> jets;
   antikt(fin, 0.4, jets);
   int nj = 0;
@@ -1363,6 +1439,7 @@ struct OracleConfig {
   double sqrt_s, alpha_s_mz, t_cut, p_s, t_start, y_fixed;
   uint64_t seed;
   const float* pdf;
+  double mll_lo, mll_hi;
 };
 
 // Per-event output, array-of-structures, caller allocated.
@@ -1388,6 +1465,7 @@ static Config to_config(const OracleConfig* c) {
   k.channel_mask = c->channel_mask; k.pair_fixed = c->pair_fixed;
   k.sqrt_s = c->sqrt_s; k.alpha_s_mz = c->alpha_s_mz; k.t_cut = c->t_cut; k.p_s = c->p_s;
   k.t_start = c->t_start; k.y_fixed = c->y_fixed; k.seed = c->seed; k.pdf = c->pdf;
+  k.mll_lo = c->mll_lo; k.mll_hi = c->mll_hi;
   return k;
 }
 
@@ -1723,6 +1801,7 @@ double oracle_born_density(const OracleConfig* c, int k, double ea, double eb) {
   return born_pair_density(ph, k, ea, eb);
 }
 double oracle_ee_dsigma(double s, int f, double cth) { return ee_dsigma_dcos(s, f, cth); }
+double oracle_ll_dsigma(double s, int f, double cth) { return ll_dsigma_dcos(s, f, cth); }
 // overestimate z range: out = {zm, delta}; returns 0 if t is above the limit
 int oracle_z_limits(int type, double t, double s, double eta, double out[2]) {
   return z_limits(type, t, s, eta, out[0], out[1]) ? 1 : 0;

@@ -39,6 +39,7 @@ class OracleConfig(ctypes.Structure):
         ("t_cut", ctypes.c_double), ("p_s", ctypes.c_double),
         ("t_start", ctypes.c_double), ("y_fixed", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("pdf", ctypes.c_void_p),
+        ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double),
     ]
 
 
@@ -88,6 +89,8 @@ def lib():
         _lib.oracle_born_density.restype = d
         _lib.oracle_ee_dsigma.argtypes = [d, i, d]
         _lib.oracle_ee_dsigma.restype = d
+        _lib.oracle_ll_dsigma.argtypes = [d, i, d]
+        _lib.oracle_ll_dsigma.restype = d
         _lib.oracle_z_limits.argtypes = [i, d, d, d, vp]
         _lib.oracle_shape_sample.argtypes = [i, d, d, d, vp]
         _lib.oracle_shape_integral.argtypes = [i, d, d]
@@ -124,12 +127,15 @@ class Settings:
     pair_fixed: int = -1
     t_start: float = 0.0
     y_fixed: float = math.nan
+    mll_lo: float = 66.0   # process 3: dilepton mass window (GeV)
+    mll_hi: float = 116.0
 
     def to_c(self, pdf: np.ndarray | None) -> OracleConfig:
         return OracleConfig(self.process, self.nf, self.nmax, int(self.fixed_alpha),
                             self.channel_mask, self.pair_fixed, self.sqrt_s, self.alpha_s_mz,
                             self.t_cut, self.p_s, self.t_start, self.y_fixed,
-                            self.seed, None if pdf is None else pdf.ctypes.data)
+                            self.seed, None if pdf is None else pdf.ctypes.data,
+                            self.mll_lo, self.mll_hi)
 
 
 COUNTER_NAMES = ("steps", "trials", "isr_trials", "vetoes", "accepts", "violations")
@@ -267,6 +273,11 @@ def born_density(settings: Settings, pdf: np.ndarray, k: int, ea: float, eb: flo
 
 def ee_dsigma(s: float, f: int, cth: float) -> float:
     return lib().oracle_ee_dsigma(s, f, cth)
+
+
+def ll_dsigma(s: float, f: int, cth: float) -> float:
+    """q qbar -> gamma*/Z -> e- e+: dsigma/dcos(theta*) in GeV^-2 (theta* between quark and electron)."""
+    return lib().oracle_ll_dsigma(s, f, cth)
 
 
 def z_limits(dtype: int, t: float, s: float, eta: float):
