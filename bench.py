@@ -41,6 +41,10 @@ WORKLOADS = {
                        "1e6 events, FP64 (per-event oracle parity)"),
     "ee91_1e4_fp64": (0, 91.2, 10_000, 10_000, 0, None,
                       "e+e- -> q qbar at 91.2 GeV, final-state shower, 1e4 events, FP64"),
+    "pp_ll_1e7": (3, 13600.0, 10_000_000, 1 << 22, 1, None,
+                  "pp -> Z/gamma* -> e- e+ at 13.6 TeV, LO with the Z/gamma interference, dilepton "
+                  "mass 66-116 GeV, initial/final-state shower, synthetic 100x50 PDF, 1e7 events per "
+                  "step in chunks of 2^22, mixed precision, learned proposal, one CUDA graph per step"),
     "mix_1e8": (2, 13600.0, 100_000_000, 1 << 22, 1, MIX_ROWS,
                 "mixed batch in one persistent launch per chunk: 50% NLO pp -> Z at 13.6 TeV "
                 "(t_c 1 GeV^2), 25% e+e- at 91.2 GeV (t_c 0.5), 25% e+e- at 500 GeV (t_c 4), "

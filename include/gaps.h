@@ -54,6 +54,11 @@ extern "C" {
 #define GAPS_EE_QQ       0   /* e+e- -> Z/gamma* -> q qbar, final-state shower */
 #define GAPS_PP_Z_LO     1   /* pp -> Z at LO, initial- and final-state shower */
 #define GAPS_PP_Z_NLO    2   /* pp -> Z, S and H events of Appendix C.4 */
+#define GAPS_PP_LL       3   /* pp -> Z/gamma* -> e- e+ at LO with the Z/gamma
+                                interference (the process GAPS 2 provides besides
+                                on-shell Z production, Sec. 4.1): dilepton mass in
+                                [mll_lo, mll_hi] by a Breit-Wigner map; records hold
+                                the beams in slots 0, 1 and e-, e+ in slots 2, 3 */
 
 /* arithmetic of the shower */
 #define GAPS_FP64        0   /* all FP64; matches the reference per event */
@@ -96,7 +101,7 @@ typedef struct gaps_ctx gaps_ctx;  /* opaque, owned by the library */
  * process, sqrt_s and t_cut and the same other settings. */
 #define GAPS_MAX_MIX 4
 typedef struct {
-    int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO or GAPS_PP_Z_NLO */
+    int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO or GAPS_PP_LL */
     double sqrt_s;        /* GeV */
     double t_cut;         /* GeV^2 */
     double fraction;      /* share of the events, > 0; the shares sum to 1 */
@@ -104,7 +109,7 @@ typedef struct {
 
 /* Configuration, copied by gaps_init. */
 typedef struct {
-    int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO or GAPS_PP_Z_NLO */
+    int process;          /* GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO or GAPS_PP_LL */
     int precision;        /* GAPS_FP64 or GAPS_MIXED */
     int nf;               /* active flavours for g -> q qbar (5) */
     int nmax_partons;     /* capacity per event, 4..128 */
@@ -130,6 +135,8 @@ typedef struct {
                              drawn; KEEP and SELECT only with GAPS_MIXED and
                              GAPS_SCHED_PERSISTENT, any other combination or value is
                              GAPS_ERR_INVALID_ARG */
+    double mll_lo, mll_hi;  /* GAPS_PP_LL (also as a row of a mixed batch): dilepton
+                             mass window in GeV, 0 < mll_lo < mll_hi <= sqrt_s */
 } gaps_config;
 
 /* Trial schemes (gaps_config.trial_mode). All three give the same

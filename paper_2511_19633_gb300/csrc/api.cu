@@ -116,7 +116,10 @@ int validate_config(const gaps_config& c) {
     }
     return std::fabs(sum - 1.0) <= 1e-9 ? GAPS_OK : GAPS_ERR_INVALID_ARG;
   }
-  if (c.process < GAPS_EE_QQ || c.process > GAPS_PP_Z_NLO) return GAPS_ERR_INVALID_ARG;
+  if (c.process < GAPS_EE_QQ || c.process > GAPS_PP_LL) return GAPS_ERR_INVALID_ARG;
+  if (c.process == GAPS_PP_LL &&
+      !(c.mll_lo > 0.0 && c.mll_lo < c.mll_hi && c.mll_hi <= c.sqrt_s && std::isfinite(c.mll_hi)))
+    return GAPS_ERR_INVALID_ARG;
   if (c.precision != GAPS_FP64 && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
   if (!(c.sqrt_s > 0.0) || !std::isfinite(c.sqrt_s)) return GAPS_ERR_INVALID_ARG;
   if (c.process != GAPS_EE_QQ && !(c.sqrt_s > 91.1876 && c.sqrt_s <= 13600.0)) return GAPS_ERR_INVALID_ARG;
@@ -172,6 +175,13 @@ void fill_params(const gaps_config& c, DevParams& P) {
   double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
   P.process = c.process;
   P.trial_mode = c.trial_mode;
+  // images of the dilepton mass window under m^2 = m_Z^2 + m_Z Gamma_Z tan(2 pi r)
+  {
+    const double mg = kMZ * kGZ, mz2 = kMZ * kMZ;
+    const double lo = c.mll_lo > 0.0 ? c.mll_lo : 66.0, hi = c.mll_hi > 0.0 ? c.mll_hi : 116.0;
+    P.ll_rlo = std::atan((lo * lo - mz2) / mg) / kGmTwoPi;
+    P.ll_rhi = std::atan((hi * hi - mz2) / mg) / kGmTwoPi;
+  }
   P.nf = c.nf;
   P.nmax = c.nmax_partons;
   P.sqrt_s = c.sqrt_s;

@@ -39,6 +39,7 @@ struct DevParams {
   int process, nf, nmax;
   double sqrt_s, s_had, t_cut, as_mz, as_over, beta0, p_s;
   int trial_mode;              // GAPS_TRIALS_* (KEEP and SELECT: mixed lane kernel only)
+  double ll_rlo, ll_rhi;       // GAPS_PP_LL: the mass window's images under the Breit-Wigner map
   int n_rows;                  // 1: one process; > 1: mixed batch
   RowParams rows[kMaxRows];    // row 0 = the fields above for one process
   double cum[kMaxRows];        // cumulative fractions, summed in row order

@@ -35,6 +35,13 @@ __device__ double ee_dsigma_dcos(double s, int f, double c) {
   return kNc * kPi * kAlphaEM * kAlphaEM / (2.0 * s) * ((1.0 + c * c) * a + 2.0 * c * b);
 }
 
+// q qbar -> gamma*/Z -> e- e+: the expression above read backwards in time,
+// with the average 1/N_c over the incoming colours in place of the sum N_c
+// over the outgoing ones; c = cosine between incoming quark and electron
+__device__ double ll_dsigma_dcos(double s, int f, double c) {
+  return ee_dsigma_dcos(s, f, c) / (kNc * kNc);
+}
+
 // ordered Born pairs: (q, qbar) for q = d u s c b, then (qbar, q)
 __device__ __forceinline__ void born_pair(int k, int& fa, int& fb) {
   int q = (k % 5) + 1;
@@ -145,6 +152,56 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     rec.set(1, En, -En * n0, -En * n1, -En * n2, -f, 0, 1);
     E.npart[e] = 2;
     E.weight[e] = ee_dsigma_dcos(s, f, c) * 2.0 * P.nf * kGeV2pb;
+    return;
+  }
+  if (P.process == GAPS_PP_LL) {
+    // m^2 by the Breit-Wigner map m^2 = m_Z^2 + m_Z Gamma_Z tan(2 pi r), y
+    // uniform in [-Y, Y], cos(theta*) and phi of the electron uniform in the
+    // dilepton rest frame (quark along +z when it comes from beam 1); the
+    // flavour pair by its share of the density
+    double r = P.ll_rlo + R0 * (P.ll_rhi - P.ll_rlo);
+    double cr, sr;
+    gm_sincos2pi(r, cr, sr);
+    double mg = kMZ * kGZ;
+    double m2 = kMZ * kMZ + mg * (sr / cr);
+    double m = sqrt(m2);
+    double Y = gm_log(P.sqrt_s / m);
+    double y = (2.0 * R1 - 1.0) * Y;
+    double tau = m / P.sqrt_s;
+    double ey = gm_exp(y), iey = gm_exp(-y);
+    double ea = ey * tau, eb = iey * tau;
+    double c = 2.0 * R3 - 1.0;
+    double dens[10], tot = 0.0;
+    for (int k = 0; k < 10; ++k) {
+      int fa, fb;
+      born_pair(k, fa, fb);
+      double Fa = pdf_xf(P, pdf_index(fa), ea, m2), Fb = pdf_xf(P, pdf_index(fb), eb, m2);
+      dens[k] = Fa * Fb * ll_dsigma_dcos(m2, fa > 0 ? fa : fb, fa > 0 ? c : -c);
+      tot += dens[k];
+    }
+    int pick = 9;
+    double target = R2 * tot, acc = 0.0;
+    for (int k = 0; k < 10; ++k) { acc += dens[k]; if (target < acc) { pick = k; break; } }
+    int fa, fb;
+    born_pair(pick, fa, fb);
+    double Ea = ea * 0.5 * P.sqrt_s, Eb = eb * 0.5 * P.sqrt_s;
+    int c0, a0, c1, a1;
+    incoming_quark_tags(fa, 1, c0, a0);
+    incoming_quark_tags(fb, 1, c1, a1);
+    rec.set(0, Ea, 0.0, 0.0, Ea, fa, c0, a0);
+    rec.set(1, Eb, 0.0, 0.0, -Eb, fb, c1, a1);
+    double cph, sph;
+    gm_sincos2pi(R4, cph, sph);  // phi = 2 pi R4
+    double st = sqrt((1.0 - c) * (1.0 + c));
+    double ch = 0.5 * (ey + iey), sh = 0.5 * (ey - iey);
+    double hm = 0.5 * m;
+    rec.set(2, hm * (ch + c * sh), hm * (st * cph), hm * (st * sph), hm * (sh + c * ch), 11, 0, 0);
+    rec.set(3, hm * (ch - c * sh), -(hm * (st * cph)), -(hm * (st * sph)), hm * (sh - c * ch), -11, 0, 0);
+    E.eta[e] = ea;
+    E.eta[E.cap + e] = eb;
+    E.npart[e] = 4;
+    // dsigma = sum_k F_a F_b / m^2 dsigma_k/dc dm^2 dy dc, with dm^2 = 2 pi m_Z Gamma_Z / cos^2 dr
+    E.weight[e] = tot / m2 * (kGmTwoPi * mg / (cr * cr)) * (P.ll_rhi - P.ll_rlo) * (2.0 * Y) * 2.0 * kGeV2pb;
     return;
   }
   double mz2 = kMZ * kMZ;

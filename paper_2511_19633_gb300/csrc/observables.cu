@@ -248,9 +248,14 @@ __global__ void k_observables(DevParams P, DevEvents E, uint64_t first, uint64_t
     int np = E.npart[e];
     int m = 0;
     const bool pp = s_pp[row] != 0;
+    double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;  // the colourless final state: Z, or e- e+
     for (int i = 0; i < np && m < kMaxFinal; ++i) {
       if (pp && i < 2) continue;
-      if (E.F(i, e) == 23) continue;
+      const int fl = E.F(i, e);
+      if (fl == 23 || fl == 11 || fl == -11) {
+        z0 += E.P(0, i, e); z1 += E.P(1, i, e); z2 += E.P(2, i, e); z3 += E.P(3, i, e);
+        continue;
+      }
       if (sizeof(R) == 4 && pp) {
         const double en = E.P(0, i, e), pz = E.P(3, i, e);
         ps[m][0] = (R)(en + pz);
@@ -271,7 +276,6 @@ __global__ void k_observables(DevParams P, DevEvents E, uint64_t first, uint64_t
       o[1] = y23;
       o[2] = y34;
     } else {
-      double z0 = E.P(0, 2, e), z1 = E.P(1, 2, e), z2 = E.P(2, 2, e), z3 = E.P(3, 2, e);
       double pt = sqrt(z1 * z1 + z2 * z2);
       o[0] = pt;
       o[1] = 0.5 * log((z0 + z3) / (z0 - z3));

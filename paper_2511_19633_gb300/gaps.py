@@ -24,7 +24,7 @@ GAPS_ERR_NUMERIC = -4
 GAPS_ERR_CUDA = -5
 GAPS_ERR_NO_DEVICE = -6
 
-GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO = 0, 1, 2
+GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO, GAPS_PP_LL = 0, 1, 2, 3
 GAPS_FP64, GAPS_MIXED = 0, 1
 GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT, GAPS_SCHED_WARP = 0, 1, 2
 GAPS_TRIALS_REDRAW, GAPS_TRIALS_KEEP, GAPS_TRIALS_SELECT = 0, 1, 2
@@ -49,6 +49,7 @@ class GapsConfig(ctypes.Structure):
         ("schedule", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
         ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
         ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_mode", ctypes.c_int),
+        ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double),
     ]
 
 
@@ -351,12 +352,14 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 alpha_s_mz: float = 0.118, nf: int = 5, nmax: int = 128, seed: int = 1,
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
-                refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None) -> GapsConfig:
+                refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None,
+                mll=(66.0, 116.0)) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied). mix: optional list of
     (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
     process, sqrt_s and t_cut. trial_mode: GAPS_TRIALS_*; None = KEEP for
-    GAPS_MIXED with the persistent lane schedule, REDRAW otherwise."""
+    GAPS_MIXED with the persistent lane schedule, REDRAW otherwise. mll: the
+    dilepton mass window of GAPS_PP_LL (GeV)."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
                    block_size, schedule, blocks_per_sm, refill_period, emit_batch)
@@ -365,6 +368,7 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
         trial_mode = (GAPS_TRIALS_KEEP if precision == GAPS_MIXED and schedule == GAPS_SCHED_PERSISTENT
                       else GAPS_TRIALS_REDRAW)
     c.trial_mode = int(trial_mode)
+    c.mll_lo, c.mll_hi = float(mll[0]), float(mll[1])
     if mix:
         if len(mix) > GAPS_MAX_MIX:
             raise ValueError("at most %d rows" % GAPS_MAX_MIX)

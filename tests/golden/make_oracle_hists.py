@@ -38,6 +38,8 @@ WORKLOADS = {
     "ee500": (0, 500.0, 10_000_000, 1.0),
     "pp_lo": (1, 13600.0, 10_000_000, 1.0),
     "pp_nlo": (2, 13600.0, 10_000_000, 1.0),
+    # pp -> gamma*/Z -> e- e+, LO, dilepton mass 66-116 GeV
+    "pp_ll": (3, 13600.0, 10_000_000, 1.0),
     # the e+e- rows of the mixed batch (their own cutoffs)
     "ee91_tc0.5": (0, 91.2, 1_000_000, 0.5),
     "ee500_tc4": (0, 500.0, 1_000_000, 4.0),

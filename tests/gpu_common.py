@@ -4,7 +4,8 @@ from __future__ import annotations
 
 import numpy as np
 
-PROCESS = {"ee91": (0, 91.2), "ee500": (0, 500.0), "pp_lo": (1, 13600.0), "pp_nlo": (2, 13600.0)}
+PROCESS = {"ee91": (0, 91.2), "ee500": (0, 500.0), "pp_lo": (1, 13600.0), "pp_nlo": (2, 13600.0),
+           "pp_ll": (3, 13600.0)}
 
 
 def gaps():

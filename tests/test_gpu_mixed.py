@@ -37,7 +37,7 @@ def test_mixed_follows_fp64_histories(G, pdf):
     assert b["stats"]["violations"] == 0 and b["stats"]["events"] == n
 
 
-@pytest.mark.parametrize("name", ["ee91", "pp_nlo"])
+@pytest.mark.parametrize("name", ["ee91", "pp_nlo", "pp_ll"])
 def test_mixed_conserves_momentum_and_colour(G, pdf, name):
     proc, sqrt_s = PROCESS[name]
     n = 10007
@@ -103,7 +103,7 @@ def _gpu_hists(G, name, pdf, precision, n, first0=0, chunk=1 << 21, trial_mode=N
     return hw.cpu().numpy(), hw2.cpu().numpy(), binning, stats
 
 
-@pytest.mark.parametrize("name,mode", [("ee91", 1), ("ee500", 1), ("pp_lo", 1), ("pp_nlo", 1),
+@pytest.mark.parametrize("name,mode", [("ee91", 1), ("ee500", 1), ("pp_lo", 1), ("pp_nlo", 1), ("pp_ll", 1),
                                        ("ee91", 2), ("pp_nlo", 2)])
 def test_mixed_histograms_match_oracle(G, pdf, name, mode):
     """chi^2/ndf < 1.2 against the FP64 oracle's histograms (independent seed,

@@ -8,7 +8,7 @@ from tests.gpu_common import PROCESS, compare, gaps, identical, run_gpu, run_ora
 pytestmark = pytest.mark.gpu
 
 # sizes the oracle finishes in seconds; not multiples of any block size
-SIZES = {"ee91": 20011, "ee500": 6007, "pp_lo": 8009, "pp_nlo": 6007}
+SIZES = {"ee91": 20011, "ee500": 6007, "pp_lo": 8009, "pp_nlo": 6007, "pp_ll": 8009}
 
 
 @pytest.fixture(scope="module")
