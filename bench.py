@@ -412,9 +412,9 @@ def run_ours(args, ws, rank, local):
             # every channel, max-veto keeping the losing trials, generate-select)
             n_tm = min(total, chunk)
             trial_modes = {}
-            for name, mode in (("redraw", G.GAPS_TRIALS_REDRAW), ("keep", G.GAPS_TRIALS_KEEP),
-                               ("select", G.GAPS_TRIALS_SELECT)):
-                trial_modes[name] = _time_variant(G, config(trial_mode=mode), ev, (1 << 51) + (2 << 24), n_tm,
+            for mode_name, mode in (("redraw", G.GAPS_TRIALS_REDRAW), ("keep", G.GAPS_TRIALS_KEEP),
+                                    ("select", G.GAPS_TRIALS_SELECT)):
+                trial_modes[mode_name] = _time_variant(G, config(trial_mode=mode), ev, (1 << 51) + (2 << 24), n_tm,
                                                   chunk, stream, learned)
 
     per_launch_events = total / n_chunks

@@ -1148,7 +1148,7 @@ __device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const L
 // MINB sets the register tier: 256-thread blocks x MINB per SM (128, 80 or
 // 64 registers per thread)
 template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_shower_mixed(MixedCtx M) {
+__global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constant__ MixedCtx M) {
   __shared__ SmemPdf S;
   // learned proposal only (dynamic size 0 otherwise): per warp 64 rows of
   // input features and 64 outputs, the height decode table and the height
@@ -1486,7 +1486,7 @@ __device__ __forceinline__ uint64_t warp_trials(const MixedCtx& M, const SmemPdf
 }
 
 template <int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(MixedCtx M) {
+__global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(const __grid_constant__ MixedCtx M) {
   __shared__ SmemPdf S;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int nw = blockDim.x >> 5;
@@ -1639,7 +1639,7 @@ namespace {
 // of the bin and 64 scales t log-spaced over [t_c, t_kin] (both ends), as ln(max(r, 1e-6)),
 // with the network's input features of the row.
 constexpr int kTeacherZ = 32, kTeacherT = 64;
-__global__ void k_isr_targets(MixedCtx M, const float4* states, uint64_t n_states, float* feats, float* targets) {
+__global__ void k_isr_targets(const __grid_constant__ MixedCtx M, const float4* states, uint64_t n_states, float* feats, float* targets) {
   __shared__ SmemPdf S;
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
