@@ -962,8 +962,9 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
 // belongs to a channel with probability rate / R. One trial is drawn from R
 // at the current scale; when it falls below the next maximum scale of an
 // inactive channel, the process restarts there with that channel added (no
-// memory). Out of line: not on the default path.
-__device__ __noinline__ void select_trial(const WS& w, int ne, float lnT, float lnTc, bool pp, uint32_t e0,
+// memory). Inline: out of line, its reference arguments would keep the trial
+// loop's running maximum in local memory on every path.
+__device__ __forceinline__ void select_trial(const WS& w, int ne, float lnT, float lnTc, bool pp, uint32_t e0,
                                           uint32_t e1, uint32_t k0, uint32_t k1, uint64_t& d, Counters32& cnt,
                                           float& best, int& bq, int& bch, float& bRz) {
   float t0 = lnT;
