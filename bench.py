@@ -71,6 +71,14 @@ OPS_PER_STEP = 190.0
 OPS_PER_ACCEPT = 1200.0
 # 32-bit lane peak of one GB300: 152 SMs x 128 lanes x 2.07 GHz.
 LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per event of the shower kernel, from one ncu capture
+# of the current kernel on a 262 144-event case of the same workload (the
+# persistent kernel's traffic grows with the events it processes); scaled to a
+# launch by its events. Workloads without a capture report null.
+SHOWER_DRAM_BYTES_PER_EVENT = {
+    ("pp_nlo_1e7", True): (19.126488e9 + 9.866132e9) / 262144,   # learned proposal
+    ("pp_nlo_1e7", False): (18.657529e9 + 8.961404e9) / 262144,  # plain bound
+}
 
 
 def algorithmic_flops(stats: dict) -> float:
@@ -422,9 +430,11 @@ def run_ours(args, ws, rank, local):
     if mixed:
         ops = algorithmic_ops_mixed(stats)
         achieved = ops / (sum(shower_ms) / 1e3) / 1e12
+        bpe = SHOWER_DRAM_BYTES_PER_EVENT.get((name, learned is not None))
         roof = {"bound": "alu", "kernel": "k_shower_mixed", "achieved": achieved, "peak": LANE_PEAK_TOPS,
                 "unit": "Tops/s (32-bit lane operations)", "frac": achieved / LANE_PEAK_TOPS,
-                "traffic": None,
+                "traffic": None if bpe is None else bpe * per_launch_events,
+                "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by events)",
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
                 "shower_ms_per_launch": mean_shower_ms, "events_per_launch": per_launch_events,
                 "ops_per_event": ops / max(1, stats["events"])}
