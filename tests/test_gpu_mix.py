@@ -85,3 +85,18 @@ def test_mixed_batch_histograms_match_oracle_rows(G, pdf, oracle_mod):
         n_r = int((rows == r).sum())
         red, chi2, ndf = chi2_summary(chi2_per_hist(w[r], w2[r], n_r, gold["sumw"], gold["sumw2"], gold["events"]))
         assert red < 1.2, (name, red)
+
+
+def test_fp64_mixed_batch_with_dilepton_row_is_bit_identical(G, oracle_mod, pdf):
+    """A batch mixing on-shell Z, Z/gamma* -> e+ e- and e+e- rows: FP64 events
+    bit-identical to the oracle's mixed batch."""
+    mix = [(2, 13600.0, 1.0, 0.4), (3, 13600.0, 1.0, 0.4), (0, 91.2, 1.0, 0.2)]
+    first, n = 777, 3001
+    g = run_gpu(G, 0, 91.2, first, n, pdf, mix=mix)
+    rows = [oracle_mod.Settings(process=p, sqrt_s=rs, t_cut=tc, nmax=128, seed=1) for p, rs, tc, _ in mix]
+    o = oracle_mod.run_mix(rows, [r[3] for r in mix], first, n, pdf, threads=8)
+    assert set(np.unique(o["row"])) == {0, 1, 2}
+    assert np.any(o["flav"][:, 2] == 11)
+    bad = identical(g, o)
+    assert not bad, bad[:10]
+    assert compare(g, o) == []

@@ -169,3 +169,28 @@ def test_trial_modes_keep_distributions(G, pdf, name):
             err = np.hypot(a.std() / np.sqrt(a.size), b.std() / np.sqrt(b.size))
             assert abs(a.mean() - b.mean()) < 5 * err, (m, a.mean(), b.mean(), err)
         assert abs(on["stats"]["accepts"] - off["stats"]["accepts"]) < 5 * np.sqrt(2 * off["stats"]["accepts"])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("n", [0, 1, 33])
+def test_trial_modes_tiny_and_empty_batches(G, pdf, mode, n):
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    g = run_gpu(G, proc, sqrt_s, 4242, n, pdf, precision=MIXED, schedule=1, trial_mode=mode)
+    assert g["stats"]["events"] == n
+    if n:
+        assert np.all(g["status"] == 1)
+        P = g["p"]
+        for e in range(n):
+            m = g["npart"][e]
+            assert np.abs(P[e, 2:m].sum(0) - (P[e, 0] + P[e, 1])).max() < 1e-11 * sqrt_s
+
+
+@pytest.mark.parametrize("period,block,bps,batch", [(1, 128, 4, 1), (8, 64, 8, 4)])
+def test_generate_select_launch_shape_does_not_change_events(G, pdf, period, block, bps, batch):
+    proc, sqrt_s = PROCESS["pp_lo"]
+    n = 5003
+    ref = run_gpu(G, proc, sqrt_s, 9, n, pdf, precision=MIXED, schedule=1, trial_mode=2)
+    g = run_gpu(G, proc, sqrt_s, 9, n, pdf, precision=MIXED, schedule=1, block_size=block,
+                blocks_per_sm=bps, refill_period=period, emit_batch=batch, trial_mode=2)
+    for k in ("p", "flav", "npart", "weight", "obs"):
+        assert np.array_equal(ref[k], g[k]), k
