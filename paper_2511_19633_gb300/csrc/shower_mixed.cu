@@ -2,21 +2,23 @@
 // of arXiv:2511.19633; the partitioning of Section 3.1 becomes live-event
 // refill). FP32 in the trial loop, the PDF interpolation, the bounds and the
 // acceptance weight; FP64 for dipole invariants, emission kinematics and the
-// II Lorentz kick. The random stream (one Philox block per dipole-end channel
-// in canonical order, two after a winner) is the same as in the FP64 kernel,
-// so most events follow the same history; the histograms agree within
-// statistics.
+// II Lorentz kick. With the trials of Fig. 1 redrawn every cycle
+// (GAPS_TRIALS_REDRAW) the random stream is the FP64 kernel's (one Philox
+// block per dipole-end channel in canonical order, two after a winner), so
+// most events follow the same history; kept trials (the default) and
+// generate-select draw fewer blocks. In every mode the histograms agree with
+// the FP64 ones within statistics.
 //
-// Layout: every lane of the persistent grid owns a working set indexed
-// [..][slot][lane] (coalesced whatever event the lane holds):
-//   p    f64 [4][nmax][L]    momenta
-//   tag  u32 [nmax][L]       flavour | colour << 8 | anticolour << 16
-//   end  f32x4 [2 nmax][L]   the event's colour ends in canonical order
-//                             (emitter ascending, colour side first):
-//                             {1/c0, 1/c1, ln t_kin, emitter | side << 8 | partner << 16}
-// (the learned proposal's bin heights, one 8-bit code per bin, and the network
-// inputs they were evaluated at live in shared memory next to the lanes that
-// read them)
+// Layout: every lane of the persistent grid owns a lane-major working set in
+// global memory (each event contiguous, so a lane walks its own cache lines):
+//   p      f64 [L][nmax][4]     momenta
+//   tag    u32 [L][nmax]        flavour | colour << 8 | anticolour << 16
+//   end    f32x4 [L][2 nmax]    the event's colour ends in canonical order
+//                               (emitter ascending, colour side first):
+//                               {1/c0, 1/c1, ln t_kin, partner slot (-1: none)}
+//   trial  f32x4 [L][2 nmax]    kept trials {ln t, R_z} of both channels
+//   lcode  u8 [L][4][2][8], lkey f32x4 [L][4]: the learned proposal's bin
+//          heights of the initial-state ends and the inputs they came from
 // `end` caches the inverse overestimate coefficients of the end's channels
 // (< 0: channel absent, 0: no phase space) and is rebuilt after every
 // accepted emission.
@@ -90,7 +92,7 @@ struct Lane {
   uint64_t ev;      // record index in the caller's arrays
   int n, n_emit, status, steps;
   int row;          // row of a mixed batch
-  int slot;         // index of the event's learned bin heights in shared memory
+  int slot;         // index of the event's learned bin heights (the lane's global index)
   bool learned_ok;  // learned bounds active for this event
   float lnT;        // ln of the current evolution scale
   double eta0, eta1;
