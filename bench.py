@@ -467,6 +467,11 @@ def run_ours(args, ws, rank, local):
         "plain_gpu": plain,
         "mixed_plain_bound": mixed_plain,
         "trial_modes": trial_modes,
+        # the paper's own GPU number for NLO pp -> Z (V100, FP64, CT14lo at 13 TeV,
+        # partitioning, 128 threads per block): context, not the target
+        "paper_context": {"value": 1.7e4, "unit": "events/s", "hardware": "V100, FP64",
+                          "workload": "NLO pp -> Z, CT14lo, 13 TeV, 1e6 events in about 60 s (the paper's CPU vs GPU comparison)"}
+        if name == "pp_nlo_1e7" else None,
         "learned": learned_info,
         "shower_stats": {k: stats[k] for k in ("events", "steps", "trials", "isr_trials", "vetoes",
                                                 "accepts", "violations", "err_capacity",

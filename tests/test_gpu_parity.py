@@ -93,10 +93,12 @@ def test_high_cutoff_and_large_event_ids(G, oracle_mod, pdf):
     assert len(compare(g, o)) <= _max_mismatch(2000)
 
 
-def test_full_size_lo_sampled_against_oracle(G, oracle_mod, pdf):
-    """pp -> Z LO at the full 1e6 events in the benchmark's persistent launch:
-    2000 events spread over the batch are recomputed by the oracle one by one."""
-    proc, sqrt_s = PROCESS["pp_lo"]
+@pytest.mark.parametrize("name", ["pp_lo", "pp_ll"])
+def test_full_size_lo_sampled_against_oracle(G, oracle_mod, pdf, name):
+    """pp -> Z and pp -> Z/gamma* -> e+ e- at LO, full 1e6 events in the
+    benchmark's persistent launch: 2000 events spread over the batch are
+    recomputed by the oracle one by one."""
+    proc, sqrt_s = PROCESS[name]
     n = 1_000_000
     g = run_gpu(G, proc, sqrt_s, 0, n, pdf, schedule=1, block_size=128, blocks_per_sm=4, obs=True)
     assert g["stats"]["events"] == n and g["stats"]["violations"] == 0
