@@ -70,3 +70,33 @@ def test_missing_pdf_is_rejected(lib):
     with pytest.raises(G.GapsError) as e:
         G.gaps_init(cfg)
     assert e.value.code == G.GAPS_ERR_INVALID_ARG
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a small C program compiled with gcc."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gaps.h"', 'int main(void) {',
+             '  printf("%%zu\\n", sizeof(%s));' % struct]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    return out[0], out[1:]
+
+
+@pytest.mark.parametrize("struct,cls", [("gaps_config", "GapsConfig"), ("gaps_events", "GapsEvents"),
+                                        ("gaps_stats", "GapsStats"), ("gaps_mix_row", "GapsMixRow"),
+                                        ("gaps_hists", "GapsHists")])
+def test_binding_structs_match_the_header_layout(struct, cls, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of
+    the C declaration (fields appended to the ABI must be appended in both)."""
+    from paper_2511_19633_gb300 import gaps as G
+    py = getattr(G, cls)
+    names = [f[0] for f in py._fields_]
+    size, offsets = _c_layout(struct, names, tmp_path)
+    assert ctypes.sizeof(py) == size
+    for name, off in zip(names, offsets):
+        assert getattr(py, name).offset == off, name
