@@ -11,8 +11,8 @@
 // paper's formulas (cited per function) and textbook definitions.
 //
 // Readings of the paper that are not fixed by its text are marked "reading:".
-// Parity-unpinned parts: the e+e- hard-process couplings (textbook formula,
-// only used as event weights) and the observable binning.
+// The e+e- and Drell-Yan angular cross sections are pinned by the tests
+// against helicity amplitudes; the observable binning is a choice (no pin).
 //
 // Conventions
 //   four-vectors (E, px, py, pz), metric (+,-,-,-), GeV.

@@ -44,6 +44,16 @@ def test_partonic_cross_section_equals_helicity_amplitudes(oracle_mod, m, f):
         assert oracle_mod.ll_dsigma(m * m, f, c) == pytest.approx(helicity_dsigma(m * m, f, c), rel=1e-12)
 
 
+@pytest.mark.parametrize("m", [20.0, MZ, 200.0, 500.0])
+@pytest.mark.parametrize("f", [1, 2, 3, 4, 5])
+def test_ee_to_qq_cross_section_equals_helicity_amplitudes(oracle_mod, m, f):
+    """e+e- -> q qbar (the e+e- hard process): the same helicity amplitudes
+    with the sum N_c over the outgoing colours in place of the average 1/N_c;
+    cos(theta) between the electron and the quark."""
+    for c in (-0.9, -0.2, 0.0, 0.5, 0.97):
+        assert oracle_mod.ee_dsigma(m * m, f, c) == pytest.approx(helicity_dsigma(m * m, f, c) * NC * NC, rel=1e-12)
+
+
 def test_partonic_photon_limit(oracle_mod):
     """Far below the pole the photon term dominates: sigma = 4 pi alpha^2 Q^2 / (3 s N_c)."""
     s = 2.0 ** 2
