@@ -538,8 +538,8 @@ void transverse_basis(const double P[4], const double K[4], double e1[4], double
 // with B the certified PDF-ratio bound (1 for final-final) and Pover one of
 //   soft: C/(1-z)   flat: C   both: C/(z(1-z))   inv: C/z.
 // Each Pover bounds kernel * Jacobian * (x for initial-state emitters) over
-// the whole (x, u) or (x, v) domain (proved in the design notes), so the
-// acceptance weight never exceeds one when B is a true bound.
+// the whole (x, u) or (x, v) domain (analytic bounds, checked by the Sudakov
+// pins), so the acceptance weight never exceeds one when B is a true bound.
 // ---------------------------------------------------------------------------
 enum Shape { kSoft = 0, kFlat = 1, kBoth = 2, kInv = 3 };
 enum DipType { kFF = 0, kFI = 1, kIF = 2, kII = 3 };
@@ -1600,9 +1600,19 @@ int oracle_mix_rows(uint64_t seed, const double* fractions, int n_rows, uint64_t
 // fraction eta), 2 II (incoming quark from beam 1 at eta + incoming antiquark
 // from beam 2 at eta2 = s/(eta * sqrt_s^2)). The shower runs from t_start
 // until its first accepted emission; out_t[i] = its scale or 0 if none.
-// Used by the Sudakov pins.
+// Used by the Sudakov pins. With out_rec != NULL the record after the first
+// emission is written too: out_rec[i][3][8] = {E, px, py, pz, flavour, colour,
+// anticolour, initial} of slots 0..2 (zero past the record), and
+// out_eta[i][2] the momentum fractions of slots 0 and 1 (used by the pins of
+// the flavour choices and the colour flow).
+int oracle_first_emission_record(const OracleConfig* c, int type, int flq, double s, double eta,
+                                 uint64_t n, double* out_t, double* out_rec, double* out_eta);
 int oracle_first_emission(const OracleConfig* c, int type, int flq, double s, double eta,
                           uint64_t n, double* out_t) {
+  return oracle_first_emission_record(c, type, flq, s, eta, n, out_t, nullptr, nullptr);
+}
+int oracle_first_emission_record(const OracleConfig* c, int type, int flq, double s, double eta,
+                                 uint64_t n, double* out_t, double* out_rec, double* out_eta) {
   Config k = to_config(c);
   Physics ph = make_physics(k);
   Event ev;
@@ -1662,6 +1672,17 @@ int oracle_first_emission(const OracleConfig* c, int type, int flq, double s, do
       ++steps;
     }
     out_t[e] = ev.t_first;
+    if (out_rec) {
+      for (int q = 0; q < 3; ++q) {
+        double* r = out_rec + (e * 3 + q) * 8;
+        for (int m = 0; m < 8; ++m) r[m] = 0.0;
+        if (q >= (int)ev.parts.size()) continue;
+        const Parton& P = ev.parts[q];
+        for (int mu = 0; mu < 4; ++mu) r[mu] = P.p[mu];
+        r[4] = P.fl; r[5] = P.col; r[6] = P.acol; r[7] = P.initial ? 1.0 : 0.0;
+      }
+    }
+    if (out_eta) { out_eta[2 * e] = ev.eta[0]; out_eta[2 * e + 1] = ev.eta[1]; }
   }
   return 0;
 }

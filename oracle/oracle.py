@@ -100,6 +100,8 @@ def lib():
         _lib.oracle_antikt.argtypes = [vp, i, d, vp]
         _lib.oracle_antikt.restype = i
         _lib.oracle_first_emission.argtypes = [P(OracleConfig), i, i, d, d, ctypes.c_uint64, vp]
+        _lib.oracle_first_emission_record.argtypes = [P(OracleConfig), i, i, d, d, ctypes.c_uint64, vp, vp,
+                                                      vp]
         _lib.oracle_if_map.argtypes = [d, d, d, vp]
         _lib.oracle_mlp_forward.argtypes = [vp, vp, ctypes.c_uint64, vp]
         _lib.oracle_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint64, d, vp]
@@ -337,6 +339,25 @@ def first_emission(settings: Settings, pdf: np.ndarray | None, dipole: int, flq:
     if rc != 0:
         raise RuntimeError("oracle_first_emission failed")
     return out
+
+
+def first_emission_record(settings: Settings, pdf: np.ndarray | None, dipole: int, flq: int,
+                          s: float, eta: float, n: int) -> dict:
+    """As first_emission, with the record after the first emission:
+    "p" [n][3][4], "flav", "col", "acol", "initial" [n][3] (slots 0..2; the
+    third is empty when nothing was emitted) and "eta" [n][2]."""
+    if pdf is not None:
+        pdf = np.ascontiguousarray(pdf, dtype=np.float32)
+    t = np.zeros(n)
+    rec = np.zeros((n, 3, 8))
+    eta_out = np.zeros((n, 2))
+    c = settings.to_c(pdf)
+    rc = lib().oracle_first_emission_record(ctypes.byref(c), dipole, flq, s, eta, n, _ptr(t), _ptr(rec),
+                                            _ptr(eta_out))
+    if rc != 0:
+        raise RuntimeError("oracle_first_emission_record failed")
+    return {"t": t, "p": rec[:, :, :4], "flav": rec[:, :, 4].astype(int), "col": rec[:, :, 5].astype(int),
+            "acol": rec[:, :, 6].astype(int), "initial": rec[:, :, 7].astype(bool), "eta": eta_out}
 
 
 def if_map(r: float, z: float, omz: float):
