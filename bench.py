@@ -51,26 +51,36 @@ WORKLOADS = {
                 "1e8 events in chunks of 2^22, learned proposal, one CUDA graph per step"),
 }
 DEFAULT_WORKLOAD = "pp_nlo_1e7"
+# the kernel that dominates a step of the mixed-precision path
+SHOWER_KERNEL = "k_shower_mixed"
 
-# Algorithmic work, counted from the formulas (see the design notes):
+# Algorithmic work per unit, as the scope of the measurement defines it: a
+# dipole trial is a log, an exp, a log for the z sample and about 25 FMA
+# (28 operations, a transcendental counting as one); an initial-state trial adds
+# two bilinear PDF interpolations (about 20 operations and 4 gathers each, 48);
+# an accepted emission about 300 FP64 operations of kinematics. The counts are
+# the library's counters of the timed run.
+ALG_OPS_PER_TRIAL = 28.0
+ALG_OPS_PER_ISR_TRIAL = 48.0
+ALG_OPS_PER_ACCEPT = 300.0
 # FP64 path: FLOP per trial / initial-state trial / cycle / accepted emission,
-# a log, exp or sqrt counting as 20 FLOP.
+# a log, exp or sqrt counting as 20 FLOP (the FP64 kernel's own arithmetic).
 FLOP_PER_TRIAL = 85.0
 FLOP_PER_ISR_TRIAL = 16.0
 FLOP_PER_STEP = 160.0
 FLOP_PER_ACCEPT = 300.0
-# FP64 peak of one GB300: 1.25 TFLOP/s nominal (dense).
-FP64_PEAK_TFLOPS = 1.25
-# Mixed path: 32-bit operations per trial (Philox-4x32-10: 10 rounds of two
-# 32x32->64 products, two 3-input XORs and two key additions = 60; uniform,
-# log, FMA, compare 7), per cycle (FP32 veto: limits, maps, kernel, two PDF
-# interpolations, alpha_s) and per accepted emission (FP64 kinematics and the
-# end-table rebuild, each operation counted once).
+# Mixed path, implementation count: 32-bit operations per trial (Philox-4x32-10:
+# 10 rounds of two 32x32->64 products, two 3-input XORs and two key additions =
+# 60; uniform, log, FMA, compare 7), per cycle (FP32 veto: limits, maps, kernel,
+# two PDF interpolations, alpha_s) and per accepted emission (FP64 kinematics and
+# the end-table rebuild, each operation counted once).
 OPS_PER_TRIAL = 67.0
 OPS_PER_STEP = 190.0
 OPS_PER_ACCEPT = 1200.0
-# 32-bit lane peak of one GB300: 152 SMs x 128 lanes x 2.07 GHz.
-LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# Nominal figures, used only when the microbenchmarks cannot run: 152 SMs x
+# 128 FP32 lanes x 2.07 GHz, and 1.25 TFLOP/s FP64 (dense).
+LANE_PEAK_TOPS_NOMINAL = 152 * 128 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS_NOMINAL = 1.25
 # DRAM bytes (read + write) per event of the shower kernel, from one ncu capture
 # of the current kernel on a 262 144-event case of the same workload (the
 # persistent kernel's traffic grows with the events it processes); scaled to a
@@ -81,13 +91,33 @@ SHOWER_DRAM_BYTES_PER_EVENT = {
 }
 
 
-def algorithmic_flops(stats: dict) -> float:
+def fp64_flops(stats: dict) -> float:
     return (stats["trials"] * FLOP_PER_TRIAL + stats["isr_trials"] * FLOP_PER_ISR_TRIAL
             + stats["steps"] * FLOP_PER_STEP + stats["accepts"] * FLOP_PER_ACCEPT)
 
 
-def algorithmic_ops_mixed(stats: dict) -> float:
+def implementation_ops_mixed(stats: dict) -> float:
     return stats["trials"] * OPS_PER_TRIAL + stats["steps"] * OPS_PER_STEP + stats["accepts"] * OPS_PER_ACCEPT
+
+
+def algorithmic_ops(stats: dict) -> float:
+    return (stats["trials"] * ALG_OPS_PER_TRIAL + stats["isr_trials"] * ALG_OPS_PER_ISR_TRIAL
+            + stats["accepts"] * ALG_OPS_PER_ACCEPT)
+
+
+def alu_peaks(G) -> dict:
+    """Instruction throughput of the FP32, FP64, special-function and integer
+    pipes, from the library's own microbenchmarks on this GPU, with the SM
+    clock sampled while they run."""
+    out = {}
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for name, kind, iters in (("ffma", G.GAPS_PEAK_FFMA, 32768), ("dfma", G.GAPS_PEAK_DFMA, 256),
+                                  ("mufu", G.GAPS_PEAK_MUFU, 4096), ("imad", G.GAPS_PEAK_IMAD, 16384)):
+            r = G.gaps_alu_peak(kind, iters)
+            out[name + "_per_s"] = r["ops_per_s"]
+            out[name + "_ms"] = r["ms"]
+    out["clocks"] = clk.summary()
+    return out
 
 
 def dist_env():
@@ -195,9 +225,16 @@ def cpu_baseline(process: int, sqrt_s: float, mix=None, target_s: float = 12.0) 
     t0 = time.perf_counter()
     _oracle_run(O, rows, fr, 20_000_000_000, n, pdf, cores)
     dt = time.perf_counter() - t0
+    # the oracle as written, on one thread, over a smaller sample
+    n1 = max(200, int(n / cores * 0.4))
+    t1 = time.perf_counter()
+    _oracle_run(O, rows, fr, 21_000_000_000, n1, pdf, 1)
+    dt1 = time.perf_counter() - t1
     return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
             "sample": "%d events of the same workload (event ids from 2e10), %.1f s, FP64 plain bound"
-                      % (n, dt)}
+                      % (n, dt),
+            "single_thread": {"value": n1 / dt1, "unit": "events/s", "cores": 1,
+                              "sample": "%d events (ids from 2.1e10), %.1f s" % (n1, dt1)}}
 
 
 def run_reference(args, ws, rank):
@@ -227,25 +264,38 @@ def run_reference(args, ws, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "description": desc, "events_per_step": n},
+            "config": {"workload": name,
+                       "description": "the FP64 CPU oracle as it stands (plain certified bound, Fig. 1 "
+                                      "max-veto redrawing every channel, no learned proposal, no GPU) on "
+                                      "%d host threads over a bounded sample of the workload's events"
+                                      % cores,
+                       "events_per_step": n},
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "events/s",
                              "sample": "%d events per step on %d threads" % (n, cores)},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _plain_pass(G, ctx, ev, first, total, chunk, stream):
-    """hard + shower + observables through the per-call entry points."""
+def _plain_pass(G, ctx, ev, first, total, chunk, stream, marks=None):
+    """hard + shower + observables through the per-call entry points; with
+    `marks`, a pair of CUDA events around each chunk's shower is appended."""
+    import torch
     for f0 in range(0, total, chunk):
         m = min(chunk, total - f0)
         G.gaps_generate_hard(ctx, first + f0, m, ev, stream)
+        if marks is not None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
         G.gaps_shower(ctx, first + f0, m, ev, stream)
+        if marks is not None:
+            b.record(stream)
+            marks.append((a, b))
         G.gaps_observables(ctx, first + f0, m, ev, None, None, stream)
 
 
 def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None):
     """Events per second of one configuration over n events (after a warm-up
-    pass), with its shower statistics."""
+    pass), the shower kernels' own time, and the shower statistics."""
     import torch
     ctx = G.gaps_init(cfg)
     try:
@@ -255,17 +305,19 @@ def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None):
         torch.cuda.synchronize()
         G.gaps_reset_stats(ctx, stream)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        marks = []
         a.record(stream)
-        _plain_pass(G, ctx, ev, first, n, chunk, stream)
+        _plain_pass(G, ctx, ev, first, n, chunk, stream, marks)
         b.record(stream)
         torch.cuda.synchronize()
         st = G.gaps_get_stats(ctx, stream)
     finally:
         G.gaps_destroy(ctx)
     return {"value": n / (a.elapsed_time(b) / 1e3), "unit": "events/s", "events": n,
+            "shower_ms": sum(x.elapsed_time(y) for x, y in marks),
             "steps_per_event": st["steps"] / max(1, st["events"]),
             "trials_per_event": st["trials"] / max(1, st["events"]),
-            "violations": st["violations"]}
+            "violations": st["violations"], "stats": st}
 
 
 def run_ours(args, ws, rank, local):
@@ -379,7 +431,7 @@ def run_ours(args, ws, rank, local):
     pdf_host = torch.from_numpy(pdf).pin_memory() if uses_pdf else None
     obs_host = torch.empty((G.GAPS_NOBS, total), dtype=torch.float64).pin_memory()
     h_host = torch.empty((2, n_rows, G.GAPS_NHIST, G.GAPS_HIST_BINS), dtype=torch.float64).pin_memory()
-    e2e_steps = 1
+    e2e_steps = args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
@@ -427,25 +479,46 @@ def run_ours(args, ws, rank, local):
 
     per_launch_events = total / n_chunks
     mean_shower_ms = sum(shower_ms) / max(1, len(shower_ms))
+    try:
+        alu = alu_peaks(G)
+        lane_peak = alu["ffma_per_s"] / 1e12
+        fp64_peak = 2.0 * alu["dfma_per_s"] / 1e12
+    except G.GapsError as err:  # the microbenchmarks failed: nominal figures, said so
+        alu = {"error": str(err), "clocks": {}}
+        lane_peak, fp64_peak = LANE_PEAK_TOPS_NOMINAL, FP64_PEAK_TFLOPS_NOMINAL
     if mixed:
-        ops = algorithmic_ops_mixed(stats)
+        ops = algorithmic_ops(stats)
         achieved = ops / (sum(shower_ms) / 1e3) / 1e12
+        impl = implementation_ops_mixed(stats) / (sum(shower_ms) / 1e3) / 1e12
         bpe = SHOWER_DRAM_BYTES_PER_EVENT.get((name, learned is not None))
-        roof = {"bound": "alu", "kernel": "k_shower_mixed", "achieved": achieved, "peak": LANE_PEAK_TOPS,
-                "unit": "Tops/s (32-bit lane operations)", "frac": achieved / LANE_PEAK_TOPS,
+        roof = {"bound": "alu", "kernel": SHOWER_KERNEL, "achieved": achieved, "peak": lane_peak,
+                "unit": "Tops/s (operations of the scope's work units per second)",
+                "frac": achieved / lane_peak,
                 "traffic": None if bpe is None else bpe * per_launch_events,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by events)",
-                "peak_source": "152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "peak_source": ("measured: FP32 FMA lane throughput of this GPU (gaps_alu_peak, "
+                                "median SM clock %s MHz)" % alu["clocks"].get("sm_mhz"))
+                if "error" not in alu else "nominal 152 x 128 lanes x 2.07 GHz (microbenchmark failed)",
                 "shower_ms_per_launch": mean_shower_ms, "events_per_launch": per_launch_events,
-                "ops_per_event": ops / max(1, stats["events"])}
+                "ops_per_event": ops / max(1, stats["events"]),
+                "implementation": {"achieved": impl, "frac": impl / lane_peak,
+                                   "ops_per_event": implementation_ops_mixed(stats) / max(1, stats["events"]),
+                                   "note": "Philox, end-table rebuild and FP64 kinematics counted as executed"}}
     else:
-        flops = algorithmic_flops(stats)
+        flops = fp64_flops(stats)
         achieved = flops / (sum(shower_ms) / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_shower_fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 (dense) from the profiling recipe",
+        roof = {"bound": "alu", "kernel": "k_shower_fp64", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "measured: FP64 FMA throughput of this GPU x 2 (gaps_alu_peak)"
+                if "error" not in alu else "nominal 1.25 TFLOP/s (microbenchmark failed)",
                 "shower_ms_per_launch": mean_shower_ms, "events_per_launch": per_launch_events,
                 "flop_per_event": flops / max(1, stats["events"])}
+    if plain is not None and plain.get("shower_ms"):
+        # the FP64 paper-layout kernel against the measured FP64 pipe
+        f = fp64_flops(plain["stats"]) / (plain["shower_ms"] / 1e3) / 1e12
+        plain["roofline"] = {"bound": "alu", "kernel": "k_shower_fp64", "achieved": f, "peak": fp64_peak,
+                             "unit": "TFLOP/s", "frac": f / fp64_peak,
+                             "peak_source": "measured FP64 FMA throughput x 2 (gaps_alu_peak)"}
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
@@ -479,6 +552,7 @@ def run_ours(args, ws, rank, local):
         "veto_rate": stats["vetoes"] / max(1, stats["steps"]),
         "lane_efficiency": stats["lane_steps"] / max(1, stats["warp_steps"]),
         "hbm_gbs_measured": peaks.get("hbm_gbs"),
+        "alu_peaks": alu,
     }
     if tuning is not None:
         line["autotune"] = {"best": tuning["best"], "sample_events": tuning["sample_events"],

@@ -137,6 +137,8 @@ typedef struct {
                              GAPS_ERR_INVALID_ARG */
     double mll_lo, mll_hi;  /* GAPS_PP_LL (also as a row of a mixed batch): dilepton
                              mass window in GeV, 0 < mll_lo < mll_hi <= sqrt_s */
+    int max_cycles;       /* veto cycles an event may take before it ends with
+                             GAPS_ERR_ITER_CAP, 0 = 200000, at most 1e9 */
 } gaps_config;
 
 /* Trial schemes (gaps_config.trial_mode). All three give the same
@@ -234,20 +236,26 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
  * gaps_shower, run with 64 blocks of 128 threads and emission batch 8, with
  * every piece of scratch memory held in device arrays of the library itself:
  * a working set for at most 32 partons per event (27.3 MB), the work counter,
- * the statistics and copies of the PDF grid and its bound tables. Every GPU
- * that loads the library keeps these arrays until the process exits.
- * It needs no context: `cfg` is read as in gaps_init (its precision and launch
- * fields are ignored) and the caller still passes the event records, written
- * by gaps_generate_hard or an equivalent. Results are identical to
- * gaps_shower with GAPS_MIXED for the same events.
+ * the statistics and copies of the PDF grid and its bound tables (27.5 MB in
+ * all). Every GPU that loads the library keeps these arrays until the process
+ * exits. It needs no context: `cfg` is read as in gaps_init and the caller
+ * still passes the event records, written by gaps_generate_hard or an
+ * equivalent. cfg's precision, schedule and launch fields (block size, blocks
+ * per SM, refill period, emission batch) are ignored. Results are identical to
+ * gaps_shower with GAPS_MIXED and the plain bounds for the same events (a
+ * learned proposal is never used here).
  *   - Rejects ev->nmax above 32 (or different from cfg->nmax_partons) and
  *     any invalid configuration with GAPS_ERR_INVALID_ARG.
  *   - The first call on a device looks up the arrays' device addresses; make
  *     that first call before any stream capture.
+ *   - When cfg->pdf_grid is set (every pp process) the call rebuilds the bound
+ *     tables on the host, copies them and the grid into the library's arrays
+ *     and synchronises `stream` before the launch (the tables' host copy lives
+ *     in the call).
+ *   - When stats != NULL it synchronises `stream` after the launch and
+ *     returns this call's counters.
  *   - All calls share the same arrays (the counters are cleared by each
- *     call): calls that overlap on the GPU, from any stream or thread, race.
- *   - When stats != NULL it synchronises `stream` and returns this call's
- *     counters. */
+ *     call): calls that overlap on the GPU, from any stream or thread, race. */
 int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
                        const gaps_events* ev, gaps_stats* stats, void* stream);
 

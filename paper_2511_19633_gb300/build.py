@@ -28,6 +28,7 @@ UNITS = {
     # acceptance test is statistical in this mode); FP64 arithmetic unchanged
     "shower_mixed.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "mlp.cu": [],
+    "peaks.cu": [],
 }
 
 
@@ -46,7 +47,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "gaps.h"))
+    headers += [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))]
     objs, jobs = [], []
     for unit, flags in UNITS.items():
         src = os.path.join(CSRC, unit)

@@ -140,6 +140,7 @@ int validate_config(const gaps_config& c) {
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
   if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
   if (c.emit_batch < 0 || c.emit_batch > 32) return GAPS_ERR_INVALID_ARG;
+  if (c.max_cycles < 0 || c.max_cycles > 1000000000) return GAPS_ERR_INVALID_ARG;
   if (c.precision == GAPS_MIXED && c.block_size != 0 && c.block_size != 64 && c.block_size != 128 &&
       c.block_size != 256)
     return GAPS_ERR_INVALID_ARG;
@@ -175,6 +176,7 @@ void fill_params(const gaps_config& c, DevParams& P) {
   double den = 1.0 + c.alpha_s_mz * beta0 * gm_log(c.t_cut / (91.1876 * 91.1876));
   P.process = c.process;
   P.trial_mode = c.trial_mode;
+  P.max_steps = c.max_cycles > 0 ? c.max_cycles : kMaxSteps;
   // images of the dilepton mass window under m^2 = m_Z^2 + m_Z Gamma_Z tan(2 pi r)
   {
     const double mg = kMZ * kGZ, mz2 = kMZ * kMZ;

@@ -19,7 +19,7 @@ constexpr int kNX = GAPS_PDF_NX, kNQ = GAPS_PDF_NQ;
 constexpr double kXMin = GAPS_PDF_XMIN, kXMax = GAPS_PDF_XMAX;
 constexpr double kQ2Min = GAPS_PDF_Q2MIN, kQ2Max = GAPS_PDF_Q2MAX;
 constexpr uint64_t kHardDrawBase = 0x8000000000000000ull;
-constexpr int kMaxSteps = 200000;
+constexpr int kMaxSteps = 200000;  // default of gaps_config.max_cycles
 
 // counters in the device stats block (uint64 each)
 enum Counter {
@@ -39,6 +39,7 @@ struct DevParams {
   int process, nf, nmax;
   double sqrt_s, s_had, t_cut, as_mz, as_over, beta0, p_s;
   int trial_mode;              // GAPS_TRIALS_* (KEEP and SELECT: mixed lane kernel only)
+  int max_steps;               // veto cycles per event before GAPS_ERR_ITER_CAP
   double ll_rlo, ll_rhi;       // GAPS_PP_LL: the mass window's images under the Breit-Wigner map
   int n_rows;                  // 1: one process; > 1: mixed batch
   RowParams rows[kMaxRows];    // row 0 = the fields above for one process

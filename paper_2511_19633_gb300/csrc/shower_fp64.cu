@@ -326,7 +326,7 @@ __device__ int run_event(const DevParams& P0, const DevEvents& E, uint64_t e, ui
   int steps = 0;
   while (st == GAPS_STATUS_ACTIVE) {
     st = shower_step(P, E, e, n, t, eta0, eta1, rng, n_emit, cnt);
-    if (++steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
+    if (++steps >= P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
   }
   E.npart[e] = n;
   E.t[e] = t;

@@ -1307,7 +1307,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
     warp_steps += 32;
     if (active && !parked) {
       int st = step_mixed(M, S, ls, w, L, M.first + L.ev, cnt, pend, parked);
-      if (++L.steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
+      if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st != GAPS_STATUS_ACTIVE) {
         L.status = st;
         store_event(M, w, L);
@@ -1564,7 +1564,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(const __grid_constan
       Emission pend;
       bool parked = false;
       st = step_veto(M, S, ls, w, L, M.first + L.ev, cnt, pend, parked, best, bq, bch, bRz);
-      if (++L.steps >= kMaxSteps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
+      if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st == GAPS_STATUS_ACTIVE && parked) {
         if (pend.kind == 1) {
           done_emit = true;  // plain rebuild after a learned-bound violation
@@ -1814,6 +1814,11 @@ constexpr size_t kStaticWorkBytes =
     (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
     (size_t)kStaticLanes * (64 + 4 * sizeof(float4));
 
+// the carve of workset_carve for the static launch shape
+static_assert(kStaticWorkBytes == (size_t)kStaticLanes * kStaticMaxNmax *
+                                      (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
+                                  (size_t)kStaticLanes * (64 + 4 * sizeof(float4)),
+              "static working set differs from workset_bytes");
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
 static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];
 static __device__ __align__(256) double g_static_tables[kBoundTableDoubles];

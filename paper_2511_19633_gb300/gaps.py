@@ -49,7 +49,7 @@ class GapsConfig(ctypes.Structure):
         ("schedule", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
         ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
         ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_mode", ctypes.c_int),
-        ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double),
+        ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double), ("max_cycles", ctypes.c_int),
     ]
 
 
@@ -87,7 +87,10 @@ EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
            "gaps_destroy", "gaps_shower_static", "gaps_collect_isr_states", "gaps_isr_targets",
            "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train",
-           "gaps_process", "gaps_process_shower_ms", "gaps_set_violation_log")
+           "gaps_process", "gaps_process_shower_ms", "gaps_set_violation_log", "gaps_alu_peak")
+
+# kinds of gaps_alu_peak (include/gaps_peaks.h)
+GAPS_PEAK_FFMA, GAPS_PEAK_DFMA, GAPS_PEAK_MUFU, GAPS_PEAK_IMAD = 0, 1, 2, 3
 
 
 class GapsError(RuntimeError):
@@ -126,6 +129,7 @@ def _load():
     lib.gaps_mlp_loss_grad.argtypes = [vp, vp, vp, u64, f, vp, vp, vp]
     lib.gaps_mlp_forward.argtypes = [vp, vp, u64, i, vp, vp]
     lib.gaps_mlp_train.argtypes = [vp, vp, vp, vp, vp, u64, u64, f, f, u64, vp, i, vp]
+    lib.gaps_alu_peak.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     return lib
 
 
@@ -266,6 +270,15 @@ def gaps_process_shower_ms(ctx, max_chunks: int = 4096) -> list:
     return [float(buf[c]) for c in range(k)]
 
 
+def gaps_alu_peak(kind: int, iters: int = 4096, stream=None) -> dict:
+    """Instruction throughput of one arithmetic pipe of the current GPU (the
+    library's own microbenchmark): {"ops_per_s", "ms"}."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.gaps_alu_peak(kind, iters, ctypes.byref(ops), ctypes.byref(ms), _stream_ptr(stream)),
+           "gaps_alu_peak")
+    return {"ops_per_s": ops.value, "ms": ms.value}
+
+
 def gaps_hist_binning(ctx, h: int) -> dict:
     lo, hi = ctypes.c_double(), ctypes.c_double()
     nb, ob, lg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -353,13 +366,14 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
                 refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None,
-                mll=(66.0, 116.0)) -> GapsConfig:
+                mll=(66.0, 116.0), max_cycles: int = 0) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied). mix: optional list of
     (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
     process, sqrt_s and t_cut. trial_mode: GAPS_TRIALS_*; None = KEEP for
     GAPS_MIXED with the persistent lane schedule, REDRAW otherwise. mll: the
-    dilepton mass window of GAPS_PP_LL (GeV)."""
+    dilepton mass window of GAPS_PP_LL (GeV). max_cycles: veto cycles per event
+    before GAPS_ERR_ITER_CAP (0 = the library default)."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
                    block_size, schedule, blocks_per_sm, refill_period, emit_batch)
@@ -369,6 +383,7 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                       else GAPS_TRIALS_REDRAW)
     c.trial_mode = int(trial_mode)
     c.mll_lo, c.mll_hi = float(mll[0]), float(mll[1])
+    c.max_cycles = int(max_cycles)
     if mix:
         if len(mix) > GAPS_MAX_MIX:
             raise ValueError("at most %d rows" % GAPS_MAX_MIX)

@@ -17,13 +17,13 @@ def gaps():
 
 def run_gpu(G, process, sqrt_s, first, n, pdf, nmax=128, seed=1, schedule=0, block_size=0,
             blocks_per_sm=0, precision=0, t_cut=1.0, obs=True, refill_period=0, emit_batch=0, mix=None,
-            trial_mode=None):
+            trial_mode=None, max_cycles=0):
     import torch
     uses_pdf = process or (mix and any(r[0] for r in mix))
     cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf else None, nmax=nmax, seed=seed,
                         schedule=schedule, block_size=block_size, blocks_per_sm=blocks_per_sm,
                         precision=precision, t_cut=t_cut, refill_period=refill_period,
-                        emit_batch=emit_batch, mix=mix, trial_mode=trial_mode)
+                        emit_batch=emit_batch, mix=mix, trial_mode=trial_mode, max_cycles=max_cycles)
     ctx = G.gaps_init(cfg)
     try:
         buf = G.EventBuffers.allocate(max(n, 1), nmax)

@@ -100,3 +100,25 @@ def test_binding_structs_match_the_header_layout(struct, cls, tmp_path):
     assert ctypes.sizeof(py) == size
     for name, off in zip(names, offsets):
         assert getattr(py, name).offset == off, name
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -1e-3])
+def test_non_finite_or_negative_pdf_grid_is_rejected(lib, pdf, bad):
+    """gaps_init validates every grid value on the host before any device
+    work: a non-finite or negative x f(x, Q^2) is an invalid argument."""
+    from paper_2511_19633_gb300 import gaps as G
+    g = pdf.copy()
+    g[3, 40, 17] = bad
+    cfg = G.make_config(2, 13600.0, pdf_grid=g)
+    with pytest.raises(G.GapsError) as e:
+        G.gaps_init(cfg)
+    assert e.value.code == G.GAPS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("value", [-1, 2_000_000_000])
+def test_cycle_cap_out_of_range_is_rejected(lib, pdf, value):
+    from paper_2511_19633_gb300 import gaps as G
+    cfg = G.make_config(2, 13600.0, pdf_grid=pdf, max_cycles=value)
+    with pytest.raises(G.GapsError) as e:
+        G.gaps_init(cfg)
+    assert e.value.code == G.GAPS_ERR_INVALID_ARG

@@ -18,5 +18,8 @@ def test_reference_arm_prints_the_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["config"]["workload"] == "ee91_1e4_fp64"
+    # the reference line describes what ran: the FP64 oracle, no GPU path
+    desc = line["config"]["description"]
+    assert "oracle" in desc and "learned" not in desc.replace("no learned", "") and "graph" not in desc
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
