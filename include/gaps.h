@@ -29,7 +29,9 @@
  *   - Device buffers are owned by the caller; the library owns its copy of
  *     the PDF grid, its bound tables, its counters and, for GAPS_MIXED, a
  *     working set of nmax partons per resident thread (allocated by the
- *     first mixed gaps_shower call; about 100 B x nmax x resident threads).
+ *     first mixed gaps_shower call; about 100 B x nmax x resident threads),
+ *     or with GAPS_SCHED_WAVE one per event of ev->capacity (about
+ *     100 B x nmax + 160 B per event).
  */
 #ifndef GAPS_H
 #define GAPS_H
@@ -69,6 +71,10 @@ extern "C" {
 #define GAPS_SCHED_PERSISTENT 1   /* persistent grid, finished lanes take the next event */
 #define GAPS_SCHED_WARP       2   /* GAPS_MIXED only: persistent grid, one event per warp
                                      in shared memory, the lanes share its trials */
+#define GAPS_SCHED_WAVE       3   /* GAPS_MIXED only: wavefront passes, one kernel per phase
+                                     (end tables, veto cycles, emissions) over lists of
+                                     live events, then the persistent grid for the events
+                                     still live; identical events to GAPS_SCHED_PERSISTENT */
 
 /* per-event status values; negative values are the error codes above */
 #define GAPS_STATUS_ACTIVE 0
@@ -133,12 +139,14 @@ typedef struct {
     gaps_mix_row mix[GAPS_MAX_MIX];
     int trial_mode;       /* GAPS_TRIALS_*: how the overestimate trials of a cycle are
                              drawn; KEEP and SELECT only with GAPS_MIXED and
-                             GAPS_SCHED_PERSISTENT, any other combination or value is
-                             GAPS_ERR_INVALID_ARG */
+                             GAPS_SCHED_PERSISTENT or GAPS_SCHED_WAVE, any other
+                             combination or value is GAPS_ERR_INVALID_ARG */
     double mll_lo, mll_hi;  /* GAPS_PP_LL (also as a row of a mixed batch): dilepton
                              mass window in GeV, 0 < mll_lo < mll_hi <= sqrt_s */
     int max_cycles;       /* veto cycles an event may take before it ends with
                              GAPS_ERR_ITER_CAP, 0 = 200000, at most 1e9 */
+    int wave_passes;      /* GAPS_SCHED_WAVE: passes before the persistent grid takes
+                             the remaining live events, 0 = 24, at most 4096 */
 } gaps_config;
 
 /* Trial schemes (gaps_config.trial_mode). All three give the same

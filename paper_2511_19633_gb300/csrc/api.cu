@@ -24,6 +24,8 @@ cudaError_t launch_mlp_image(const float* params, void* image, cudaStream_t stre
 size_t mlp_image_bytes();
 cudaError_t launch_shower_warp(const DevParams&, const DevEvents&, const LearnedCfg&, uint64_t, uint64_t, int, int,
                                int, int, unsigned long long*, cudaStream_t);
+cudaError_t launch_shower_wave(const DevParams&, const DevEvents&, const WorkSet&, const WaveSet&, const LearnedCfg&,
+                               uint64_t, uint64_t, int, int, int, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
                                const HistSet&, double*, double*, int, cudaStream_t);
 }  // namespace gaps
@@ -42,6 +44,9 @@ struct gaps_ctx {
   int q_independent = 0;     // every Q^2 column of the grid is identical
   void* d_work = nullptr;    // mixed-precision working set
   size_t work_bytes = 0;
+  void* d_wave = nullptr;    // wavefront schedule: working set with one lane per event, then its state
+  size_t wave_bytes = 0;
+  uint64_t wave_cap = 0;
   float* d_mlp = nullptr;    // learned-proposal network (FP32 parameters)
   void* d_mlp_image = nullptr;  // its BF16 weight image for the shower
   int learned = 0;
@@ -130,12 +135,16 @@ int validate_config(const gaps_config& c) {
   if (c.process == GAPS_PP_Z_NLO && !(c.p_s > 0.0 && c.p_s < 1.0)) return GAPS_ERR_INVALID_ARG;
   if (c.process != GAPS_EE_QQ && !c.pdf_grid) return GAPS_ERR_INVALID_ARG;
   if (c.block_size < 0 || c.block_size > 1024 || (c.block_size % 32) != 0) return GAPS_ERR_INVALID_ARG;
-  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT && c.schedule != GAPS_SCHED_WARP)
+  if (c.schedule != GAPS_SCHED_PER_EVENT && c.schedule != GAPS_SCHED_PERSISTENT && c.schedule != GAPS_SCHED_WARP &&
+      c.schedule != GAPS_SCHED_WAVE)
     return GAPS_ERR_INVALID_ARG;
-  if (c.schedule == GAPS_SCHED_WARP && c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  if ((c.schedule == GAPS_SCHED_WARP || c.schedule == GAPS_SCHED_WAVE) && c.precision != GAPS_MIXED)
+    return GAPS_ERR_INVALID_ARG;
+  if (c.wave_passes < 0 || c.wave_passes > 4096) return GAPS_ERR_INVALID_ARG;
   if (c.trial_mode != GAPS_TRIALS_REDRAW && c.trial_mode != GAPS_TRIALS_KEEP && c.trial_mode != GAPS_TRIALS_SELECT)
     return GAPS_ERR_INVALID_ARG;
-  if (c.trial_mode != GAPS_TRIALS_REDRAW && (c.precision != GAPS_MIXED || c.schedule != GAPS_SCHED_PERSISTENT))
+  if (c.trial_mode != GAPS_TRIALS_REDRAW &&
+      (c.precision != GAPS_MIXED || (c.schedule != GAPS_SCHED_PERSISTENT && c.schedule != GAPS_SCHED_WAVE)))
     return GAPS_ERR_INVALID_ARG;
   if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return GAPS_ERR_INVALID_ARG;
   if (c.refill_period < 0 || c.refill_period > 1000000) return GAPS_ERR_INVALID_ARG;
@@ -348,6 +357,48 @@ int ensure_workset(gaps_ctx* ctx, int& blocks, int& bs, WorkSet& W) {
   return GAPS_OK;
 }
 
+// working set and state of the wavefront schedule for `cap` events
+// (allocated on first use, grown when a larger capacity comes)
+constexpr int kWavePassesDefault = 24;
+constexpr int kWaveBudget = 512;  // veto cycles of one event in one pass
+int ensure_wave(gaps_ctx* ctx, uint64_t cap, WorkSet& W, WaveSet& V) {
+  const int nmax = ctx->cfg.nmax_partons;
+  // the kernels index the working set with unsigned 32-bit element offsets
+  if (cap * 4 * (uint64_t)nmax >= ((uint64_t)1 << 32) || cap >= ((uint64_t)1 << 31)) return GAPS_ERR_INVALID_ARG;
+  const size_t wb = (workset_bytes((int)cap, nmax) + 255) / 256 * 256;
+  const size_t need = wb + wave_state_bytes(cap);
+  if (need > ctx->wave_bytes || cap > ctx->wave_cap) {
+    if (ctx->d_wave) cudaFree(ctx->d_wave);
+    ctx->d_wave = nullptr;
+    ctx->wave_bytes = 0;
+    ctx->wave_cap = 0;
+    if (cudaMalloc(&ctx->d_wave, need) != cudaSuccess) {
+      cudaGetLastError();
+      return GAPS_ERR_CUDA;
+    }
+    ctx->wave_bytes = need;
+    ctx->wave_cap = cap;
+  }
+  workset_carve(ctx->d_wave, (int)cap, nmax, W);
+  wave_state_carve((char*)ctx->d_wave + wb, cap, V);
+  return GAPS_OK;
+}
+
+int shower_wave(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,
+                void* stream) {
+  const gaps_config& c = ctx->cfg;
+  WorkSet W;
+  WaveSet V;
+  const int rc = ensure_wave(ctx, ev->capacity, W, V);
+  if (rc != GAPS_OK) return rc;
+  const int bs = c.block_size > 0 ? c.block_size : 128;
+  const int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
+  const int passes = c.wave_passes > 0 ? c.wave_passes : kWavePassesDefault;
+  return cuda_fail(launch_shower_wave(ctx->P, dev_events(ev), W, V, Lc, first_event, n, passes, kWaveBudget,
+                                      ctx->n_sm * per_sm, bs, ctx->n_sm, c.refill_period, c.emit_batch,
+                                      ctx->q_independent, (cudaStream_t)stream));
+}
+
 int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,
                  void* stream) {
   const gaps_config& c = ctx->cfg;
@@ -381,6 +432,7 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
                                           per_sm, ctx->q_independent, ctx->d_counters + C_NCOUNTERS,
                                           (cudaStream_t)stream));
     }
+    if (c.schedule == GAPS_SCHED_WAVE) return shower_wave(ctx, first_event, n, ev, Lc, stream);
     return shower_mixed(ctx, first_event, n, ev, Lc, stream);
   }
   int bs = c.block_size > 0 ? c.block_size : 128;
@@ -467,10 +519,16 @@ int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_eve
   const uint64_t cap = ev->capacity;
   if (!events_ok(ctx, ev, n < cap ? n : cap)) return GAPS_ERR_INVALID_ARG;
   // everything the launches need is allocated before the capture
-  if (ctx->cfg.precision == GAPS_MIXED && ctx->cfg.schedule != GAPS_SCHED_WARP) {
+  if (ctx->cfg.precision == GAPS_MIXED && ctx->cfg.schedule == GAPS_SCHED_PERSISTENT) {
     int blocks, bs;
     WorkSet W;
     const int rc = ensure_workset(ctx, blocks, bs, W);
+    if (rc != GAPS_OK) return rc;
+  }
+  if (ctx->cfg.precision == GAPS_MIXED && ctx->cfg.schedule == GAPS_SCHED_WAVE) {
+    WorkSet W;
+    WaveSet V;
+    const int rc = ensure_wave(ctx, cap, W, V);
     if (rc != GAPS_OK) return rc;
   }
   if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -581,6 +639,7 @@ void gaps_destroy(gaps_ctx* ctx) {
   if (ctx->d_tables) cudaFree(ctx->d_tables);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->d_work) cudaFree(ctx->d_work);
+  if (ctx->d_wave) cudaFree(ctx->d_wave);
   if (ctx->d_mlp) cudaFree(ctx->d_mlp);
   if (ctx->d_mlp_image) cudaFree(ctx->d_mlp_image);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);

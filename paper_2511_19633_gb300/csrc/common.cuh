@@ -64,6 +64,30 @@ struct WorkSet {
   int lanes;
 };
 
+// State of the wavefront schedule (GAPS_SCHED_WAVE): per event of a chunk,
+// structure of arrays in library-owned device memory, beside a working set
+// (WorkSet) with one lane per event.
+struct WaveSet {
+  float* lnT;               // [cap] ln of the current evolution scale
+  int* n;                   // [cap] partons in the event
+  int* n_emit;              // [cap] accepted emissions
+  int* status;              // [cap] GAPS_STATUS_* or an error code
+  int* steps;               // [cap] veto cycles so far
+  int* flags;               // [cap] bit 0: learned bounds active; bit 1: write the record
+                            // back; bit 2: write the status back only; bits 8..15: mix row
+  int* keep;                // [cap] ends that may keep their trials at the next rebuild (-1: none)
+  double* eta;              // [2][cap] momentum fractions of slots 0 and 1
+  uint64_t* draw;           // [cap] next Philox block of the event's stream
+  unsigned char* pend;      // [cap][kWavePendBytes] the parked emission of the pass
+  uint32_t* list;           // [4][cap] live events of even / odd passes, emissions, rebuilds
+  unsigned long long* ctl;  // [8] lengths of the four lists, work counter of the veto pass
+  uint64_t cap;
+};
+constexpr int kWavePendBytes = 64;
+enum WaveList { WL_LIVE0 = 0, WL_LIVE1 = 1, WL_EMIT = 2, WL_REBUILD = 3, WL_GRAB = 4, WL_NCTL = 8 };
+size_t wave_state_bytes(uint64_t cap);
+void wave_state_carve(void* base, uint64_t cap, WaveSet& V);
+
 // learned initial-state proposal and sample collection of one launch
 struct LearnedCfg {
   int learned;                    // use the learned bin heights

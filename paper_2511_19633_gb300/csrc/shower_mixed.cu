@@ -77,6 +77,11 @@ struct MixedCtx {
   int emit_batch;      // build parked emissions once this many lanes of a warp wait
   int emit_wait;       // ... or after this many cycles
   float lnTc, asOver2pi, lxminf, dlxf, lqminf, dlqf;
+  // wavefront schedule: per-event state, parity of the pass (its live list),
+  // veto cycles an event may take in one pass
+  WaveSet V;
+  int wave_par;
+  int wave_budget;
 };
 
 __device__ __forceinline__ float u24(uint32_t w) { return ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f); }
@@ -213,19 +218,25 @@ __device__ __forceinline__ float shape_val32(int sh, float coef, float z, float 
 // Lane-major: each lane's event is contiguous (a slot's four momentum
 // components in 32 bytes, the end table in 2 nmax x 16 bytes), so the trial
 // loop walks its own cache lines and the cooperative rebuild reads one
-// event's lines. 32-bit element indices: lanes x 4 nmax < 2^31 (checked by
-// the launcher).
+// event's lines. Unsigned 32-bit element indices: lanes x 4 nmax < 2^32
+// (checked by the launcher).
 struct WS {
   const WorkSet& W;
   int lane, nmax;
   __device__ __forceinline__ double& P(int mu, int slot) const {
-    return W.p[(unsigned)((lane * nmax + slot) * 4 + mu)];
+    return W.p[((unsigned)lane * (unsigned)nmax + (unsigned)slot) * 4u + (unsigned)mu];
   }
-  __device__ __forceinline__ uint32_t& T(int slot) const { return W.tag[(unsigned)(lane * nmax + slot)]; }
-  __device__ __forceinline__ float4& End(int q) const { return W.end[(unsigned)(lane * 2 * nmax + q)]; }
+  __device__ __forceinline__ uint32_t& T(int slot) const {
+    return W.tag[(unsigned)lane * (unsigned)nmax + (unsigned)slot];
+  }
+  __device__ __forceinline__ float4& End(int q) const {
+    return W.end[(unsigned)lane * (unsigned)(2 * nmax) + (unsigned)q];
+  }
   // kept trials of end q: {ln t, R_z} of channel 0, then of channel 1; a NaN
   // ln t of channel 0 marks an end whose channels draw in the next cycle
-  __device__ __forceinline__ float4& Trial(int q) const { return W.trial[(unsigned)(lane * 2 * nmax + q)]; }
+  __device__ __forceinline__ float4& Trial(int q) const {
+    return W.trial[(unsigned)lane * (unsigned)(2 * nmax) + (unsigned)q];
+  }
   static constexpr bool kTrials = true;
 };
 
@@ -667,8 +678,7 @@ __device__ __forceinline__ bool ii_map_mixed(double r, double z, double omz, dou
 // colour update; the warp then rebuilds the event's end table cooperatively.
 // Kept out of line: it runs on the parked lanes of a warp only.
 template <class W>
-__device__ __noinline__ bool emit(const MixedCtx& M, const SmemPdf& S, const W& w, Lane& L,
-                                  const Emission& em) {
+__device__ __noinline__ bool emit(const MixedCtx& M, const W& w, Lane& L, const Emission& em) {
   const int bi = em.bi, k = em.k, bside = em.bside, ch = em.ch, type = em.type;
   const int new_fl_i = em.new_fl_i, fl_j = em.fl_j;
   const float z = em.z, omz = em.omz, tw = em.tw;
@@ -787,6 +797,8 @@ __device__ __noinline__ bool emit(const MixedCtx& M, const SmemPdf& S, const W& 
   L.n_emit += 1;
   return true;
 }
+
+static_assert(sizeof(Emission) <= kWavePendBytes, "parked emission exceeds its slot");
 
 struct Counters32 {
   unsigned long long steps = 0, trials = 0, isr_trials = 0, vetoes = 0, accepts = 0, violations = 0;
@@ -1126,10 +1138,12 @@ __device__ __noinline__ void load_event(const MixedCtx& M, const WS& w, const Le
   }
 }
 
-__device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const Lane& L) {
+// with_record: the event's partons were loaded into the working set (an event
+// that was not active when loaded only has its scalars written back)
+__device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const Lane& L, bool with_record = true) {
   const DevEvents& E = M.E;
   const uint64_t e = L.ev;
-  if (L.n >= 2 && L.n <= M.P.nmax) {
+  if (with_record && L.n >= 2 && L.n <= M.P.nmax) {
     for (int s = 0; s < L.n; ++s) {
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) E.P(mu, s, e) = w.P(mu, s);
@@ -1148,32 +1162,33 @@ __device__ __noinline__ void store_event(const MixedCtx& M, const WS& w, const L
   E.draw[e] = L.draw;
 }
 
-// MINB sets the register tier: 256-thread blocks x MINB per SM (128, 80 or
-// 64 registers per thread)
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constant__ MixedCtx M) {
-  __shared__ SmemPdf S;
-  // learned proposal only (dynamic size 0 otherwise): per warp 64 rows of
-  // input features and 64 outputs, the height decode table and the height
-  // codes; the network's weight image stays in global memory (read through L1)
-  extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
-  // per warp: the tags of the event being rebuilt, then (learned proposal)
-  // staging and heights
-  uint32_t* tag_stage = reinterpret_cast<uint32_t*>(dyn_lane_smem);
-  unsigned char* learned_smem = dyn_lane_smem + tag_stage_bytes(blockDim.x >> 5, M.P.nmax);
-  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
-  float(*stage)[64][4] = reinterpret_cast<float(*)[64][4]>(learned_smem);
-  float(*ustage)[64] = reinterpret_cast<float(*)[64]>(learned_smem + (blockDim.x >> 5) * 64 * 4 * sizeof(float));
+// Shared memory of the mixed-precision kernels besides the PDF tables: per
+// warp the tags of the event being rebuilt and, with the learned proposal, 64
+// rows of network inputs and outputs, then the height decode table (dynamic
+// shared memory; the network's weight image stays in global memory, read
+// through L1).
+struct MixedSmem {
+  uint32_t* tag_stage;
+  float (*stage)[64][4];
+  float (*ustage)[64];
   LearnedSmem ls;
-  ls.code = nullptr;
-  ls.dec = nullptr;
-  ls.key = nullptr;
+};
+
+// Fills the block's PDF tables and decode table (the caller synchronises).
+__device__ __forceinline__ void mixed_prologue(const MixedCtx& M, SmemPdf& S, unsigned char* dyn, MixedSmem& D) {
+  const int nw = blockDim.x >> 5;
+  D.tag_stage = reinterpret_cast<uint32_t*>(dyn);
+  unsigned char* learned_smem = dyn + tag_stage_bytes(nw, M.P.nmax);
+  D.stage = reinterpret_cast<float(*)[64][4]>(learned_smem);
+  D.ustage = reinterpret_cast<float(*)[64]>(learned_smem + (size_t)nw * 64 * 4 * sizeof(float));
+  D.ls.code = nullptr;
+  D.ls.dec = nullptr;
+  D.ls.key = nullptr;
   if (M.Lc.learned) {
-    unsigned char* base = learned_smem + (size_t)(blockDim.x >> 5) * 64 * 5 * sizeof(float);
-    float* dec = reinterpret_cast<float*>(base);
-    ls.dec = dec;
-    ls.code = M.W.lcode;
-    ls.key = M.W.lkey;
+    float* dec = reinterpret_cast<float*>(learned_smem + (size_t)nw * 64 * 5 * sizeof(float));
+    D.ls.dec = dec;
+    D.ls.code = M.W.lcode;
+    D.ls.key = M.W.lkey;
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
@@ -1188,13 +1203,101 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
   for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
     S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
   load_rows(S, M.P);
+}
+
+// dynamic shared memory of a mixed-precision block of `block_size` threads
+__host__ __device__ constexpr size_t mixed_dyn_bytes(int block_size, int nmax, bool learned) {
+  return tag_stage_bytes(block_size / 32, nmax) +
+         (learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) : 0);
+}
+
+// ---- wavefront schedule: per-event lane state in the WaveSet arrays -------
+__device__ __forceinline__ void wave_load(const MixedCtx& M, Lane& L, uint64_t e) {
+  const WaveSet& V = M.V;
+  L.ev = e;
+  L.slot = (int)e;
+  L.n = V.n[e];
+  L.n_emit = V.n_emit[e];
+  L.status = V.status[e];
+  L.steps = V.steps[e];
+  L.eta0 = V.eta[e];
+  L.eta1 = V.eta[V.cap + e];
+  L.draw = V.draw[e];
+  L.lnT = V.lnT[e];
+  const int f = V.flags[e];
+  L.learned_ok = (f & 1) != 0;
+  L.row = (f >> 8) & 0xff;
+}
+
+__device__ __forceinline__ void wave_store(const MixedCtx& M, const Lane& L) {
+  const WaveSet& V = M.V;
+  const uint64_t e = L.ev;
+  V.n[e] = L.n;
+  V.n_emit[e] = L.n_emit;
+  V.status[e] = L.status;
+  V.steps[e] = L.steps;
+  V.eta[e] = L.eta0;
+  V.eta[V.cap + e] = L.eta1;
+  V.draw[e] = L.draw;
+  V.lnT[e] = L.lnT;
+  V.flags[e] = (V.flags[e] & ~1) | (L.learned_ok ? 1 : 0);
+}
+
+// Appends e to list `which` for every lane with `want` (one atomic per warp);
+// all 32 lanes call it.
+__device__ __forceinline__ void wave_append(const MixedCtx& M, int which, bool want, uint64_t e, int lane_id) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane_id == leader) base = atomicAdd(&M.V.ctl[which], (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (want) M.V.list[(size_t)which * M.V.cap + base + __popc(m & ((1u << lane_id) - 1u))] = (uint32_t)e;
+}
+
+// counters: warp sums, one atomic per warp and counter
+__device__ __forceinline__ void flush_counters(const MixedCtx& M, const Counters32& cnt, unsigned long long finished,
+                                               unsigned long long err_cap, unsigned long long err_iter,
+                                               unsigned long long err_num, unsigned long long lane_steps,
+                                               unsigned long long warp_steps, unsigned long long rebuilds,
+                                               unsigned long long mlp_tiles, int lane_id) {
+  unsigned long long v[14] = {finished, cnt.steps, cnt.trials, cnt.isr_trials, cnt.vetoes, cnt.accepts,
+                              cnt.violations, err_cap, err_iter, err_num, lane_steps, warp_steps, rebuilds,
+                              mlp_tiles};
+  const int idx[14] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
+                       C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES};
+#pragma unroll 1
+  for (int q = 0; q < 14; ++q) {
+    unsigned long long x = v[q];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane_id == 0 && x) atomicAdd(&M.P.counters[idx[q]], x);
+  }
+}
+
+// The persistent mixed-precision shower. MINB sets the register tier:
+// 256-thread blocks x MINB per SM (128, 80 or 64 registers per thread).
+// WAVE = false: lane g owns working-set lane g and takes events 0 .. n-1 of
+// the chunk from the work counter (records loaded and stored by the kernel).
+// WAVE = true: the wavefront schedule's final pass; the lanes take the events
+// of the live list, whose working-set lanes and end tables the wavefront
+// passes left ready, and write their state back to the WaveSet arrays.
+template <int MINB, bool WAVE>
+__global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constant__ MixedCtx M) {
+  __shared__ SmemPdf S;
+  extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
+  MixedSmem D;
+  mixed_prologue(M, S, dyn_lane_smem, D);
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  const LearnedSmem& ls = D.ls;
   __syncthreads();
 
   const int lane_id = threadIdx.x & 31;
   const int gl = blockIdx.x * blockDim.x + threadIdx.x;
-  const int warp_base = gl - lane_id;
   const int warp_id = threadIdx.x >> 5;
-  WS w{M.W, gl, M.P.nmax};
+  // the events of this launch: 0 .. n-1, or the live list of the wavefront
+  const uint32_t* live = WAVE ? M.V.list + (size_t)M.wave_par * M.V.cap : nullptr;
+  const uint64_t n_work = WAVE ? M.V.ctl[M.wave_par] : M.n;
+  unsigned long long* work = WAVE ? &M.V.ctl[WL_GRAB] : M.next;
   Lane L;
   L.slot = gl;
   L.ev = 0;
@@ -1220,17 +1323,22 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
       since_refill = 0;
       int cnt_idle = __popc(idle);
       unsigned long long base = 0;
-      if (lane_id == 0) base = atomicAdd(M.next, (unsigned long long)cnt_idle);
+      if (lane_id == 0) base = atomicAdd(work, (unsigned long long)cnt_idle);
       base = __shfl_sync(0xffffffffu, base, 0);
-      if (base >= M.n) exhausted = true;
+      if (base >= n_work) exhausted = true;
       bool loaded = false;
       if (!active) {
         int rank = __popc(idle & ((1u << lane_id) - 1u));
         uint64_t e = base + rank;
-        if (e < M.n) {
-          load_event(M, w, ls, L, e);
-          if (L.status == GAPS_STATUS_ACTIVE) active = loaded = true;
-          else { store_event(M, w, L); finished += 1; }
+        if (e < n_work) {
+          if (WAVE) {
+            wave_load(M, L, live[e]);
+            active = L.status == GAPS_STATUS_ACTIVE;
+          } else {
+            load_event(M, WS{M.W, L.slot, M.P.nmax}, ls, L, e);
+            if (L.status == GAPS_STATUS_ACTIVE) active = loaded = true;
+            else { store_event(M, WS{M.W, L.slot, M.P.nmax}, L, false); finished += 1; }
+          }
         }
       }
       // cooperative end tables of the freshly loaded events
@@ -1244,10 +1352,10 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
         const bool lok = __shfl_sync(0xffffffffu, L.learned_ok ? 1 : 0, src) != 0;
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
-        mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
-                                  WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
-                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, cache ? 0 : -1,
-                                  lane_id);
+        const int slot_src = __shfl_sync(0xffffffffu, L.slot, src);
+        mlp_tiles += rebuild_coop(M, S, mlp_s, ls, D.stage[warp_id], D.ustage[warp_id],
+                                  WS{M.W, slot_src, M.P.nmax}, D.tag_stage + warp_id * M.P.nmax, true,
+                                  slot_src, ev_src, n_src, e0, e1, row_src, lok, cache ? 0 : -1, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1275,13 +1383,13 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
           done_emit = true;
           keep = cache ? 0 : -1;
         } else {
-          done_emit = emit(M, S, w, L, pend);
+          done_emit = emit(M, WS{M.W, L.slot, M.P.nmax}, L, pend);
           if (done_emit) {
             cnt.accepts += 1;
             keep = cache ? 2 * (L.n - 1) : -1;  // the ends that existed before
           } else {
             cnt.vetoes += 1;  // the map failed: the winner's end draws again
-            if (cache) w.Trial(2 * pend.bi + pend.bside).x = __uint_as_float(0x7fc00000u);
+            if (cache) WS{M.W, L.slot, M.P.nmax}.Trial(2 * pend.bi + pend.bside).x = __uint_as_float(0x7fc00000u);
           }
         }
       }
@@ -1296,9 +1404,10 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
         const int row_src = __shfl_sync(0xffffffffu, L.row, src);
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         const int keep_src = __shfl_sync(0xffffffffu, keep, src);
-        mlp_tiles += rebuild_coop(M, S, mlp_s, ls, stage[warp_id], ustage[warp_id],
-                                  WS{M.W, warp_base + src, M.P.nmax}, tag_stage + warp_id * M.P.nmax, true,
-                                  warp_base + src, ev_src, n_src, e0, e1, row_src, lok, keep_src, lane_id);
+        const int slot_src = __shfl_sync(0xffffffffu, L.slot, src);
+        mlp_tiles += rebuild_coop(M, S, mlp_s, ls, D.stage[warp_id], D.ustage[warp_id],
+                                  WS{M.W, slot_src, M.P.nmax}, D.tag_stage + warp_id * M.P.nmax, true,
+                                  slot_src, ev_src, n_src, e0, e1, row_src, lok, keep_src, lane_id);
         rebuilds += 1;
       }
       __syncwarp();
@@ -1306,11 +1415,12 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
     lane_steps += __popc(__ballot_sync(0xffffffffu, active && !parked));
     warp_steps += 32;
     if (active && !parked) {
-      int st = step_mixed(M, S, ls, w, L, M.first + L.ev, cnt, pend, parked);
+      int st = step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked);
       if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st != GAPS_STATUS_ACTIVE) {
         L.status = st;
-        store_event(M, w, L);
+        if (WAVE) wave_store(M, L);
+        else store_event(M, WS{M.W, L.slot, M.P.nmax}, L);
         active = false;
         finished += 1;
         if (st == GAPS_ERR_CAPACITY) err_cap += 1;
@@ -1319,18 +1429,311 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
       }
     }
   }
-  // counters: warp sums, one atomic per warp and counter
-  unsigned long long v[14] = {finished, cnt.steps, cnt.trials, cnt.isr_trials, cnt.vetoes, cnt.accepts,
-                              cnt.violations, err_cap, err_iter, err_num,
-                              lane_id == 0 ? lane_steps : 0ull, lane_id == 0 ? warp_steps : 0ull,
-                              lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull};
-  const int idx[14] = {C_EVENTS, C_STEPS, C_TRIALS, C_ISR_TRIALS, C_VETOES, C_ACCEPTS, C_VIOLATIONS,
-                       C_ERR_CAP, C_ERR_ITER, C_ERR_NUM, C_LANE_STEPS, C_WARP_STEPS, C_REBUILDS, C_MLP_TILES};
-#pragma unroll 1
-  for (int q = 0; q < 14; ++q) {
-    unsigned long long x = v[q];
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane_id == 0 && x) atomicAdd(&M.P.counters[idx[q]], x);
+  flush_counters(M, cnt, finished, err_cap, err_iter, err_num, lane_id == 0 ? lane_steps : 0ull,
+                 lane_id == 0 ? warp_steps : 0ull, lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull,
+                 lane_id);
+}
+
+// ---------------------------------------------------------------------------
+// Wavefront schedule (GAPS_SCHED_WAVE). The persistent kernel above mixes
+// every phase of an event's evolution in one warp: trial scans, vetoes, FP64
+// emissions, end-table rebuilds with network tiles and refills, so the lanes
+// of a warp diverge and the code of all phases competes for the instruction
+// cache. The wavefront schedule runs the same per-event steps in passes,
+// each phase as its own kernel over a list of events (the paper's
+// kernel-per-step structure, Sec. 3, with live-event lists in place of its
+// partitioning):
+//   ends  one warp per event of the rebuild list: the cooperative end-table
+//         rebuild, with the learned proposal's network tiles;
+//   veto  persistent lanes over the live list: max-veto cycles of one event
+//         until an emission is accepted (parked), the event ends, or the pass's
+//         cycle budget is used up (the event stays live);
+//   emit  one thread per parked emission: the FP64 maps and the colour update;
+//         the event joins the next rebuild list and the next live list.
+// After the fixed number of passes the remaining live events finish in the
+// persistent kernel above (WAVE = true). Every event takes the same steps
+// with the same random numbers as in the persistent kernel, so the two
+// schedules give identical events. The working set has one lane per event of
+// the chunk (lane = event index), so no state moves between the kernels.
+// ---------------------------------------------------------------------------
+
+// Records of the chunk into the working set and the WaveSet arrays; active
+// events start the live list and the rebuild list.
+__global__ void k_wave_init(const __grid_constant__ MixedCtx M) {
+  LearnedSmem ls;
+  ls.code = M.Lc.learned ? M.W.lcode : nullptr;
+  ls.key = M.Lc.learned ? M.W.lkey : nullptr;
+  ls.dec = nullptr;
+  const int lane_id = threadIdx.x & 31;
+  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
+  unsigned long long finished = 0, err_num = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // whole warps iterate together (the appends are warp-collective)
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < M.n; b += stride) {
+    const uint64_t e = b + lane_id;
+    bool live = false;
+    if (e < M.n) {
+      Lane L;
+      L.slot = (int)e;
+      load_event(M, WS{M.W, (int)e, M.P.nmax}, ls, L, e);
+      live = L.status == GAPS_STATUS_ACTIVE;
+      // bit 1: the record was loaded and is written back; bit 2: only the
+      // status changed (a record that could not be read)
+      const int wb = live ? 2 : (L.status != M.E.status[e] ? 4 : 0);
+      M.V.flags[e] = 1 | wb | (L.row << 8);
+      M.V.keep[e] = cache ? 0 : -1;
+      wave_store(M, L);
+      if (!live) {
+        finished += 1;
+        if (L.status == GAPS_ERR_NUMERIC) err_num += 1;
+      }
+    }
+    wave_append(M, WL_LIVE0, live, e, lane_id);
+    wave_append(M, WL_REBUILD, live, e, lane_id);
+  }
+  Counters32 cnt;
+  flush_counters(M, cnt, finished, 0, 0, err_num, 0, 0, 0, 0, lane_id);
+}
+
+// The trials of the ends a rebuild marked (kept-trial scheme), drawn by the
+// warp together, one end per lane: the same Philox blocks, in the same
+// canonical order, as the first cycle's trial loop would draw them one by one
+// (each end's first counter is the event's counter plus a warp prefix sum of
+// the draws of the marked ends before it), so the events are unchanged and
+// the cycle that follows only scans. Returns the event's counter after the
+// draws (every lane).
+__device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const SmemPdf& S, const WS& w, uint64_t id,
+                                                     int n, int row, float lnT, uint64_t d, int lane_id,
+                                                     Counters32& cnt) {
+  const unsigned full = 0xffffffffu;
+  const bool pp = S.pp[row] != 0;
+  const float lnTc = S.lnTc[row];
+  const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+  const int ne = 2 * n;
+  for (int q0 = 0; q0 < ne; q0 += 32) {
+    const int q = q0 + lane_id;
+    bool marked = false;
+    float4 rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
+    int nd = 0;  // Philox blocks of this end: one per channel present
+    if (q < ne) {
+      marked = isnan(w.Trial(q).x);
+      if (marked) {
+        rec = w.End(q);
+        if (__float_as_int(rec.w) >= 0) nd = (rec.x >= 0.0f ? 1 : 0) + (rec.y >= 0.0f ? 1 : 0);
+      }
+    }
+    int inc = nd;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(full, inc, off);
+      if (lane_id >= off) inc += t;
+    }
+    const int tot = __shfl_sync(full, inc, 31);
+    if (marked) {
+      float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+      if (__float_as_int(rec.w) >= 0) {
+        uint64_t dd = d + (uint64_t)(inc - nd);
+        const float lnTmax = fminf(lnT, rec.z);
+        const bool live = lnTmax > lnTc;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float ic = c == 0 ? rec.x : rec.y;  // 1/c
+          if (ic < 0.0f) continue;                  // channel absent for this emitter
+          const uint64_t dc = dd++;
+          if (!(live && ic > 0.0f)) continue;
+          uint32_t out[4];
+          philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
+          cnt.trials += 1;
+          if (pp && q < 4) cnt.isr_trials += 1;
+          const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+          if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
+          else { tr.z = lt; tr.w = u24(out[3]); }
+        }
+      }
+      w.Trial(q) = tr;
+    }
+    d += (uint64_t)tot;
+  }
+  return d;
+}
+
+// One warp per event of the rebuild list: the end table, then (kept trials)
+// the trials of the ends it marked. Also clears, for the passes after it, the
+// lists this pass's later kernels fill.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__ MixedCtx M) {
+  __shared__ SmemPdf S;
+  extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
+  MixedSmem D;
+  mixed_prologue(M, S, dyn_lane_smem, D);
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    M.V.ctl[WL_LIVE0 + (M.wave_par ^ 1)] = 0;  // the next pass's live list
+    M.V.ctl[WL_EMIT] = 0;
+    M.V.ctl[WL_GRAB] = 0;
+  }
+  const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
+  const uint64_t count = M.V.ctl[WL_REBUILD];
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
+  unsigned long long rebuilds = 0, mlp_tiles = 0;
+  Counters32 cnt;
+  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id; i < count; i += nw) {
+    const uint64_t e = M.V.list[(size_t)WL_REBUILD * M.V.cap + i];
+    const int flags = M.V.flags[e], n = M.V.n[e], row = (flags >> 8) & 0xff;
+    const WS w{M.W, (int)e, M.P.nmax};
+    mlp_tiles += rebuild_coop(M, S, mlp_s, D.ls, D.stage[warp_id], D.ustage[warp_id], w,
+                              D.tag_stage + warp_id * M.P.nmax, true, (int)e, e, n, M.V.eta[e],
+                              M.V.eta[M.V.cap + e], row, (flags & 1) != 0, M.V.keep[e], lane_id);
+    rebuilds += 1;
+    if (cache) {
+      const uint64_t d = draw_marked_ends(M, S, w, M.first + e, n, row, M.V.lnT[e], M.V.draw[e], lane_id, cnt);
+      __syncwarp();  // every lane has read the old counter
+      if (lane_id == 0) M.V.draw[e] = d;
+    }
+  }
+  flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull,
+                 lane_id);
+}
+
+// Persistent lanes over the live list: each lane runs max-veto cycles of one
+// event until it parks an emission, ends, or uses up the pass's budget, then
+// takes the next event.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__ MixedCtx M) {
+  __shared__ SmemPdf S;
+  extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
+  MixedSmem D;
+  mixed_prologue(M, S, dyn_lane_smem, D);
+  const LearnedSmem& ls = D.ls;
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) M.V.ctl[WL_REBUILD] = 0;  // filled by this pass's emissions
+  const int lane_id = threadIdx.x & 31;
+  const uint32_t* live = M.V.list + (size_t)M.wave_par * M.V.cap;
+  const uint64_t n_work = M.V.ctl[M.wave_par];
+  const int next_live = WL_LIVE0 + (M.wave_par ^ 1);
+  Lane L;
+  L.slot = 0;
+  L.ev = 0;
+  L.n = 0;
+  L.row = 0;
+  L.learned_ok = false;
+  bool active = false, exhausted = false, parked = false;
+  int cycles = 0, since_refill = M.period;
+  Emission pend;
+  Counters32 cnt;
+  unsigned long long finished = 0, err_cap = 0, err_iter = 0, err_num = 0, lane_steps = 0, warp_steps = 0;
+  while (true) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (idle && !exhausted && since_refill >= M.period) {
+      since_refill = 0;
+      unsigned long long base = 0;
+      if (lane_id == 0) base = atomicAdd(&M.V.ctl[WL_GRAB], (unsigned long long)__popc(idle));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= n_work) exhausted = true;
+      if (!active) {
+        const uint64_t i = base + __popc(idle & ((1u << lane_id) - 1u));
+        if (i < n_work) {
+          wave_load(M, L, live[i]);
+          active = true;
+          cycles = 0;
+        }
+      }
+    }
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (act == 0) {
+      if (exhausted) break;
+      since_refill = M.period;
+      continue;
+    }
+    since_refill += 1;
+    lane_steps += __popc(act);
+    warp_steps += 32;
+    bool to_emit = false, to_next = false;
+    if (active) {
+      int st = step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked);
+      if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
+      ++cycles;
+      if (st != GAPS_STATUS_ACTIVE) {
+        L.status = st;
+        finished += 1;
+        if (st == GAPS_ERR_CAPACITY) err_cap += 1;
+        else if (st == GAPS_ERR_ITER_CAP) err_iter += 1;
+        else if (st == GAPS_ERR_NUMERIC) err_num += 1;
+        wave_store(M, L);
+        active = false;
+      } else if (parked) {
+        // the emission (or the plain rebuild after a learned-bound
+        // violation) is built by the emission pass
+        parked = false;
+        *reinterpret_cast<Emission*>(M.V.pend + L.ev * kWavePendBytes) = pend;
+        wave_store(M, L);
+        to_emit = true;
+        active = false;
+      } else if (cycles >= M.wave_budget) {
+        wave_store(M, L);  // continues in the next pass
+        to_next = true;
+        active = false;
+      }
+    }
+    wave_append(M, WL_EMIT, to_emit, L.ev, lane_id);
+    wave_append(M, next_live, to_next, L.ev, lane_id);
+  }
+  flush_counters(M, cnt, finished, err_cap, err_iter, err_num, lane_id == 0 ? lane_steps : 0ull,
+                 lane_id == 0 ? warp_steps : 0ull, 0, 0, lane_id);
+}
+
+// One thread per parked emission: the FP64 kinematics and colours of the
+// persistent kernel's flush; the event joins the next live list and, when its
+// end table changed, the rebuild list.
+__global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ MixedCtx M) {
+  const int lane_id = threadIdx.x & 31;
+  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
+  const uint64_t count = M.V.ctl[WL_EMIT];
+  const int next_live = WL_LIVE0 + (M.wave_par ^ 1);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  Counters32 cnt;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < count; b += stride) {
+    const uint64_t i = b + lane_id;
+    bool have = i < count, rebuild = false;
+    uint64_t e = 0;
+    if (have) {
+      e = M.V.list[(size_t)WL_EMIT * M.V.cap + i];
+      Lane L;
+      wave_load(M, L, e);
+      const Emission em = *reinterpret_cast<const Emission*>(M.V.pend + e * kWavePendBytes);
+      int keep = -1;
+      if (em.kind == 1) {
+        rebuild = true;
+        keep = cache ? 0 : -1;
+      } else if (emit(M, WS{M.W, (int)e, M.P.nmax}, L, em)) {
+        cnt.accepts += 1;
+        rebuild = true;
+        keep = cache ? 2 * (L.n - 1) : -1;
+      } else {
+        cnt.vetoes += 1;  // the map failed: the winner's end draws again
+        if (cache) WS{M.W, (int)e, M.P.nmax}.Trial(2 * em.bi + em.bside).x = __uint_as_float(0x7fc00000u);
+      }
+      M.V.keep[e] = keep;
+      wave_store(M, L);
+    }
+    wave_append(M, WL_REBUILD, rebuild, e, lane_id);
+    wave_append(M, next_live, have, e, lane_id);
+  }
+  flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, 0, 0, lane_id);
+}
+
+// The working set and the WaveSet arrays back into the caller's records.
+__global__ void k_wave_final(const __grid_constant__ MixedCtx M) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M.n; e += stride) {
+    const int f = M.V.flags[e];
+    if (!(f & 6)) continue;
+    Lane L;
+    wave_load(M, L, e);
+    store_event(M, WS{M.W, (int)e, M.P.nmax}, L, (f & 2) != 0);
   }
 }
 
@@ -1569,7 +1972,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(const __grid_constan
         if (pend.kind == 1) {
           done_emit = true;  // plain rebuild after a learned-bound violation
         } else {
-          done_emit = emit(M, S, w, L, pend);
+          done_emit = emit(M, w, L, pend);
           if (done_emit) cnt.accepts += 1;
           else cnt.vetoes += 1;
         }
@@ -1715,13 +2118,26 @@ constexpr int kWarpKernelMaxDyn = 200 * 1024;
 // Opt-in for the dynamic shared memory of the mixed-precision kernels (the
 // learned proposal's, up to 64 KB; the warp-per-event kernel's events, up to
 // 200 KB) on the current device; called when a context is created.
+template <class K>
+cudaError_t opt_in(K kernel, int bytes, cudaError_t e) {
+  return e == cudaSuccess ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) : e;
+}
+
 cudaError_t mixed_kernels_init() {
   const int bytes = 64 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_shower_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_shower_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_shower_mixed<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaSuccess;
+  e = opt_in(k_shower_mixed<2, false>, bytes, e);
+  e = opt_in(k_shower_mixed<3, false>, bytes, e);
+  e = opt_in(k_shower_mixed<4, false>, bytes, e);
+  e = opt_in(k_shower_mixed<2, true>, bytes, e);
+  e = opt_in(k_shower_mixed<3, true>, bytes, e);
+  e = opt_in(k_shower_mixed<4, true>, bytes, e);
+  e = opt_in(k_wave_ends<2>, bytes, e);
+  e = opt_in(k_wave_ends<3>, bytes, e);
+  e = opt_in(k_wave_ends<4>, bytes, e);
+  e = opt_in(k_wave_veto<2>, bytes, e);
+  e = opt_in(k_wave_veto<3>, bytes, e);
+  e = opt_in(k_wave_veto<4>, bytes, e);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_shower_warp<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpKernelMaxDyn);
   if (e == cudaSuccess)
@@ -1763,11 +2179,9 @@ cudaError_t launch_shower_warp(const DevParams& P, const DevEvents& E, const Lea
   return cudaGetLastError();
 }
 
-cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, const LearnedCfg& Lc,
-                                uint64_t first, uint64_t n, int blocks, int block_size, int sm_count, int period,
-                                int emit_batch, int q_independent, unsigned long long* next,
-                                cudaStream_t stream) {
-  if (n == 0) return cudaSuccess;
+namespace {
+MixedCtx mixed_ctx(const DevParams& P, const DevEvents& E, const WorkSet& W, const LearnedCfg& Lc, uint64_t first,
+                   uint64_t n, int period, int emit_batch, int q_independent, unsigned long long* next) {
   MixedCtx M;
   M.P = P; M.E = E; M.W = W; M.Lc = Lc; M.first = first; M.n = n; M.next = next;
   M.q_independent = q_independent;
@@ -1777,17 +2191,104 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   M.lnTc = (float)gm_log(P.t_cut);
   M.asOver2pi = (float)(P.as_over / (2.0 * kPi));
   M.lxminf = (float)P.lxmin; M.dlxf = (float)P.dlx; M.lqminf = (float)P.lqmin; M.dlqf = (float)P.dlq;
+  M.V = WaveSet{};
+  M.wave_par = 0;
+  M.wave_budget = 0;
+  return M;
+}
+
+// register tier of a launch: the resident threads per SM it asks for
+int mixed_tier(int blocks, int block_size, int sm_count) {
+  const int threads_per_sm = blocks * block_size / max(1, sm_count);
+  return threads_per_sm <= 512 ? 2 : (threads_per_sm <= 768 ? 3 : 4);
+}
+
+template <bool WAVE>
+void launch_persistent(const MixedCtx& M, int tier, int blocks, int block_size, size_t dyn, cudaStream_t stream) {
+  if (tier == 2) k_shower_mixed<2, WAVE><<<blocks, block_size, dyn, stream>>>(M);
+  else if (tier == 3) k_shower_mixed<3, WAVE><<<blocks, block_size, dyn, stream>>>(M);
+  else k_shower_mixed<4, WAVE><<<blocks, block_size, dyn, stream>>>(M);
+}
+}  // namespace
+
+cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const WorkSet& W, const LearnedCfg& Lc,
+                                uint64_t first, uint64_t n, int blocks, int block_size, int sm_count, int period,
+                                int emit_batch, int q_independent, unsigned long long* next,
+                                cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const MixedCtx M = mixed_ctx(P, E, W, Lc, first, n, period, emit_batch, q_independent, next);
   cudaError_t err = cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream);
   if (err != cudaSuccess) return err;
   // learned proposal: per-warp staging, height decode table, 64 bytes of
   // height codes per lane
-  const size_t dyn = tag_stage_bytes(block_size / 32, P.nmax) +
-                     (Lc.learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) : 0);
-  // the register tier follows the resident threads the launch asks for
-  const int threads_per_sm = blocks * block_size / max(1, sm_count);
-  if (threads_per_sm <= 512) k_shower_mixed<2><<<blocks, block_size, dyn, stream>>>(M);
-  else if (threads_per_sm <= 768) k_shower_mixed<3><<<blocks, block_size, dyn, stream>>>(M);
-  else k_shower_mixed<4><<<blocks, block_size, dyn, stream>>>(M);
+  const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0);
+  launch_persistent<false>(M, mixed_tier(blocks, block_size, sm_count), blocks, block_size, dyn, stream);
+  return cudaGetLastError();
+}
+
+// Per-event state of the wavefront schedule for `cap` events: sizes and
+// carve (every array 256-byte aligned).
+namespace {
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+size_t wave_state_bytes(uint64_t cap) {
+  return al256(cap * sizeof(float)) + 6 * al256(cap * sizeof(int)) + al256(2 * cap * sizeof(double)) +
+         al256(cap * sizeof(uint64_t)) + al256(cap * (size_t)kWavePendBytes) + al256(4 * cap * sizeof(uint32_t)) +
+         al256(WL_NCTL * sizeof(unsigned long long));
+}
+
+void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
+  char* p = (char*)base;
+  auto take = [&](size_t b) { char* q = p; p += al256(b); return q; };
+  V.cap = cap;
+  V.lnT = (float*)take(cap * sizeof(float));
+  V.n = (int*)take(cap * sizeof(int));
+  V.n_emit = (int*)take(cap * sizeof(int));
+  V.status = (int*)take(cap * sizeof(int));
+  V.steps = (int*)take(cap * sizeof(int));
+  V.flags = (int*)take(cap * sizeof(int));
+  V.keep = (int*)take(cap * sizeof(int));
+  V.eta = (double*)take(2 * cap * sizeof(double));
+  V.draw = (uint64_t*)take(cap * sizeof(uint64_t));
+  V.pend = (unsigned char*)take(cap * (size_t)kWavePendBytes);
+  V.list = (uint32_t*)take(4 * cap * sizeof(uint32_t));
+  V.ctl = (unsigned long long*)take(WL_NCTL * sizeof(unsigned long long));
+}
+
+// The wavefront schedule over events first .. first + n - 1 (records 0 .. n-1):
+// `passes` passes of (ends, veto, emit), the last rebuilds, the persistent
+// kernel over the events still live, and the records written back. W has one
+// lane per event (W.lanes >= n), V is carved for at least n events.
+cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const WorkSet& W, const WaveSet& V,
+                               const LearnedCfg& Lc, uint64_t first, uint64_t n, int passes, int budget,
+                               int blocks, int block_size, int sm_count, int period, int emit_batch,
+                               int q_independent, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  if (n > V.cap || (uint64_t)W.lanes < n || passes < 0 || budget < 1) return cudaErrorInvalidValue;
+  MixedCtx M = mixed_ctx(P, E, W, Lc, first, n, period, emit_batch, q_independent, nullptr);
+  M.V = V;
+  M.wave_budget = budget;
+  cudaError_t err = cudaMemsetAsync(V.ctl, 0, WL_NCTL * sizeof(unsigned long long), stream);
+  if (err != cudaSuccess) return err;
+  const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0);
+  const int tier = mixed_tier(blocks, block_size, sm_count);
+  // grid-stride kernels: enough warps to cover the SMs several times
+  const int flat_blocks = sm_count * 16;
+  k_wave_init<<<flat_blocks, 128, 0, stream>>>(M);
+  for (int w = 0; w <= passes; ++w) {
+    M.wave_par = w & 1;
+    if (tier == 2) k_wave_ends<2><<<blocks, block_size, dyn, stream>>>(M);
+    else if (tier == 3) k_wave_ends<3><<<blocks, block_size, dyn, stream>>>(M);
+    else k_wave_ends<4><<<blocks, block_size, dyn, stream>>>(M);
+    if (w == passes) break;  // the last rebuilds, then the persistent kernel
+    if (tier == 2) k_wave_veto<2><<<blocks, block_size, dyn, stream>>>(M);
+    else if (tier == 3) k_wave_veto<3><<<blocks, block_size, dyn, stream>>>(M);
+    else k_wave_veto<4><<<blocks, block_size, dyn, stream>>>(M);
+    k_wave_emit<<<flat_blocks, 128, 0, stream>>>(M);
+  }
+  launch_persistent<true>(M, tier, blocks, block_size, dyn, stream);
+  k_wave_final<<<flat_blocks, 128, 0, stream>>>(M);
   return cudaGetLastError();
 }
 

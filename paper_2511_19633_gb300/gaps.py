@@ -26,7 +26,7 @@ GAPS_ERR_NO_DEVICE = -6
 
 GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO, GAPS_PP_LL = 0, 1, 2, 3
 GAPS_FP64, GAPS_MIXED = 0, 1
-GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT, GAPS_SCHED_WARP = 0, 1, 2
+GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT, GAPS_SCHED_WARP, GAPS_SCHED_WAVE = 0, 1, 2, 3
 GAPS_TRIALS_REDRAW, GAPS_TRIALS_KEEP, GAPS_TRIALS_SELECT = 0, 1, 2
 GAPS_STATUS_ACTIVE, GAPS_STATUS_DONE = 0, 1
 GAPS_NOBS, GAPS_NHIST, GAPS_HIST_BINS = 8, 6, 66
@@ -50,6 +50,7 @@ class GapsConfig(ctypes.Structure):
         ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
         ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_mode", ctypes.c_int),
         ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double), ("max_cycles", ctypes.c_int),
+        ("wave_passes", ctypes.c_int),
     ]
 
 
@@ -366,24 +367,26 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
                 refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None,
-                mll=(66.0, 116.0), max_cycles: int = 0) -> GapsConfig:
+                mll=(66.0, 116.0), max_cycles: int = 0, wave_passes: int = 0) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied). mix: optional list of
     (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
     process, sqrt_s and t_cut. trial_mode: GAPS_TRIALS_*; None = KEEP for
     GAPS_MIXED with the persistent lane schedule, REDRAW otherwise. mll: the
     dilepton mass window of GAPS_PP_LL (GeV). max_cycles: veto cycles per event
-    before GAPS_ERR_ITER_CAP (0 = the library default)."""
+    before GAPS_ERR_ITER_CAP (0 = the library default). wave_passes: passes of
+    the wavefront schedule (0 = the library default)."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
                    block_size, schedule, blocks_per_sm, refill_period, emit_batch)
-    # kept trials by default where they apply (mixed precision, lane schedule)
+    # kept trials by default where they apply (mixed precision, lane or wavefront schedule)
     if trial_mode is None:
-        trial_mode = (GAPS_TRIALS_KEEP if precision == GAPS_MIXED and schedule == GAPS_SCHED_PERSISTENT
-                      else GAPS_TRIALS_REDRAW)
+        trial_mode = (GAPS_TRIALS_KEEP if precision == GAPS_MIXED
+                      and schedule in (GAPS_SCHED_PERSISTENT, GAPS_SCHED_WAVE) else GAPS_TRIALS_REDRAW)
     c.trial_mode = int(trial_mode)
     c.mll_lo, c.mll_hi = float(mll[0]), float(mll[1])
     c.max_cycles = int(max_cycles)
+    c.wave_passes = int(wave_passes)
     if mix:
         if len(mix) > GAPS_MAX_MIX:
             raise ValueError("at most %d rows" % GAPS_MAX_MIX)

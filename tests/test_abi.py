@@ -54,7 +54,8 @@ def test_error_strings(lib):
 @pytest.mark.parametrize("field,value", [("process", 7), ("sqrt_s", -1.0), ("t_cut", 0.1),
                                          ("nmax_partons", 2), ("nmax_partons", 1000), ("nf", 9),
                                          ("block_size", 48), ("p_s", 1.5), ("schedule", 5),
-                                         ("alpha_s_mz", 2.0)])
+                                         ("alpha_s_mz", 2.0), ("schedule", 3), ("wave_passes", -1),
+                                         ("wave_passes", 5000), ("max_cycles", -5)])
 def test_invalid_configuration_is_rejected_without_a_device(lib, pdf, field, value):
     from paper_2511_19633_gb300 import gaps as G
     cfg = G.make_config(2, 13600.0, pdf_grid=pdf)
