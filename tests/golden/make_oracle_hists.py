@@ -32,7 +32,7 @@ BINNING = {
 }
 NBINS = 66
 
-# name: (process, sqrt_s, events, t_cut)
+# name: (process, sqrt_s, events, t_cut[, seed]); seed 2 unless given
 WORKLOADS = {
     "ee91": (0, 91.2, 10_000_000, 1.0),
     "ee500": (0, 500.0, 10_000_000, 1.0),
@@ -41,8 +41,12 @@ WORKLOADS = {
     # pp -> gamma*/Z -> e- e+, LO, dilepton mass 66-116 GeV
     "pp_ll": (3, 13600.0, 10_000_000, 1.0),
     # the e+e- rows of the mixed batch (their own cutoffs)
-    "ee91_tc0.5": (0, 91.2, 1_000_000, 0.5),
-    "ee500_tc4": (0, 500.0, 1_000_000, 4.0),
+    "ee91_tc0.5": (0, 91.2, 10_000_000, 0.5),
+    "ee500_tc4": (0, 500.0, 10_000_000, 4.0),
+    # the same seed and events as the GPU runs of the precision comparison
+    # (events 0 .. 1e6 - 1 of seed 1): the mixed-precision path's error per
+    # observable on the same events
+    "pp_nlo_seed1": (2, 13600.0, 1_000_000, 1.0, 1),
 }
 SEED = 2
 
@@ -75,12 +79,13 @@ def fill(hsum, hsum2, obs, w, family):
 def make(name: str, threads: int, n_override: int | None = None) -> dict:
     from oracle import oracle as O
     from paper_2511_19633_gb300 import inputs
-    process, sqrt_s, n, t_cut = WORKLOADS[name]
+    process, sqrt_s, n, t_cut = WORKLOADS[name][:4]
+    seed = WORKLOADS[name][4] if len(WORKLOADS[name]) > 4 else SEED
     if n_override:
         n = n_override
     pdf = inputs.synthetic_pdf_grid()
     family = "ee" if process == 0 else "pp"
-    st = O.Settings(process=process, sqrt_s=sqrt_s, t_cut=t_cut, nmax=128, seed=SEED)
+    st = O.Settings(process=process, sqrt_s=sqrt_s, t_cut=t_cut, nmax=128, seed=seed)
     hsum = np.zeros((6, NBINS))
     hsum2 = np.zeros((6, NBINS))
     counters = np.zeros(6, dtype=np.int64)
@@ -94,7 +99,7 @@ def make(name: str, threads: int, n_override: int | None = None) -> dict:
         bad += int((~done).sum())
         fill(hsum, hsum2, r["obs"][done], r["weight"][done], family)
         counters += r["counters"].astype(np.int64).sum(0)
-    return {"workload": name, "process": process, "sqrt_s": sqrt_s, "t_cut": t_cut, "events": n, "seed": SEED,
+    return {"workload": name, "process": process, "sqrt_s": sqrt_s, "t_cut": t_cut, "events": n, "seed": seed,
             "not_done": bad, "binning": BINNING[family], "sumw": hsum.tolist(), "sumw2": hsum2.tolist(),
             "oracle_counters": dict(zip(("steps", "trials", "isr_trials", "vetoes", "accepts",
                                          "violations"), counters.tolist())),
