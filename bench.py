@@ -361,8 +361,9 @@ def run_ours(args, ws, rank, local):
         learned = (res["params"], res["log_margins"])
         learned_info = {"train_seconds": time.perf_counter() - t0, "states": res["states"],
                         "training_rows": res["rows"], "holdout_states": res["holdout_states"],
-                        "mean_bin_height": res["mean_bin_height"], "loss_last": res["loss_last"],
-                        "cells_calibrated": res["cells_seen"]}
+                        "mean_bin_height": res["mean_bin_height"], "loss_first": res["loss_first"],
+                        "loss_last": res["loss_last"], "cells_calibrated": res["cells_calibrated"],
+                        "fit_rmse": res["fit_rmse"], "pipeline": "gaps_train_learned_proposal (one C-ABI call)"}
 
     shape = {"block_size": args.block, "blocks_per_sm": args.bps, "refill_period": args.period,
              "emit_batch": args.emit_batch}

@@ -29,9 +29,9 @@
  *   - Device buffers are owned by the caller; the library owns its copy of
  *     the PDF grid, its bound tables, its counters and, for GAPS_MIXED, a
  *     working set of nmax partons per resident thread (allocated by the
- *     first mixed gaps_shower call; about 100 B x nmax x resident threads),
+ *     first mixed gaps_shower call; about 132 B x nmax x resident threads),
  *     or with GAPS_SCHED_WAVE one per event of ev->capacity (about
- *     100 B x nmax + 160 B per event).
+ *     132 B x nmax + 160 B per event).
  */
 #ifndef GAPS_H
 #define GAPS_H
@@ -147,6 +147,8 @@ typedef struct {
                              GAPS_ERR_ITER_CAP, 0 = 200000, at most 1e9 */
     int wave_passes;      /* GAPS_SCHED_WAVE: passes before the persistent grid takes
                              the remaining live events, 0 = 24, at most 4096 */
+    int wave_cycles;      /* GAPS_SCHED_WAVE: veto cycles of one event in one pass
+                             before it waits for the next pass, 0 = 64, 1..1e6 */
 } gaps_config;
 
 /* Trial schemes (gaps_config.trial_mode). All three give the same
@@ -243,8 +245,8 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
  * The paper has no counterpart: it is the GAPS_MIXED persistent shower of
  * gaps_shower, run with 64 blocks of 128 threads and emission batch 8, with
  * every piece of scratch memory held in device arrays of the library itself:
- * a working set for at most 32 partons per event (27.3 MB), the work counter,
- * the statistics and copies of the PDF grid and its bound tables (27.5 MB in
+ * a working set for at most 32 partons per event (35.7 MB), the work counter,
+ * the statistics and copies of the PDF grid and its bound tables (35.9 MB in
  * all). Every GPU that loads the library keeps these arrays until the process
  * exits. It needs no context: `cfg` is read as in gaps_init and the caller
  * still passes the event records, written by gaps_generate_hard or an
@@ -315,6 +317,54 @@ int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states,
  * Later GAPS_MIXED showers of the context use them. params == NULL returns
  * to the plain bounds. Non-finite values give GAPS_ERR_INVALID_ARG. */
 int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* log_margins);
+
+/* The whole training pipeline of the learned proposal behind one call, on the
+ * context's device and stream (the build's own addition to the method; the
+ * paper's initial-state overestimate is a fitted PDF-ratio bound, App. A.2):
+ *   1. collect: the plain GAPS_MIXED shower of n_events events from
+ *      first_event logs initial-state colour ends (gaps_collect_isr_states),
+ *      kept with a fraction set by a pilot run of 2^14 events so that about
+ *      0.95 x capacity states are logged over the whole range;
+ *   2. the states are sorted into a canonical order (dipole type, PDF index,
+ *      eta, s), so that the network does not depend on the logging order;
+ *   3. targets (gaps_isr_targets), floored at target_floor;
+ *   4. training (gaps_mlp_train) from a Philox-seeded He initialisation:
+ *      steps/2 Adam steps at lr, steps/4 at 0.3 lr, the rest at 0.1 lr;
+ *   5. held-out states from holdout_events events at holdout_first (up to
+ *      holdout_capacity), sorted and with targets the same way;
+ *   6. calibration with the shower's BF16 inference numerics: per (class, eta
+ *      bucket, bin) cell, margin = max(target - network) over the rows of
+ *      both sets + ln(1 + slack) where the cell has min_rows rows, else 30
+ *      (height 1, the plain bound);
+ *   7. install (gaps_set_learned_proposal).
+ * The context must hold one pp process with GAPS_MIXED. The call allocates
+ * and frees its own scratch (event records for chunks of 2^19 events,
+ * states, rows) and synchronises the stream. params_out
+ * (GAPS_MLP_PARAMS floats) and log_margins_out (GAPS_ISR_CLASSES x
+ * GAPS_ISR_ETA_BINS x GAPS_ISR_BINS floats) are host arrays that receive the
+ * installed proposal when not NULL. Returns GAPS_ERR_INVALID_ARG for a bad
+ * configuration, GAPS_ERR_CUDA on device errors. */
+typedef struct {
+    uint64_t first_event, n_events, capacity;
+    uint64_t holdout_first, holdout_events, holdout_capacity;
+    uint64_t steps;       /* Adam steps in all (>= 4) */
+    float lr, tau;        /* learning rate; expectile of the loss, in (0, 1) */
+    uint64_t seed;        /* initialisation and minibatches */
+    float slack;          /* relative margin above the calibration maximum, >= 0 */
+    uint32_t min_rows;    /* rows a calibration cell needs */
+    float target_floor;   /* smallest target (log of the ratio) */
+} gaps_learn_config;
+
+typedef struct {
+    uint64_t states, rows, holdout_states;
+    float loss_first, loss_last;      /* minibatch loss of the first and last step */
+    uint32_t cells_calibrated;        /* cells with a learned margin */
+    float mean_bin_height;            /* mean calibrated height over the training rows */
+    float fit_rmse;                   /* rms of network - target over the training rows */
+} gaps_learn_report;
+
+int gaps_train_learned_proposal(gaps_ctx* ctx, const gaps_learn_config* cfg, float* params_out,
+                                float* log_margins_out, gaps_learn_report* report, void* stream);
 
 /* Violation log of the learned proposal (device arrays, caller-owned; log ==
  * NULL switches it off): every acceptance weight above one met with the learned

@@ -29,6 +29,7 @@ UNITS = {
     "shower_mixed.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "mlp.cu": [],
     "peaks.cu": [],
+    "learn.cu": [],
 }
 
 

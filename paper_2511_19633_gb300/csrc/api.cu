@@ -28,6 +28,16 @@ cudaError_t launch_shower_wave(const DevParams&, const DevEvents&, const WorkSet
                                uint64_t, uint64_t, int, int, int, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
                                const HistSet&, double*, double*, int, cudaStream_t);
+cudaError_t sort_states(float4*, uint64_t, cudaStream_t);
+cudaError_t floor_values(float*, uint64_t, float, cudaStream_t);
+cudaError_t mlp_init(float*, uint64_t, cudaStream_t);
+cudaError_t calibration_init(int*, unsigned*, cudaStream_t);
+cudaError_t calibration_accumulate(const float*, const float*, const float*, uint64_t, int*, unsigned*,
+                                   cudaStream_t);
+cudaError_t calibration_margins(const int*, const unsigned*, unsigned, float, float, float*, unsigned*,
+                                cudaStream_t);
+cudaError_t calibration_stats(const float*, const float*, const float*, uint64_t, const float*, double*,
+                              cudaStream_t);
 }  // namespace gaps
 
 using namespace gaps;
@@ -141,6 +151,7 @@ int validate_config(const gaps_config& c) {
   if ((c.schedule == GAPS_SCHED_WARP || c.schedule == GAPS_SCHED_WAVE) && c.precision != GAPS_MIXED)
     return GAPS_ERR_INVALID_ARG;
   if (c.wave_passes < 0 || c.wave_passes > 4096) return GAPS_ERR_INVALID_ARG;
+  if (c.wave_cycles < 0 || c.wave_cycles > 1000000) return GAPS_ERR_INVALID_ARG;
   if (c.trial_mode != GAPS_TRIALS_REDRAW && c.trial_mode != GAPS_TRIALS_KEEP && c.trial_mode != GAPS_TRIALS_SELECT)
     return GAPS_ERR_INVALID_ARG;
   if (c.trial_mode != GAPS_TRIALS_REDRAW &&
@@ -360,7 +371,7 @@ int ensure_workset(gaps_ctx* ctx, int& blocks, int& bs, WorkSet& W) {
 // working set and state of the wavefront schedule for `cap` events
 // (allocated on first use, grown when a larger capacity comes)
 constexpr int kWavePassesDefault = 24;
-constexpr int kWaveBudget = 512;  // veto cycles of one event in one pass
+constexpr int kWaveCyclesDefault = 64;  // veto cycles of one event in one pass
 int ensure_wave(gaps_ctx* ctx, uint64_t cap, WorkSet& W, WaveSet& V) {
   const int nmax = ctx->cfg.nmax_partons;
   // the kernels index the working set with unsigned 32-bit element offsets
@@ -394,7 +405,8 @@ int shower_wave(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
   const int bs = c.block_size > 0 ? c.block_size : 128;
   const int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
   const int passes = c.wave_passes > 0 ? c.wave_passes : kWavePassesDefault;
-  return cuda_fail(launch_shower_wave(ctx->P, dev_events(ev), W, V, Lc, first_event, n, passes, kWaveBudget,
+  const int cycles = c.wave_cycles > 0 ? c.wave_cycles : kWaveCyclesDefault;
+  return cuda_fail(launch_shower_wave(ctx->P, dev_events(ev), W, V, Lc, first_event, n, passes, cycles,
                                       ctx->n_sm * per_sm, bs, ctx->n_sm, c.refill_period, c.emit_batch,
                                       ctx->q_independent, (cudaStream_t)stream));
 }
@@ -491,6 +503,204 @@ int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* l
   if (launch_mlp_image(ctx->d_mlp, ctx->d_mlp_image, nullptr) != cudaSuccess) return GAPS_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return GAPS_ERR_CUDA;
   ctx->learned = 1;
+  return GAPS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// device scratch of the training pipeline, freed on every return path
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  T* get(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+};
+
+// event records of `cap` events with nmax slots, carved from one allocation
+bool alloc_events(Scratch& sc, uint64_t cap, int nmax, gaps_events& ev) {
+  ev.capacity = cap;
+  ev.nmax = nmax;
+  ev.p = sc.get<double>(4 * (size_t)nmax * cap);
+  ev.flav = sc.get<int32_t>((size_t)nmax * cap);
+  ev.col = sc.get<int32_t>((size_t)nmax * cap);
+  ev.acol = sc.get<int32_t>((size_t)nmax * cap);
+  ev.npart = sc.get<int32_t>(cap);
+  ev.status = sc.get<int32_t>(cap);
+  ev.n_emit = sc.get<int32_t>(cap);
+  ev.weight = sc.get<double>(cap);
+  ev.t = sc.get<double>(cap);
+  ev.eta = sc.get<double>(2 * cap);
+  ev.draw = sc.get<uint64_t>(cap);
+  return ev.p && ev.flav && ev.col && ev.acol && ev.npart && ev.status && ev.n_emit && ev.weight && ev.t &&
+         ev.eta && ev.draw;
+}
+
+uint64_t pow2_at_least(uint64_t n) {
+  uint64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// Showers n events from `first` in chunks and logs up to `capacity` states
+// (kept with a fraction from a pilot run), sorted canonically; then the
+// training rows. Returns the number of states, or a negative error code.
+int64_t collect_rows(gaps_ctx* ctx, Scratch& sc, const gaps_events& ev, uint64_t first, uint64_t n,
+                     uint64_t capacity, float floor, float*& feats, float*& targ, cudaStream_t st) {
+  const uint64_t chunk = ev.capacity;
+  uint64_t* d_count = sc.get<uint64_t>(1);
+  if (!d_count) return GAPS_ERR_CUDA;
+  // pilot: states per event with every state kept
+  const uint64_t pilot = n < (1u << 14) ? n : (1u << 14);
+  float* probe = sc.get<float>(4 * pilot * 64);
+  if (!probe) return GAPS_ERR_CUDA;
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st) != cudaSuccess) return GAPS_ERR_CUDA;
+  int rc = gaps_generate_hard(ctx, first - pilot, pilot, &ev, st);
+  if (rc == GAPS_OK) rc = gaps_collect_isr_states(ctx, first - pilot, pilot, &ev, 1.0f, probe, pilot * 64, d_count, st);
+  if (rc != GAPS_OK) return rc;
+  uint64_t h_count = 0;
+  if (cudaMemcpyAsync(&h_count, d_count, sizeof h_count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  double per_event = (double)h_count / (double)(pilot ? pilot : 1);
+  if (per_event < 1.0) per_event = 1.0;
+  double keep = 0.95 * (double)capacity / (per_event * (double)n);
+  if (keep > 1.0) keep = 1.0;
+  if (!(keep > 0.0)) keep = 1e-9;
+  const uint64_t cap2 = pow2_at_least(capacity);
+  float* states = sc.get<float>(4 * cap2);
+  if (!states) return GAPS_ERR_CUDA;
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st) != cudaSuccess) return GAPS_ERR_CUDA;
+  for (uint64_t f0 = 0; f0 < n; f0 += chunk) {
+    const uint64_t m = n - f0 < chunk ? n - f0 : chunk;
+    rc = gaps_generate_hard(ctx, first + f0, m, &ev, st);
+    if (rc == GAPS_OK) rc = gaps_collect_isr_states(ctx, first + f0, m, &ev, (float)keep, states, capacity, d_count, st);
+    if (rc != GAPS_OK) return rc;
+  }
+  if (cudaMemcpyAsync(&h_count, d_count, sizeof h_count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  const uint64_t m = h_count < capacity ? h_count : capacity;
+  if (sort_states(reinterpret_cast<float4*>(states), m, st) != cudaSuccess) return GAPS_ERR_CUDA;
+  feats = sc.get<float>(4 * 16 * m);
+  targ = sc.get<float>(16 * m);
+  if (!feats || !targ) return GAPS_ERR_CUDA;
+  rc = gaps_isr_targets(ctx, states, m, feats, targ, st);
+  if (rc != GAPS_OK) return rc;
+  if (floor_values(targ, 16 * m, floor, st) != cudaSuccess) return GAPS_ERR_CUDA;
+  return (int64_t)m;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gaps_train_learned_proposal(gaps_ctx* ctx, const gaps_learn_config* lc, float* params_out,
+                                float* log_margins_out, gaps_learn_report* report, void* stream) {
+  if (!ctx || !lc) return GAPS_ERR_INVALID_ARG;
+  const gaps_config& c = ctx->cfg;
+  if (c.n_mix > 0 || c.process == GAPS_EE_QQ || c.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  if (lc->n_events == 0 || lc->capacity == 0 || lc->holdout_events == 0 || lc->holdout_capacity == 0 ||
+      lc->steps < 4 || !(lc->lr > 0.0f) || !(lc->tau > 0.0f && lc->tau < 1.0f) || !(lc->slack >= 0.0f) ||
+      !std::isfinite(lc->target_floor) || lc->first_event < (1u << 14) || lc->holdout_first < (1u << 14) ||
+      lc->capacity > (1ull << 28) || lc->holdout_capacity > (1ull << 28))
+    return GAPS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc;
+  const uint64_t chunk = lc->n_events < (1u << 19) ? (lc->n_events < (1u << 14) ? (1u << 14) : lc->n_events)
+                                                   : (1u << 19);
+  gaps_events ev;
+  if (!alloc_events(sc, chunk, c.nmax_partons, ev)) return GAPS_ERR_CUDA;
+  // the collection runs the plain bound whatever the context holds
+  const int had_learned = ctx->learned;
+  ctx->learned = 0;
+  float *feats = nullptr, *targ = nullptr, *hf = nullptr, *ht = nullptr;
+  int64_t m = collect_rows(ctx, sc, ev, lc->first_event, lc->n_events, lc->capacity, lc->target_floor, feats, targ, st);
+  int64_t mh = m < 0 ? m
+                     : collect_rows(ctx, sc, ev, lc->holdout_first, lc->holdout_events, lc->holdout_capacity,
+                                    lc->target_floor, hf, ht, st);
+  ctx->learned = had_learned;
+  if (m < 0) return (int)m;
+  if (mh < 0) return (int)mh;
+  if (m == 0) return GAPS_ERR_INVALID_ARG;  // nothing to train on
+  const uint64_t rows = 16 * (uint64_t)m, hrows = 16 * (uint64_t)mh;
+  // training
+  float* P = sc.get<float>(GAPS_MLP_PARAMS);
+  float* am = sc.get<float>(GAPS_MLP_PARAMS);
+  float* av = sc.get<float>(GAPS_MLP_PARAMS);
+  float* hist = sc.get<float>(lc->steps + 1);
+  if (!P || !am || !av || !hist) return GAPS_ERR_CUDA;
+  if (mlp_init(P, lc->seed, st) != cudaSuccess) return GAPS_ERR_CUDA;
+  if (cudaMemsetAsync(am, 0, GAPS_MLP_PARAMS * sizeof(float), st) != cudaSuccess ||
+      cudaMemsetAsync(av, 0, GAPS_MLP_PARAMS * sizeof(float), st) != cudaSuccess ||
+      cudaMemsetAsync(hist, 0, (lc->steps + 1) * sizeof(float), st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  const uint64_t phase[3] = {lc->steps / 2, lc->steps / 4, lc->steps - lc->steps / 2 - lc->steps / 4};
+  const float lrs[3] = {lc->lr, lc->lr * 0.3f, lc->lr * 0.1f};
+  uint64_t done = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int rc = gaps_mlp_train(P, am, av, feats, targ, rows, phase[k], lrs[k], lc->tau, lc->seed + k, hist + done, 1,
+                                  st);
+    if (rc != GAPS_OK) return rc;
+    done += phase[k];
+  }
+  // calibration: BF16 outputs of both sets, the largest gap per cell
+  constexpr int ncell = GAPS_ISR_CLASSES * GAPS_ISR_ETA_BINS * GAPS_ISR_BINS;
+  float* out = sc.get<float>(rows);
+  float* hout = sc.get<float>(hrows);
+  int* gap = sc.get<int>(ncell);
+  unsigned* cnt = sc.get<unsigned>(ncell + 1);
+  float* margins = sc.get<float>(ncell);
+  double* sums = sc.get<double>(2);
+  if (!out || !hout || !gap || !cnt || !margins || !sums) return GAPS_ERR_CUDA;
+  int rc = gaps_mlp_forward(P, feats, rows, 1, out, st);
+  if (rc == GAPS_OK && hrows) rc = gaps_mlp_forward(P, hf, hrows, 1, hout, st);
+  if (rc != GAPS_OK) return rc;
+  if (calibration_init(gap, cnt, st) != cudaSuccess ||
+      cudaMemsetAsync(cnt + ncell, 0, sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(sums, 0, 2 * sizeof(double), st) != cudaSuccess ||
+      calibration_accumulate(feats, targ, out, rows, gap, cnt, st) != cudaSuccess ||
+      calibration_accumulate(hf, ht, hout, hrows, gap, cnt, st) != cudaSuccess ||
+      calibration_margins(gap, cnt, lc->min_rows, lc->slack, 30.0f, margins, cnt + ncell, st) != cudaSuccess ||
+      calibration_stats(feats, targ, out, rows, margins, sums, st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  std::vector<float> hp(GAPS_MLP_PARAMS), hm(ncell);
+  std::vector<float> hh(lc->steps);
+  unsigned seen = 0;
+  double hs[2] = {0.0, 0.0};
+  if (cudaMemcpyAsync(hp.data(), P, hp.size() * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(hm.data(), margins, hm.size() * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(hh.data(), hist, hh.size() * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&seen, cnt + ncell, sizeof seen, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GAPS_ERR_CUDA;
+  rc = gaps_set_learned_proposal(ctx, hp.data(), hm.data());
+  if (rc != GAPS_OK) return rc;
+  if (params_out) std::memcpy(params_out, hp.data(), hp.size() * sizeof(float));
+  if (log_margins_out) std::memcpy(log_margins_out, hm.data(), hm.size() * sizeof(float));
+  if (report) {
+    report->states = (uint64_t)m;
+    report->rows = rows;
+    report->holdout_states = (uint64_t)mh;
+    report->loss_first = hh.empty() ? 0.0f : hh.front();
+    report->loss_last = hh.empty() ? 0.0f : hh.back();
+    report->cells_calibrated = seen;
+    report->mean_bin_height = (float)(hs[0] / (double)rows);
+    report->fit_rmse = (float)std::sqrt(hs[1] / (double)rows);
+  }
   return GAPS_OK;
 }
 

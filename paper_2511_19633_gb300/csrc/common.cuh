@@ -59,6 +59,7 @@ struct WorkSet {
   uint32_t* tag;
   float4* end;
   float4* trial;         // kept trials {ln t, R_z} of both channels per end [lanes][2 nmax]
+  float4* aux;           // the veto's inputs per end {s, eta, emitter tag, partner tag} [lanes][2 nmax]
   float4* lkey;          // learned proposal: network inputs of the last evaluation [lanes][4 ends]
   unsigned char* lcode;  // learned proposal: 8-bit bin-height codes [lanes][4 ends][2][8]
   int lanes;

@@ -17,6 +17,8 @@
 //                               (emitter ascending, colour side first):
 //                               {1/c0, 1/c1, ln t_kin, partner slot (-1: none)}
 //   trial  f32x4 [L][2 nmax]    kept trials {ln t, R_z} of both channels
+//   aux    f32x4 [L][2 nmax]    per end: {s, eta, tag of the emitter, tag of the
+//                               partner}, the veto's inputs as of the last rebuild
 //   lcode  u8 [L][4][2][8], lkey f32x4 [L][4]: the learned proposal's bin
 //          heights of the initial-state ends and the inputs they came from
 // `end` caches the inverse overestimate coefficients of the end's channels
@@ -237,6 +239,9 @@ struct WS {
   __device__ __forceinline__ float4& Trial(int q) const {
     return W.trial[(unsigned)lane * (unsigned)(2 * nmax) + (unsigned)q];
   }
+  __device__ __forceinline__ float4& Aux(int q) const {
+    return W.aux[(unsigned)lane * (unsigned)(2 * nmax) + (unsigned)q];
+  }
   static constexpr bool kTrials = true;
 };
 
@@ -245,10 +250,12 @@ struct WSS {
   double* p;        // [4][nmax]
   uint32_t* tag;    // [nmax]
   float4* end;      // [2 nmax]
+  float4* aux;      // [2 nmax]
   int nmax;
   __device__ __forceinline__ double& P(int mu, int slot) const { return p[mu * nmax + slot]; }
   __device__ __forceinline__ uint32_t& T(int slot) const { return tag[slot]; }
   __device__ __forceinline__ float4& End(int q) const { return end[q]; }
+  __device__ __forceinline__ float4& Aux(int q) const { return aux[q]; }
   static constexpr bool kTrials = false;  // no kept trials in this schedule
 };
 // bytes of the lane kernel's per-warp tag staging (16-byte multiple)
@@ -258,7 +265,7 @@ __host__ __device__ constexpr size_t tag_stage_bytes(int warps, int nmax) {
 
 // bytes of one warp's event in shared memory
 __host__ __device__ constexpr size_t wss_bytes(int nmax) {
-  return (size_t)nmax * (4 * sizeof(double) + sizeof(uint32_t) + 2 * sizeof(float4));
+  return (size_t)nmax * (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4));
 }
 
 // colour partner of end (i, side) among the event's tags (shared memory)
@@ -352,12 +359,14 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
 }
 
 // Cached record of colour end q = 2 slot + side of an event: {1/c0, 1/c1,
-// ln t_kin, partner} (partner -1: no dipole on this side).
+// ln t_kin, partner} (partner -1: no dipole on this side), and in aux_out the
+// veto's inputs {s, eta, emitter tag, partner tag}.
 template <class W>
 __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, const uint32_t* tg, int n,
                              double eta0, double eta1, int row, int q, float& s_out, float& eta_out,
-                             int& type_out) {
+                             int& type_out, float4& aux_out) {
   type_out = -1;
+  aux_out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const bool pp = S.pp[row] != 0;
   const int i = q >> 1, side = q & 1;
   const uint32_t ti = tg[i];
@@ -377,6 +386,7 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, co
   s_out = s;
   eta_out = eta;
   type_out = type;
+  aux_out = make_float4(s, eta, __uint_as_float(ti), __uint_as_float(tg[k]));
   const int first = ini ? (fi == 21 ? 5 : 3) : (fi == 21 ? 1 : 0);
   const int nch = (!ini && fi != 21) ? 1 : 2;
   const float tc = __expf(S.lnTc[row]);
@@ -483,7 +493,9 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   for (int q = lane_id; q < 2 * n; q += 32) {
     float s_, eta_;
     int type_;
-    const float4 rec = end_record(M, S, w, tg, n, eta0, eta1, row, q, s_, eta_, type_);
+    float4 aux;
+    const float4 rec = end_record(M, S, w, tg, n, eta0, eta1, row, q, s_, eta_, type_, aux);
+    w.Aux(q) = aux;
     if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
     else set_end(w, q, rec, keep_ends);
   }
@@ -829,27 +841,23 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
   philox(e0, e1, (uint32_t)(L.draw + 1), (uint32_t)((L.draw + 1) >> 32), k0, k1, o2);
   L.draw += 2;
   const float Rveto = u24(o1[1]);
-  const double Rphi = u01(o1[2], o1[3]);
   const float Rfl = u24(o2[1]);
   const float lnT_before = L.lnT;
   L.lnT = best;
   const float tw = __expf(best);
 
-  // the winner's dipole, re-derived
-  const uint32_t ti = w.T(bi);
+  // the winner's dipole: its invariant, momentum fraction and tags as the
+  // last rebuild of the end table stored them (momenta, tags and eta change
+  // only in emissions, which are followed by a rebuild)
+  const float4 ax = w.Aux(bq);
+  const uint32_t ti = __float_as_uint(ax.z);
   const int fl_i = tag_fl(ti);
   const bool ini = pp && bi < 2;
   const bool ink = pp && k < 2;
   const int type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
   const int ch = (ini ? (fl_i == 21 ? 5 : 3) : (fl_i == 21 ? 1 : 0)) + bch;
-  double Pm[4], K[4];
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu) { Pm[mu] = w.P(mu, bi); K[mu] = w.P(mu, k); }
-  const double sd = 2.0 * dot4(Pm, K);
-  const float s = (float)sd;
-  float eta = 0.0f;
-  if (type == kFI) eta = (float)(k == 0 ? L.eta0 : L.eta1);
-  if (type == kIF || type == kII) eta = (float)(bi == 0 ? L.eta0 : L.eta1);
+  const float s = ax.x;
+  const float eta = ax.y;
   int shape;
   double coefd;
   channel_over(ch, type, M.P.nf, shape, coefd);
@@ -909,7 +917,7 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
     if (ch == 0) kk = (float)kCF * (2.0f / den - (1.0f + z));
     else if (ch == 1) kk = (float)kCA * 0.5f * (2.0f / den - 2.0f + z * omz);
     else kk = M.P.nf * (float)kTR * 0.5f * (1.0f - 2.0f * z * omz);
-    int f = pdf_index(tag_fl(w.T(k)));
+    int f = pdf_index(tag_fl(__float_as_uint(ax.w)));
     B = bound32(M, S, f, f, eta);
     float F1 = pdf32(M, S, f, eta * (1.0f + rho), tw);
     float F0 = pdf32(M, S, f, eta, tw);
@@ -938,7 +946,7 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
       // bounds from the scale before this cycle
       L.learned_ok = false;
       L.lnT = lnT_before;
-      pend = Emission{1, bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, Rphi, ti};
+      pend = Emission{1, bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, u01(o1[2], o1[3]), ti};
       parked = true;
       return GAPS_STATUS_ACTIVE;
     }
@@ -963,7 +971,7 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
 
   // accepted: the emission is built later, together with the other parked
   // lanes of the warp (see the kernel loop)
-  pend = Emission{0, bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, Rphi, ti};
+  pend = Emission{0, bi, k, bside, ch, type, new_fl_i, fl_j, z, omz, tw, u01(o1[2], o1[3]), ti};
   parked = true;
   return GAPS_STATUS_ACTIVE;
 }
@@ -1756,7 +1764,8 @@ __device__ __forceinline__ WSS warp_event_smem(unsigned char* base, int nmax) {
   w.nmax = nmax;
   w.p = reinterpret_cast<double*>(base);
   w.end = reinterpret_cast<float4*>(base + (size_t)nmax * 4 * sizeof(double));
-  w.tag = reinterpret_cast<uint32_t*>(base + (size_t)nmax * (4 * sizeof(double) + 2 * sizeof(float4)));
+  w.aux = reinterpret_cast<float4*>(base + (size_t)nmax * (4 * sizeof(double) + 2 * sizeof(float4)));
+  w.tag = reinterpret_cast<uint32_t*>(base + (size_t)nmax * (4 * sizeof(double) + 4 * sizeof(float4)));
   return w;
 }
 
@@ -2017,7 +2026,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(const __grid_constan
 }  // namespace
 
 size_t workset_bytes(int lanes, int nmax) {
-  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
          (size_t)lanes * (64 + 4 * sizeof(float4));
 }
 
@@ -2029,6 +2038,8 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   W.end = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
   W.trial = (float4*)p;
+  p += (size_t)lanes * nmax * 2 * sizeof(float4);
+  W.aux = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
   W.lkey = (float4*)p;
   p += (size_t)lanes * 4 * sizeof(float4);
@@ -2312,12 +2323,12 @@ constexpr int kStaticBlocks = 64, kStaticThreads = 128;
 constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
 constexpr size_t kStaticWorkBytes =
-    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
+    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
     (size_t)kStaticLanes * (64 + 4 * sizeof(float4));
 
 // the carve of workset_carve for the static launch shape
 static_assert(kStaticWorkBytes == (size_t)kStaticLanes * kStaticMaxNmax *
-                                      (4 * sizeof(double) + sizeof(uint32_t) + 4 * sizeof(float4)) +
+                                      (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
                                   (size_t)kStaticLanes * (64 + 4 * sizeof(float4)),
               "static working set differs from workset_bytes");
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];

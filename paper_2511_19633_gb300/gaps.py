@@ -50,7 +50,7 @@ class GapsConfig(ctypes.Structure):
         ("refill_period", ctypes.c_int), ("emit_batch", ctypes.c_int),
         ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_mode", ctypes.c_int),
         ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double), ("max_cycles", ctypes.c_int),
-        ("wave_passes", ctypes.c_int),
+        ("wave_passes", ctypes.c_int), ("wave_cycles", ctypes.c_int),
     ]
 
 
@@ -77,6 +77,24 @@ class GapsStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in STAT_FIELDS]
 
 
+class GapsLearnConfig(ctypes.Structure):
+    _fields_ = [("first_event", ctypes.c_uint64), ("n_events", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
+                ("holdout_first", ctypes.c_uint64), ("holdout_events", ctypes.c_uint64),
+                ("holdout_capacity", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("lr", ctypes.c_float),
+                ("tau", ctypes.c_float), ("seed", ctypes.c_uint64), ("slack", ctypes.c_float),
+                ("min_rows", ctypes.c_uint32), ("target_floor", ctypes.c_float)]
+
+
+REPORT_FIELDS = ("states", "rows", "holdout_states", "loss_first", "loss_last", "cells_calibrated",
+                 "mean_bin_height", "fit_rmse")
+
+
+class GapsLearnReport(ctypes.Structure):
+    _fields_ = [("states", ctypes.c_uint64), ("rows", ctypes.c_uint64), ("holdout_states", ctypes.c_uint64),
+                ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float), ("cells_calibrated", ctypes.c_uint32),
+                ("mean_bin_height", ctypes.c_float), ("fit_rmse", ctypes.c_float)]
+
+
 GAPS_MLP_PARAMS = 4545
 GAPS_ISR_BINS = 8
 GAPS_ISR_CLASSES = 44
@@ -88,7 +106,8 @@ EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_hist_binning", "gaps_get_stats", "gaps_reset_stats", "gaps_error_string",
            "gaps_destroy", "gaps_shower_static", "gaps_collect_isr_states", "gaps_isr_targets",
            "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train",
-           "gaps_process", "gaps_process_shower_ms", "gaps_set_violation_log", "gaps_alu_peak")
+           "gaps_process", "gaps_process_shower_ms", "gaps_set_violation_log", "gaps_alu_peak",
+           "gaps_train_learned_proposal")
 
 # kinds of gaps_alu_peak (include/gaps_peaks.h)
 GAPS_PEAK_FFMA, GAPS_PEAK_DFMA, GAPS_PEAK_MUFU, GAPS_PEAK_IMAD = 0, 1, 2, 3
@@ -131,6 +150,7 @@ def _load():
     lib.gaps_mlp_forward.argtypes = [vp, vp, u64, i, vp, vp]
     lib.gaps_mlp_train.argtypes = [vp, vp, vp, vp, vp, u64, u64, f, f, u64, vp, i, vp]
     lib.gaps_alu_peak.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+    lib.gaps_train_learned_proposal.argtypes = [vp, P(GapsLearnConfig), vp, vp, P(GapsLearnReport), vp]
     return lib
 
 
@@ -211,6 +231,22 @@ def gaps_set_learned_proposal(ctx, params, log_margins=0.0):
     m = np.ascontiguousarray(np.broadcast_to(np.asarray(log_margins, dtype=np.float32),
                                              (GAPS_ISR_CLASSES, GAPS_ISR_ETA_BINS, GAPS_ISR_BINS)))
     _check(_lib.gaps_set_learned_proposal(ctx, p.ctypes.data, m.ctypes.data), "gaps_set_learned_proposal")
+
+
+def gaps_train_learned_proposal(ctx, cfg: GapsLearnConfig, stream=None) -> dict:
+    """The library's training pipeline of the learned proposal (collect, sort,
+    targets, train, calibrate, install). Returns the report with the installed
+    parameters and margins (numpy)."""
+    import numpy as np
+    params = np.zeros(GAPS_MLP_PARAMS, dtype=np.float32)
+    margins = np.zeros((GAPS_ISR_CLASSES, GAPS_ISR_ETA_BINS, GAPS_ISR_BINS), dtype=np.float32)
+    rep = GapsLearnReport()
+    _check(_lib.gaps_train_learned_proposal(ctx, ctypes.byref(cfg), params.ctypes.data, margins.ctypes.data,
+                                            ctypes.byref(rep), _stream_ptr(stream)), "gaps_train_learned_proposal")
+    out = {n: getattr(rep, n) for n in REPORT_FIELDS}
+    out["params"] = params
+    out["log_margins"] = margins
+    return out
 
 
 def gaps_set_violation_log(ctx, log: torch.Tensor | None, count: torch.Tensor | None = None):
@@ -367,7 +403,8 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 p_s: float = 0.5, precision: int = GAPS_FP64, block_size: int = 0,
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
                 refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None,
-                mll=(66.0, 116.0), max_cycles: int = 0, wave_passes: int = 0) -> GapsConfig:
+                mll=(66.0, 116.0), max_cycles: int = 0, wave_passes: int = 0,
+                wave_cycles: int = 0) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied). mix: optional list of
     (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
@@ -375,7 +412,8 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
     GAPS_MIXED with the persistent lane schedule, REDRAW otherwise. mll: the
     dilepton mass window of GAPS_PP_LL (GeV). max_cycles: veto cycles per event
     before GAPS_ERR_ITER_CAP (0 = the library default). wave_passes: passes of
-    the wavefront schedule (0 = the library default)."""
+    the wavefront schedule and wave_cycles: veto cycles of an event per pass (0 = the
+    library defaults)."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
                    block_size, schedule, blocks_per_sm, refill_period, emit_batch)
@@ -387,6 +425,7 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
     c.mll_lo, c.mll_hi = float(mll[0]), float(mll[1])
     c.max_cycles = int(max_cycles)
     c.wave_passes = int(wave_passes)
+    c.wave_cycles = int(wave_cycles)
     if mix:
         if len(mix) > GAPS_MAX_MIX:
             raise ValueError("at most %d rows" % GAPS_MAX_MIX)

@@ -90,7 +90,8 @@ def _c_layout(struct, fields, tmp_path):
 
 @pytest.mark.parametrize("struct,cls", [("gaps_config", "GapsConfig"), ("gaps_events", "GapsEvents"),
                                         ("gaps_stats", "GapsStats"), ("gaps_mix_row", "GapsMixRow"),
-                                        ("gaps_hists", "GapsHists")])
+                                        ("gaps_hists", "GapsHists"), ("gaps_learn_config", "GapsLearnConfig"),
+                                        ("gaps_learn_report", "GapsLearnReport")])
 def test_binding_structs_match_the_header_layout(struct, cls, tmp_path):
     """Every ctypes structure of the binding has the size and field offsets of
     the C declaration (fields appended to the ABI must be appended in both)."""

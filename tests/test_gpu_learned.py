@@ -75,8 +75,8 @@ def test_training_fits_a_known_function(G, oracle_mod):
 
 @pytest.fixture(scope="module")
 def trained(G, pdf):
-    """Network trained on states of NLO events with seed 1 from an event range
-    disjoint from every test range."""
+    """Network trained by the library's pipeline (one C-ABI call) on states of
+    NLO events with seed 1 from an event range disjoint from every test range."""
     from paper_2511_19633_gb300 import learned
     proc, sqrt_s = PROCESS["pp_nlo"]
     cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=G.GAPS_MIXED, schedule=1,
@@ -89,15 +89,30 @@ def trained(G, pdf):
     return res
 
 
+def _states_and_targets(G, ctx, first, n, cap):
+    import torch
+    buf = G.EventBuffers.allocate(n, 128)
+    ev = buf.view()
+    states = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    G.gaps_generate_hard(ctx, first, n, ev)
+    G.gaps_collect_isr_states(ctx, first, n, ev, states, count, 1.0)
+    torch.cuda.synchronize()
+    m = min(int(count.item()), cap)
+    feats = torch.zeros((m * 16, 4), dtype=torch.float32, device="cuda")
+    targ = torch.zeros(m * 16, dtype=torch.float32, device="cuda")
+    G.gaps_isr_targets(ctx, states, m, feats, targ)
+    torch.cuda.synchronize()
+    return states[:m], feats, targ
+
+
 def test_teacher_targets_respect_the_plain_bound(G, pdf):
     """The plain bound is certified, so every teacher target ln r is <= 0."""
-    from paper_2511_19633_gb300 import learned
     proc, sqrt_s = PROCESS["pp_nlo"]
     cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=G.GAPS_MIXED, schedule=1)
     ctx = G.gaps_init(cfg)
     try:
-        states = learned.collect_states(ctx, 5 << 40, 20000, 1 << 18)
-        feats, targ = learned.make_dataset(ctx, states)
+        states, feats, targ = _states_and_targets(G, ctx, 5 << 40, 20000, 1 << 18)
     finally:
         G.gaps_destroy(ctx)
     t = targ.cpu().numpy()
@@ -138,6 +153,42 @@ def _shower_hists(G, pdf, params, margin, n, first=0, chunk=1 << 21):
     st["violation_log"] = vlog[: min(64, int(vcount.item()))].cpu().numpy()
     assert int(vcount.item()) == (st["violations"] if params is not None else 0)
     return hw.cpu().numpy(), hw2.cpu().numpy(), st
+
+
+def test_pipeline_report_and_determinism(G, pdf, trained):
+    """The C-ABI pipeline reports what it did, and it is deterministic: the
+    logged states are sorted before training, so a second run from the same
+    settings gives the same network bit for bit (small settings here)."""
+    from paper_2511_19633_gb300 import learned
+    assert trained["states"] > 100_000 and trained["rows"] == 16 * trained["states"]
+    assert trained["holdout_states"] > 100_000 and trained["cells_calibrated"] > 500
+    assert 0.0 < trained["mean_bin_height"] < 1.0 and trained["loss_last"] < trained["loss_first"]
+    assert np.all(np.isfinite(trained["log_margins"]))
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    out = []
+    for _ in range(2):
+        cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=G.GAPS_MIXED, schedule=1)
+        ctx = G.gaps_init(cfg)
+        try:
+            out.append(learned.train_and_install(ctx, first_event=9 << 40, n_events=1 << 17, capacity=1 << 16,
+                                                 holdout_events=1 << 16, holdout_capacity=1 << 16, steps=1000))
+        finally:
+            G.gaps_destroy(ctx)
+    assert np.array_equal(out[0]["params"], out[1]["params"])
+    assert np.array_equal(out[0]["log_margins"], out[1]["log_margins"])
+
+
+def test_shrunk_margins_are_caught_and_fall_back(G, pdf, trained):
+    """Heights shrunk by e^-3 below the calibrated ones: the shower meets
+    acceptance weights above one, counts and logs each as a violation, goes on
+    with the plain bound for that event, and every event still finishes."""
+    n = 200_000
+    w, w2, st = _shower_hists(G, pdf, trained["params"], trained["log_margins"] - 3.0, n, first=11 << 40)
+    assert st["events"] == n and st["err_numeric"] == 0 and st["err_iter_cap"] == 0
+    assert st["violations"] > 100
+    log = st["violation_log"]
+    assert np.all(log[:, 3] > 1.0)  # the logged weights exceed one
+    assert np.all((log[:, 0] > 0) & (log[:, 0] < 1))  # eta
 
 
 def test_learned_proposal_is_exact_and_cheaper(G, pdf, trained):

@@ -93,11 +93,11 @@ def test_high_cutoff_and_large_event_ids(G, oracle_mod, pdf):
     assert len(compare(g, o)) <= _max_mismatch(2000)
 
 
-@pytest.mark.parametrize("name", ["pp_lo", "pp_ll"])
+@pytest.mark.parametrize("name", ["pp_lo", "pp_ll", "pp_nlo"])
 def test_full_size_lo_sampled_against_oracle(G, oracle_mod, pdf, name):
-    """pp -> Z and pp -> Z/gamma* -> e+ e- at LO, full 1e6 events in the
-    benchmark's persistent launch: 2000 events spread over the batch are
-    recomputed by the oracle one by one."""
+    """pp -> Z and pp -> Z/gamma* -> e+ e- at LO and NLO-matched pp -> Z,
+    full 1e6-event batches in the persistent FP64 launch: 2000 events spread
+    over the batch are recomputed by the oracle one by one."""
     proc, sqrt_s = PROCESS[name]
     n = 1_000_000
     g = run_gpu(G, proc, sqrt_s, 0, n, pdf, schedule=1, block_size=128, blocks_per_sm=4, obs=True)
