@@ -139,7 +139,8 @@ typedef struct {
     gaps_mix_row mix[GAPS_MAX_MIX];
     int trial_mode;       /* GAPS_TRIALS_*: how the overestimate trials of a cycle are
                              drawn; KEEP and SELECT only with GAPS_MIXED and
-                             GAPS_SCHED_PERSISTENT or GAPS_SCHED_WAVE, any other
+                             GAPS_SCHED_PERSISTENT or GAPS_SCHED_WAVE, VETOMAX only
+                             with GAPS_MIXED and GAPS_SCHED_PERSISTENT; any other
                              combination or value is GAPS_ERR_INVALID_ARG */
     double mll_lo, mll_hi;  /* GAPS_PP_LL (also as a row of a mixed batch): dilepton
                              mass window in GeV, 0 < mll_lo < mll_hi <= sqrt_s */
@@ -163,10 +164,15 @@ typedef struct {
  *   SELECT  generate-select (the alternative named in Sec. 2's footnote):
  *           one trial from the summed rate of the channels active at the
  *           current scale, restarted at each channel's maximum scale as it
- *           is passed, and the channel chosen with probability rate / sum */
+ *           is passed, and the channel chosen with probability rate / sum
+ *   VETOMAX veto-max (Sec. 2): every channel runs its own veto algorithm to
+ *           its first accepted point, the largest wins; the accepted points
+ *           are kept while their end's record is unchanged. Persistent
+ *           schedule only; the plain bounds (a learned proposal is not used) */
 #define GAPS_TRIALS_REDRAW 0
 #define GAPS_TRIALS_KEEP 1
 #define GAPS_TRIALS_SELECT 2
+#define GAPS_TRIALS_VETOMAX 3
 
 /* Event records: structure of arrays in device memory, caller-owned, event
  * index fastest so that a warp's loads are coalesced. `capacity` is the

@@ -152,7 +152,10 @@ int validate_config(const gaps_config& c) {
     return GAPS_ERR_INVALID_ARG;
   if (c.wave_passes < 0 || c.wave_passes > 4096) return GAPS_ERR_INVALID_ARG;
   if (c.wave_cycles < 0 || c.wave_cycles > 1000000) return GAPS_ERR_INVALID_ARG;
-  if (c.trial_mode != GAPS_TRIALS_REDRAW && c.trial_mode != GAPS_TRIALS_KEEP && c.trial_mode != GAPS_TRIALS_SELECT)
+  if (c.trial_mode != GAPS_TRIALS_REDRAW && c.trial_mode != GAPS_TRIALS_KEEP && c.trial_mode != GAPS_TRIALS_SELECT &&
+      c.trial_mode != GAPS_TRIALS_VETOMAX)
+    return GAPS_ERR_INVALID_ARG;
+  if (c.trial_mode == GAPS_TRIALS_VETOMAX && (c.precision != GAPS_MIXED || c.schedule != GAPS_SCHED_PERSISTENT))
     return GAPS_ERR_INVALID_ARG;
   if (c.trial_mode != GAPS_TRIALS_REDRAW &&
       (c.precision != GAPS_MIXED || (c.schedule != GAPS_SCHED_PERSISTENT && c.schedule != GAPS_SCHED_WAVE)))
@@ -431,7 +434,8 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
     LearnedCfg Lc{};
     bool any_pp = false;
     for (int r = 0; r < ctx->P.n_rows; ++r) any_pp = any_pp || ctx->P.rows[r].process != GAPS_EE_QQ;
-    Lc.learned = ctx->learned && ctx->d_mlp && any_pp;
+    // veto-max runs every channel's veto with the plain bounds
+    Lc.learned = ctx->learned && ctx->d_mlp && any_pp && c.trial_mode != GAPS_TRIALS_VETOMAX;
     Lc.mlp = ctx->d_mlp;
     Lc.image = ctx->d_mlp_image;
     Lc.vlog = reinterpret_cast<float4*>(ctx->vlog);

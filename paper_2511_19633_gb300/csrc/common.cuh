@@ -81,11 +81,12 @@ struct WaveSet {
   uint64_t* draw;           // [cap] next Philox block of the event's stream
   unsigned char* pend;      // [cap][kWavePendBytes] the parked emission of the pass
   uint32_t* list;           // [4][cap] live events of even / odd passes, emissions, rebuilds
-  unsigned long long* ctl;  // [8] lengths of the four lists, work counter of the veto pass
+  float4* mlpq;             // [4 cap][3] initial-state ends queued for the dense network pass
+  unsigned long long* ctl;  // [8] lengths of the four lists, work counter of the veto pass, network queue length
   uint64_t cap;
 };
 constexpr int kWavePendBytes = 64;
-enum WaveList { WL_LIVE0 = 0, WL_LIVE1 = 1, WL_EMIT = 2, WL_REBUILD = 3, WL_GRAB = 4, WL_NCTL = 8 };
+enum WaveList { WL_LIVE0 = 0, WL_LIVE1 = 1, WL_EMIT = 2, WL_REBUILD = 3, WL_GRAB = 4, WL_MLP = 5, WL_NCTL = 8 };
 size_t wave_state_bytes(uint64_t cap);
 void wave_state_carve(void* base, uint64_t cap, WaveSet& V);
 

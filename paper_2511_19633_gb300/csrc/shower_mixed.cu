@@ -462,6 +462,74 @@ __device__ __forceinline__ void set_end(const W& w, int q, const float4& rec, in
   w.End(q) = rec;
 }
 
+// The warp evaluates the learned bound of up to four initial-state ends. Lane
+// j (0..3) describes end j: eta, s, dipole type, emitter flavour, t_c of its
+// row, and where its heights go (slot_j, end q_j); bit j of `eval` selects the
+// ends to evaluate. Rows r = lane and lane + 32 of the staging hold end r / 16,
+// channel (r / 8) % 2, bin r % 8: one 16-row tensor-core tile per end. Writes
+// the ends' 8-bit height codes and keys and returns on lane j the coefficient
+// scales of end j's two channels, 8 / the sum of its heights.
+__device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& mlp, const LearnedSmem& ls,
+                                             float (*stage)[4], float* ustage, unsigned eval, float tc,
+                                             float isr_eta, float isr_s, int isr_type, int fl_i, int slot_j, int q_j,
+                                             int lane_id, float& scale0, float& scale1) {
+  int cls_j[2];  // margin row: (class, eta bucket)
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
+    const float eta_e = __shfl_sync(0xffffffffu, isr_eta, e);
+    const float s_e = __shfl_sync(0xffffffffu, isr_s, e);
+    const int type_e = __shfl_sync(0xffffffffu, isr_type, e);
+    const int fl_e = __shfl_sync(0xffffffffu, fl_i, e);
+    const float tc_e = __shfl_sync(0xffffffffu, tc, e);
+    cls_j[j] = 0;
+    if ((eval >> e) & 1u) {
+      const int cls = isr_class(type_e, (fl_e == 21 ? 5 : 3) + c, fl_e);
+      mlp_features(eta_e, s_e, tc_e, m, cls, stage[r]);
+      cls_j[j] = cls * kEtaBins + eta_bucket(stage[r][0]);
+    }
+  }
+  // calibration margins of (class, eta bucket, bin), after the parameters,
+  // loaded before the tiles
+  float mg[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int r = lane_id + 32 * j;
+    if ((eval >> (r >> 4)) & 1u) mg[j] = __ldg(&M.Lc.mlp[kMlpParams + cls_j[j] * kIsrBins + (r & 7)]);
+  }
+  __syncwarp();
+  for (int tile = 0; tile < 4; ++tile)
+    if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
+  __syncwarp();
+  float tot[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
+    const int slot_e = __shfl_sync(0xffffffffu, slot_j, e);
+    const int q_e = __shfl_sync(0xffffffffu, q_j, e);
+    float U = 0.0f;
+    if ((eval >> e) & 1u) {
+      const int hc = height_code(__expf(ustage[r] + mg[j]));
+      ls.at(q_e, c, slot_e)[m] = (unsigned char)hc;
+      U = ls.dec[hc];
+    }
+    // the channel's sum over its 8 bins, in bin order (the order the veto sums them)
+    float t = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) t += __shfl_sync(0xffffffffu, U, (lane_id & ~7) + b);
+    tot[j] = t;
+  }
+  // end e = lane (0..3): rows 16 e + 8 c + m, held by lanes 16 (e % 2) + 8 c + m in row set e / 2
+  const int base = (lane_id & 1) * 16;
+  const float t00 = __shfl_sync(0xffffffffu, tot[0], base), t01 = __shfl_sync(0xffffffffu, tot[1], base);
+  const float t10 = __shfl_sync(0xffffffffu, tot[0], base + 8), t11 = __shfl_sync(0xffffffffu, tot[1], base + 8);
+  const float tc0 = (lane_id & 2) ? t01 : t00, tc1 = (lane_id & 2) ? t11 : t10;
+  scale0 = tc0 > 0.0f ? 8.0f / tc0 : 0.0f;
+  scale1 = tc1 > 0.0f ? 8.0f / tc1 : 0.0f;
+  if (lane_id < 4 && ((eval >> lane_id) & 1u))
+    ls.keyat(q_j, slot_j) = make_float4(isr_eta, isr_s, (float)(isr_type * 32 + pdf_index(fl_i)), 0.0f);
+}
+
 // The whole warp rebuilds the colour-end table of the event held by lane
 // `src` (one end per lane), after an emission or a refill of that lane. With
 // the learned proposal the warp then evaluates the network for those of the
@@ -473,7 +541,9 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
                                          const LearnedSmem& ls, float (*stage)[4], float* ustage,
                                          const W& w, uint32_t* tg, bool stage_tags, int slot, uint64_t ev_src,
                                          int n, double eta0, double eta1, int row, bool learned_src,
-                                         int keep_ends, int lane_id) {
+                                         int keep_ends, int lane_id, bool defer = false,
+                                         unsigned* defer_mask = nullptr, float4* deferred = nullptr,
+                                         float4* isr_plain = nullptr) {
   // the event's tags in shared memory: every end scans them for its partner
   if (stage_tags) {
     for (int m = lane_id; m < n; m += 32) tg[m] = w.T(m);
@@ -526,66 +596,22 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   const bool need = use && !(key.x == isr_eta && key.y == isr_s && key.z == code);
   const unsigned eval = __ballot_sync(0xffffffffu, need) & 0xFu;
   float scale0 = 0.0f, scale1 = 0.0f;  // 8 / sum of the new heights (lanes 0..3)
-  if (eval) {
-    const float tc = __expf(S.lnTc[row]);
-    // rows r = lane and lane + 32: end r / 16, channel (r / 8) % 2, bin r % 8
-    int cls_j[2];  // margin row: (class, eta bucket)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
-      const float eta_e = __shfl_sync(0xffffffffu, isr_eta, e);
-      const float s_e = __shfl_sync(0xffffffffu, isr_s, e);
-      const int type_e = __shfl_sync(0xffffffffu, isr_type, e);
-      const int fl_e = __shfl_sync(0xffffffffu, fl_i, e);
-      cls_j[j] = 0;
-      if ((eval >> e) & 1u) {
-        const int cls = isr_class(type_e, (fl_e == 21 ? 5 : 3) + c, fl_e);
-        mlp_features(eta_e, s_e, tc, m, cls, stage[r]);
-        cls_j[j] = cls * kEtaBins + eta_bucket(stage[r][0]);
-      }
-    }
-    // calibration margins of (class, eta bucket, bin), after the parameters,
-    // loaded before the tiles
-    float mg[2] = {0.0f, 0.0f};
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = lane_id + 32 * j;
-      if ((eval >> (r >> 4)) & 1u) mg[j] = __ldg(&M.Lc.mlp[kMlpParams + cls_j[j] * kIsrBins + (r & 7)]);
-    }
-    __syncwarp();
-    for (int tile = 0; tile < 4; ++tile)
-      if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
-    __syncwarp();
-    float tot[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
-      float U = 0.0f;
-      if ((eval >> e) & 1u) {
-        const int hc = height_code(__expf(ustage[r] + mg[j]));
-        ls.at(e, c, slot)[m] = (unsigned char)hc;
-        U = ls.dec[hc];
-      }
-      // the channel's sum over its 8 bins, in bin order (the order the veto sums them)
-      float t = 0.0f;
-#pragma unroll
-      for (int b = 0; b < 8; ++b) t += __shfl_sync(0xffffffffu, U, (lane_id & ~7) + b);
-      tot[j] = t;
-    }
-    // end e = lane (0..3): rows 16 e + 8 c + m, held by lanes 16 (e % 2) + 8 c + m in row set e / 2
-    const int base = (lane_id & 1) * 16;
-    const float t00 = __shfl_sync(0xffffffffu, tot[0], base), t01 = __shfl_sync(0xffffffffu, tot[1], base);
-    const float t10 = __shfl_sync(0xffffffffu, tot[0], base + 8), t11 = __shfl_sync(0xffffffffu, tot[1], base + 8);
-    const float tc0 = (lane_id & 2) ? t01 : t00, tc1 = (lane_id & 2) ? t11 : t10;
-    scale0 = tc0 > 0.0f ? 8.0f / tc0 : 0.0f;
-    scale1 = tc1 > 0.0f ? 8.0f / tc1 : 0.0f;
-    if (need) ls.keyat(lane_id, slot) = make_float4(isr_eta, isr_s, code, 0.0f);
+  if (defer) *defer_mask = eval;
+  if (eval && defer) {
+    // the wavefront's dense network pass evaluates these ends; their records
+    // and trials are finished there
+    if (need) *deferred = make_float4(isr_eta, isr_s, __int_as_float(isr_type), __int_as_float(fl_i));
+  } else if (eval) {
+    learned_heights(M, mlp, ls, stage, ustage, eval, __expf(S.lnTc[row]), isr_eta, isr_s, isr_type, fl_i, slot,
+                    lane_id, lane_id, scale0, scale1);
   }
   if (mine) {
     if (use) {
       // the coefficient scale c * mean(U): new heights, or the unchanged
       // inputs' record of the last evaluation (the same product)
-      if (need) {
+      if (need && defer) {
+        *isr_plain = isr_rec;  // scaled by the dense pass
+      } else if (need) {
         isr_rec.x *= scale0;
         isr_rec.y *= scale1;
       } else {
@@ -599,10 +625,11 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
       for (int c = 0; c < 2; ++c) *reinterpret_cast<uint2*>(ls.at(lane_id, c, slot)) = make_uint2(0u, 0u);
       ls.keyat(lane_id, slot) = make_float4(-1.0f, -1.0f, -1.0f, 0.0f);
     }
-    set_end(w, lane_id, isr_rec, keep_ends);
+    // an end whose network inputs changed draws anew (with kept trials)
+    set_end(w, lane_id, isr_rec, (need && keep_ends >= 0) ? 0 : keep_ends);
   }
   __syncwarp();
-  return __popc(eval);
+  return defer ? 0 : __popc(eval);
 }
 
 struct Emission {
@@ -976,6 +1003,178 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
   return GAPS_STATUS_ACTIVE;
 }
 
+// ---- veto-max (Sec. 2: each emission channel runs its own veto algorithm to
+// its first accepted point, and the largest accepted scale wins) ----------
+struct ChannelWeight {
+  float w, z, omz, x, sumF;
+  int ch, type, k, new_fl_i, fl_j;
+  uint32_t ti;
+  bool ok;  // inside the true z range and the map's domain
+};
+
+// Acceptance weight of a trial of end q, channel c at scale tw with z draw
+// Rz, with the plain bounds: the arithmetic of the max-veto winner's weight.
+template <class W>
+__device__ __noinline__ ChannelWeight channel_weight(const MixedCtx& M, const SmemPdf& S, const W& w, const Lane& L,
+                                                     int q, int c, float tw, float Rz) {
+  ChannelWeight r;
+  r.ok = false;
+  r.w = 0.0f;
+  const bool pp = S.pp[L.row] != 0;
+  const float lnTc = S.lnTc[L.row];
+  const int bi = q >> 1;
+  r.k = __float_as_int(w.End(q).w);
+  const float4 ax = w.Aux(q);
+  r.ti = __float_as_uint(ax.z);
+  const int fl_i = tag_fl(r.ti);
+  const bool ini = pp && bi < 2, ink = pp && r.k < 2;
+  r.type = ini ? (ink ? kII : kIF) : (ink ? kFI : kFF);
+  r.ch = (ini ? (fl_i == 21 ? 5 : 3) : (fl_i == 21 ? 1 : 0)) + c;
+  r.new_fl_i = fl_i;
+  r.fl_j = 21;
+  r.x = 1.0f;
+  r.sumF = 0.0f;
+  const float s = ax.x, eta = ax.y;
+  int shape;
+  double coefd;
+  channel_over(r.ch, r.type, M.P.nf, shape, coefd);
+  const float coef = (float)coefd;
+  float zm, delta;
+  zlim32(r.type, __expf(lnTc), s, eta, zm, delta);
+  shape_sample32(shape, zm, delta, Rz, r.z, r.omz);
+  const float z = r.z, omz = r.omz;
+  float zm_t, delta_t;
+  if (!zlim32(r.type, tw, s, eta, zm_t, delta_t) || !(omz > delta_t) || !(z > zm_t)) return r;
+  const float pover = shape_val32(shape, coef, z, omz);
+  const float as_t = (float)M.P.as_mz / (1.0f + (float)M.P.as_mz * (float)M.P.beta0 * __logf(tw / (float)(kMZ * kMZ)));
+  const float as_ratio = as_t / (S.asOver2pi[L.row] * 2.0f * (float)kPi);
+  const int ch = r.ch;
+  if (r.type == kFF) {
+    const float y = tw / (z * omz * s);
+    const float den = omz + z * y;
+    float kk;
+    if (ch == 0) kk = (float)kCF * (2.0f / den - (1.0f + z));
+    else if (ch == 1) kk = (float)kCA * 0.5f * (2.0f / den - 2.0f + z * omz);
+    else kk = M.P.nf * (float)kTR * 0.5f * (1.0f - 2.0f * z * omz);
+    r.w = as_ratio * (1.0f - y) * kk / pover;
+  } else if (r.type == kFI) {
+    const float rho = tw / (z * omz * s);
+    const float x = 1.0f / (1.0f + rho), omx = rho / (1.0f + rho);
+    const float den = omz + omx;
+    float kk;
+    if (ch == 0) kk = (float)kCF * (2.0f / den - (1.0f + z));
+    else if (ch == 1) kk = (float)kCA * 0.5f * (2.0f / den - 2.0f + z * omz);
+    else kk = M.P.nf * (float)kTR * 0.5f * (1.0f - 2.0f * z * omz);
+    const int f = pdf_index(tag_fl(__float_as_uint(ax.w)));
+    const float B = bound32(M, S, f, f, eta);
+    const float F1 = pdf32(M, S, f, eta * (1.0f + rho), tw);
+    const float F0 = pdf32(M, S, f, eta, tw);
+    const float ratio = F0 > 0.0f ? x * F1 / F0 : 0.0f;
+    r.w = as_ratio * kk / pover * ratio / B;
+  } else {
+    const IsrEval ev = isr_eval32(M, S, r.type, ch, fl_i, eta, s, tw, z, omz, pover);
+    if (!ev.ok) return r;
+    r.x = ev.x;
+    r.sumF = ev.sumF;
+    r.w = as_ratio * ev.r;
+    if (ch == 4) { r.new_fl_i = 21; r.fl_j = -fl_i; }
+    if (ch == 5) { r.new_fl_i = 21; r.fl_j = 21; }
+  }
+  r.ok = true;
+  return r;
+}
+
+// One cycle of veto-max: the marked ends' channels first run their own veto
+// algorithms from the event's scale to their first accepted points (kept, as
+// kept trials are, while the end's record is unchanged); the largest accepted
+// point is the emission. Trial blocks use word 1 for t, word 3 for z and
+// word 2 for the acceptance; the emission then draws one block for the
+// flavour choice and the azimuth.
+template <class W>
+__device__ int step_vetomax(const MixedCtx& M, const SmemPdf& S, const W& w, Lane& L, uint64_t id, Counters32& cnt,
+                            Emission& pend, bool& parked) {
+  const bool pp = S.pp[L.row] != 0;
+  const float lnTc = S.lnTc[L.row];
+  const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+  cnt.steps += 1;
+  float best = -INFINITY, bRz = 0.5f;
+  int bq = -1, bch = 0;
+  uint64_t d = L.draw;
+  const int ne = 2 * L.n;
+#pragma unroll 1
+  for (int q = 0; q < ne; ++q) {
+    float4 tr = w.Trial(q);
+    if (isnan(tr.x)) {
+      tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+      const float4 rec = w.End(q);
+      if (__float_as_int(rec.w) >= 0) {
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+          const float ic = c == 0 ? rec.x : rec.y;
+          if (ic < 0.0f) continue;  // channel absent for this emitter
+          float lnT = fminf(L.lnT, rec.z), lt = -INFINITY, rz = 0.5f;
+#pragma unroll 1
+          while (lnT > lnTc && ic > 0.0f) {
+            const uint64_t dd = d++;
+            uint32_t out[4];
+            philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+            cnt.trials += 1;
+            if (pp && q < 4) cnt.isr_trials += 1;
+            const float t1 = fmaf(__logf(u24(out[1])), ic, lnT);
+            if (!(t1 > lnTc)) break;
+            const ChannelWeight cw = channel_weight(M, S, w, L, q, c, __expf(t1), u24(out[3]));
+            if (cw.ok && cw.w > 1.0f) cnt.violations += 1;
+            if (cw.ok && u24(out[2]) < cw.w) {
+              lt = t1;
+              rz = u24(out[3]);
+              break;
+            }
+            cnt.vetoes += 1;
+            lnT = t1;
+          }
+          if (c == 0) { tr.x = lt; tr.y = rz; }
+          else { tr.z = lt; tr.w = rz; }
+        }
+      }
+      w.Trial(q) = tr;
+    }
+    if (tr.x > best) { best = tr.x; bq = q; bch = 0; bRz = tr.y; }
+    if (tr.z > best) { best = tr.z; bq = q; bch = 1; bRz = tr.w; }
+  }
+  L.draw = d;
+  if (bq < 0 || !(best > lnTc)) return GAPS_STATUS_DONE;
+  // the winner was accepted when its channel ran: the emission
+  L.lnT = best;
+  const float tw = __expf(best);
+  const ChannelWeight cw = channel_weight(M, S, w, L, bq, bch, tw, bRz);
+  uint32_t o[4];
+  const uint64_t dd = L.draw++;
+  philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, o);
+  const float Rfl = u24(o[1]);
+  int new_fl_i = cw.new_fl_i, fl_j = cw.fl_j;
+  const float4 ax = w.Aux(bq);
+  const float eta = ax.y;
+  if (cw.ch == 2) {
+    int f = 1 + (int)floorf(Rfl * M.P.nf);
+    if (f > M.P.nf) f = M.P.nf;
+    new_fl_i = f; fl_j = -f;
+  } else if (cw.ch == 6) {
+    float target = Rfl * cw.sumF, acc = 0.0f;
+    int pick = 10;
+    for (int f = 1; f <= 10; ++f) {
+      acc += pdf32(M, S, f, eta / cw.x, tw);
+      if (target < acc) { pick = f; break; }
+    }
+    const int fl = pick <= 5 ? pick : -(pick - 5);
+    new_fl_i = fl; fl_j = fl;
+  }
+  if (L.n >= M.P.nmax) return GAPS_ERR_CAPACITY;
+  pend = Emission{0, bq >> 1, cw.k, bq & 1, cw.ch, cw.type, new_fl_i, fl_j, cw.z, cw.omz, tw, u01(o[2], o[3]), cw.ti};
+  parked = true;
+  return GAPS_STATUS_ACTIVE;
+}
+
 
 // Generate-select (the alternative to max-veto in Sec. 2's footnote): the
 // superposition of every channel's overestimate process is a Poisson process
@@ -1289,7 +1488,7 @@ __device__ __forceinline__ void flush_counters(const MixedCtx& M, const Counters
 // WAVE = true: the wavefront schedule's final pass; the lanes take the events
 // of the live list, whose working-set lanes and end tables the wavefront
 // passes left ready, and write their state back to the WaveSet arrays.
-template <int MINB, bool WAVE>
+template <int MINB, bool WAVE, bool VMAX = false>
 __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constant__ MixedCtx M) {
   __shared__ SmemPdf S;
   extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
@@ -1323,7 +1522,9 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
   bool parked = false;
   Emission pend;
   int since_flush = 0;
-  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
+  // ends keep their trials (max-veto) or accepted points (veto-max) while
+  // their records are unchanged
+  const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP || VMAX;
   while (true) {
     // warp-aggregated refill of idle lanes
     unsigned idle = __ballot_sync(0xffffffffu, !active);
@@ -1423,7 +1624,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
     lane_steps += __popc(__ballot_sync(0xffffffffu, active && !parked));
     warp_steps += 32;
     if (active && !parked) {
-      int st = step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked);
+      int st = VMAX ? step_vetomax(M, S, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked)
+                    : step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked);
       if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st != GAPS_STATUS_ACTIVE) {
         L.status = st;
@@ -1512,7 +1714,7 @@ __global__ void k_wave_init(const __grid_constant__ MixedCtx M) {
 // draws (every lane).
 __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const SmemPdf& S, const WS& w, uint64_t id,
                                                      int n, int row, float lnT, uint64_t d, int lane_id,
-                                                     Counters32& cnt) {
+                                                     Counters32& cnt, unsigned defer_mask, uint64_t& defer_off) {
   const unsigned full = 0xffffffffu;
   const bool pp = S.pp[row] != 0;
   const float lnTc = S.lnTc[row];
@@ -1538,6 +1740,11 @@ __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const Sm
       if (lane_id >= off) inc += t;
     }
     const int tot = __shfl_sync(full, inc, 31);
+    if (marked && q < 4 && ((defer_mask >> q) & 1u)) {
+      // the dense network pass draws this end's trials from here
+      defer_off = d + (uint64_t)(inc - nd);
+      marked = false;
+    }
     if (marked) {
       float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
       if (__float_as_int(rec.w) >= 0) {
@@ -1592,18 +1799,117 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
     const uint64_t e = M.V.list[(size_t)WL_REBUILD * M.V.cap + i];
     const int flags = M.V.flags[e], n = M.V.n[e], row = (flags >> 8) & 0xff;
     const WS w{M.W, (int)e, M.P.nmax};
+    unsigned defer_mask = 0;
+    float4 deferred = make_float4(0.0f, 0.0f, 0.0f, 0.0f), plain = deferred;
     mlp_tiles += rebuild_coop(M, S, mlp_s, D.ls, D.stage[warp_id], D.ustage[warp_id], w,
                               D.tag_stage + warp_id * M.P.nmax, true, (int)e, e, n, M.V.eta[e],
-                              M.V.eta[M.V.cap + e], row, (flags & 1) != 0, M.V.keep[e], lane_id);
+                              M.V.eta[M.V.cap + e], row, (flags & 1) != 0, M.V.keep[e], lane_id, cache, &defer_mask,
+                              &deferred, &plain);
     rebuilds += 1;
     if (cache) {
-      const uint64_t d = draw_marked_ends(M, S, w, M.first + e, n, row, M.V.lnT[e], M.V.draw[e], lane_id, cnt);
+      uint64_t off = 0;
+      const uint64_t d = draw_marked_ends(M, S, w, M.first + e, n, row, M.V.lnT[e], M.V.draw[e], lane_id, cnt,
+                                          defer_mask, off);
       __syncwarp();  // every lane has read the old counter
       if (lane_id == 0) M.V.draw[e] = d;
+      // initial-state ends whose network inputs changed: to the dense pass
+      const bool mine = lane_id < 4 && ((defer_mask >> lane_id) & 1u);
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      if (m) {
+        unsigned long long base = 0;
+        if (lane_id == 0) base = atomicAdd(&M.V.ctl[WL_MLP], (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (mine) {
+          float4* q = M.V.mlpq + 3 * (base + __popc(m & ((1u << lane_id) - 1u)));
+          q[0] = plain;
+          q[1] = deferred;
+          q[2] = make_float4(__uint_as_float((uint32_t)e), __int_as_float(lane_id | (row << 8)),
+                             __uint_as_float((uint32_t)off), __uint_as_float((uint32_t)(off >> 32)));
+        }
+      }
     }
   }
   flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull,
                  lane_id);
+}
+
+// The dense network pass of the learned proposal: four queued initial-state
+// ends per warp iteration (one 16-row tile each), from whatever events the
+// rebuild pass queued them. Each end gets its height codes and key, its
+// record scaled by c * mean(U), and its two trials drawn at the Philox
+// counters the rebuild pass reserved for it, as the persistent kernel's
+// inline evaluation and first trial loop would give them.
+__global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedCtx M) {
+  __shared__ float dec[256];
+  __shared__ float stage_s[8][64][4];
+  __shared__ float ustage_s[8][64];
+  __shared__ float lnTc[kMaxRows];
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
+  if (threadIdx.x < kMaxRows) {
+    const RowParams& R = M.P.rows[threadIdx.x < M.P.n_rows ? threadIdx.x : 0];
+    lnTc[threadIdx.x] = (float)gm_log(R.t_cut);
+  }
+  __syncthreads();
+  LearnedSmem ls;
+  ls.code = M.W.lcode;
+  ls.key = M.W.lkey;
+  ls.dec = dec;
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
+  const uint64_t count = M.V.ctl[WL_MLP];
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  Counters32 cnt;
+  unsigned long long tiles = 0;
+  for (uint64_t g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id; 4 * g < count; g += nw) {
+    const uint64_t j = 4 * g + lane_id;
+    const bool have = lane_id < 4 && j < count;
+    float4 plain = make_float4(0.0f, 0.0f, 0.0f, 0.0f), in = plain, tag = plain;
+    if (have) {
+      const float4* q = M.V.mlpq + 3 * j;
+      plain = q[0];
+      in = q[1];
+      tag = q[2];
+    }
+    const unsigned eval = __ballot_sync(0xffffffffu, have) & 0xFu;
+    const int e = (int)__float_as_uint(tag.x), qq = __float_as_int(tag.y) & 0xff, row = __float_as_int(tag.y) >> 8;
+    const float tc = have ? __expf(lnTc[row]) : 1.0f;
+    float scale0 = 0.0f, scale1 = 0.0f;
+    learned_heights(M, mlp_s, ls, stage_s[warp_id], ustage_s[warp_id], eval, tc, in.x, in.y, __float_as_int(in.z),
+                    __float_as_int(in.w), e, qq, lane_id, scale0, scale1);
+    tiles += __popc(eval);
+    if (have) {
+      const WS w{M.W, e, M.P.nmax};
+      float4 rec = plain;
+      rec.x *= scale0;
+      rec.y *= scale1;
+      w.End(qq) = rec;
+      // the end's trials, channel by channel, from its reserved counter
+      uint64_t dd = ((uint64_t)__float_as_uint(tag.w) << 32) | (uint64_t)__float_as_uint(tag.z);
+      const uint64_t id = M.first + (uint64_t)e;
+      const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+      const float lnTmax = fminf(M.V.lnT[e], rec.z);
+      const bool live = lnTmax > lnTc[row];
+      float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float ic = c == 0 ? rec.x : rec.y;
+        if (ic < 0.0f) continue;
+        const uint64_t dc = dd++;
+        if (!(live && ic > 0.0f)) continue;
+        uint32_t out[4];
+        philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
+        cnt.trials += 1;
+        cnt.isr_trials += 1;
+        const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+        if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
+        else { tr.z = lt; tr.w = u24(out[3]); }
+      }
+      w.Trial(qq) = tr;
+    }
+    __syncwarp();
+  }
+  flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, 0, lane_id == 0 ? tiles : 0ull, lane_id);
 }
 
 // Persistent lanes over the live list: each lane runs max-veto cycles of one
@@ -1617,7 +1923,10 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
   mixed_prologue(M, S, dyn_lane_smem, D);
   const LearnedSmem& ls = D.ls;
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x == 0) M.V.ctl[WL_REBUILD] = 0;  // filled by this pass's emissions
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    M.V.ctl[WL_REBUILD] = 0;  // filled by this pass's emissions
+    M.V.ctl[WL_MLP] = 0;      // filled by the next pass's rebuilds
+  }
   const int lane_id = threadIdx.x & 31;
   const uint32_t* live = M.V.list + (size_t)M.wave_par * M.V.cap;
   const uint64_t n_work = M.V.ctl[M.wave_par];
@@ -2143,6 +2452,9 @@ cudaError_t mixed_kernels_init() {
   e = opt_in(k_shower_mixed<2, true>, bytes, e);
   e = opt_in(k_shower_mixed<3, true>, bytes, e);
   e = opt_in(k_shower_mixed<4, true>, bytes, e);
+  e = opt_in(k_shower_mixed<2, false, true>, bytes, e);
+  e = opt_in(k_shower_mixed<3, false, true>, bytes, e);
+  e = opt_in(k_shower_mixed<4, false, true>, bytes, e);
   e = opt_in(k_wave_ends<2>, bytes, e);
   e = opt_in(k_wave_ends<3>, bytes, e);
   e = opt_in(k_wave_ends<4>, bytes, e);
@@ -2214,11 +2526,11 @@ int mixed_tier(int blocks, int block_size, int sm_count) {
   return threads_per_sm <= 512 ? 2 : (threads_per_sm <= 768 ? 3 : 4);
 }
 
-template <bool WAVE>
+template <bool WAVE, bool VMAX = false>
 void launch_persistent(const MixedCtx& M, int tier, int blocks, int block_size, size_t dyn, cudaStream_t stream) {
-  if (tier == 2) k_shower_mixed<2, WAVE><<<blocks, block_size, dyn, stream>>>(M);
-  else if (tier == 3) k_shower_mixed<3, WAVE><<<blocks, block_size, dyn, stream>>>(M);
-  else k_shower_mixed<4, WAVE><<<blocks, block_size, dyn, stream>>>(M);
+  if (tier == 2) k_shower_mixed<2, WAVE, VMAX><<<blocks, block_size, dyn, stream>>>(M);
+  else if (tier == 3) k_shower_mixed<3, WAVE, VMAX><<<blocks, block_size, dyn, stream>>>(M);
+  else k_shower_mixed<4, WAVE, VMAX><<<blocks, block_size, dyn, stream>>>(M);
 }
 }  // namespace
 
@@ -2233,7 +2545,9 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   // learned proposal: per-warp staging, height decode table, 64 bytes of
   // height codes per lane
   const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0);
-  launch_persistent<false>(M, mixed_tier(blocks, block_size, sm_count), blocks, block_size, dyn, stream);
+  const int tier = mixed_tier(blocks, block_size, sm_count);
+  if (P.trial_mode == GAPS_TRIALS_VETOMAX) launch_persistent<false, true>(M, tier, blocks, block_size, dyn, stream);
+  else launch_persistent<false>(M, tier, blocks, block_size, dyn, stream);
   return cudaGetLastError();
 }
 
@@ -2246,7 +2560,7 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 size_t wave_state_bytes(uint64_t cap) {
   return al256(cap * sizeof(float)) + 6 * al256(cap * sizeof(int)) + al256(2 * cap * sizeof(double)) +
          al256(cap * sizeof(uint64_t)) + al256(cap * (size_t)kWavePendBytes) + al256(4 * cap * sizeof(uint32_t)) +
-         al256(WL_NCTL * sizeof(unsigned long long));
+         al256(12 * cap * sizeof(float4)) + al256(WL_NCTL * sizeof(unsigned long long));
 }
 
 void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
@@ -2264,6 +2578,7 @@ void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
   V.draw = (uint64_t*)take(cap * sizeof(uint64_t));
   V.pend = (unsigned char*)take(cap * (size_t)kWavePendBytes);
   V.list = (uint32_t*)take(4 * cap * sizeof(uint32_t));
+  V.mlpq = (float4*)take(12 * cap * sizeof(float4));
   V.ctl = (unsigned long long*)take(WL_NCTL * sizeof(unsigned long long));
 }
 
@@ -2292,6 +2607,7 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
     if (tier == 2) k_wave_ends<2><<<blocks, block_size, dyn, stream>>>(M);
     else if (tier == 3) k_wave_ends<3><<<blocks, block_size, dyn, stream>>>(M);
     else k_wave_ends<4><<<blocks, block_size, dyn, stream>>>(M);
+    if (Lc.learned) k_wave_mlp<<<sm_count * 4, 256, 0, stream>>>(M);
     if (w == passes) break;  // the last rebuilds, then the persistent kernel
     if (tier == 2) k_wave_veto<2><<<blocks, block_size, dyn, stream>>>(M);
     else if (tier == 3) k_wave_veto<3><<<blocks, block_size, dyn, stream>>>(M);

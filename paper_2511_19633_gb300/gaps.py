@@ -27,7 +27,7 @@ GAPS_ERR_NO_DEVICE = -6
 GAPS_EE_QQ, GAPS_PP_Z_LO, GAPS_PP_Z_NLO, GAPS_PP_LL = 0, 1, 2, 3
 GAPS_FP64, GAPS_MIXED = 0, 1
 GAPS_SCHED_PER_EVENT, GAPS_SCHED_PERSISTENT, GAPS_SCHED_WARP, GAPS_SCHED_WAVE = 0, 1, 2, 3
-GAPS_TRIALS_REDRAW, GAPS_TRIALS_KEEP, GAPS_TRIALS_SELECT = 0, 1, 2
+GAPS_TRIALS_REDRAW, GAPS_TRIALS_KEEP, GAPS_TRIALS_SELECT, GAPS_TRIALS_VETOMAX = 0, 1, 2, 3
 GAPS_STATUS_ACTIVE, GAPS_STATUS_DONE = 0, 1
 GAPS_NOBS, GAPS_NHIST, GAPS_HIST_BINS = 8, 6, 66
 

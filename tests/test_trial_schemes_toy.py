@@ -1,7 +1,8 @@
-"""The three trial schemes of the mixed shower (GAPS_TRIALS_REDRAW, KEEP and
-SELECT) give the first accepted emission the same distribution. This is the
-reason the GPU kernel may keep losing trials or draw one trial from the summed
-rate (Sec. 2, Fig. 1 and its footnote on generate-select).
+"""The trial schemes of the mixed shower (GAPS_TRIALS_REDRAW, KEEP, SELECT and
+VETOMAX) give the first accepted emission the same distribution. This is the
+reason the GPU kernel may keep losing trials, draw one trial from the summed
+rate, or run each channel's own veto algorithm and take the largest accepted
+scale (Sec. 2, Fig. 1 and its remarks on veto-max and generate-select).
 
 A toy veto algorithm checks it against closed forms, with no GPU and none of
 the library's code. K channels have overestimate rates c_i in ln t below their
@@ -104,7 +105,24 @@ def select(rng):
     return None
 
 
-@pytest.mark.parametrize("scheme", [redraw, keep, select])
+def vetomax(rng):
+    """each channel runs its own veto algorithm from the starting scale to its
+    first accepted point; the largest accepted point wins"""
+    best, bi = -math.inf, None
+    for i in range(len(RATES)):
+        lnT = LN_T0
+        while True:
+            lnT = draw(rng, lnT, i)
+            if lnT < LN_TC:
+                break
+            if rng.random() < accept(i, lnT):
+                if lnT > best:
+                    best, bi = lnT, i
+                break
+    return None if bi is None else (best, bi)
+
+
+@pytest.mark.parametrize("scheme", [redraw, keep, select, vetomax])
 def test_first_emission_distribution(scheme):
     rng = np.random.default_rng(12345)
     n = 20000
@@ -148,3 +166,25 @@ def test_kept_trials_and_select_draw_fewer_uniforms():
             scheme(c)
         counts[scheme.__name__] = c.n
     assert counts["keep"] < counts["redraw"] and counts["select"] < counts["redraw"], counts
+
+
+def test_vetomax_evaluates_every_channel():
+    """Veto-max evaluates the acceptance of every channel's trials down to its
+    first accepted point (or the cutoff), max-veto only the winners'."""
+    def count_accepts(scheme, seed):
+        calls = [0]
+        global accept
+        orig = accept
+
+        def counted(i, lt):
+            calls[0] += 1
+            return orig(i, lt)
+        accept = counted
+        try:
+            rng = np.random.default_rng(seed)
+            for _ in range(2000):
+                scheme(rng)
+        finally:
+            accept = orig
+        return calls[0]
+    assert count_accepts(vetomax, 3) > 1.5 * count_accepts(keep, 3)
