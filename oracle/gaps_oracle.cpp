@@ -49,6 +49,7 @@ constexpr double kQ2Min = 0.5, kQ2Max = 13600.0 * 13600.0;
 constexpr int kStatusActive = 0, kStatusDone = 1;
 constexpr int kErrCapacity = -2, kErrIterCap = -3, kErrNumeric = -4;
 constexpr long kMaxSteps = 200000;
+constexpr double kHqFloor = 1e-3;  // heavy-quark trials end at m_q^2 (1 + kHqFloor)
 
 // ---------------------------------------------------------------------------
 // Random numbers: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written
@@ -203,7 +204,15 @@ struct Pdf {
   // certified bound tables (see pdf_ratio_bound)
   double umax[12][kNX];   // max over Q^2 nodes of the node value
   double sufmax[12][kNX + 1];  // max over x nodes j >= k of umax
-  double lmin[12][kNX];   // min over Q^2 nodes of the node value
+  double lmin[12][kNX];   // min over Q^2 nodes of the node value (above the
+                          // threshold for a heavy flavour with one)
+  // Heavy-quark thresholds (App. A.2; c, b, cbar, bbar only): a flavour whose
+  // nodes vanish for every x at all Q^2 nodes up to thr[f] and are positive
+  // above has its mass m2[f] on node thr[f]; first[f][ix] is its node value
+  // on node thr[f] + 1. thr[f] = -1: no threshold.
+  int thr[12];
+  double m2[12];
+  double first[12][kNX];
 
   double node(int f, int ix, int iq) const {
     return (double)grid[((size_t)f * kNX + ix) * kNQ + iq];
@@ -217,6 +226,23 @@ struct Pdf {
     return f == 11 ? node_sum(ix, iq) : node(f, ix, iq);
   }
 
+  // threshold node of a heavy flavour, or -1
+  int find_threshold(int f) const {
+    if (f != 4 && f != 5 && f != 9 && f != 10) return -1;
+    int k0 = -1;
+    for (int iq = 0; iq < kNQ; ++iq) {
+      bool zero = true;
+      for (int ix = 0; ix < kNX && zero; ++ix) zero = node(f, ix, iq) == 0.0;
+      if (!zero) break;
+      k0 = iq;
+    }
+    if (k0 < 0 || k0 >= kNQ - 1) return -1;
+    for (int iq = k0 + 1; iq < kNQ; ++iq)
+      for (int ix = 0; ix < kNX; ++ix)
+        if (!(node(f, ix, iq) > 0.0)) return -1;
+    return k0;
+  }
+
   void init(const float* g) {
     grid = g;
     lxmin = lg(kXMin);
@@ -224,12 +250,16 @@ struct Pdf {
     lqmin = lg(kQ2Min);
     dlq = (lg(kQ2Max) - lqmin) / (kNQ - 1);
     for (int f = 0; f < 12; ++f) {
+      thr[f] = f < 11 ? find_threshold(f) : -1;
+      m2[f] = thr[f] >= 0 ? ex(lqmin + (double)thr[f] * dlq) : 0.0;
       for (int ix = 0; ix < kNX; ++ix) {
+        first[f][ix] = thr[f] >= 0 ? node(f, ix, thr[f] + 1) : 0.0;
         double mx = -1.0, mn = 0.0;
         for (int iq = 0; iq < kNQ; ++iq) {
           double v = node_any(f, ix, iq);
           if (iq == 0 || v > mx) mx = v;
-          if (iq == 0 || v < mn) mn = v;
+          if (iq <= thr[f]) continue;  // the minimum over the nodes above a threshold
+          if (iq == thr[f] + 1 || iq == 0 || v < mn) mn = v;
         }
         umax[f][ix] = mx;
         lmin[f][ix] = mn;
@@ -279,6 +309,16 @@ struct Pdf {
   //   numerator   <= max(interp of per-node maxima at eta, max of nodes above the cell)
   //   denominator >= interp of per-node minima at eta.
   // Returns 0 when eta is off the grid or the denominator bound vanishes.
+  //
+  // Heavy denominator with a threshold (App. A.2): the bound is of the ratio
+  // times (t - m^2)/t, the measure correction's factor, for t > m^2. In the
+  // first cell above the mass the denominator is phi * first(eta) with
+  // phi = ln(t/m^2)/dlq in (0, 1] and (t - m^2)/t = 1 - exp(-phi dlq) <= phi
+  // dlq, so the corrected ratio is at most dlq * numerator / first(eta);
+  // above that cell it is at most numerator / lmin(eta) (the factor is at
+  // most one). The same bound holds for the uncorrected ratio of two
+  // densities of this flavour at one t (the final-initial spectator), which
+  // is at most numerator / first in the first cell.
   double ratio_bound(int num, int den, double eta) const {
     int ix;
     double fx;
@@ -287,6 +327,11 @@ struct Pdf {
     double un = std::max(uin, sufmax[num][ix + 1]);
     double ld = (1.0 - fx) * lmin[den][ix] + fx * lmin[den][ix + 1];
     if (!(ld > 0.0)) return 0.0;
+    if (thr[den] >= 0) {
+      double fd = (1.0 - fx) * first[den][ix] + fx * first[den][ix + 1];
+      if (!(fd > 0.0)) return 0.0;
+      return un * std::max(dlq / fd, 1.0 / ld);
+    }
     return un / ld;
   }
 };
@@ -688,6 +733,7 @@ struct Trial {
   double coef, zm, delta;
   double s, eta;  // dipole invariant and the relevant momentum fraction
   double B;       // PDF bound used
+  double m2;      // heavy-quark measure dt/(t - m2) of the trial, 0: dt/t
 };
 
 bool is_coloured(const Parton& P) { return P.col != 0 || P.acol != 0; }
@@ -750,6 +796,19 @@ void shower_step(const Physics& ph, Event& ev) {
         if (cf.channel_mask != 0 && !((cf.channel_mask >> ch) & 1u)) continue;
         double tmax = std::min(ev.t, t_kin_max(type, s, eta));
         if (!(tmax > cf.t_cut)) continue;
+        // Heavy-quark measure correction (App. A.2): an incoming c or b whose
+        // density has a threshold draws its q <- q and q <- g trials in
+        // dt/(t - m_q^2), with the PDF ratio times (t - m_q^2)/t. Reading
+        // (the paper is silent): the channel's trials end at the floor
+        // m_q^2 (1 + kHqFloor) (or the cutoff, if higher), where the
+        // backward step to a gluon may be kinematically closed and the
+        // trials would otherwise pile up at m_q^2 without end.
+        double mq2 = 0.0;
+        if ((type == kIF || type == kII) && (ch == 3 || ch == 4)) {
+          int fe = pdf_index(Pi.fl);
+          if (fe >= 0 && ph.pdf.thr[fe] >= 0) mq2 = ph.pdf.m2[fe];
+        }
+        if (mq2 > 0.0 && !(tmax > mq2 * (1.0 + kHqFloor))) continue;
         double zm, delta;
         if (!z_limits(type, cf.t_cut, s, eta, zm, delta)) continue;
         ChannelOver ov = channel_over(ch, type, cf.nf);
@@ -767,11 +826,12 @@ void shower_step(const Physics& ph, Event& ev) {
         if (!(cc > 0.0)) continue;
         ev.cnt.trials += 1;
         if (type != kFF && type != kFI) ev.cnt.isr_trials += 1;
-        double tt = tmax * ex(lg(Rt) / cc);
+        double tt = mq2 > 0.0 ? mq2 + (tmax - mq2) * ex(lg(Rt) / cc) : tmax * ex(lg(Rt) / cc);
+        if (mq2 > 0.0 && !(tt > mq2 * (1.0 + kHqFloor))) continue;  // below the channel's floor
         if (tt > best.t) {
           best.i = i; best.k = k; best.side = side; best.ch = ch; best.type = type;
           best.t = tt; best.Rz = Rz; best.c = cc; best.shape = ov.shape; best.coef = ov.coef;
-          best.zm = zm; best.delta = delta; best.s = s; best.eta = eta; best.B = B;
+          best.zm = zm; best.delta = delta; best.s = s; best.eta = eta; best.B = B; best.m2 = mq2;
         }
       }
     }
@@ -866,6 +926,8 @@ void shower_step(const Physics& ph, Event& ev) {
       F1 = ph.pdf.xf(num, eta / x, t);
     }
     double Fratio = (F0 > 0.0) ? F1 / F0 : 0.0;
+    // heavy-quark measure correction: the ratio times (t - m_q^2)/t
+    if (best.m2 > 0.0) Fratio = Fratio * ((t - best.m2) / t);
     // f_a(eta/x)/f(eta) = x F_a(eta/x)/F(eta): the factor x is part of the
     // bounded kernel product
     w = as_ratio * k * J * x / pover * Fratio / best.B;

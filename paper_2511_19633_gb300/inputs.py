@@ -15,6 +15,12 @@ sbar, cbar, bbar.
           (so that the valence number sum rules give 2 and 1)
   sea     (a, b) = (-0.2, 7), N = 0.1 (every antiquark, s, c, b)
   u = u_v + sea, d = d_v + sea
+With heavy-quark thresholds (synthetic_pdf_grid(thresholds=True), the
+stand-in for a PDF whose c and b densities vanish at their masses, App. A.2):
+the c, b, cbar and bbar densities are sea(x) (1 - m_q^2/Q^2) above m_q^2 and
+zero at and below it, with m_c^2 and m_b^2 on Q^2 nodes 3 and 9 of the grid
+(1.674 and 18.73 GeV^2, m_c = 1.29 GeV, m_b = 4.33 GeV), so that the
+interpolated density vanishes exactly at the mass.
 """
 from __future__ import annotations
 
@@ -73,12 +79,22 @@ def synthetic_flavour_xf(flavour: str, x: np.ndarray) -> np.ndarray:
     return sea
 
 
-def synthetic_pdf_grid() -> np.ndarray:
+# Q^2 node of each heavy flavour's mass (thresholded table)
+HQ_THRESHOLD_NODE = {"c": 3, "b": 9, "cbar": 3, "bbar": 9}
+
+
+def synthetic_pdf_grid(thresholds: bool = False) -> np.ndarray:
     """float32 array [11][100][50] of x f(x, Q^2) on the grid nodes."""
     x = x_nodes()
+    q2 = q2_nodes()
     grid = np.empty((PDF_NFL, PDF_NX, PDF_NQ), dtype=np.float64)
     for i, fl in enumerate(FLAVOURS):
         grid[i] = synthetic_flavour_xf(fl, x)[:, None]
+        if thresholds and fl in HQ_THRESHOLD_NODE:
+            k0 = HQ_THRESHOLD_NODE[fl]
+            h = np.zeros(PDF_NQ)
+            h[k0 + 1:] = 1.0 - q2[k0] / q2[k0 + 1:]
+            grid[i] *= h[None, :]
     return np.ascontiguousarray(grid.astype(np.float32))
 
 

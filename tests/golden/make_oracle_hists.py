@@ -47,6 +47,9 @@ WORKLOADS = {
     # (events 0 .. 1e6 - 1 of seed 1): the mixed-precision path's error per
     # observable on the same events
     "pp_nlo_seed1": (2, 13600.0, 1_000_000, 1.0, 1),
+    # NLO pp -> Z with the thresholded synthetic table (c and b densities that
+    # vanish at their masses): the heavy-quark measure correction of App. A.2
+    "pp_nlo_hq": (2, 13600.0, 2_000_000, 1.0, 2, "thresholds"),
 }
 SEED = 2
 
@@ -81,9 +84,10 @@ def make(name: str, threads: int, n_override: int | None = None) -> dict:
     from paper_2511_19633_gb300 import inputs
     process, sqrt_s, n, t_cut = WORKLOADS[name][:4]
     seed = WORKLOADS[name][4] if len(WORKLOADS[name]) > 4 else SEED
+    thresholds = len(WORKLOADS[name]) > 5 and WORKLOADS[name][5] == "thresholds"
     if n_override:
         n = n_override
-    pdf = inputs.synthetic_pdf_grid()
+    pdf = inputs.synthetic_pdf_grid(thresholds=thresholds)
     family = "ee" if process == 0 else "pp"
     st = O.Settings(process=process, sqrt_s=sqrt_s, t_cut=t_cut, nmax=128, seed=seed)
     hsum = np.zeros((6, NBINS))
@@ -100,6 +104,7 @@ def make(name: str, threads: int, n_override: int | None = None) -> dict:
         fill(hsum, hsum2, r["obs"][done], r["weight"][done], family)
         counters += r["counters"].astype(np.int64).sum(0)
     return {"workload": name, "process": process, "sqrt_s": sqrt_s, "t_cut": t_cut, "events": n, "seed": seed,
+            "pdf": "thresholded" if thresholds else "plain",
             "not_done": bad, "binning": BINNING[family], "sumw": hsum.tolist(), "sumw2": hsum2.tolist(),
             "oracle_counters": dict(zip(("steps", "trials", "isr_trials", "vetoes", "accepts",
                                          "violations"), counters.tolist())),
