@@ -1,8 +1,10 @@
-"""Launch-shape autotuner for the persistent mixed-precision shower.
+"""Launch-shape autotuner for the mixed-precision shower.
 
-Sweeps threads per block x resident blocks per SM x refill (compaction)
-period x emission batch on a sample of the workload, timing gaps_shower with
-CUDA events, and returns the fastest shape with the whole table. The sample
+Sweeps, on a sample of the workload, threads per block x resident blocks per
+SM x refill (compaction) period x emission batch for the persistent schedule,
+or block shape x wavefront passes x veto cycles per pass for the wavefront
+schedule, timing gaps_shower with CUDA events, and returns the fastest shape
+with the whole table. The sample
 must give every lane of the widest grid several events (2^21 events for up to
 155 648 lanes), or the tail of the launch decides. The paper
 tunes a single block size for all its kernels by hand (Section 3.2); here the
@@ -22,15 +24,24 @@ DEFAULT_GRID = {
     "refill_period": (1, 4),
     "emit_batch": (8, 16),
 }
+WAVE_GRID = {
+    "block_size": (256,),
+    "blocks_per_sm": (2, 3, 4),
+    "wave_passes": (16, 24, 32),
+    "wave_cycles": (32, 64),
+    "refill_period": (1,),
+    "emit_batch": (16,),
+}
 
 
 def time_shape(process, sqrt_s, pdf, shape: dict, n_events: int, precision=G.GAPS_MIXED,
-               first: int = 1 << 44, reps: int = 1, mix=None, learned=None) -> dict:
+               first: int = 1 << 44, reps: int = 1, mix=None, learned=None,
+               schedule=G.GAPS_SCHED_PERSISTENT) -> dict:
     """Shower time of one launch shape; mix: rows of a mixed batch; learned:
     (params, log_margins) of the learned proposal."""
     uses_pdf = process or (mix and any(r[0] for r in mix))
     cfg = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf else None, nmax=128,
-                        precision=precision, schedule=G.GAPS_SCHED_PERSISTENT, mix=mix, **shape)
+                        precision=precision, schedule=schedule, mix=mix, **shape)
     ctx = G.gaps_init(cfg)
     try:
         if learned is not None:
@@ -60,15 +71,16 @@ def time_shape(process, sqrt_s, pdf, shape: dict, n_events: int, precision=G.GAP
 
 
 def autotune(process, sqrt_s, pdf, n_events: int = 1 << 21, grid: dict | None = None,
-             precision=G.GAPS_MIXED, mix=None, learned=None) -> dict:
-    grid = grid or DEFAULT_GRID
+             precision=G.GAPS_MIXED, mix=None, learned=None, schedule=G.GAPS_SCHED_PERSISTENT) -> dict:
+    grid = grid or (WAVE_GRID if schedule == G.GAPS_SCHED_WAVE else DEFAULT_GRID)
     keys = list(grid)
     table = []
     for values in itertools.product(*(grid[k] for k in keys)):
         shape = dict(zip(keys, values))
         if shape.get("block_size", 128) * shape.get("blocks_per_sm", 1) > 2048:
             continue  # more threads than an SM holds
-        table.append(time_shape(process, sqrt_s, pdf, shape, n_events, precision, mix=mix, learned=learned))
+        table.append(time_shape(process, sqrt_s, pdf, shape, n_events, precision, mix=mix, learned=learned,
+                                schedule=schedule))
     best = min(table, key=lambda r: r["ms"])
     return {"best": {k: best[k] for k in keys}, "best_events_per_s": best["events_per_s"],
             "sample_events": n_events, "table": table}

@@ -77,24 +77,56 @@ namespace gaps {
 // ingredients of the certified PDF-ratio bound (index 11 = sum of the ten
 // quark and antiquark densities). `out` holds kBoundTableDoubles values:
 // umax [12][NX], sufmax [12][NX+1], lmin [12][NX].
-void build_bound_tables(const float* g, double* out) {
+//
+// Heavy-quark thresholds (App. A.2): a c, b, cbar or bbar table whose nodes
+// vanish for every x on all Q^2 nodes up to k0 and are positive above has its
+// mass on node k0; for it lmin is the minimum over the nodes above k0 and
+// first[f][ix] the value on node k0 + 1 (the tables of the measure
+// correction's bound). thr / m2 (when not NULL, [12]) receive k0 (-1: none)
+// and the mass squared, exp(ln Q2min + k0 dlq).
+void build_bound_tables(const float* g, double* out, int* thr, double* m2) {
   const int NX = GAPS_PDF_NX, NQ = GAPS_PDF_NQ;
   double* umax = out;
   double* sufmax = umax + 12 * NX;
   double* lmin = sufmax + 12 * (NX + 1);
+  double* first = lmin + 12 * NX;
   auto node = [&](int f, int ix, int iq) -> double {
     if (f < 11) return (double)g[((size_t)f * NX + ix) * NQ + iq];
     double s = 0.0;
     for (int k = 1; k <= 10; ++k) s += (double)g[((size_t)k * NX + ix) * NQ + iq];
     return s;
   };
+  auto threshold = [&](int f) -> int {
+    if (f != 4 && f != 5 && f != 9 && f != 10) return -1;
+    int k0 = -1;
+    for (int iq = 0; iq < NQ; ++iq) {
+      bool zero = true;
+      for (int ix = 0; ix < NX && zero; ++ix) zero = node(f, ix, iq) == 0.0;
+      if (!zero) break;
+      k0 = iq;
+    }
+    if (k0 < 0 || k0 >= NQ - 1) return -1;
+    for (int iq = k0 + 1; iq < NQ; ++iq)
+      for (int ix = 0; ix < NX; ++ix)
+        if (!(node(f, ix, iq) > 0.0)) return -1;
+    return k0;
+  };
+  const double lqmin = gm_log(GAPS_PDF_Q2MIN);
+  const double dlq = (gm_log(GAPS_PDF_Q2MAX) - lqmin) / (GAPS_PDF_NQ - 1);
   for (int f = 0; f < 12; ++f) {
+    const int k0 = f < 11 ? threshold(f) : -1;
+    if (thr) thr[f] = k0;
+    if (m2) m2[f] = k0 >= 0 ? gm_exp(lqmin + (double)k0 * dlq) : 0.0;
     for (int ix = 0; ix < NX; ++ix) {
-      double mx = node(f, ix, 0), mn = mx;
+      first[f * NX + ix] = k0 >= 0 ? node(f, ix, k0 + 1) : 0.0;
+      double mx = node(f, ix, 0), mn = 0.0;
       for (int iq = 1; iq < NQ; ++iq) {
         double v = node(f, ix, iq);
         if (v > mx) mx = v;
-        if (v < mn) mn = v;
+      }
+      for (int iq = k0 + 1; iq < NQ; ++iq) {
+        double v = node(f, ix, iq);
+        if (iq == k0 + 1 || v < mn) mn = v;
       }
       umax[f * NX + ix] = mx;
       lmin[f * NX + ix] = mn;
@@ -104,6 +136,21 @@ void build_bound_tables(const float* g, double* out) {
       double a = umax[f * NX + ix], b = sufmax[f * (NX + 1) + ix + 1];
       sufmax[f * (NX + 1) + ix] = a > b ? a : b;
     }
+  }
+}
+
+// the device tables of a context or call: pointers into one array of
+// kBoundTableDoubles values and the thresholds of the host grid
+void set_bound_tables(DevParams& P, const double* t, const float* host_grid) {
+  P.umax = t;
+  P.sufmax = t + 12 * GAPS_PDF_NX;
+  P.lmin = t + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
+  P.first = t + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1) + 12 * GAPS_PDF_NX;
+  std::vector<double> tmp(kBoundTableDoubles);
+  if (host_grid) {
+    build_bound_tables(host_grid, tmp.data(), P.thr, P.m2);
+  } else {
+    for (int f = 0; f < 12; ++f) { P.thr[f] = -1; P.m2[f] = 0.0; }
   }
 }
 
@@ -175,6 +222,16 @@ int validate_config(const gaps_config& c) {
     const size_t gsz = (size_t)GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ;
     for (size_t q = 0; q < gsz; ++q)
       if (!std::isfinite(c.pdf_grid[q]) || c.pdf_grid[q] < 0.0f) return GAPS_ERR_INVALID_ARG;
+    // heavy-quark thresholds: the measure correction is built into the FP64
+    // kernels and the mixed-precision trials of the kept and redrawn schemes
+    std::vector<double> tmp(kBoundTableDoubles);
+    int thr[12];
+    build_bound_tables(c.pdf_grid, tmp.data(), thr, nullptr);
+    bool heavy = false;
+    for (int f = 0; f < 12; ++f) heavy = heavy || thr[f] >= 0;
+    if (heavy && c.precision == GAPS_MIXED &&
+        (c.schedule == GAPS_SCHED_WARP || c.trial_mode == GAPS_TRIALS_SELECT || c.trial_mode == GAPS_TRIALS_VETOMAX))
+      return GAPS_ERR_INVALID_ARG;
   }
   return GAPS_OK;
 }
@@ -333,9 +390,7 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
   DevParams& P = ctx->P;
   fill_params(c, P);
   P.grid = ctx->d_grid;
-  P.umax = ctx->d_tables;
-  P.sufmax = ctx->d_tables + 12 * GAPS_PDF_NX;
-  P.lmin = ctx->d_tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
+  set_bound_tables(P, ctx->d_tables, c.pdf_grid);
   P.counters = ctx->d_counters;
   for (int r = 0; r < P.n_rows; ++r) set_hist_defs(P.rows[r].process, ctx->H.h[r]);
   *out = ctx;

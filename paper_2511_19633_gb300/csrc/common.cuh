@@ -48,7 +48,10 @@ struct DevParams {
   const float* grid;      // [11][100][50] x f
   const double* umax;     // [12][100] max over Q^2 nodes (index 11 = sum of quarks)
   const double* sufmax;   // [12][101] suffix max over x nodes of umax
-  const double* lmin;     // [12][100] min over Q^2 nodes
+  const double* lmin;     // [12][100] min over Q^2 nodes (above the threshold of a heavy flavour)
+  const double* first;    // [12][100] node value on the first Q^2 node above a heavy flavour's threshold
+  int thr[12];            // Q^2 node of a heavy flavour's mass (c, b, cbar, bbar), -1: no threshold
+  double m2[12];          // that mass squared (the node's Q^2), 0 without a threshold
   double lxmin, dlx, lqmin, dlq;
   unsigned long long* counters;  // [C_NCOUNTERS]
 };
@@ -105,8 +108,11 @@ struct LearnedCfg {
 };
 
 // host helpers shared by the entry points (api.cu); none allocates memory
-constexpr int kBoundTableDoubles = 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1) + 12 * GAPS_PDF_NX;
-void build_bound_tables(const float* grid, double* out);
+constexpr int kBoundTableDoubles = 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1) + 12 * GAPS_PDF_NX + 12 * GAPS_PDF_NX;
+// heavy-quark trials of the measure dt/(t - m^2) end at m^2 (1 + kHqFloor)
+constexpr double kHqFloor = 1e-3;
+void build_bound_tables(const float* grid, double* out, int* thr = nullptr, double* m2 = nullptr);
+void set_bound_tables(DevParams& P, const double* dev_tables, const float* host_grid);
 int validate_config(const gaps_config& c);
 void fill_params(const gaps_config& c, DevParams& P);
 int grid_q_independent(const float* grid);

@@ -254,7 +254,7 @@ cudaError_t launch_mlp_image(const float* params, void* image, cudaStream_t stre
   k_mlp_image<<<1, 256, 0, stream>>>(params, reinterpret_cast<MlpSmem*>(image));
   return cudaGetLastError();
 }
-size_t mlp_image_bytes() { return sizeof(MlpSmem); }
+size_t mlp_image_bytes() { return kMlpSmemBytes; }
 
 }  // namespace gaps
 

@@ -62,6 +62,14 @@ __device__ __forceinline__ double pdf_ratio_bound(const DevParams& P, int num, i
   double un = fmax(uin, __ldg(&P.sufmax[num * (kNX + 1) + ix + 1]));
   double ld = (1.0 - fx) * __ldg(&P.lmin[den * kNX + ix]) + fx * __ldg(&P.lmin[den * kNX + ix + 1]);
   if (!(ld > 0.0)) return 0.0;
+  if (P.thr[den] >= 0) {
+    // heavy denominator with a threshold: the bound of the ratio times
+    // (t - m^2)/t, dlq x numerator / first in the first cell above the mass,
+    // numerator / lmin above it (App. A.2)
+    double fd = (1.0 - fx) * __ldg(&P.first[den * kNX + ix]) + fx * __ldg(&P.first[den * kNX + ix + 1]);
+    if (!(fd > 0.0)) return 0.0;
+    return un * fmax(P.dlq / fd, 1.0 / ld);
+  }
   return un / ld;
 }
 

@@ -22,6 +22,7 @@ struct Counters {
 struct Winner {
   int i, k, side, ch, type, shape;
   double t, Rz, coef, zm, delta, s, eta, B;
+  double m2;  // heavy-quark measure dt/(t - m2) of the trial, 0: dt/t
 };
 
 // One max-veto cycle for event e. Returns the new status (ACTIVE, DONE or an
@@ -32,6 +33,7 @@ __device__ int shower_step(const DevParams& P, const DevEvents& E, uint64_t e, i
   Winner best;
   best.t = -1.0;
   best.i = -1;
+  best.m2 = 0.0;
   for (int i = 0; i < n; ++i) {
     int ci = E.C(i, e), ai = E.A(i, e);
     if (ci == 0 && ai == 0) continue;
@@ -63,6 +65,15 @@ __device__ int shower_step(const DevParams& P, const DevEvents& E, uint64_t e, i
         rng.next2(Rt, Rz);
         double tmax = fmin(t, t_kin_max(type, s, eta));
         if (!(tmax > P.t_cut)) continue;
+        // heavy-quark measure correction (App. A.2): an incoming c or b with a
+        // threshold draws its q <- q and q <- g trials in dt/(t - m_q^2), down to
+        // m_q^2 (1 + kHqFloor)
+        double mq2 = 0.0;
+        if ((type == kIF || type == kII) && (ch == 3 || ch == 4)) {
+          const int fe = pdf_index(fi);
+          if (fe >= 0 && P.thr[fe] >= 0) mq2 = P.m2[fe];
+        }
+        if (mq2 > 0.0 && !(tmax > mq2 * (1.0 + kHqFloor))) continue;
         double zm, delta;
         if (!z_limits(type, P.t_cut, s, eta, zm, delta)) continue;
         int shape;
@@ -82,11 +93,12 @@ __device__ int shower_step(const DevParams& P, const DevEvents& E, uint64_t e, i
         if (!(cc > 0.0)) continue;
         cnt.trials += 1;
         if (type == kIF || type == kII) cnt.isr_trials += 1;
-        double tt = tmax * gm_exp(gm_log(Rt) / cc);
+        double tt = mq2 > 0.0 ? mq2 + (tmax - mq2) * gm_exp(gm_log(Rt) / cc) : tmax * gm_exp(gm_log(Rt) / cc);
+        if (mq2 > 0.0 && !(tt > mq2 * (1.0 + kHqFloor))) continue;  // below the channel's floor
         if (tt > best.t) {
           best.i = i; best.k = k; best.side = side; best.ch = ch; best.type = type;
           best.t = tt; best.Rz = Rz; best.shape = shape; best.coef = coef;
-          best.zm = zm; best.delta = delta; best.s = s; best.eta = eta; best.B = B;
+          best.zm = zm; best.delta = delta; best.s = s; best.eta = eta; best.B = B; best.m2 = mq2;
         }
       }
     }
@@ -168,6 +180,7 @@ __device__ int shower_step(const DevParams& P, const DevEvents& E, uint64_t e, i
       F1 = pdf_xf(P, num, eta / x, tw);
     }
     double Fratio = (F0 > 0.0) ? F1 / F0 : 0.0;
+    if (best.m2 > 0.0) Fratio = Fratio * ((tw - best.m2) / tw);  // heavy-quark measure correction
     w = as_ratio * k * J * x / pover * Fratio / best.B;
     if (ch == 4) { new_fl_i = 21; fl_j = -fl_i; }
     if (ch == 5) { new_fl_i = 21; fl_j = 21; }

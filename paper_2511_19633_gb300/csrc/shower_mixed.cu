@@ -53,6 +53,10 @@ struct SmemPdf {
   float umax[12][kSmNX];
   float sufmax[12][kSmNX + 1];
   float lmin[12][kSmNX];
+  // heavy-quark thresholds (App. A.2): node values above the mass and the
+  // mass squared (0: no threshold)
+  float first[12][kSmNX];
+  float m2[12];
   // per row of a mixed batch: ln t_c, alpha_s(t_c) / 2 pi, pp process
   float lnTc[kMaxRows], asOver2pi[kMaxRows];
   int pp[kMaxRows];
@@ -147,8 +151,32 @@ __device__ __noinline__ float bound32(const MixedCtx& M, const SmemPdf& S, int n
   float un = fmaxf(uin, S.sufmax[num][ix + 1]);
   float ld = (1.0f - fx) * S.lmin[den][ix] + fx * S.lmin[den][ix + 1];
   if (!(ld > 0.0f)) return 0.0f;
+  if (S.m2[den] > 0.0f) {
+    // heavy denominator with a threshold: bound of the ratio times (t - m^2)/t
+    const float fd = (1.0f - fx) * S.first[den][ix] + fx * S.first[den][ix + 1];
+    if (!(fd > 0.0f)) return 0.0f;
+    return un * fmaxf(M.dlqf / fd, 1.0f / ld) * 1.0001f;
+  }
   // relative slack for the rounding of the FP32 interpolation
   return un / ld * 1.0001f;
+}
+
+// Mass squared of the heavy-quark measure of end q's channels: an incoming c
+// or b whose density has a threshold (both its channels, q <- q and q <- g,
+// draw in dt/(t - m^2)); 0 for every other end.
+__device__ __forceinline__ float end_m2(const SmemPdf& S, const float4& aux, int q, int row) {
+  if (q >= 4 || !S.pp[row]) return 0.0f;
+  const int fe = pdf_index(tag_fl(__float_as_uint(aux.z)));
+  return fe > 0 ? S.m2[fe] : 0.0f;
+}
+
+// ln of a channel's next trial scale below t_max: t_max R^(1/c) in the
+// measure dt/t, or m^2 + (t_max - m^2) R^(1/c) in dt/(t - m^2) for a heavy
+// quark (m2 > 0), -infinity below the heavy channel's floor m^2 (1 + 1e-3)
+__device__ __forceinline__ float trial_lnt(float lnTmax, float ic, float lnR, float m2) {
+  if (!(m2 > 0.0f)) return fmaf(lnR, ic, lnTmax);
+  const float t = m2 + (__expf(lnTmax) - m2) * __expf(lnR * ic);
+  return t > m2 * (1.0f + (float)kHqFloor) ? __logf(t) : -INFINITY;
 }
 
 // ---- FP32 kinematic limits and overestimate shapes -------------------------
@@ -352,7 +380,11 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
   const float F0 = pdf32(M, S, den, eta, tw);
   const float F1 = pdf32(M, S, num, eta / x, tw);
   if (ch == 6) e.sumF = F1;
-  const float Fratio = F0 > 0.0f ? F1 / F0 : 0.0f;
+  float Fratio = F0 > 0.0f ? F1 / F0 : 0.0f;
+  if (ch == 3 || ch == 4) {
+    const float m2 = S.m2[pdf_index(fl_i)];
+    if (m2 > 0.0f) Fratio *= (tw - m2) / tw;  // heavy-quark measure correction
+  }
   e.r = B > 0.0f ? kk * J * x / pover * Fratio / B : 0.0f;
   e.ok = true;
   return e;
@@ -472,7 +504,7 @@ __device__ __forceinline__ void set_end(const W& w, int q, const float4& rec, in
 __device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& mlp, const LearnedSmem& ls,
                                              float (*stage)[4], float* ustage, unsigned eval, float tc,
                                              float isr_eta, float isr_s, int isr_type, int fl_i, int slot_j, int q_j,
-                                             int lane_id, float& scale0, float& scale1) {
+                                             int lane_id, float& scale0, float& scale1, bool four = false) {
   int cls_j[2];  // margin row: (class, eta bucket)
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -498,8 +530,12 @@ __device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& m
     if ((eval >> (r >> 4)) & 1u) mg[j] = __ldg(&M.Lc.mlp[kMlpParams + cls_j[j] * kIsrBins + (r & 7)]);
   }
   __syncwarp();
-  for (int tile = 0; tile < 4; ++tile)
-    if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
+  if (four) {
+    mlp_tile4(mlp, stage, ustage);  // all four tiles (rows of unselected ends unused)
+  } else {
+    for (int tile = 0; tile < 4; ++tile)
+      if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
+  }
   __syncwarp();
   float tot[2];
 #pragma unroll
@@ -1261,40 +1297,54 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
   uint64_t d = L.draw;
   const bool select = M.P.trial_mode == GAPS_TRIALS_SELECT;
   if (select) select_trial(w, ne, L.lnT, lnTc, pp, e0, e1, k0, k1, d, cnt, best, bq, bch, bRz);
-  // one copy of the trial code (instruction-cache footprint); the next end's
-  // load is issued before the current end's trials
-  const float4 marked = make_float4(__uint_as_float(0x7fc00000u), 0.5f, -INFINITY, 0.5f);
-  float4 nxt = cache ? w.Trial(0) : marked;
+  // the ends' trials: with kept trials the ends are read four at a time (four
+  // loads in flight), and only ends a rebuild marked draw, one by one in
+  // canonical order; redrawing every cycle, every end draws. One copy of the
+  // drawing code (instruction-cache footprint).
+  const float4 none = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+  const int nq = select ? 0 : ne;
 #pragma unroll 1
-  for (int q = 0; q < (select ? 0 : ne); ++q) {
-    float4 tr = nxt;
-    if (cache && q + 1 < ne) nxt = w.Trial(q + 1);
-    if (isnan(tr.x)) {  // this end draws
-      tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
-      const float4 rec = w.End(q);
-      if (__float_as_int(rec.w) >= 0) {  // a dipole on this side
-        const float lnTmax = fminf(L.lnT, rec.z);
-        const bool live = lnTmax > lnTc;
+  for (int q0 = 0; q0 < nq; q0 += 4) {
+    float4 t4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t4[j] = (cache && q0 + j < nq) ? w.Trial(q0 + j) : none;
+    const bool draws = !cache || isnan(t4[0].x) || isnan(t4[1].x) || isnan(t4[2].x) || isnan(t4[3].x);
+    if (draws) {
 #pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-          const float ic = c == 0 ? rec.x : rec.y;  // 1/c
-          if (ic < 0.0f) continue;  // channel absent for this emitter
-          const uint64_t dd = d++;
-          if (!(live && ic > 0.0f)) continue;
-          uint32_t out[4];
-          philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
-          cnt.trials += 1;
-          if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
-          const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);  // ln(t_max R^(1/c))
-          if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
-          else { tr.z = lt; tr.w = u24(out[3]); }
+      for (int q = q0; q < q0 + 4 && q < nq; ++q) {
+        if (cache && !isnan(w.Trial(q).x)) continue;  // kept
+        float4 tr = none;
+        const float4 rec = w.End(q);
+        if (__float_as_int(rec.w) >= 0) {  // a dipole on this side
+          const float lnTmax = fminf(L.lnT, rec.z);
+          const bool live = lnTmax > lnTc;
+          const float m2 = q < 4 ? end_m2(S, w.Aux(q), q, L.row) : 0.0f;
+#pragma unroll 1
+          for (int c = 0; c < 2; ++c) {
+            const float ic = c == 0 ? rec.x : rec.y;  // 1/c
+            if (ic < 0.0f) continue;  // channel absent for this emitter
+            const uint64_t dd = d++;
+            if (!(live && ic > 0.0f)) continue;
+            uint32_t out[4];
+            philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
+            cnt.trials += 1;
+            if (pp && q < 4) cnt.isr_trials += 1;  // emitter in slot 0 or 1
+            const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);  // ln(t_max R^(1/c))
+            if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
+            else { tr.z = lt; tr.w = u24(out[3]); }
+          }
         }
+        w.Trial(q) = tr;  // with redraw, the cycle's trials (read back below)
       }
-      if (cache) w.Trial(q) = tr;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t4[j] = q0 + j < nq ? w.Trial(q0 + j) : none;
     }
     // the largest wins, the earlier one on ties
-    if (tr.x > best) { best = tr.x; bq = q; bch = 0; bRz = tr.y; }
-    if (tr.z > best) { best = tr.z; bq = q; bch = 1; bRz = tr.w; }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (t4[j].x > best) { best = t4[j].x; bq = q0 + j; bch = 0; bRz = t4[j].y; }
+      if (t4[j].z > best) { best = t4[j].z; bq = q0 + j; bch = 1; bRz = t4[j].w; }
+    }
   }
   L.draw = d;
   const int st = step_veto(M, S, ls, w, L, id, cnt, pend, parked, best, bq, bch, bRz);
@@ -1310,7 +1360,8 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
       philox(e0, e1, (uint32_t)dd, (uint32_t)(dd >> 32), k0, k1, out);
       cnt.trials += 1;
       if (pp && bq < 4) cnt.isr_trials += 1;
-      lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+      const float m2 = bq < 4 ? end_m2(S, w.Aux(bq), bq, L.row) : 0.0f;
+      lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
       rz = u24(out[3]);
     }
     float4 tr = w.Trial(bq);
@@ -1409,6 +1460,8 @@ __device__ __forceinline__ void mixed_prologue(const MixedCtx& M, SmemPdf& S, un
   }
   for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
     S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) S.first[q / kSmNX][q % kSmNX] = (float)M.P.first[q];
+  if (threadIdx.x < 12) S.m2[threadIdx.x] = (float)M.P.m2[threadIdx.x];
   load_rows(S, M.P);
 }
 
@@ -1751,6 +1804,7 @@ __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const Sm
         uint64_t dd = d + (uint64_t)(inc - nd);
         const float lnTmax = fminf(lnT, rec.z);
         const bool live = lnTmax > lnTc;
+        const float m2 = q < 4 ? end_m2(S, w.Aux(q), q, row) : 0.0f;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const float ic = c == 0 ? rec.x : rec.y;  // 1/c
@@ -1761,7 +1815,7 @@ __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const Sm
           philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
           cnt.trials += 1;
           if (pp && q < 4) cnt.isr_trials += 1;
-          const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+          const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
           if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
           else { tr.z = lt; tr.w = u24(out[3]); }
         }
@@ -1780,17 +1834,19 @@ template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__ MixedCtx M) {
   __shared__ SmemPdf S;
   extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
-  MixedSmem D;
-  mixed_prologue(M, S, dyn_lane_smem, D);
-  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
-  __syncthreads();
+  const uint64_t count = M.V.ctl[WL_REBUILD];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     M.V.ctl[WL_LIVE0 + (M.wave_par ^ 1)] = 0;  // the next pass's live list
     M.V.ctl[WL_EMIT] = 0;
     M.V.ctl[WL_GRAB] = 0;
   }
+  // blocks past the list's last warp leave before loading their tables
+  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= count) return;
+  MixedSmem D;
+  mixed_prologue(M, S, dyn_lane_smem, D);
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  __syncthreads();
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
-  const uint64_t count = M.V.ctl[WL_REBUILD];
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
   unsigned long long rebuilds = 0, mlp_tiles = 0;
@@ -1840,10 +1896,17 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
 // counters the rebuild pass reserved for it, as the persistent kernel's
 // inline evaluation and first trial loop would give them.
 __global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedCtx M) {
+  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 4 >= M.V.ctl[WL_MLP]) return;  // nothing queued for this block
   __shared__ float dec[256];
   __shared__ float stage_s[8][64][4];
   __shared__ float ustage_s[8][64];
   __shared__ float lnTc[kMaxRows];
+  __shared__ __align__(16) unsigned char wimg[kMlpSmemBytes];  // the network's BF16 image
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(M.Lc.image);
+    uint4* dst = reinterpret_cast<uint4*>(wimg);
+    for (int k = threadIdx.x; k < (int)(kMlpSmemBytes / 16); k += blockDim.x) dst[k] = src[k];
+  }
   for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
   if (threadIdx.x < kMaxRows) {
     const RowParams& R = M.P.rows[threadIdx.x < M.P.n_rows ? threadIdx.x : 0];
@@ -1854,7 +1917,7 @@ __global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedC
   ls.code = M.W.lcode;
   ls.key = M.W.lkey;
   ls.dec = dec;
-  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
+  const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(wimg);
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
   const uint64_t count = M.V.ctl[WL_MLP];
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
@@ -1876,7 +1939,7 @@ __global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedC
     const float tc = have ? __expf(lnTc[row]) : 1.0f;
     float scale0 = 0.0f, scale1 = 0.0f;
     learned_heights(M, mlp_s, ls, stage_s[warp_id], ustage_s[warp_id], eval, tc, in.x, in.y, __float_as_int(in.z),
-                    __float_as_int(in.w), e, qq, lane_id, scale0, scale1);
+                    __float_as_int(in.w), e, qq, lane_id, scale0, scale1, true);
     tiles += __popc(eval);
     if (have) {
       const WS w{M.W, e, M.P.nmax};
@@ -1890,6 +1953,9 @@ __global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedC
       const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
       const float lnTmax = fminf(M.V.lnT[e], rec.z);
       const bool live = lnTmax > lnTc[row];
+      // heavy-quark measure of an incoming c or b (its two channels)
+      const int fe = pdf_index(tag_fl(__float_as_uint(w.Aux(qq).z)));
+      const float m2 = fe > 0 ? (float)M.P.m2[fe] : 0.0f;
       float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -1901,7 +1967,7 @@ __global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedC
         philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
         cnt.trials += 1;
         cnt.isr_trials += 1;
-        const float lt = fmaf(__logf(u24(out[1])), ic, lnTmax);
+        const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
         if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
         else { tr.z = lt; tr.w = u24(out[3]); }
       }
@@ -1919,17 +1985,19 @@ template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__ MixedCtx M) {
   __shared__ SmemPdf S;
   extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
-  MixedSmem D;
-  mixed_prologue(M, S, dyn_lane_smem, D);
-  const LearnedSmem& ls = D.ls;
-  __syncthreads();
+  const uint64_t n_work = M.V.ctl[M.wave_par];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     M.V.ctl[WL_REBUILD] = 0;  // filled by this pass's emissions
     M.V.ctl[WL_MLP] = 0;      // filled by the next pass's rebuilds
   }
+  // blocks with more lanes than the list has events leave before loading their tables
+  if ((uint64_t)blockIdx.x * blockDim.x >= n_work) return;
+  MixedSmem D;
+  mixed_prologue(M, S, dyn_lane_smem, D);
+  const LearnedSmem& ls = D.ls;
+  __syncthreads();
   const int lane_id = threadIdx.x & 31;
   const uint32_t* live = M.V.list + (size_t)M.wave_par * M.V.cap;
-  const uint64_t n_work = M.V.ctl[M.wave_par];
   const int next_live = WL_LIVE0 + (M.wave_par ^ 1);
   Lane L;
   L.slot = 0;
@@ -2006,9 +2074,10 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
 // persistent kernel's flush; the event joins the next live list and, when its
 // end table changed, the rebuild list.
 __global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ MixedCtx M) {
+  const uint64_t count = M.V.ctl[WL_EMIT];
+  if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
   const int lane_id = threadIdx.x & 31;
   const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
-  const uint64_t count = M.V.ctl[WL_EMIT];
   const int next_live = WL_LIVE0 + (M.wave_par ^ 1);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   Counters32 cnt;
@@ -2246,6 +2315,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(const __grid_constan
   }
   for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
     S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) S.first[q / kSmNX][q % kSmNX] = (float)M.P.first[q];
+  if (threadIdx.x < 12) S.m2[threadIdx.x] = (float)M.P.m2[threadIdx.x];
   load_rows(S, M.P);
   __syncthreads();
 
@@ -2378,6 +2449,8 @@ __global__ void k_isr_targets(const __grid_constant__ MixedCtx M, const float4* 
   }
   for (int q = threadIdx.x; q < 12 * (kSmNX + 1); q += blockDim.x)
     S.sufmax[q / (kSmNX + 1)][q % (kSmNX + 1)] = (float)M.P.sufmax[q];
+  for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) S.first[q / kSmNX][q % kSmNX] = (float)M.P.first[q];
+  if (threadIdx.x < 12) S.m2[threadIdx.x] = (float)M.P.m2[threadIdx.x];
   __syncthreads();
   const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n_states * 16) return;
@@ -2607,7 +2680,7 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
     if (tier == 2) k_wave_ends<2><<<blocks, block_size, dyn, stream>>>(M);
     else if (tier == 3) k_wave_ends<3><<<blocks, block_size, dyn, stream>>>(M);
     else k_wave_ends<4><<<blocks, block_size, dyn, stream>>>(M);
-    if (Lc.learned) k_wave_mlp<<<sm_count * 4, 256, 0, stream>>>(M);
+    if (Lc.learned) k_wave_mlp<<<sm_count * 2, 256, 0, stream>>>(M);
     if (w == passes) break;  // the last rebuilds, then the persistent kernel
     if (tier == 2) k_wave_veto<2><<<blocks, block_size, dyn, stream>>>(M);
     else if (tier == 3) k_wave_veto<3><<<blocks, block_size, dyn, stream>>>(M);
@@ -2721,9 +2794,7 @@ extern "C" int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, 
   if (cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * (C_NCOUNTERS + 1), st) != cudaSuccess)
     return GAPS_ERR_CUDA;
   P.grid = a.grid;
-  P.umax = a.tables;
-  P.sufmax = a.tables + 12 * GAPS_PDF_NX;
-  P.lmin = a.tables + 12 * GAPS_PDF_NX + 12 * (GAPS_PDF_NX + 1);
+  set_bound_tables(P, a.tables, cfg->pdf_grid);
   P.counters = a.counters;
   DevEvents E;
   E.cap = ev->capacity; E.nmax = ev->nmax; E.p = ev->p; E.flav = ev->flav; E.col = ev->col;

@@ -124,3 +124,17 @@ def test_cycle_cap_out_of_range_is_rejected(lib, pdf, value):
     with pytest.raises(G.GapsError) as e:
         G.gaps_init(cfg)
     assert e.value.code == G.GAPS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision,schedule,trial_mode", [(1, 2, 0), (1, 1, 2), (1, 1, 3)])
+def test_thresholded_grid_needs_a_supported_scheme(lib, precision, schedule, trial_mode):
+    """A table with heavy-quark thresholds (the measure correction of App.
+    A.2) runs in FP64 and in the mixed-precision kept or redrawn trials of the
+    persistent and wavefront schedules; the other combinations are rejected
+    before any device work."""
+    from paper_2511_19633_gb300 import gaps as G, inputs
+    g = inputs.synthetic_pdf_grid(thresholds=True)
+    cfg = G.make_config(2, 13600.0, pdf_grid=g, precision=precision, schedule=schedule, trial_mode=trial_mode)
+    with pytest.raises(G.GapsError) as e:
+        G.gaps_init(cfg)
+    assert e.value.code == G.GAPS_ERR_INVALID_ARG

@@ -104,14 +104,14 @@ def _gpu_hists(G, name, pdf, precision, n, first0=0, chunk=1 << 21, trial_mode=N
 
 
 @pytest.mark.parametrize("name,mode", [("ee91", 1), ("ee500", 1), ("pp_lo", 1), ("pp_nlo", 1), ("pp_ll", 1),
-                                       ("ee91", 2), ("pp_nlo", 2)])
+                                       ("ee91", 2), ("pp_nlo", 2), ("ee91", 3), ("pp_nlo", 3)])
 def test_mixed_histograms_match_oracle(G, pdf, name, mode):
     """chi^2/ndf < 1.2 against the FP64 oracle's histograms (independent seed,
     1e7 events) for samples of 1e7 events. With about 200 degrees of freedom a
     correct generator exceeds 1.2 on about 2.6% of samples, so the bar is put
     on the median of three independent event ranges (at least two of three
     samples pass), with 1.5 as the limit for every sample. Mode 1 keeps the
-    losing trials (the default), mode 2 is generate-select."""
+    losing trials (the default), mode 2 is generate-select, mode 3 veto-max."""
     import os
     from tests.hist_common import GOLDEN
     if not os.path.exists(os.path.join(GOLDEN, "oracle_hists_%s.json" % name)):
@@ -130,13 +130,15 @@ def test_mixed_histograms_match_oracle(G, pdf, name, mode):
     assert float(np.median(reds)) < 1.2 and max(reds) < 1.5, reds
 
 def test_trial_modes_need_persistent_mixed(G, pdf):
-    for mode in (G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT):
+    for mode in (G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT, G.GAPS_TRIALS_VETOMAX):
         for prec, sched in ((0, 0), (0, 1), (MIXED, 2)):
             with pytest.raises(G.GapsError) as e:
                 G.gaps_init(G.make_config(0, 91.2, precision=prec, schedule=sched, trial_mode=mode))
             assert e.value.code == G.GAPS_ERR_INVALID_ARG
+    with pytest.raises(G.GapsError):  # veto-max: the persistent schedule only
+        G.gaps_init(G.make_config(0, 91.2, precision=MIXED, schedule=3, trial_mode=G.GAPS_TRIALS_VETOMAX))
     with pytest.raises(G.GapsError):
-        G.gaps_init(G.make_config(0, 91.2, precision=MIXED, schedule=1, trial_mode=3))
+        G.gaps_init(G.make_config(0, 91.2, precision=MIXED, schedule=1, trial_mode=4))
 
 
 @pytest.mark.parametrize("name", ["ee500", "pp_nlo"])
@@ -148,14 +150,19 @@ def test_trial_modes_keep_distributions(G, pdf, name):
     proc, sqrt_s = PROCESS[name]
     n = 200003
     runs = {m: run_gpu(G, proc, sqrt_s, 31, n, pdf, precision=MIXED, schedule=1, trial_mode=m)
-            for m in (G.GAPS_TRIALS_REDRAW, G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT)}
+            for m in (G.GAPS_TRIALS_REDRAW, G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT, G.GAPS_TRIALS_VETOMAX)}
     for g in runs.values():
         assert np.all(g["status"] == 1) and g["stats"]["events"] == n and g["stats"]["violations"] == 0
     off = runs[G.GAPS_TRIALS_REDRAW]
     tr = {m: g["stats"]["trials"] for m, g in runs.items()}
     assert tr[G.GAPS_TRIALS_KEEP] < 0.8 * tr[G.GAPS_TRIALS_REDRAW], tr
     assert tr[G.GAPS_TRIALS_SELECT] < 0.8 * tr[G.GAPS_TRIALS_REDRAW], tr
-    for m in (G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT):
+    # veto-max evaluates the acceptance of every channel's trials, not only the
+    # winners': many more weights than max-veto's vetoes
+    vm = runs[G.GAPS_TRIALS_VETOMAX]["stats"]
+    kp = runs[G.GAPS_TRIALS_KEEP]["stats"]
+    assert vm["vetoes"] > 1.5 * kp["vetoes"], (vm["vetoes"], kp["vetoes"])
+    for m in (G.GAPS_TRIALS_KEEP, G.GAPS_TRIALS_SELECT, G.GAPS_TRIALS_VETOMAX):
         on = runs[m]
         # the hard process is drawn before the shower: identical in all
         assert np.array_equal(on["weight"], off["weight"])
@@ -171,7 +178,7 @@ def test_trial_modes_keep_distributions(G, pdf, name):
         assert abs(on["stats"]["accepts"] - off["stats"]["accepts"]) < 5 * np.sqrt(2 * off["stats"]["accepts"])
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("n", [0, 1, 33])
 def test_trial_modes_tiny_and_empty_batches(G, pdf, mode, n):
     proc, sqrt_s = PROCESS["pp_nlo"]
