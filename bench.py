@@ -35,7 +35,7 @@ WORKLOADS = {
     "pp_nlo_1e7": (2, 13600.0, 10_000_000, 1 << 22, 1, None,
                    "NLO-matched pp -> Z at 13.6 TeV, synthetic 100x50 PDF, 1e7 events per step in "
                    "chunks of 2^22, FP32 trials/PDF + FP64 kinematics, learned initial-state proposal, "
-                   "persistent compacted shower, one CUDA graph per step"),
+                   "wavefront shower over live-event lists, one CUDA graph per step"),
     "pp_lo_1e6_fp64": (1, 13600.0, 1_000_000, 1_000_000, 0, None,
                        "pp -> Z at 13.6 TeV, LO + initial/final-state shower, synthetic 100x50 PDF, "
                        "1e6 events, FP64 (per-event oracle parity)"),
@@ -293,7 +293,7 @@ def _plain_pass(G, ctx, ev, first, total, chunk, stream, marks=None):
         G.gaps_observables(ctx, first + f0, m, ev, None, None, stream)
 
 
-def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None):
+def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None, fit=None):
     """Events per second of one configuration over n events (after a warm-up
     pass), the shower kernels' own time, and the shower statistics."""
     import torch
@@ -301,6 +301,8 @@ def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None):
     try:
         if learned is not None:
             G.gaps_set_learned_proposal(ctx, *learned)
+        if fit is not None:
+            G.gaps_set_pdf_ratio_fit(ctx, fit)
         _plain_pass(G, ctx, ev, first - (1 << 40), min(n, 1 << 16), chunk, stream)
         torch.cuda.synchronize()
         G.gaps_reset_stats(ctx, stream)
@@ -318,6 +320,25 @@ def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None):
             "steps_per_event": st["steps"] / max(1, st["events"]),
             "trials_per_event": st["trials"] / max(1, st["events"]),
             "violations": st["violations"], "stats": st}
+
+
+def _pdf_ratio_fit(G, cfg, ev, first, n, stream):
+    """The paper's percentile fit of the PDF ratios (App. A.2), from the ratios
+    a shower with the certified bounds evaluates for n events."""
+    import torch
+    ctx = G.gaps_init(cfg)
+    try:
+        cap = 1 << 23
+        samples = torch.empty((cap, 4), dtype=torch.float32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        G.gaps_generate_hard(ctx, first, n, ev, stream)
+        G.gaps_collect_pdf_ratios(ctx, first, n, ev, samples, count, keep_fraction=0.1, stream=stream)
+        torch.cuda.synchronize()
+        m = min(int(count.item()), cap)
+        fit = G.gaps_fit_pdf_ratios(samples[:m].cpu().numpy())
+    finally:
+        G.gaps_destroy(ctx)
+    return fit, m
 
 
 def run_ours(args, ws, rank, local):
@@ -365,19 +386,30 @@ def run_ours(args, ws, rank, local):
                         "loss_last": res["loss_last"], "cells_calibrated": res["cells_calibrated"],
                         "fit_rmse": res["fit_rmse"], "pipeline": "gaps_train_learned_proposal (one C-ABI call)"}
 
+    # mixed precision: the wavefront schedule (default) or the persistent one;
+    # FP64: persistent or one thread per event
+    if mixed:
+        schedule = G.GAPS_SCHED_WAVE if args.schedule == 3 else G.GAPS_SCHED_PERSISTENT
+    else:
+        schedule = G.GAPS_SCHED_PERSISTENT if args.schedule else G.GAPS_SCHED_PER_EVENT
     shape = {"block_size": args.block, "blocks_per_sm": args.bps, "refill_period": args.period,
              "emit_batch": args.emit_batch}
+    if schedule == G.GAPS_SCHED_WAVE:
+        shape.update(wave_passes=args.passes, wave_cycles=args.cycles)
     tuning = None
     if mixed and not args.no_autotune:
         from paper_2511_19633_gb300 import autotune
-        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 21, mix=mix, learned=learned)
+        tuning = autotune.autotune(process, sqrt_s, pdf, n_events=1 << 21, mix=mix, learned=learned,
+                                   schedule=schedule)
         shape = tuning["best"]
-    schedule = G.GAPS_SCHED_PERSISTENT if (mixed or args.schedule) else G.GAPS_SCHED_PER_EVENT
 
-    def config(pdf_ptr=None, trial_mode=None):
+    def config(pdf_ptr=None, trial_mode=None, sched=None):
+        sh = dict(shape)
+        if sched is not None and sched != schedule:  # another schedule: its own defaults
+            sh = {"block_size": 256, "blocks_per_sm": 4, "refill_period": 1, "emit_batch": 16}
         c = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf and pdf_ptr is None else None, nmax=nmax,
-                          seed=1, precision=precision, schedule=schedule, mix=mix, trial_mode=trial_mode,
-                          **shape)
+                          seed=1, precision=precision, schedule=schedule if sched is None else sched, mix=mix,
+                          trial_mode=trial_mode, **sh)
         if pdf_ptr is not None:
             c.pdf_grid = pdf_ptr
         return c
@@ -424,7 +456,13 @@ def run_ours(args, ws, rank, local):
         from paper_2511_19633_gb300.sharding import max_over_ranks
         ms = max_over_ranks(ms, dist, device="cuda")
     value = total * args.steps * ws / (ms / 1e3)
-    launches = 3 * n_chunks * args.steps  # hard, shower and observables kernels per chunk
+    # kernels per chunk: hard process, the shower's kernels, observables
+    if schedule == G.GAPS_SCHED_WAVE:
+        P = shape.get("wave_passes", 24)
+        shower_kernels = 1 + (P + 1) * (2 if learned is not None else 1) + 2 * P + 2
+    else:
+        shower_kernels = 1
+    launches = (2 + shower_kernels) * n_chunks * args.steps
 
     # end to end through the C ABI with host buffers: a fresh context per step
     # (PDF grid and network from host memory), the full path as one graph,
@@ -455,7 +493,7 @@ def run_ours(args, ws, rank, local):
     # algorithm (FP64, one thread per event, no compaction, plain bound: the
     # paper's layout) and the compacted mixed-precision shower without the
     # learned proposal
-    plain = mixed_plain = trial_modes = None
+    plain = mixed_plain = trial_modes = persistent = None
     if not args.no_plain:
         n_plain = min(total, 1 << 19)
         cfgp = G.make_config(process, sqrt_s, pdf_grid=pdf if uses_pdf else None, nmax=nmax, seed=1,
@@ -468,15 +506,35 @@ def run_ours(args, ws, rank, local):
             mixed_plain["mode"] = "same shape and precision, plain bound (no learned proposal)"
             with_l = _time_variant(G, config(), ev, (1 << 51) + (1 << 24), n_mp, chunk, stream, learned)
             mixed_plain["learned_same_events"] = with_l
-        if mixed and schedule == G.GAPS_SCHED_PERSISTENT:
-            # the three trial schemes on the same events (max-veto redrawing
-            # every channel, max-veto keeping the losing trials, generate-select)
+            mixed_plain["learned_gain"] = with_l["value"] / mixed_plain["value"]
+            # the paper's fitted PDF-ratio overestimate in place of the certified
+            # bound (fit from other events; acceptance weights above one counted)
+            if uses_pdf:
+                fit, n_samples = _pdf_ratio_fit(G, config(), ev, (1 << 51) + (3 << 24), min(n_mp, 1 << 19), stream)
+                fitted = _time_variant(G, config(), ev, (1 << 51) + (1 << 24), n_mp, chunk, stream, None, fit)
+                fitted["mode"] = ("percentile-fitted PDF-ratio overestimate (App. A.2: max(P99, P99.99 eta), "
+                                  "P99.99 sqrt(eta) for g <- sum q), fit from %d sampled ratios; not a strict "
+                                  "bound, violations counted" % n_samples)
+                fitted["gain_vs_certified"] = fitted["value"] / mixed_plain["value"]
+                mixed_plain["fitted_pdf_bound"] = fitted
+        if mixed and schedule == G.GAPS_SCHED_WAVE:
+            # the persistent schedule (one kernel, lanes refilled) on the same events
+            n_mp = min(total, chunk)
+            persistent = _time_variant(G, config(sched=G.GAPS_SCHED_PERSISTENT), ev, (1 << 51) + (1 << 24), n_mp,
+                                       chunk, stream, learned)
+            persistent["mode"] = "persistent schedule, 256 x 4 per SM, same events and proposal"
+        if mixed:
+            # the trial schemes on the same events, persistent schedule: max-veto
+            # redrawing every channel, max-veto keeping the losing trials,
+            # generate-select, veto-max (plain bounds)
             n_tm = min(total, chunk)
             trial_modes = {}
             for mode_name, mode in (("redraw", G.GAPS_TRIALS_REDRAW), ("keep", G.GAPS_TRIALS_KEEP),
-                                    ("select", G.GAPS_TRIALS_SELECT)):
-                trial_modes[mode_name] = _time_variant(G, config(trial_mode=mode), ev, (1 << 51) + (2 << 24), n_tm,
-                                                  chunk, stream, learned)
+                                    ("select", G.GAPS_TRIALS_SELECT), ("vetomax", G.GAPS_TRIALS_VETOMAX)):
+                lrn = None if mode == G.GAPS_TRIALS_VETOMAX else learned
+                trial_modes[mode_name] = _time_variant(G, config(trial_mode=mode, sched=G.GAPS_SCHED_PERSISTENT), ev,
+                                                       (1 << 51) + (2 << 24), n_tm, chunk, stream, lrn)
+                trial_modes[mode_name]["learned_proposal"] = lrn is not None
 
     per_launch_events = total / n_chunks
     mean_shower_ms = sum(shower_ms) / max(1, len(shower_ms))
@@ -492,7 +550,10 @@ def run_ours(args, ws, rank, local):
         achieved = ops / (sum(shower_ms) / 1e3) / 1e12
         impl = implementation_ops_mixed(stats) / (sum(shower_ms) / 1e3) / 1e12
         bpe = SHOWER_DRAM_BYTES_PER_EVENT.get((name, learned is not None))
-        roof = {"bound": "alu", "kernel": SHOWER_KERNEL, "achieved": achieved, "peak": lane_peak,
+        kname = SHOWER_KERNEL if schedule != G.GAPS_SCHED_WAVE else (
+            "the shower phase of a chunk: k_wave_veto, k_wave_ends, k_wave_mlp, k_wave_emit, "
+            "k_wave_init/final and the k_shower_mixed drain, timed together")
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": lane_peak,
                 "unit": "Tops/s (operations of the scope's work units per second)",
                 "frac": achieved / lane_peak,
                 "traffic": None if bpe is None else bpe * per_launch_events,
@@ -528,7 +589,10 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic",
         "config": {"workload": name, "description": desc, "events_per_step": total, "chunk": chunk,
                    "parallelism": "independent event ranges per GPU" if ws > 1 else "single GPU",
-                   "schedule": "persistent, live-event refill" if schedule else "one thread per event",
+                   "schedule": {G.GAPS_SCHED_WAVE: "wavefront passes (rebuild, network, veto, emission kernels "
+                                                   "over live-event lists), persistent kernel for the last events",
+                                G.GAPS_SCHED_PERSISTENT: "persistent, live-event refill",
+                                G.GAPS_SCHED_PER_EVENT: "one thread per event"}[schedule],
                    "launch_shape": shape, "learned_proposal": learned is not None,
                    "cuda_graph": "one graph per step (all chunks), parameters updated in place",
                    "l2": "event records of %.1f GB per chunk rewritten every chunk (> 129 MB L2)"
@@ -540,6 +604,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "plain_gpu": plain,
         "mixed_plain_bound": mixed_plain,
+        "persistent_schedule": persistent,
         "trial_modes": trial_modes,
         # the paper's own GPU number for NLO pp -> Z (V100, FP64, CT14lo at 13 TeV,
         # partitioning, 128 threads per block): context, not the target
@@ -575,9 +640,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--events", type=int, default=0, help="override events per step")
-    ap.add_argument("--schedule", type=int, default=1)
-    ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--bps", type=int, default=8)
+    ap.add_argument("--schedule", type=int, default=3,
+                    help="mixed precision: 3 wavefront, 1 persistent; FP64: 1 persistent, 0 per event")
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--bps", type=int, default=4)
+    ap.add_argument("--passes", type=int, default=24)
+    ap.add_argument("--cycles", type=int, default=64)
     ap.add_argument("--period", type=int, default=1)
     ap.add_argument("--emit-batch", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")

@@ -280,10 +280,14 @@ int gaps_shower_static(const gaps_config* cfg, uint64_t first_event, uint64_t n,
  * piecewise constant over GAPS_ISR_BINS bins of zeta, the coordinate in which
  * z is sampled; bin heights come from a 4 -> 64 -> 64 -> 1 ReLU network with
  * inputs (ln eta, ln(s/t_c), bin centre in zeta, class of dipole type, channel
- * and flavour), evaluated with BF16 weights and FP32 accumulation. Every
- * acceptance weight is checked; a weight above one is counted as a violation
- * and the event continues with the plain certified bound, so the result is
- * the plain algorithm's whenever the violation count is zero.
+ * and flavour), evaluated with BF16 weights and FP32 accumulation. The
+ * heights are calibrated on sampled states, not certified: the acceptance
+ * weight of every winner (accepted or vetoed) is checked, and a weight above
+ * one is counted as a violation and sends the event back to the plain
+ * certified bound from the scale before that cycle. A zero violation count
+ * shows that the heights held wherever a winner landed; the result is the
+ * plain algorithm's only where they bound the ratio over the whole bin, which
+ * the histogram tests check statistically.
  * Parameter layout (FP32): W1 [64][4], b1 [64], W2 [64][64], b2 [64], W3 [64],
  * b3. */
 #define GAPS_MLP_PARAMS  4545
@@ -372,10 +376,43 @@ typedef struct {
 int gaps_train_learned_proposal(gaps_ctx* ctx, const gaps_learn_config* cfg, float* params_out,
                                 float* log_margins_out, gaps_learn_report* report, void* stream);
 
-/* Violation log of the learned proposal (device arrays, caller-owned; log ==
- * NULL switches it off): every acceptance weight above one met with the learned
- * bounds appends 8 floats {eta, s, t, w, class, bin, z, zeta} to
- * log[capacity][8] and increments *count (also past capacity). */
+/* The paper's fitted PDF-ratio overestimate (App. A.2) as a comparison mode
+ * of the mixed-precision shower; the plain shower's bound is certified
+ * instead (it bounds the ratio on the whole grid).
+ * gaps_collect_pdf_ratios: runs the GAPS_MIXED shower of events first_event ..
+ *   first_event + n - 1 with the certified bounds and logs the PDF ratios it
+ *   evaluates for winners, x' f(x') / (eta f(eta)) of initial-state channels
+ *   (times (t - m^2)/t for a heavy quark) and of final-initial spectators,
+ *   each with probability keep_fraction (a hash of event and Philox counter
+ *   decides): samples[capacity][4] (device) = {numerator table index,
+ *   denominator table index, eta, ratio}; *count (device) counts past
+ *   capacity.
+ * gaps_fit_pdf_ratios: host arrays; per (numerator, denominator) transition
+ *   the nearest-rank 99th and 99.99th percentiles of the sampled ratios,
+ *   fit[12][12][2] (0 without samples).
+ * gaps_set_pdf_ratio_fit: installs a fit (host array, copied; NULL returns to
+ *   the certified bounds). Later GAPS_MIXED showers of the context use
+ *   max(P99, P99.99 eta) per transition (eq. pdfmax) and P99.99 sqrt(eta) for
+ *   a gluon from the summed quarks, which holds the u and d parents of eq.
+ *   pdfmax_ud; transitions without samples keep the certified bound. It is not
+ *   a strict bound: acceptance weights above one are counted as violations in
+ *   gaps_stats (and accepted). FP64 contexts ignore it. */
+int gaps_collect_pdf_ratios(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
+                            float keep_fraction, float* samples, uint64_t capacity, uint64_t* count,
+                            void* stream);
+int gaps_fit_pdf_ratios(const float* samples, uint64_t n, float* fit);
+int gaps_set_pdf_ratio_fit(gaps_ctx* ctx, const float* fit);
+
+/* Violation log (device arrays, caller-owned; log == NULL switches it off):
+ * every acceptance weight above one of the GAPS_MIXED shower appends 8 floats
+ * to log[capacity][8] and increments *count (also past capacity): with the
+ * learned bounds {eta, s, t, w, class, bin, z, zeta}; with the plain bounds
+ * (the fitted PDF-ratio overestimate, or FP32 rounding at the edge of a
+ * certified bound) {eta, s, t, w, -1 - (8 dipole type + channel), -1, z, 0},
+ * dipole type 0 FF, 1 FI, 2 IF, 3 II and channel 0..6 as in the kernels
+ * (final state: 0 q -> qg, 1 g -> gg, 2 g -> qqbar; initial state, backward:
+ * 3 a quark stays a quark, 4 a quark becomes a gluon, 5 a gluon stays a
+ * gluon, 6 a gluon becomes a quark). */
 int gaps_set_violation_log(gaps_ctx* ctx, float* log, uint64_t capacity, uint64_t* count);
 
 /* Network kernels (device arrays; features [n][4]):

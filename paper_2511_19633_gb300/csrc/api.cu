@@ -1,6 +1,7 @@
 // C ABI of the shower library (include/gaps.h): configuration checks, the
 // library-owned device state (PDF grid, certified bound tables, counters) and
 // the launches of the hard-process, shower and observable kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -257,6 +258,9 @@ void fill_params(const gaps_config& c, DevParams& P) {
   P.process = c.process;
   P.trial_mode = c.trial_mode;
   P.max_steps = c.max_cycles > 0 ? c.max_cycles : kMaxSteps;
+  P.fit_on = 0;
+  for (int a = 0; a < 12; ++a)
+    for (int b = 0; b < 12; ++b) P.fit[a][b][0] = P.fit[a][b][1] = 0.0f;
   // images of the dilepton mass window under m^2 = m_Z^2 + m_Z Gamma_Z tan(2 pi r)
   {
     const double mg = kMZ * kGZ, mz2 = kMZ * kMZ;
@@ -760,6 +764,65 @@ int gaps_train_learned_proposal(gaps_ctx* ctx, const gaps_learn_config* lc, floa
     report->mean_bin_height = (float)(hs[0] / (double)rows);
     report->fit_rmse = (float)std::sqrt(hs[1] / (double)rows);
   }
+  return GAPS_OK;
+}
+
+int gaps_collect_pdf_ratios(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
+                            float keep_fraction, float* samples, uint64_t capacity, uint64_t* count,
+                            void* stream) {
+  if (!ctx || !events_ok(ctx, ev, n) || !samples || !count) return GAPS_ERR_INVALID_ARG;
+  if (!(keep_fraction > 0.0f && keep_fraction <= 1.0f)) return GAPS_ERR_INVALID_ARG;
+  if (ctx->cfg.precision != GAPS_MIXED) return GAPS_ERR_INVALID_ARG;
+  LearnedCfg Lc{};
+  Lc.rlog = reinterpret_cast<float4*>(samples);
+  Lc.rcount = reinterpret_cast<unsigned long long*>(count);
+  Lc.rcap = capacity;
+  Lc.rkeep = keep_fraction >= 1.0f ? 0xFFFFFFFFu : (uint32_t)((double)keep_fraction * 4294967296.0);
+  // the certified bounds, whatever fit the context holds
+  const int fit_on = ctx->P.fit_on;
+  ctx->P.fit_on = 0;
+  const int rc = shower_mixed(ctx, first_event, n, ev, Lc, stream);
+  ctx->P.fit_on = fit_on;
+  return rc;
+}
+
+int gaps_fit_pdf_ratios(const float* samples, uint64_t n, float* fit) {
+  if ((!samples && n) || !fit) return GAPS_ERR_INVALID_ARG;
+  std::vector<std::vector<float>> by(12 * 12);
+  for (uint64_t i = 0; i < n; ++i) {
+    const float* r = samples + 4 * i;
+    const int num = (int)r[0], den = (int)r[1];
+    if (num < 0 || num > 11 || den < 0 || den > 11 || !std::isfinite(r[3])) return GAPS_ERR_INVALID_ARG;
+    if (r[3] > 0.0f) by[num * 12 + den].push_back(r[3]);
+  }
+  // nearest-rank percentiles: the smallest sample with at least p of the
+  // samples at or below it
+  auto pct = [](std::vector<float>& v, double p) -> float {
+    size_t k = (size_t)std::ceil(p * (double)v.size());
+    if (k < 1) k = 1;
+    std::nth_element(v.begin(), v.begin() + (k - 1), v.end());
+    return v[k - 1];
+  };
+  for (int q = 0; q < 144; ++q) {
+    std::vector<float>& v = by[q];
+    fit[2 * q] = v.empty() ? 0.0f : pct(v, 0.99);
+    fit[2 * q + 1] = v.empty() ? 0.0f : pct(v, 0.9999);
+  }
+  return GAPS_OK;
+}
+
+int gaps_set_pdf_ratio_fit(gaps_ctx* ctx, const float* fit) {
+  if (!ctx) return GAPS_ERR_INVALID_ARG;
+  if (!fit) {
+    ctx->P.fit_on = 0;
+    return GAPS_OK;
+  }
+  for (int q = 0; q < 288; ++q)
+    if (!std::isfinite(fit[q]) || fit[q] < 0.0f) return GAPS_ERR_INVALID_ARG;
+  for (int a = 0; a < 12; ++a)
+    for (int b = 0; b < 12; ++b)
+      for (int k = 0; k < 2; ++k) ctx->P.fit[a][b][k] = fit[(a * 12 + b) * 2 + k];
+  ctx->P.fit_on = 1;
   return GAPS_OK;
 }
 

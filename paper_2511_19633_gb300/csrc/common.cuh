@@ -52,6 +52,12 @@ struct DevParams {
   const double* first;    // [12][100] node value on the first Q^2 node above a heavy flavour's threshold
   int thr[12];            // Q^2 node of a heavy flavour's mass (c, b, cbar, bbar), -1: no threshold
   double m2[12];          // that mass squared (the node's Q^2), 0 without a threshold
+  // the paper's percentile-fitted PDF-ratio overestimate (App. A.2, eqs.
+  // pdfmax and pdfmax_ud) in place of the certified bound (mixed precision):
+  // fit[num][den] = {99th, 99.99th percentile}; a transition without samples
+  // (99.99th percentile 0) keeps the certified bound
+  int fit_on;
+  float fit[12][12][2];
   double lxmin, dlx, lqmin, dlq;
   unsigned long long* counters;  // [C_NCOUNTERS]
 };
@@ -105,6 +111,10 @@ struct LearnedCfg {
   float4* vlog;                   // violations of the learned bound: 2 float4 per entry
   unsigned long long* vcount;
   uint64_t vcap;
+  float4* rlog;                   // logged PDF ratios {numerator index, denominator index, eta, ratio}
+  unsigned long long* rcount;
+  uint64_t rcap;
+  uint32_t rkeep;                 // a ratio is logged when its 32-bit hash is below this
 };
 
 // host helpers shared by the entry points (api.cu); none allocates memory

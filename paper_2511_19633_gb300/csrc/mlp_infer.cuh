@@ -142,20 +142,21 @@ static __device__ __noinline__ void mlp_tile(const MlpSmem& S, const float (*fea
   __syncwarp();
 }
 
-// Four 16-row tiles at once (rows feat[0..63] -> out[0..63]): every weight
-// fragment is loaded once and feeds the four tiles' mma's, so their
-// tensor-core work interleaves. For the dense pass, which has the registers
-// to spare; the same numerics as mlp_tile, row by row.
-static __device__ __noinline__ void mlp_tile4(const MlpSmem& S, const float (*feat)[4], float* out) {
+// NT 16-row tiles at once (rows feat[0 .. 16 NT) -> out): every weight
+// fragment is loaded once and feeds the NT tiles' mma's, so their tensor-core
+// work interleaves. For the dense pass; the same numerics as mlp_tile, row by
+// row.
+template <int NT>
+__device__ __noinline__ void mlp_tiles(const MlpSmem& S, const float (*feat)[4], float* out) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  uint32_t X[4][2];  // layer-1 inputs (K = 16: features 0..3, zero padding)
+  uint32_t X[NT][2];  // layer-1 inputs (K = 16: features 0..3, zero padding)
 #pragma unroll
-  for (int tt = 0; tt < 4; ++tt) {
+  for (int tt = 0; tt < NT; ++tt) {
     const float (*f)[4] = feat + 16 * tt;
     X[tt][0] = t < 2 ? pack_bf16(f[g][2 * t], f[g][2 * t + 1]) : 0u;
     X[tt][1] = t < 2 ? pack_bf16(f[g + 8][2 * t], f[g + 8][2 * t + 1]) : 0u;
   }
-  uint32_t A1[4][4][4];  // [tile][k-step of layer 2][fragment]
+  uint32_t A1[NT][4][4];  // [tile][k-step of layer 2][fragment]
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
 #pragma unroll
@@ -165,7 +166,7 @@ static __device__ __noinline__ void mlp_tile4(const MlpSmem& S, const float (*fe
       const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w1[n][2 * t + 8]);
       const float c0 = S.b1[nt * 8 + 2 * t], c1 = S.b1[nt * 8 + 2 * t + 1];
 #pragma unroll
-      for (int tt = 0; tt < 4; ++tt) {
+      for (int tt = 0; tt < NT; ++tt) {
         const uint32_t a[4] = {X[tt][0], X[tt][1], 0u, 0u};
         float h[4] = {c0, c1, c0, c1};
         mma16816(h, a, b0, b1);
@@ -175,18 +176,18 @@ static __device__ __noinline__ void mlp_tile4(const MlpSmem& S, const float (*fe
     }
   }
   // layers 2 and 3, k-step j3 of layer 3 = column tiles 2 j3, 2 j3 + 1 of layer 2
-  float o[4][4];
+  float o[NT][4];
 #pragma unroll
-  for (int tt = 0; tt < 4; ++tt) o[tt][0] = o[tt][1] = o[tt][2] = o[tt][3] = S.b3;
+  for (int tt = 0; tt < NT; ++tt) o[tt][0] = o[tt][1] = o[tt][2] = o[tt][3] = S.b3;
 #pragma unroll 1
   for (int j3 = 0; j3 < 4; ++j3) {
-    float h[4][2][4];
+    float h[NT][2][4];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int nt = 2 * j3 + u, n = nt * 8 + g;
       const float c0 = S.b2[nt * 8 + 2 * t], c1 = S.b2[nt * 8 + 2 * t + 1];
 #pragma unroll
-      for (int tt = 0; tt < 4; ++tt) {
+      for (int tt = 0; tt < NT; ++tt) {
         h[tt][u][0] = c0;
         h[tt][u][1] = c1;
         h[tt][u][2] = c0;
@@ -197,13 +198,13 @@ static __device__ __noinline__ void mlp_tile4(const MlpSmem& S, const float (*fe
         const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w2[n][16 * j + 2 * t]);
         const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w2[n][16 * j + 8 + 2 * t]);
 #pragma unroll
-        for (int tt = 0; tt < 4; ++tt) mma16816(h[tt][u], A1[tt][j], b0, b1);
+        for (int tt = 0; tt < NT; ++tt) mma16816(h[tt][u], A1[tt][j], b0, b1);
       }
     }
     const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w3[g][16 * j3 + 2 * t]);
     const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w3[g][16 * j3 + 8 + 2 * t]);
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
+    for (int tt = 0; tt < NT; ++tt) {
       const uint32_t A3[4] = {pack_bf16(fmaxf(h[tt][0][0], 0.0f), fmaxf(h[tt][0][1], 0.0f)),
                               pack_bf16(fmaxf(h[tt][0][2], 0.0f), fmaxf(h[tt][0][3], 0.0f)),
                               pack_bf16(fmaxf(h[tt][1][0], 0.0f), fmaxf(h[tt][1][1], 0.0f)),
@@ -213,7 +214,7 @@ static __device__ __noinline__ void mlp_tile4(const MlpSmem& S, const float (*fe
   }
   if (t == 0) {
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
+    for (int tt = 0; tt < NT; ++tt) {
       out[16 * tt + g] = o[tt][0];
       out[16 * tt + g + 8] = o[tt][2];
     }

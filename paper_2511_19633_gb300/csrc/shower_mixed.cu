@@ -144,6 +144,13 @@ __device__ __noinline__ float pdf32(const MixedCtx& M, const SmemPdf& S, int f, 
 
 __device__ __noinline__ float bound32(const MixedCtx& M, const SmemPdf& S, int num, int den, float eta) {
   if (num < 0 || num > 11 || den < 0 || den > 11) return 0.0f;
+  if (M.P.fit_on && den < 11 && M.P.fit[num][den][1] > 0.0f) {
+    // the paper's fitted overestimate (App. A.2): max(P99, P99.99 eta), or
+    // P99.99 sqrt(eta) for a gluon from the quarks (its u and d parents)
+    const float p99 = M.P.fit[num][den][0], p9999 = M.P.fit[num][den][1];
+    if (!(eta >= (float)kXMin && eta <= (float)kXMax)) return 0.0f;
+    return (num == 11 && den == 0) ? p9999 * sqrtf(eta) : fmaxf(p99, p9999 * eta);
+  }
   int ix;
   float fx;
   if (!loc_x(M, eta, ix, fx)) return 0.0f;
@@ -336,6 +343,8 @@ __device__ __forceinline__ void mlp_features(float eta, float s, float tc, int b
 
 struct IsrEval {
   float r, x, omx, u, omu, v, sumF;
+  float fr;       // the PDF ratio F(eta/x)/F(eta) (corrected for a heavy quark)
+  int num, den;   // its table indices
   bool ok;
 };
 
@@ -347,6 +356,7 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
   IsrEval e;
   e.ok = false;
   e.r = 0.0f; e.x = 1.0f; e.omx = 0.0f; e.u = 0.0f; e.omu = 1.0f; e.v = 0.0f; e.sumF = 0.0f;
+  e.fr = 0.0f; e.num = 0; e.den = 0;
   const float r = tw / s;
   float J;
   if (type == kIF) {
@@ -386,6 +396,9 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
     if (m2 > 0.0f) Fratio *= (tw - m2) / tw;  // heavy-quark measure correction
   }
   e.r = B > 0.0f ? kk * J * x / pover * Fratio / B : 0.0f;
+  e.fr = Fratio;
+  e.num = num;
+  e.den = den;
   e.ok = true;
   return e;
 }
@@ -531,7 +544,9 @@ __device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& m
   }
   __syncwarp();
   if (four) {
-    mlp_tile4(mlp, stage, ustage);  // all four tiles (rows of unselected ends unused)
+    // all four tiles, two at a time (rows of unselected ends are unused)
+    mlp_tiles<2>(mlp, stage, ustage);
+    mlp_tiles<2>(mlp, stage + 32, ustage + 32);
   } else {
     for (int tile = 0; tile < 4; ++tile)
       if ((eval >> tile) & 1u) mlp_tile(mlp, stage + 16 * tile, ustage + 16 * tile);
@@ -875,6 +890,32 @@ __device__ __noinline__ bool emit(const MixedCtx& M, const W& w, Lane& L, const 
 
 static_assert(sizeof(Emission) <= kWavePendBytes, "parked emission exceeds its slot");
 
+// logs a sampled PDF ratio of a winner (the paper's data for its fitted
+// overestimate, App. A.2); the sample is decided by a hash of (event, draw)
+__device__ __noinline__ void log_ratio(const MixedCtx& M, uint64_t id, uint64_t draw, int num, int den, float eta,
+                                       float ratio) {
+  uint64_t h = id * 0x9E3779B97F4A7C15ull ^ (draw * 0xD6E8FEB86659FD93ull);
+  h ^= h >> 31;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 29;
+  if (!((uint32_t)(h >> 32) < M.Lc.rkeep || M.Lc.rkeep == 0xFFFFFFFFu)) return;
+  const unsigned long long at = atomicAdd(M.Lc.rcount, 1ull);
+  if (at < M.Lc.rcap) M.Lc.rlog[at] = make_float4((float)num, (float)den, eta, ratio);
+}
+
+// a weight above one met with the plain bounds (the fitted PDF-ratio
+// overestimate, or rounding at the edge of a certified bound): logged with
+// class -1 - (8 type + channel) and bin -1
+__device__ __noinline__ void log_plain_violation(const MixedCtx& M, float eta, float s, float tw, float w, int type,
+                                                 int ch, float z) {
+  if (!M.Lc.vlog) return;
+  const unsigned long long at = atomicAdd(M.Lc.vcount, 1ull);
+  if (at < M.Lc.vcap) {
+    M.Lc.vlog[2 * at] = make_float4(eta, s, tw, w);
+    M.Lc.vlog[2 * at + 1] = make_float4(-1.0f - (float)(8 * type + ch), -1.0f, z, 0.0f);
+  }
+}
+
 struct Counters32 {
   unsigned long long steps = 0, trials = 0, isr_trials = 0, vetoes = 0, accepts = 0, violations = 0;
 };
@@ -986,11 +1027,13 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
     float F0 = pdf32(M, S, f, eta, tw);
     float ratio = F0 > 0.0f ? x * F1 / F0 : 0.0f;
     w8 = as_ratio * kk / pover * ratio / B;
+    if (M.Lc.rlog) log_ratio(M, id, L.draw, f, f, eta, F0 > 0.0f ? F1 / F0 : 0.0f);
   } else {
     const IsrEval ev = isr_eval32(M, S, type, ch, fl_i, eta, s, tw, z, omz, pover);
     if (!ev.ok) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
     x = ev.x; omx = ev.omx; u = ev.u; omu = ev.omu; v = ev.v; sumF = ev.sumF;
     w8 = as_ratio * ev.r / Um;
+    if (M.Lc.rlog) log_ratio(M, id, L.draw, ev.num, ev.den, eta, ev.fr);
     if (ch == 4) { new_fl_i = 21; fl_j = -fl_i; }
     if (ch == 5) { new_fl_i = 21; fl_j = 21; }
   }
@@ -1013,6 +1056,7 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
       parked = true;
       return GAPS_STATUS_ACTIVE;
     }
+    log_plain_violation(M, eta, s, tw, w8, type, ch, z);
   }
   if (!(Rveto < w8)) { cnt.vetoes += 1; return GAPS_STATUS_ACTIVE; }
 
@@ -1160,7 +1204,10 @@ __device__ int step_vetomax(const MixedCtx& M, const SmemPdf& S, const W& w, Lan
             const float t1 = fmaf(__logf(u24(out[1])), ic, lnT);
             if (!(t1 > lnTc)) break;
             const ChannelWeight cw = channel_weight(M, S, w, L, q, c, __expf(t1), u24(out[3]));
-            if (cw.ok && cw.w > 1.0f) cnt.violations += 1;
+            if (cw.ok && cw.w > 1.0f) {
+              cnt.violations += 1;
+              log_plain_violation(M, w.Aux(q).y, w.Aux(q).x, __expf(t1), cw.w, cw.type, cw.ch, cw.z);
+            }
             if (cw.ok && u24(out[2]) < cw.w) {
               lt = t1;
               rz = u24(out[3]);
@@ -1895,7 +1942,7 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
 // record scaled by c * mean(U), and its two trials drawn at the Philox
 // counters the rebuild pass reserved for it, as the persistent kernel's
 // inline evaluation and first trial loop would give them.
-__global__ void __launch_bounds__(256) k_wave_mlp(const __grid_constant__ MixedCtx M) {
+__global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ MixedCtx M) {
   if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 4 >= M.V.ctl[WL_MLP]) return;  // nothing queued for this block
   __shared__ float dec[256];
   __shared__ float stage_s[8][64][4];

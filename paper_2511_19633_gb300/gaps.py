@@ -107,7 +107,8 @@ EXPORTS = ("gaps_init", "gaps_generate_hard", "gaps_shower", "gaps_observables",
            "gaps_destroy", "gaps_shower_static", "gaps_collect_isr_states", "gaps_isr_targets",
            "gaps_set_learned_proposal", "gaps_mlp_loss_grad", "gaps_mlp_forward", "gaps_mlp_train",
            "gaps_process", "gaps_process_shower_ms", "gaps_set_violation_log", "gaps_alu_peak",
-           "gaps_train_learned_proposal")
+           "gaps_train_learned_proposal", "gaps_collect_pdf_ratios", "gaps_fit_pdf_ratios",
+           "gaps_set_pdf_ratio_fit")
 
 # kinds of gaps_alu_peak (include/gaps_peaks.h)
 GAPS_PEAK_FFMA, GAPS_PEAK_DFMA, GAPS_PEAK_MUFU, GAPS_PEAK_IMAD = 0, 1, 2, 3
@@ -151,6 +152,9 @@ def _load():
     lib.gaps_mlp_train.argtypes = [vp, vp, vp, vp, vp, u64, u64, f, f, u64, vp, i, vp]
     lib.gaps_alu_peak.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.gaps_train_learned_proposal.argtypes = [vp, P(GapsLearnConfig), vp, vp, P(GapsLearnReport), vp]
+    lib.gaps_collect_pdf_ratios.argtypes = [vp, u64, u64, P(GapsEvents), f, vp, u64, vp, vp]
+    lib.gaps_fit_pdf_ratios.argtypes = [vp, u64, vp]
+    lib.gaps_set_pdf_ratio_fit.argtypes = [vp, vp]
     return lib
 
 
@@ -247,6 +251,34 @@ def gaps_train_learned_proposal(ctx, cfg: GapsLearnConfig, stream=None) -> dict:
     out["params"] = params
     out["log_margins"] = margins
     return out
+
+
+def gaps_collect_pdf_ratios(ctx, first_event: int, n: int, ev: GapsEvents, samples: torch.Tensor,
+                            count: torch.Tensor, keep_fraction: float = 1.0, stream=None):
+    """samples: float32 [capacity, 4] device; count: int64 [1] device (incremented)."""
+    _check(_lib.gaps_collect_pdf_ratios(ctx, first_event, n, ctypes.byref(ev), float(keep_fraction),
+                                        samples.data_ptr(), samples.shape[0], count.data_ptr(),
+                                        _stream_ptr(stream)), "gaps_collect_pdf_ratios")
+
+
+def gaps_fit_pdf_ratios(samples):
+    """samples: host float32 [n, 4]; returns the fit [12][12][2] (numpy)."""
+    import numpy as np
+    a = np.ascontiguousarray(samples, dtype=np.float32).reshape(-1, 4)
+    fit = np.zeros((12, 12, 2), dtype=np.float32)
+    _check(_lib.gaps_fit_pdf_ratios(a.ctypes.data if a.size else None, a.shape[0], fit.ctypes.data),
+           "gaps_fit_pdf_ratios")
+    return fit
+
+
+def gaps_set_pdf_ratio_fit(ctx, fit):
+    """fit: [12][12][2] float32 (copied) or None for the certified bounds."""
+    import numpy as np
+    if fit is None:
+        _check(_lib.gaps_set_pdf_ratio_fit(ctx, None), "gaps_set_pdf_ratio_fit")
+        return
+    f = np.ascontiguousarray(fit, dtype=np.float32)
+    _check(_lib.gaps_set_pdf_ratio_fit(ctx, f.ctypes.data), "gaps_set_pdf_ratio_fit")
 
 
 def gaps_set_violation_log(ctx, log: torch.Tensor | None, count: torch.Tensor | None = None):

@@ -138,3 +138,31 @@ def test_thresholded_grid_needs_a_supported_scheme(lib, precision, schedule, tri
     with pytest.raises(G.GapsError) as e:
         G.gaps_init(cfg)
     assert e.value.code == G.GAPS_ERR_INVALID_ARG
+
+
+def test_percentile_fit_of_pdf_ratios(lib):
+    """gaps_fit_pdf_ratios (host): per transition the nearest-rank 99th and
+    99.99th percentiles of the sampled ratios, against numpy."""
+    import numpy as np
+    from paper_2511_19633_gb300 import gaps as G
+    rng = np.random.default_rng(3)
+    rows = []
+    for num, den, m in ((0, 4, 50000), (11, 0, 20000), (3, 3, 7)):
+        r = rng.lognormal(0.0, 1.0, m).astype(np.float32)
+        rows.append(np.stack([np.full(m, num), np.full(m, den), rng.uniform(1e-5, 0.9, m), r], 1))
+    s = np.concatenate(rows).astype(np.float32)
+    fit = G.gaps_fit_pdf_ratios(s)
+    for num, den in ((0, 4), (11, 0), (3, 3)):
+        r = np.sort(s[(s[:, 0] == num) & (s[:, 1] == den), 3])
+        for k, p in ((0, 0.99), (1, 0.9999)):
+            assert fit[num, den, k] == r[int(np.ceil(p * r.size)) - 1]
+    assert fit[5, 5, 0] == 0.0 and fit[5, 5, 1] == 0.0
+
+
+def test_percentile_fit_rejects_bad_input(lib):
+    import numpy as np
+    from paper_2511_19633_gb300 import gaps as G
+    for row in ([12, 0, 0.1, 1.0], [0, -1, 0.1, 1.0], [0, 0, 0.1, np.inf]):
+        with pytest.raises(Exception):
+            G.gaps_fit_pdf_ratios(np.array([row], dtype=np.float32))
+    assert np.all(G.gaps_fit_pdf_ratios(np.zeros((0, 4), dtype=np.float32)) == 0.0)

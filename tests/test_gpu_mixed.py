@@ -201,3 +201,36 @@ def test_generate_select_launch_shape_does_not_change_events(G, pdf, period, blo
                 blocks_per_sm=bps, refill_period=period, emit_batch=batch, trial_mode=2)
     for k in ("p", "flav", "npart", "weight", "obs"):
         assert np.array_equal(ref[k], g[k]), k
+
+
+def test_plain_bound_weights_above_one_are_rounding(G, pdf):
+    """Veto-max evaluates the acceptance weight of every channel's trials with
+    the certified bounds (about 2e9 weights for 2^22 NLO events): a weight
+    above one can only be FP32 rounding at the edge of a bound. Every one is
+    logged with its dipole type and channel and must stay within 1e-5 of one."""
+    import torch
+    proc, sqrt_s = PROCESS["pp_nlo"]
+    n = 1 << 22
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=MIXED, schedule=1,
+                        trial_mode=G.GAPS_TRIALS_VETOMAX)
+    ctx = G.gaps_init(cfg)
+    try:
+        log = torch.zeros((1024, 8), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        G.gaps_set_violation_log(ctx, log, cnt)
+        buf = G.EventBuffers.allocate(n, 128)
+        ev = buf.view()
+        G.gaps_generate_hard(ctx, 77 << 32, n, ev)
+        G.gaps_shower(ctx, 77 << 32, n, ev)
+        torch.cuda.synchronize()
+        st = G.gaps_get_stats(ctx)
+        m = int(cnt.item())
+        entries = log[:min(m, 1024)].cpu().numpy()
+    finally:
+        G.gaps_destroy(ctx)
+    print("veto-max weights above one:", st["violations"], entries.tolist())
+    assert m == st["violations"]
+    assert st["violations"] < 1e-7 * st["vetoes"]
+    for e in entries:
+        assert e[4] < 0 and e[5] == -1  # plain bounds
+        assert 1.0 < e[3] < 1.0 + 1e-5, e

@@ -63,11 +63,15 @@ def G():
     return gaps()
 
 
-def test_precision_error_per_observable_same_events(G, pdf):
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_precision_error_per_observable_same_events(G, pdf, schedule):
+    """Lane-per-event persistent kernel (1) and the warp-per-event kernel (2),
+    whose lanes draw one dipole end each and take the winner by a warp
+    arg-max."""
     gold = load_golden("pp_nlo_seed1")
     assert gold["seed"] == 1
     n = gold["events"]
-    w, w2, st = _gpu_hists(G, pdf, n, G.GAPS_TRIALS_REDRAW, G.GAPS_SCHED_PERSISTENT)
+    w, w2, st = _gpu_hists(G, pdf, n, G.GAPS_TRIALS_REDRAW, schedule)
     assert st["events"] == n and st["violations"] == 0
     res = per_observable(w, w2, n, gold)
     print("mixed precision vs FP64 oracle, same events:", res)
