@@ -395,7 +395,7 @@ def run_ours(args, ws, rank, local):
     shape = {"block_size": args.block, "blocks_per_sm": args.bps, "refill_period": args.period,
              "emit_batch": args.emit_batch}
     if schedule == G.GAPS_SCHED_WAVE:
-        shape.update(wave_passes=args.passes, wave_cycles=args.cycles)
+        shape.update(wave_passes=args.passes, wave_cycles=args.cycles, wave_veto_blocks_per_sm=args.veto_bps)
     tuning = None
     if mixed and not args.no_autotune:
         from paper_2511_19633_gb300 import autotune
@@ -645,6 +645,7 @@ def main():
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--bps", type=int, default=4)
     ap.add_argument("--passes", type=int, default=24)
+    ap.add_argument("--veto-bps", type=int, default=2)
     ap.add_argument("--cycles", type=int, default=64)
     ap.add_argument("--period", type=int, default=1)
     ap.add_argument("--emit-batch", type=int, default=16)

@@ -150,6 +150,10 @@ typedef struct {
                              the remaining live events, 0 = 24, at most 4096 */
     int wave_cycles;      /* GAPS_SCHED_WAVE: veto cycles of one event in one pass
                              before it waits for the next pass, 0 = 64, 1..1e6 */
+    int wave_veto_blocks_per_sm; /* GAPS_SCHED_WAVE: resident blocks of block_size
+                             threads per SM of the veto kernel, which sets its
+                             register budget (2: 128, 3: 80, 4: 64 registers a
+                             thread); 0 = 2, else 2..4 */
 } gaps_config;
 
 /* Trial schemes (gaps_config.trial_mode). All three give the same

@@ -26,9 +26,10 @@ DEFAULT_GRID = {
 }
 WAVE_GRID = {
     "block_size": (256,),
-    "blocks_per_sm": (2, 3, 4),
+    "blocks_per_sm": (3, 4),
+    "wave_veto_blocks_per_sm": (2, 3, 4),
     "wave_passes": (16, 24, 32),
-    "wave_cycles": (32, 64),
+    "wave_cycles": (64,),
     "refill_period": (1,),
     "emit_batch": (16,),
 }

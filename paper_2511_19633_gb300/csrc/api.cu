@@ -15,7 +15,6 @@ namespace gaps {
 cudaError_t launch_generate_hard(const DevParams&, const DevEvents&, uint64_t, uint64_t, cudaStream_t);
 cudaError_t launch_shower_fp64(const DevParams&, const DevEvents&, uint64_t, uint64_t, int, int,
                                unsigned long long*, cudaStream_t);
-size_t workset_bytes(int lanes, int nmax);
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
 cudaError_t launch_shower_mixed(const DevParams&, const DevEvents&, const WorkSet&, const LearnedCfg&, uint64_t,
                                 uint64_t, int, int, int, int, int, int, unsigned long long*, cudaStream_t);
@@ -26,7 +25,7 @@ size_t mlp_image_bytes();
 cudaError_t launch_shower_warp(const DevParams&, const DevEvents&, const LearnedCfg&, uint64_t, uint64_t, int, int,
                                int, int, unsigned long long*, cudaStream_t);
 cudaError_t launch_shower_wave(const DevParams&, const DevEvents&, const WorkSet&, const WaveSet&, const LearnedCfg&,
-                               uint64_t, uint64_t, int, int, int, int, int, int, int, int, cudaStream_t);
+                               uint64_t, uint64_t, int, int, int, int, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
                                const HistSet&, double*, double*, int, cudaStream_t);
 cudaError_t sort_states(float4*, uint64_t, cudaStream_t);
@@ -200,6 +199,8 @@ int validate_config(const gaps_config& c) {
     return GAPS_ERR_INVALID_ARG;
   if (c.wave_passes < 0 || c.wave_passes > 4096) return GAPS_ERR_INVALID_ARG;
   if (c.wave_cycles < 0 || c.wave_cycles > 1000000) return GAPS_ERR_INVALID_ARG;
+  if (c.wave_veto_blocks_per_sm != 0 && (c.wave_veto_blocks_per_sm < 2 || c.wave_veto_blocks_per_sm > 4))
+    return GAPS_ERR_INVALID_ARG;
   if (c.trial_mode != GAPS_TRIALS_REDRAW && c.trial_mode != GAPS_TRIALS_KEEP && c.trial_mode != GAPS_TRIALS_SELECT &&
       c.trial_mode != GAPS_TRIALS_VETOMAX)
     return GAPS_ERR_INVALID_ARG;
@@ -468,9 +469,11 @@ int shower_wave(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
   const int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
   const int passes = c.wave_passes > 0 ? c.wave_passes : kWavePassesDefault;
   const int cycles = c.wave_cycles > 0 ? c.wave_cycles : kWaveCyclesDefault;
+  // the veto kernel runs best with 128 registers a thread (no spills)
+  const int veto_per_sm = c.wave_veto_blocks_per_sm > 0 ? c.wave_veto_blocks_per_sm : 2;
   return cuda_fail(launch_shower_wave(ctx->P, dev_events(ev), W, V, Lc, first_event, n, passes, cycles,
-                                      ctx->n_sm * per_sm, bs, ctx->n_sm, c.refill_period, c.emit_batch,
-                                      ctx->q_independent, (cudaStream_t)stream));
+                                      ctx->n_sm * per_sm, ctx->n_sm * veto_per_sm, bs, ctx->n_sm, c.refill_period,
+                                      c.emit_batch, ctx->q_independent, (cudaStream_t)stream));
 }
 
 int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,

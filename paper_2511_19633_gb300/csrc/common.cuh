@@ -69,10 +69,22 @@ struct WorkSet {
   float4* end;
   float4* trial;         // kept trials {ln t, R_z} of both channels per end [lanes][2 nmax]
   float4* aux;           // the veto's inputs per end {s, eta, emitter tag, partner tag} [lanes][2 nmax]
+  float* tmx;            // per end the larger of its two kept trials' ln t (NaN: draws next cycle),
+                         // [lanes][tmx_stride(nmax)]: the scan of a veto cycle reads only these
   float4* lkey;          // learned proposal: network inputs of the last evaluation [lanes][4 ends]
   unsigned char* lcode;  // learned proposal: 8-bit bin-height codes [lanes][4 ends][2][8]
   int lanes;
 };
+
+// floats per lane of WorkSet::tmx: 2 nmax rounded up to a multiple of four, so
+// that four consecutive ends load as one aligned float4
+__host__ __device__ constexpr unsigned tmx_stride(int nmax) { return (unsigned)(2 * nmax + 3) & ~3u; }
+
+// bytes of a working set of `lanes` lanes (workset_carve's layout)
+constexpr size_t workset_bytes(int lanes, int nmax) {
+  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
+         (size_t)lanes * tmx_stride(nmax) * sizeof(float) + (size_t)lanes * (64 + 4 * sizeof(float4));
+}
 
 // State of the wavefront schedule (GAPS_SCHED_WAVE): per event of a chunk,
 // structure of arrays in library-owned device memory, beside a working set

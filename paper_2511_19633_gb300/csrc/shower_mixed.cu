@@ -277,6 +277,24 @@ struct WS {
   __device__ __forceinline__ float4& Aux(int q) const {
     return W.aux[(unsigned)lane * (unsigned)(2 * nmax) + (unsigned)q];
   }
+  // the larger ln t of end q's two kept trials (NaN with the mark above)
+  __device__ __forceinline__ float& Tmx(int q) const {
+    return W.tmx[(unsigned)lane * tmx_stride(nmax) + (unsigned)q];
+  }
+  // ends q0 .. q0 + 3 (q0 a multiple of four)
+  __device__ __forceinline__ float4 Tmx4(int q0) const {
+    return *reinterpret_cast<const float4*>(W.tmx + (unsigned)lane * tmx_stride(nmax) + (unsigned)q0);
+  }
+  // writes end q's kept trials and their maximum
+  __device__ __forceinline__ void SetTrial(int q, const float4& tr) const {
+    Trial(q) = tr;
+    Tmx(q) = tr.z > tr.x ? tr.z : tr.x;
+  }
+  // marks end q: its channels draw in the next cycle
+  __device__ __forceinline__ void MarkTrial(int q) const {
+    Trial(q).x = __uint_as_float(0x7fc00000u);
+    Tmx(q) = __uint_as_float(0x7fc00000u);
+  }
   static constexpr bool kTrials = true;
 };
 
@@ -293,9 +311,13 @@ struct WSS {
   __device__ __forceinline__ float4& Aux(int q) const { return aux[q]; }
   static constexpr bool kTrials = false;  // no kept trials in this schedule
 };
-// bytes of the lane kernel's per-warp tag staging (16-byte multiple)
+// 32-bit words of one warp's tag staging in the lane kernels: the event's
+// tags, then the colour-partner table (2 x 256 bytes: the slot owning each
+// colour tag, then each anticolour tag; 0xff none)
+__host__ __device__ constexpr int tag_stage_words(int nmax) { return nmax + 128; }
+// bytes of the per-warp tag staging of a block (16-byte multiple)
 __host__ __device__ constexpr size_t tag_stage_bytes(int warps, int nmax) {
-  return ((size_t)warps * nmax * sizeof(uint32_t) + 15) / 16 * 16;
+  return ((size_t)warps * tag_stage_words(nmax) * sizeof(uint32_t) + 15) / 16 * 16;
 }
 
 // bytes of one warp's event in shared memory
@@ -311,6 +333,13 @@ __device__ __forceinline__ int find_partner_tags(const uint32_t* tg, int n, int 
     if (side == 0 ? (tag_acol(t) == tag) : (tag_col(t) == tag)) return m;
   }
   return -1;
+}
+
+// the same from the partner table of unique tags (own: the slot of each
+// colour tag, then of each anticolour tag)
+__device__ __forceinline__ int partner_from_table(const unsigned char* own, int i, int side, int tag) {
+  const int m = own[side == 0 ? 256 + tag : tag];
+  return (m == 0xff || m == i) ? -1 : m;
 }
 
 template <class W>
@@ -407,16 +436,16 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
 // ln t_kin, partner} (partner -1: no dipole on this side), and in aux_out the
 // veto's inputs {s, eta, emitter tag, partner tag}.
 template <class W>
-__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, const uint32_t* tg, int n,
-                             double eta0, double eta1, int row, int q, float& s_out, float& eta_out,
-                             int& type_out, float4& aux_out) {
+__device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, const uint32_t* tg,
+                             const unsigned char* own, int n, double eta0, double eta1, int row, int q,
+                             float& s_out, float& eta_out, int& type_out, float4& aux_out) {
   type_out = -1;
   aux_out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const bool pp = S.pp[row] != 0;
   const int i = q >> 1, side = q & 1;
   const uint32_t ti = tg[i];
   const int tag = side == 0 ? tag_col(ti) : tag_acol(ti);
-  const int k = tag ? find_partner_tags(tg, n, i, side, tag) : -1;
+  const int k = !tag ? -1 : (own ? partner_from_table(own, i, side, tag) : find_partner_tags(tg, n, i, side, tag));
   if (k < 0) return make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
   const int fi = tag_fl(ti);
   const bool ini = pp && i < 2, ink = pp && k < 2;
@@ -499,9 +528,9 @@ __device__ __forceinline__ void set_end(const W& w, int q, const float4& rec, in
       if (__float_as_uint(old.x) == __float_as_uint(rec.x) && __float_as_uint(old.y) == __float_as_uint(rec.y) &&
           __float_as_uint(old.z) == __float_as_uint(rec.z) && __float_as_uint(old.w) == __float_as_uint(rec.w))
         return;
-      w.Trial(q).x = __uint_as_float(0x7fc00000u);
+      w.MarkTrial(q);
     } else {
-      w.Trial(q).x = __uint_as_float(0x7fc00000u);
+      w.MarkTrial(q);
     }
   }
   w.End(q) = rec;
@@ -595,10 +624,30 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
                                          int keep_ends, int lane_id, bool defer = false,
                                          unsigned* defer_mask = nullptr, float4* deferred = nullptr,
                                          float4* isr_plain = nullptr) {
-  // the event's tags in shared memory: every end scans them for its partner
+  // the event's tags in shared memory, and (lane kernels) the table of the
+  // slot owning each colour and anticolour tag, so that an end finds its
+  // partner in one lookup; with a tag held by two partons (not a leading-
+  // colour event) every end scans the tags instead, as the table cannot give
+  // the first match
+  unsigned char* own = nullptr;
   if (stage_tags) {
+    own = reinterpret_cast<unsigned char*>(tg + M.P.nmax);
+    uint32_t* ow = reinterpret_cast<uint32_t*>(own);
+    for (int k = lane_id; k < 128; k += 32) ow[k] = 0xffffffffu;
     for (int m = lane_id; m < n; m += 32) tg[m] = w.T(m);
     __syncwarp();
+    for (int m = lane_id; m < n; m += 32) {
+      const uint32_t t = tg[m];
+      if (tag_col(t)) own[tag_col(t)] = (unsigned char)m;
+      if (tag_acol(t)) own[256 + tag_acol(t)] = (unsigned char)m;
+    }
+    __syncwarp();
+    bool dup = false;
+    for (int m = lane_id; m < n; m += 32) {
+      const uint32_t t = tg[m];
+      dup = dup || (tag_col(t) && own[tag_col(t)] != m) || (tag_acol(t) && own[256 + tag_acol(t)] != m);
+    }
+    if (__any_sync(0xffffffffu, dup)) own = nullptr;
   }
   const bool pp = S.pp[row] != 0;
   // the learned state of the initial-state ends, loaded before the records
@@ -615,7 +664,7 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
     float s_, eta_;
     int type_;
     float4 aux;
-    const float4 rec = end_record(M, S, w, tg, n, eta0, eta1, row, q, s_, eta_, type_, aux);
+    const float4 rec = end_record(M, S, w, tg, own, n, eta0, eta1, row, q, s_, eta_, type_, aux);
     w.Aux(q) = aux;
     if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
     else set_end(w, q, rec, keep_ends);
@@ -1220,7 +1269,7 @@ __device__ int step_vetomax(const MixedCtx& M, const SmemPdf& S, const W& w, Lan
           else { tr.z = lt; tr.w = rz; }
         }
       }
-      w.Trial(q) = tr;
+      w.SetTrial(q, tr);
     }
     if (tr.x > best) { best = tr.x; bq = q; bch = 0; bRz = tr.y; }
     if (tr.z > best) { best = tr.z; bq = q; bch = 1; bRz = tr.w; }
@@ -1344,23 +1393,30 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
   uint64_t d = L.draw;
   const bool select = M.P.trial_mode == GAPS_TRIALS_SELECT;
   if (select) select_trial(w, ne, L.lnT, lnTc, pp, e0, e1, k0, k1, d, cnt, best, bq, bch, bRz);
-  // the ends' trials: with kept trials the ends are read four at a time (four
-  // loads in flight), and only ends a rebuild marked draw, one by one in
-  // canonical order; redrawing every cycle, every end draws. One copy of the
-  // drawing code (instruction-cache footprint).
-  const float4 none = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+  // the ends' trials: the scan reads each end's larger trial scale, four ends
+  // per load (one aligned float4 of the per-end maxima); only ends a rebuild
+  // marked (NaN) draw, one by one in canonical order; redrawing every cycle,
+  // every end draws. One copy of the drawing code (instruction-cache
+  // footprint). The winning end's trials are read once at the end.
   const int nq = select ? 0 : ne;
 #pragma unroll 1
   for (int q0 = 0; q0 < nq; q0 += 4) {
-    float4 t4[4];
+    float m4[4];
+    if (cache) {
+      const float4 v = w.Tmx4(q0);
+      m4[0] = v.x; m4[1] = v.y; m4[2] = v.z; m4[3] = v.w;
+    }
+    bool draws = !cache;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) t4[j] = (cache && q0 + j < nq) ? w.Trial(q0 + j) : none;
-    const bool draws = !cache || isnan(t4[0].x) || isnan(t4[1].x) || isnan(t4[2].x) || isnan(t4[3].x);
+    for (int j = 0; j < 4; ++j) {
+      if (q0 + j >= nq) m4[j] = -INFINITY;  // past the event's ends
+      else if (cache) draws = draws || isnan(m4[j]);
+    }
     if (draws) {
 #pragma unroll 1
       for (int q = q0; q < q0 + 4 && q < nq; ++q) {
-        if (cache && !isnan(w.Trial(q).x)) continue;  // kept
-        float4 tr = none;
+        if (cache && !isnan(w.Tmx(q))) continue;  // kept
+        float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
         const float4 rec = w.End(q);
         if (__float_as_int(rec.w) >= 0) {  // a dipole on this side
           const float lnTmax = fminf(L.lnT, rec.z);
@@ -1381,17 +1437,19 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
             else { tr.z = lt; tr.w = u24(out[3]); }
           }
         }
-        w.Trial(q) = tr;  // with redraw, the cycle's trials (read back below)
+        w.SetTrial(q, tr);  // with redraw, the cycle's trials (read back below)
+        m4[q - q0] = tr.z > tr.x ? tr.z : tr.x;
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) t4[j] = q0 + j < nq ? w.Trial(q0 + j) : none;
     }
-    // the largest wins, the earlier one on ties
+    // the largest wins, the earlier end on ties (and channel 0 within an end)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (t4[j].x > best) { best = t4[j].x; bq = q0 + j; bch = 0; bRz = t4[j].y; }
-      if (t4[j].z > best) { best = t4[j].z; bq = q0 + j; bch = 1; bRz = t4[j].w; }
-    }
+    for (int j = 0; j < 4; ++j)
+      if (m4[j] > best) { best = m4[j]; bq = q0 + j; }
+  }
+  if (!select && bq >= 0) {
+    const float4 tr = w.Trial(bq);
+    bch = tr.z > tr.x ? 1 : 0;
+    bRz = bch ? tr.w : tr.y;
   }
   L.draw = d;
   const int st = step_veto(M, S, ls, w, L, id, cnt, pend, parked, best, bq, bch, bRz);
@@ -1413,7 +1471,7 @@ __device__ int step_mixed(const MixedCtx& M, const SmemPdf& S, const LearnedSmem
     }
     float4 tr = w.Trial(bq);
     if (bch == 0) { tr.x = lt; tr.y = rz; } else { tr.z = lt; tr.w = rz; }
-    w.Trial(bq) = tr;
+    w.SetTrial(bq, tr);
   }
   return st;
 }
@@ -1663,7 +1721,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
         const uint64_t ev_src = __shfl_sync(0xffffffffu, L.ev, src);
         const int slot_src = __shfl_sync(0xffffffffu, L.slot, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, D.stage[warp_id], D.ustage[warp_id],
-                                  WS{M.W, slot_src, M.P.nmax}, D.tag_stage + warp_id * M.P.nmax, true,
+                                  WS{M.W, slot_src, M.P.nmax}, D.tag_stage + warp_id * tag_stage_words(M.P.nmax), true,
                                   slot_src, ev_src, n_src, e0, e1, row_src, lok, cache ? 0 : -1, lane_id);
         rebuilds += 1;
       }
@@ -1698,7 +1756,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
             keep = cache ? 2 * (L.n - 1) : -1;  // the ends that existed before
           } else {
             cnt.vetoes += 1;  // the map failed: the winner's end draws again
-            if (cache) WS{M.W, L.slot, M.P.nmax}.Trial(2 * pend.bi + pend.bside).x = __uint_as_float(0x7fc00000u);
+            if (cache) WS{M.W, L.slot, M.P.nmax}.MarkTrial(2 * pend.bi + pend.bside);
           }
         }
       }
@@ -1715,7 +1773,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
         const int keep_src = __shfl_sync(0xffffffffu, keep, src);
         const int slot_src = __shfl_sync(0xffffffffu, L.slot, src);
         mlp_tiles += rebuild_coop(M, S, mlp_s, ls, D.stage[warp_id], D.ustage[warp_id],
-                                  WS{M.W, slot_src, M.P.nmax}, D.tag_stage + warp_id * M.P.nmax, true,
+                                  WS{M.W, slot_src, M.P.nmax}, D.tag_stage + warp_id * tag_stage_words(M.P.nmax), true,
                                   slot_src, ev_src, n_src, e0, e1, row_src, lok, keep_src, lane_id);
         rebuilds += 1;
       }
@@ -1827,7 +1885,7 @@ __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const Sm
     float4 rec = make_float4(-1.0f, -1.0f, 0.0f, __int_as_float(-1));
     int nd = 0;  // Philox blocks of this end: one per channel present
     if (q < ne) {
-      marked = isnan(w.Trial(q).x);
+      marked = isnan(w.Tmx(q));
       if (marked) {
         rec = w.End(q);
         if (__float_as_int(rec.w) >= 0) nd = (rec.x >= 0.0f ? 1 : 0) + (rec.y >= 0.0f ? 1 : 0);
@@ -1867,7 +1925,7 @@ __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const Sm
           else { tr.z = lt; tr.w = u24(out[3]); }
         }
       }
-      w.Trial(q) = tr;
+      w.SetTrial(q, tr);
     }
     d += (uint64_t)tot;
   }
@@ -1905,7 +1963,7 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
     unsigned defer_mask = 0;
     float4 deferred = make_float4(0.0f, 0.0f, 0.0f, 0.0f), plain = deferred;
     mlp_tiles += rebuild_coop(M, S, mlp_s, D.ls, D.stage[warp_id], D.ustage[warp_id], w,
-                              D.tag_stage + warp_id * M.P.nmax, true, (int)e, e, n, M.V.eta[e],
+                              D.tag_stage + warp_id * tag_stage_words(M.P.nmax), true, (int)e, e, n, M.V.eta[e],
                               M.V.eta[M.V.cap + e], row, (flags & 1) != 0, M.V.keep[e], lane_id, cache, &defer_mask,
                               &deferred, &plain);
     rebuilds += 1;
@@ -2018,7 +2076,7 @@ __global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ Mix
         if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
         else { tr.z = lt; tr.w = u24(out[3]); }
       }
-      w.Trial(qq) = tr;
+      w.SetTrial(qq, tr);
     }
     __syncwarp();
   }
@@ -2147,7 +2205,7 @@ __global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ Mixed
         keep = cache ? 2 * (L.n - 1) : -1;
       } else {
         cnt.vetoes += 1;  // the map failed: the winner's end draws again
-        if (cache) WS{M.W, (int)e, M.P.nmax}.Trial(2 * em.bi + em.bside).x = __uint_as_float(0x7fc00000u);
+        if (cache) WS{M.W, (int)e, M.P.nmax}.MarkTrial(2 * em.bi + em.bside);
       }
       M.V.keep[e] = keep;
       wave_store(M, L);
@@ -2452,11 +2510,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_shower_warp(const __grid_constan
 
 }  // namespace
 
-size_t workset_bytes(int lanes, int nmax) {
-  return (size_t)lanes * nmax * (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
-         (size_t)lanes * (64 + 4 * sizeof(float4));
-}
-
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   char* p = (char*)base;
   W.lanes = lanes;
@@ -2468,6 +2521,8 @@ void workset_carve(void* base, int lanes, int nmax, WorkSet& W) {
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
   W.aux = (float4*)p;
   p += (size_t)lanes * nmax * 2 * sizeof(float4);
+  W.tmx = (float*)p;
+  p += (size_t)lanes * tmx_stride(nmax) * sizeof(float);
   W.lkey = (float4*)p;
   p += (size_t)lanes * 4 * sizeof(float4);
   W.lcode = (unsigned char*)p;
@@ -2708,8 +2763,8 @@ void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
 // lane per event (W.lanes >= n), V is carved for at least n events.
 cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const WorkSet& W, const WaveSet& V,
                                const LearnedCfg& Lc, uint64_t first, uint64_t n, int passes, int budget,
-                               int blocks, int block_size, int sm_count, int period, int emit_batch,
-                               int q_independent, cudaStream_t stream) {
+                               int blocks, int veto_blocks, int block_size, int sm_count, int period,
+                               int emit_batch, int q_independent, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   if (n > V.cap || (uint64_t)W.lanes < n || passes < 0 || budget < 1) return cudaErrorInvalidValue;
   MixedCtx M = mixed_ctx(P, E, W, Lc, first, n, period, emit_batch, q_independent, nullptr);
@@ -2719,6 +2774,8 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
   if (err != cudaSuccess) return err;
   const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0);
   const int tier = mixed_tier(blocks, block_size, sm_count);
+  // the veto kernel's own residency (its register budget)
+  const int veto_tier = mixed_tier(veto_blocks, block_size, sm_count);
   // grid-stride kernels: enough warps to cover the SMs several times
   const int flat_blocks = sm_count * 16;
   k_wave_init<<<flat_blocks, 128, 0, stream>>>(M);
@@ -2729,9 +2786,9 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
     else k_wave_ends<4><<<blocks, block_size, dyn, stream>>>(M);
     if (Lc.learned) k_wave_mlp<<<sm_count * 2, 256, 0, stream>>>(M);
     if (w == passes) break;  // the last rebuilds, then the persistent kernel
-    if (tier == 2) k_wave_veto<2><<<blocks, block_size, dyn, stream>>>(M);
-    else if (tier == 3) k_wave_veto<3><<<blocks, block_size, dyn, stream>>>(M);
-    else k_wave_veto<4><<<blocks, block_size, dyn, stream>>>(M);
+    if (veto_tier == 2) k_wave_veto<2><<<veto_blocks, block_size, dyn, stream>>>(M);
+    else if (veto_tier == 3) k_wave_veto<3><<<veto_blocks, block_size, dyn, stream>>>(M);
+    else k_wave_veto<4><<<veto_blocks, block_size, dyn, stream>>>(M);
     k_wave_emit<<<flat_blocks, 128, 0, stream>>>(M);
   }
   launch_persistent<true>(M, tier, blocks, block_size, dyn, stream);
@@ -2758,15 +2815,9 @@ namespace {
 constexpr int kStaticBlocks = 64, kStaticThreads = 128;
 constexpr int kStaticLanes = kStaticBlocks * kStaticThreads;
 constexpr int kStaticMaxNmax = 32;
-constexpr size_t kStaticWorkBytes =
-    (size_t)kStaticLanes * kStaticMaxNmax * (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
-    (size_t)kStaticLanes * (64 + 4 * sizeof(float4));
-
-// the carve of workset_carve for the static launch shape
-static_assert(kStaticWorkBytes == (size_t)kStaticLanes * kStaticMaxNmax *
-                                      (4 * sizeof(double) + sizeof(uint32_t) + 6 * sizeof(float4)) +
-                                  (size_t)kStaticLanes * (64 + 4 * sizeof(float4)),
-              "static working set differs from workset_bytes");
+// the carve of workset_carve for the static launch shape (a record with fewer
+// parton slots carves less)
+constexpr size_t kStaticWorkBytes = workset_bytes(kStaticLanes, kStaticMaxNmax);
 static __device__ __align__(256) unsigned char g_static_work[kStaticWorkBytes];
 static __device__ __align__(256) float g_static_grid[GAPS_PDF_NFL * GAPS_PDF_NX * GAPS_PDF_NQ];
 static __device__ __align__(256) double g_static_tables[kBoundTableDoubles];

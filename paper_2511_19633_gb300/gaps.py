@@ -51,6 +51,7 @@ class GapsConfig(ctypes.Structure):
         ("n_mix", ctypes.c_int), ("mix", GapsMixRow * GAPS_MAX_MIX), ("trial_mode", ctypes.c_int),
         ("mll_lo", ctypes.c_double), ("mll_hi", ctypes.c_double), ("max_cycles", ctypes.c_int),
         ("wave_passes", ctypes.c_int), ("wave_cycles", ctypes.c_int),
+        ("wave_veto_blocks_per_sm", ctypes.c_int),
     ]
 
 
@@ -436,7 +437,7 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
                 schedule: int = GAPS_SCHED_PER_EVENT, blocks_per_sm: int = 0,
                 refill_period: int = 0, emit_batch: int = 0, mix=None, trial_mode=None,
                 mll=(66.0, 116.0), max_cycles: int = 0, wave_passes: int = 0,
-                wave_cycles: int = 0) -> GapsConfig:
+                wave_cycles: int = 0, wave_veto_blocks_per_sm: int = 0) -> GapsConfig:
     """Builds a gaps_config; pdf_grid is a float32 numpy array [11][100][50] that
     must stay alive until gaps_init returns (it is copied). mix: optional list of
     (process, sqrt_s, t_cut, fraction) rows of a mixed batch; they replace
@@ -445,7 +446,8 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
     dilepton mass window of GAPS_PP_LL (GeV). max_cycles: veto cycles per event
     before GAPS_ERR_ITER_CAP (0 = the library default). wave_passes: passes of
     the wavefront schedule and wave_cycles: veto cycles of an event per pass (0 = the
-    library defaults)."""
+    library defaults); wave_veto_blocks_per_sm: the veto kernel's resident blocks
+    per SM (0 = 2)."""
     ptr = None if pdf_grid is None else pdf_grid.ctypes.data
     c = GapsConfig(process, precision, nf, nmax, sqrt_s, alpha_s_mz, t_cut, p_s, seed, ptr,
                    block_size, schedule, blocks_per_sm, refill_period, emit_batch)
@@ -458,6 +460,7 @@ def make_config(process: int, sqrt_s: float, *, pdf_grid=None, t_cut: float = 1.
     c.max_cycles = int(max_cycles)
     c.wave_passes = int(wave_passes)
     c.wave_cycles = int(wave_cycles)
+    c.wave_veto_blocks_per_sm = int(wave_veto_blocks_per_sm)
     if mix:
         if len(mix) > GAPS_MAX_MIX:
             raise ValueError("at most %d rows" % GAPS_MAX_MIX)
