@@ -303,6 +303,10 @@ def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None, fit=None):
             G.gaps_set_learned_proposal(ctx, *learned)
         if fit is not None:
             G.gaps_set_pdf_ratio_fit(ctx, fit)
+        # every acceptance weight above one, logged with its dipole type and channel
+        vlog = torch.zeros((64, 8), dtype=torch.float32, device="cuda")
+        vcnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        G.gaps_set_violation_log(ctx, vlog, vcnt)
         _plain_pass(G, ctx, ev, first - (1 << 40), min(n, 1 << 16), chunk, stream)
         torch.cuda.synchronize()
         G.gaps_reset_stats(ctx, stream)
@@ -313,13 +317,17 @@ def _time_variant(G, cfg, ev, first, n, chunk, stream, learned=None, fit=None):
         b.record(stream)
         torch.cuda.synchronize()
         st = G.gaps_get_stats(ctx, stream)
+        nv = min(int(vcnt.item()), vlog.shape[0])
+        # entries of the timed run and the warm-up before it: {eta, s, t, w, class or
+        # -1 - (8 type + channel), bin, z, zeta}
+        logged = [[round(float(x), 7) for x in row] for row in vlog[:nv].cpu().tolist()]
     finally:
         G.gaps_destroy(ctx)
     return {"value": n / (a.elapsed_time(b) / 1e3), "unit": "events/s", "events": n,
             "shower_ms": sum(x.elapsed_time(y) for x, y in marks),
             "steps_per_event": st["steps"] / max(1, st["events"]),
             "trials_per_event": st["trials"] / max(1, st["events"]),
-            "violations": st["violations"], "stats": st}
+            "violations": st["violations"], "violation_log": logged[:8], "stats": st}
 
 
 def _pdf_ratio_fit(G, cfg, ev, first, n, stream):

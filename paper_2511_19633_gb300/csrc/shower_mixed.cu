@@ -113,7 +113,12 @@ struct Lane {
 // ---- FP32 PDF -------------------------------------------------------------
 __device__ __forceinline__ bool loc_x(const MixedCtx& M, float x, int& ix, float& fx) {
   if (!(x >= (float)kXMin && x <= (float)kXMax)) return false;
-  float u = (__logf(x) - M.lxminf) / M.dlxf;
+  // ln x to full FP32 precision above x = 1/2: in the last cell the density
+  // falls linearly in ln x to zero at x_max = 1 - 1e-6, and the fast
+  // logarithm's absolute error (about 2^-21) is then comparable with the
+  // distance to x_max, which could break the certified ratio bound there
+  const float lx = x > 0.5f ? logf(x) : __logf(x);
+  float u = (lx - M.lxminf) / M.dlxf;
   ix = (int)floorf(u);
   ix = min(max(ix, 0), kNX - 2);
   fx = u - (float)ix;
@@ -1783,7 +1788,8 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
     warp_steps += 32;
     if (active && !parked) {
       int st = VMAX ? step_vetomax(M, S, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked)
-                    : step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked);
+                    : step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt,
+                                                     pend, parked);
       if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       if (st != GAPS_STATUS_ACTIVE) {
         L.status = st;
@@ -2143,7 +2149,8 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
     warp_steps += 32;
     bool to_emit = false, to_next = false;
     if (active) {
-      int st = step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend, parked);
+      int st = step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend,
+                                              parked);
       if (++L.steps >= M.P.max_steps && st == GAPS_STATUS_ACTIVE) st = GAPS_ERR_ITER_CAP;
       ++cycles;
       if (st != GAPS_STATUS_ACTIVE) {
@@ -2791,7 +2798,8 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
     else k_wave_veto<4><<<veto_blocks, block_size, dyn, stream>>>(M);
     k_wave_emit<<<flat_blocks, 128, 0, stream>>>(M);
   }
-  launch_persistent<true>(M, tier, blocks, block_size, dyn, stream);
+  // the remaining events: a tail of long showers, run like the veto kernel
+  launch_persistent<true>(M, veto_tier, veto_blocks, block_size, dyn, stream);
   k_wave_final<<<flat_blocks, 128, 0, stream>>>(M);
   return cudaGetLastError();
 }
