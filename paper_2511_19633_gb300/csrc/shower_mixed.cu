@@ -1543,21 +1543,30 @@ struct MixedSmem {
 };
 
 // Fills the block's PDF tables and decode table (the caller synchronises).
-__device__ __forceinline__ void mixed_prologue(const MixedCtx& M, SmemPdf& S, unsigned char* dyn, MixedSmem& D) {
+// Dynamic shared memory: the warps' tag staging, then with the learned
+// proposal the height decode table and, for kernels that evaluate the
+// network inside a rebuild (with_stage), the warps' 64-row tile staging.
+__device__ __forceinline__ void mixed_prologue(const MixedCtx& M, SmemPdf& S, unsigned char* dyn, MixedSmem& D,
+                                               bool with_stage) {
   const int nw = blockDim.x >> 5;
   D.tag_stage = reinterpret_cast<uint32_t*>(dyn);
   unsigned char* learned_smem = dyn + tag_stage_bytes(nw, M.P.nmax);
-  D.stage = reinterpret_cast<float(*)[64][4]>(learned_smem);
-  D.ustage = reinterpret_cast<float(*)[64]>(learned_smem + (size_t)nw * 64 * 4 * sizeof(float));
+  D.stage = nullptr;
+  D.ustage = nullptr;
   D.ls.code = nullptr;
   D.ls.dec = nullptr;
   D.ls.key = nullptr;
   if (M.Lc.learned) {
-    float* dec = reinterpret_cast<float*>(learned_smem + (size_t)nw * 64 * 5 * sizeof(float));
+    float* dec = reinterpret_cast<float*>(learned_smem);
     D.ls.dec = dec;
     D.ls.code = M.W.lcode;
     D.ls.key = M.W.lkey;
     for (int k = threadIdx.x; k < 256; k += blockDim.x) dec[k] = k < 255 ? exp2f(-(float)k * 0.0625f) : 0.0f;
+    if (with_stage) {
+      unsigned char* st = learned_smem + 256 * sizeof(float);
+      D.stage = reinterpret_cast<float(*)[64][4]>(st);
+      D.ustage = reinterpret_cast<float(*)[64]>(st + (size_t)nw * 64 * 4 * sizeof(float));
+    }
   }
   for (int q = threadIdx.x; q < 12 * kSmNX; q += blockDim.x) {
     int f = q / kSmNX, ix = q % kSmNX;
@@ -1576,9 +1585,11 @@ __device__ __forceinline__ void mixed_prologue(const MixedCtx& M, SmemPdf& S, un
 }
 
 // dynamic shared memory of a mixed-precision block of `block_size` threads
-__host__ __device__ constexpr size_t mixed_dyn_bytes(int block_size, int nmax, bool learned) {
+// (mixed_prologue's layout)
+__host__ __device__ constexpr size_t mixed_dyn_bytes(int block_size, int nmax, bool learned, bool with_stage) {
   return tag_stage_bytes(block_size / 32, nmax) +
-         (learned ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) + 256 * sizeof(float) : 0);
+         (learned ? 256 * sizeof(float) + (with_stage ? (size_t)(block_size / 32) * 64 * 5 * sizeof(float) : 0)
+                  : 0);
 }
 
 // ---- wavefront schedule: per-event lane state in the WaveSet arrays -------
@@ -1656,7 +1667,7 @@ __global__ void __launch_bounds__(256, MINB) k_shower_mixed(const __grid_constan
   __shared__ SmemPdf S;
   extern __shared__ __align__(16) unsigned char dyn_lane_smem[];
   MixedSmem D;
-  mixed_prologue(M, S, dyn_lane_smem, D);
+  mixed_prologue(M, S, dyn_lane_smem, D, true);
   const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
   const LearnedSmem& ls = D.ls;
   __syncthreads();
@@ -1948,13 +1959,12 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
   const uint64_t count = M.V.ctl[WL_REBUILD];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     M.V.ctl[WL_LIVE0 + (M.wave_par ^ 1)] = 0;  // the next pass's live list
-    M.V.ctl[WL_EMIT] = 0;
     M.V.ctl[WL_GRAB] = 0;
   }
   // blocks past the list's last warp leave before loading their tables
   if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= count) return;
   MixedSmem D;
-  mixed_prologue(M, S, dyn_lane_smem, D);
+  mixed_prologue(M, S, dyn_lane_smem, D, M.P.trial_mode != GAPS_TRIALS_KEEP);
   const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
   __syncthreads();
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
@@ -1979,21 +1989,18 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
                                           defer_mask, off);
       __syncwarp();  // every lane has read the old counter
       if (lane_id == 0) M.V.draw[e] = d;
-      // initial-state ends whose network inputs changed: to the dense pass
+      // initial-state ends whose network inputs changed: to the dense pass,
+      // in the event's own slots (no queue counter), flagged in bits 4..7
       const bool mine = lane_id < 4 && ((defer_mask >> lane_id) & 1u);
-      const unsigned m = __ballot_sync(0xffffffffu, mine);
-      if (m) {
-        unsigned long long base = 0;
-        if (lane_id == 0) base = atomicAdd(&M.V.ctl[WL_MLP], (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (mine) {
-          float4* q = M.V.mlpq + 3 * (base + __popc(m & ((1u << lane_id) - 1u)));
-          q[0] = plain;
-          q[1] = deferred;
-          q[2] = make_float4(__uint_as_float((uint32_t)e), __int_as_float(lane_id | (row << 8)),
-                             __uint_as_float((uint32_t)off), __uint_as_float((uint32_t)(off >> 32)));
-        }
+      const unsigned m = __ballot_sync(0xffffffffu, mine) & 0xFu;
+      if (mine) {
+        float4* q = M.V.mlpq + 3 * (4 * e + lane_id);
+        q[0] = plain;
+        q[1] = deferred;
+        q[2] = make_float4(__uint_as_float((uint32_t)e), __int_as_float(lane_id | (row << 8)),
+                           __uint_as_float((uint32_t)off), __uint_as_float((uint32_t)(off >> 32)));
       }
+      if (lane_id == 0) M.V.flags[e] = (flags & ~(0xF << kWaveMlpShift)) | (int)(m << kWaveMlpShift);
     }
   }
   flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull,
@@ -2007,7 +2014,9 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
 // counters the rebuild pass reserved for it, as the persistent kernel's
 // inline evaluation and first trial loop would give them.
 __global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ MixedCtx M) {
-  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 4 >= M.V.ctl[WL_MLP]) return;  // nothing queued for this block
+  // the events the rebuild pass just took, 32 per warp step
+  const uint64_t count = M.V.ctl[WL_REBUILD];
+  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 32 >= count) return;  // nothing for this block
   __shared__ float dec[256];
   __shared__ float stage_s[8][64][4];
   __shared__ float ustage_s[8][64];
@@ -2030,61 +2039,90 @@ __global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ Mix
   ls.dec = dec;
   const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(wimg);
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
-  const uint64_t count = M.V.ctl[WL_MLP];
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
+  const uint32_t* rebuilt = M.V.list + (size_t)WL_REBUILD * M.V.cap;
   Counters32 cnt;
   unsigned long long tiles = 0;
-  for (uint64_t g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id; 4 * g < count; g += nw) {
-    const uint64_t j = 4 * g + lane_id;
-    const bool have = lane_id < 4 && j < count;
-    float4 plain = make_float4(0.0f, 0.0f, 0.0f, 0.0f), in = plain, tag = plain;
-    if (have) {
-      const float4* q = M.V.mlpq + 3 * j;
-      plain = q[0];
-      in = q[1];
-      tag = q[2];
-    }
-    const unsigned eval = __ballot_sync(0xffffffffu, have) & 0xFu;
-    const int e = (int)__float_as_uint(tag.x), qq = __float_as_int(tag.y) & 0xff, row = __float_as_int(tag.y) >> 8;
-    const float tc = have ? __expf(lnTc[row]) : 1.0f;
-    float scale0 = 0.0f, scale1 = 0.0f;
-    learned_heights(M, mlp_s, ls, stage_s[warp_id], ustage_s[warp_id], eval, tc, in.x, in.y, __float_as_int(in.z),
-                    __float_as_int(in.w), e, qq, lane_id, scale0, scale1, true);
-    tiles += __popc(eval);
-    if (have) {
-      const WS w{M.W, e, M.P.nmax};
-      float4 rec = plain;
-      rec.x *= scale0;
-      rec.y *= scale1;
-      w.End(qq) = rec;
-      // the end's trials, channel by channel, from its reserved counter
-      uint64_t dd = ((uint64_t)__float_as_uint(tag.w) << 32) | (uint64_t)__float_as_uint(tag.z);
-      const uint64_t id = M.first + (uint64_t)e;
-      const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
-      const float lnTmax = fminf(M.V.lnT[e], rec.z);
-      const bool live = lnTmax > lnTc[row];
-      // heavy-quark measure of an incoming c or b (its two channels)
-      const int fe = pdf_index(tag_fl(__float_as_uint(w.Aux(qq).z)));
-      const float m2 = fe > 0 ? (float)M.P.m2[fe] : 0.0f;
-      float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+  for (uint64_t g32 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id) * 32; g32 < count; g32 += nw * 32) {
+    // lane l: event l of the batch and its flagged ends; the warp's ends in
+    // order (event, end), taken four at a time
+    const uint64_t i = g32 + lane_id;
+    const uint32_t ev = i < count ? rebuilt[i] : 0u;
+    const unsigned fm = i < count ? ((unsigned)M.V.flags[ev] >> kWaveMlpShift) & 0xFu : 0u;
+    const int nc = __popc(fm);
+    int incl = nc;  // inclusive prefix sum of the counts
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float ic = c == 0 ? rec.x : rec.y;
-        if (ic < 0.0f) continue;
-        const uint64_t dc = dd++;
-        if (!(live && ic > 0.0f)) continue;
-        uint32_t out[4];
-        philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
-        cnt.trials += 1;
-        cnt.isr_trials += 1;
-        const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
-        if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
-        else { tr.z = lt; tr.w = u24(out[3]); }
-      }
-      w.SetTrial(qq, tr);
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane_id >= off) incl += t;
     }
-    __syncwarp();
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int g = 0; g < total; g += 4) {
+      // end p = g + j (j < 4) belongs to the lane whose range [incl - c, incl) holds it
+      int src = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = g + j;
+        const unsigned own = __ballot_sync(0xffffffffu, p >= incl - nc && p < incl);
+        if (lane_id == j) src = own ? __ffs(own) - 1 : -1;
+      }
+      const int base_src = __shfl_sync(0xffffffffu, incl - nc, src < 0 ? 0 : src);
+      const unsigned fm_src = __shfl_sync(0xffffffffu, fm, src < 0 ? 0 : src);
+      const uint32_t ev_src = __shfl_sync(0xffffffffu, ev, src < 0 ? 0 : src);
+      const bool have = lane_id < 4 && src >= 0;
+      float4 plain = make_float4(0.0f, 0.0f, 0.0f, 0.0f), in = plain, tag = plain;
+      if (have) {
+        // the (g + lane - base)-th flagged end of the event
+        unsigned bits = fm_src;
+        for (int r = g + lane_id - base_src; r > 0; --r) bits &= bits - 1u;
+        const int q = __ffs(bits) - 1;
+        const float4* qe = M.V.mlpq + 3 * (4 * (uint64_t)ev_src + q);
+        plain = qe[0];
+        in = qe[1];
+        tag = qe[2];
+      }
+      const unsigned eval = __ballot_sync(0xffffffffu, have) & 0xFu;
+      const int e = (int)__float_as_uint(tag.x), qq = __float_as_int(tag.y) & 0xff, row = __float_as_int(tag.y) >> 8;
+      const float tc = have ? __expf(lnTc[row]) : 1.0f;
+      float scale0 = 0.0f, scale1 = 0.0f;
+      learned_heights(M, mlp_s, ls, stage_s[warp_id], ustage_s[warp_id], eval, tc, in.x, in.y, __float_as_int(in.z),
+                      __float_as_int(in.w), e, qq, lane_id, scale0, scale1, true);
+      tiles += __popc(eval);
+      if (have) {
+        const WS w{M.W, e, M.P.nmax};
+        float4 rec = plain;
+        rec.x *= scale0;
+        rec.y *= scale1;
+        w.End(qq) = rec;
+        // the end's trials, channel by channel, from its reserved counter
+        uint64_t dd = ((uint64_t)__float_as_uint(tag.w) << 32) | (uint64_t)__float_as_uint(tag.z);
+        const uint64_t id = M.first + (uint64_t)e;
+        const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+        const float lnTmax = fminf(M.V.lnT[e], rec.z);
+        const bool live = lnTmax > lnTc[row];
+        // heavy-quark measure of an incoming c or b (its two channels)
+        const int fe = pdf_index(tag_fl(__float_as_uint(w.Aux(qq).z)));
+        const float m2 = fe > 0 ? (float)M.P.m2[fe] : 0.0f;
+        float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
+  #pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float ic = c == 0 ? rec.x : rec.y;
+          if (ic < 0.0f) continue;
+          const uint64_t dc = dd++;
+          if (!(live && ic > 0.0f)) continue;
+          uint32_t out[4];
+          philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
+          cnt.trials += 1;
+          cnt.isr_trials += 1;
+          const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
+          if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
+          else { tr.z = lt; tr.w = u24(out[3]); }
+        }
+        w.SetTrial(qq, tr);
+      }
+      __syncwarp();
+    }
   }
   flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, 0, lane_id == 0 ? tiles : 0ull, lane_id);
 }
@@ -2099,12 +2137,11 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
   const uint64_t n_work = M.V.ctl[M.wave_par];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     M.V.ctl[WL_REBUILD] = 0;  // filled by this pass's emissions
-    M.V.ctl[WL_MLP] = 0;      // filled by the next pass's rebuilds
   }
   // blocks with more lanes than the list has events leave before loading their tables
   if ((uint64_t)blockIdx.x * blockDim.x >= n_work) return;
   MixedSmem D;
-  mixed_prologue(M, S, dyn_lane_smem, D);
+  mixed_prologue(M, S, dyn_lane_smem, D, false);
   const LearnedSmem& ls = D.ls;
   __syncthreads();
   const int lane_id = threadIdx.x & 31;
@@ -2118,36 +2155,47 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
   L.learned_ok = false;
   bool active = false, exhausted = false, parked = false;
   int cycles = 0, since_refill = M.period;
+  // the warp's share of the live list: [gnext, gend), kWaveGrab events taken
+  // with one atomic on the work counter (warp-uniform)
+  uint64_t gnext = 0, gend = 0;
   Emission pend;
   Counters32 cnt;
   unsigned long long finished = 0, err_cap = 0, err_iter = 0, err_num = 0, lane_steps = 0, warp_steps = 0;
   while (true) {
     const unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (idle && !exhausted && since_refill >= M.period) {
+    if (idle && since_refill >= M.period && !(exhausted && gnext >= gend)) {
       since_refill = 0;
-      unsigned long long base = 0;
-      if (lane_id == 0) base = atomicAdd(&M.V.ctl[WL_GRAB], (unsigned long long)__popc(idle));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base >= n_work) exhausted = true;
-      if (!active) {
-        const uint64_t i = base + __popc(idle & ((1u << lane_id) - 1u));
-        if (i < n_work) {
-          wave_load(M, L, live[i]);
-          active = true;
-          cycles = 0;
+      if (gnext >= gend) {
+        unsigned long long base = 0;
+        if (lane_id == 0) base = atomicAdd(&M.V.ctl[WL_GRAB], (unsigned long long)kWaveGrab);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_work) {
+          exhausted = true;
+          gnext = gend = n_work;
+        } else {
+          gnext = base;
+          gend = base + kWaveGrab < n_work ? base + kWaveGrab : n_work;
         }
       }
+      const uint64_t i = gnext + __popc(idle & ((1u << lane_id) - 1u));
+      if (!active && i < gend) {
+        wave_load(M, L, live[i]);
+        active = true;
+        cycles = 0;
+      }
+      const uint64_t take = (uint64_t)__popc(idle);
+      gnext = gnext + take < gend ? gnext + take : gend;
     }
     const unsigned act = __ballot_sync(0xffffffffu, active);
     if (act == 0) {
-      if (exhausted) break;
+      if (exhausted && gnext >= gend) break;
       since_refill = M.period;
       continue;
     }
     since_refill += 1;
     lane_steps += __popc(act);
     warp_steps += 32;
-    bool to_emit = false, to_next = false;
+    bool to_next = false;
     if (active) {
       int st = step_mixed(M, S, ls, WS{M.W, L.slot, M.P.nmax}, L, M.first + L.ev, cnt, pend,
                                               parked);
@@ -2167,7 +2215,7 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
         parked = false;
         *reinterpret_cast<Emission*>(M.V.pend + L.ev * kWavePendBytes) = pend;
         wave_store(M, L);
-        to_emit = true;
+        M.V.flags[L.ev] |= kWaveParked;  // the emission pass takes it from the live list
         active = false;
       } else if (cycles >= M.wave_budget) {
         wave_store(M, L);  // continues in the next pass
@@ -2175,18 +2223,19 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
         active = false;
       }
     }
-    wave_append(M, WL_EMIT, to_emit, L.ev, lane_id);
     wave_append(M, next_live, to_next, L.ev, lane_id);
   }
   flush_counters(M, cnt, finished, err_cap, err_iter, err_num, lane_id == 0 ? lane_steps : 0ull,
                  lane_id == 0 ? warp_steps : 0ull, 0, 0, lane_id);
 }
 
-// One thread per parked emission: the FP64 kinematics and colours of the
-// persistent kernel's flush; the event joins the next live list and, when its
-// end table changed, the rebuild list.
+// One thread per event of the pass's live list; those the veto pass parked
+// an emission for get the FP64 kinematics and colours of the persistent
+// kernel's flush, then join the next live list and, when their end table
+// changed, the rebuild list.
 __global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ MixedCtx M) {
-  const uint64_t count = M.V.ctl[WL_EMIT];
+  const uint64_t count = M.V.ctl[M.wave_par];
+  const uint32_t* live = M.V.list + (size_t)M.wave_par * M.V.cap;
   if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
   const int lane_id = threadIdx.x & 31;
   const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
@@ -2195,10 +2244,15 @@ __global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ Mixed
   Counters32 cnt;
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < count; b += stride) {
     const uint64_t i = b + lane_id;
-    bool have = i < count, rebuild = false;
+    bool have = false, rebuild = false;
     uint64_t e = 0;
+    if (i < count) {
+      e = live[i];
+      const int f = M.V.flags[e];
+      have = (f & kWaveParked) != 0;
+      if (have) M.V.flags[e] = f & ~kWaveParked;
+    }
     if (have) {
-      e = M.V.list[(size_t)WL_EMIT * M.V.cap + i];
       Lane L;
       wave_load(M, L, e);
       const Emission em = *reinterpret_cast<const Emission*>(M.V.pend + e * kWavePendBytes);
@@ -2726,7 +2780,7 @@ cudaError_t launch_shower_mixed(const DevParams& P, const DevEvents& E, const Wo
   if (err != cudaSuccess) return err;
   // learned proposal: per-warp staging, height decode table, 64 bytes of
   // height codes per lane
-  const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0);
+  const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0, true);
   const int tier = mixed_tier(blocks, block_size, sm_count);
   if (P.trial_mode == GAPS_TRIALS_VETOMAX) launch_persistent<false, true>(M, tier, blocks, block_size, dyn, stream);
   else launch_persistent<false>(M, tier, blocks, block_size, dyn, stream);
@@ -2779,7 +2833,13 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
   M.wave_budget = budget;
   cudaError_t err = cudaMemsetAsync(V.ctl, 0, WL_NCTL * sizeof(unsigned long long), stream);
   if (err != cudaSuccess) return err;
-  const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, Lc.learned != 0);
+  // dynamic shared memory: the rebuild kernel evaluates the network itself
+  // only when it redraws (with kept trials the network pass does), the veto
+  // kernel only decodes heights, the persistent kernel does both
+  const bool learned = Lc.learned != 0;
+  const size_t dyn_ends = mixed_dyn_bytes(block_size, P.nmax, learned, P.trial_mode != GAPS_TRIALS_KEEP);
+  const size_t dyn_veto = mixed_dyn_bytes(block_size, P.nmax, learned, false);
+  const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, learned, true);
   const int tier = mixed_tier(blocks, block_size, sm_count);
   // the veto kernel's own residency (its register budget)
   const int veto_tier = mixed_tier(veto_blocks, block_size, sm_count);
@@ -2788,14 +2848,14 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
   k_wave_init<<<flat_blocks, 128, 0, stream>>>(M);
   for (int w = 0; w <= passes; ++w) {
     M.wave_par = w & 1;
-    if (tier == 2) k_wave_ends<2><<<blocks, block_size, dyn, stream>>>(M);
-    else if (tier == 3) k_wave_ends<3><<<blocks, block_size, dyn, stream>>>(M);
-    else k_wave_ends<4><<<blocks, block_size, dyn, stream>>>(M);
+    if (tier == 2) k_wave_ends<2><<<blocks, block_size, dyn_ends, stream>>>(M);
+    else if (tier == 3) k_wave_ends<3><<<blocks, block_size, dyn_ends, stream>>>(M);
+    else k_wave_ends<4><<<blocks, block_size, dyn_ends, stream>>>(M);
     if (Lc.learned) k_wave_mlp<<<sm_count * 2, 256, 0, stream>>>(M);
     if (w == passes) break;  // the last rebuilds, then the persistent kernel
-    if (veto_tier == 2) k_wave_veto<2><<<veto_blocks, block_size, dyn, stream>>>(M);
-    else if (veto_tier == 3) k_wave_veto<3><<<veto_blocks, block_size, dyn, stream>>>(M);
-    else k_wave_veto<4><<<veto_blocks, block_size, dyn, stream>>>(M);
+    if (veto_tier == 2) k_wave_veto<2><<<veto_blocks, block_size, dyn_veto, stream>>>(M);
+    else if (veto_tier == 3) k_wave_veto<3><<<veto_blocks, block_size, dyn_veto, stream>>>(M);
+    else k_wave_veto<4><<<veto_blocks, block_size, dyn_veto, stream>>>(M);
     k_wave_emit<<<flat_blocks, 128, 0, stream>>>(M);
   }
   // the remaining events: a tail of long showers, run like the veto kernel
