@@ -255,8 +255,8 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n,
  * The paper has no counterpart: it is the GAPS_MIXED persistent shower of
  * gaps_shower, run with 64 blocks of 128 threads and emission batch 8, with
  * every piece of scratch memory held in device arrays of the library itself:
- * a working set for at most 32 partons per event (35.7 MB), the work counter,
- * the statistics and copies of the PDF grid and its bound tables (35.9 MB in
+ * a working set for at most 32 partons per event (37.7 MB), the work counter,
+ * the statistics and copies of the PDF grid and its bound tables (38.0 MB in
  * all). Every GPU that loads the library keeps these arrays until the process
  * exits. It needs no context: `cfg` is read as in gaps_init and the caller
  * still passes the event records, written by gaps_generate_hard or an

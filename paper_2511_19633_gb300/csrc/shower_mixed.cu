@@ -2873,7 +2873,7 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
 // device footprint), or code whose memory is fixed before it starts. For them
 // the mixed-precision shower runs with every piece of its scratch memory in
 // file-scope device arrays: the per-lane working set of 64 blocks x 128 threads
-// for at most 32 partons per event (27.3 MB), the work counter, the
+// for at most 32 partons per event (37.7 MB), the work counter, the
 // statistics, and copies of the PDF grid and its bound tables. Every GPU that
 // loads the library holds these arrays until the process exits.
 // ---------------------------------------------------------------------------

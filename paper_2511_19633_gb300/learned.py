@@ -18,7 +18,7 @@ from . import gaps as G
 # disjoint from every measured range)
 DEFAULTS = dict(first_event=3 << 40, n_events=1 << 22, capacity=1 << 20, holdout_offset=1 << 36,
                 holdout_events=1 << 21, holdout_capacity=2 << 20, steps=40000, lr=2e-3, tau=0.97, seed=3,
-                slack=0.2, min_rows=64, target_floor=math.log(1e-4))
+                slack=0.2, min_rows=2048, target_floor=math.log(1e-4))
 
 
 def learn_config(**kw) -> G.GapsLearnConfig:
