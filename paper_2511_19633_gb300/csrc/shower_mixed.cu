@@ -473,7 +473,9 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, co
   float zm, delta;
   const bool ok = tk > tc && zlim32(type, tc, s, eta, zm, delta);
   float ic[2] = {0.0f, -1.0f};
-  for (int c = 0; c < nch; ++c) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (c >= nch) continue;
     ic[c] = 0.0f;
     if (!ok) continue;
     const int ch = first + c;
@@ -620,15 +622,18 @@ __device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& m
 // the learned proposal the warp then evaluates the network for those of the
 // (up to four) initial-state ends whose inputs changed since their last
 // evaluation: 2 channels x 8 bins = one 16-row tile per end, two rows per
-// lane for the inputs and the bin heights.
+// lane for the inputs and the bin heights. The body is inlined into the
+// wavefront's rebuild kernel (a call there costs parameter and register
+// traffic through local memory) and called out of line elsewhere
+// (rebuild_coop: one copy in each of the larger kernels' code).
 template <class W>
-__device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
-                                         const LearnedSmem& ls, float (*stage)[4], float* ustage,
-                                         const W& w, uint32_t* tg, bool stage_tags, int slot, uint64_t ev_src,
-                                         int n, double eta0, double eta1, int row, bool learned_src,
-                                         int keep_ends, int lane_id, bool defer = false,
-                                         unsigned* defer_mask = nullptr, float4* deferred = nullptr,
-                                         float4* isr_plain = nullptr) {
+__device__ __forceinline__ int rebuild_body(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
+                                            const LearnedSmem& ls, float (*stage)[4], float* ustage,
+                                            const W& w, uint32_t* tg, bool stage_tags, int slot, uint64_t ev_src,
+                                            int n, double eta0, double eta1, int row, bool learned_src,
+                                            int keep_ends, int lane_id, bool defer = false,
+                                            unsigned* defer_mask = nullptr, float4* deferred = nullptr,
+                                            float4* isr_plain = nullptr) {
   // the event's tags in shared memory, and (lane kernels) the table of the
   // slot owning each colour and anticolour tag, so that an end finds its
   // partner in one lookup; with a tag held by two partons (not a leading-
@@ -735,6 +740,16 @@ __device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, co
   }
   __syncwarp();
   return defer ? 0 : __popc(eval);
+}
+
+template <class W>
+__device__ __noinline__ int rebuild_coop(const MixedCtx& M, const SmemPdf& S, const MlpSmem& mlp,
+                                         const LearnedSmem& ls, float (*stage)[4], float* ustage,
+                                         const W& w, uint32_t* tg, bool stage_tags, int slot, uint64_t ev_src,
+                                         int n, double eta0, double eta1, int row, bool learned_src,
+                                         int keep_ends, int lane_id) {
+  return rebuild_body(M, S, mlp, ls, stage, ustage, w, tg, stage_tags, slot, ev_src, n, eta0, eta1, row,
+                      learned_src, keep_ends, lane_id);
 }
 
 struct Emission {
@@ -1978,7 +1993,7 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
     const WS w{M.W, (int)e, M.P.nmax};
     unsigned defer_mask = 0;
     float4 deferred = make_float4(0.0f, 0.0f, 0.0f, 0.0f), plain = deferred;
-    mlp_tiles += rebuild_coop(M, S, mlp_s, D.ls, D.stage[warp_id], D.ustage[warp_id], w,
+    mlp_tiles += rebuild_body(M, S, mlp_s, D.ls, D.stage[warp_id], D.ustage[warp_id], w,
                               D.tag_stage + warp_id * tag_stage_words(M.P.nmax), true, (int)e, e, n, M.V.eta[e],
                               M.V.eta[M.V.cap + e], row, (flags & 1) != 0, M.V.keep[e], lane_id, cache, &defer_mask,
                               &deferred, &plain);
