@@ -97,22 +97,24 @@ struct WaveSet {
   int* steps;               // [cap] veto cycles so far
   int* flags;               // [cap] bit 0: learned bounds active; bit 1: write the record
                             // back; bit 2: write the status back only; bit 3: an emission
-                            // is parked; bits 4..7: initial-state ends for the network
-                            // pass; bits 8..15: mix row
+                            // is parked; bits 8..15: mix row
   int* keep;                // [cap] ends that may keep their trials at the next rebuild (-1: none)
   double* eta;              // [2][cap] momentum fractions of slots 0 and 1
   uint64_t* draw;           // [cap] next Philox block of the event's stream
   unsigned char* pend;      // [cap][kWavePendBytes] the parked emission of the pass
   uint32_t* list;           // [4][cap] live events of even / odd passes, (unused), rebuilds
   float4* mlpq;             // [cap][4 ends][3] initial-state ends for the dense network pass
+  uint32_t* mlpi;           // [4 cap] the pass's queue of those ends: 4 event + end
   unsigned long long* ctl;  // [8] lengths of the lists, work counter of the veto pass
   uint64_t cap;
 };
 constexpr int kWavePendBytes = 64;
-enum WaveList { WL_LIVE0 = 0, WL_LIVE1 = 1, WL_REBUILD = 3, WL_GRAB = 4, WL_NCTL = 8 };
+enum WaveList { WL_LIVE0 = 0, WL_LIVE1 = 1, WL_REBUILD = 3, WL_GRAB = 4, WL_MLP = 5, WL_NCTL = 8 };
+// entries of a rebuild warp's network-queue buffer in shared memory (one
+// atomic on the queue length per flush)
+constexpr int kMlpBuf = 256;
 // WaveSet::flags bits
 constexpr int kWaveParked = 8;
-constexpr int kWaveMlpShift = 4;
 // events of the live list a veto warp takes with one atomic on the work counter
 constexpr int kWaveGrab = 32;
 size_t wave_state_bytes(uint64_t cap);

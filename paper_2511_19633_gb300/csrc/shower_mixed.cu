@@ -1979,12 +1979,28 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
   // blocks past the list's last warp leave before loading their tables
   if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= count) return;
   MixedSmem D;
-  mixed_prologue(M, S, dyn_lane_smem, D, M.P.trial_mode != GAPS_TRIALS_KEEP);
+  const bool with_stage = M.P.trial_mode != GAPS_TRIALS_KEEP;
+  mixed_prologue(M, S, dyn_lane_smem, D, with_stage);
   const MlpSmem& mlp_s = *reinterpret_cast<const MlpSmem*>(M.Lc.image);
   __syncthreads();
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const bool cache = M.P.trial_mode == GAPS_TRIALS_KEEP;
+  // the warp's buffer of initial-state ends for the network pass (with the
+  // learned proposal and kept trials), after the prologue's shared memory
+  uint32_t* mbuf = reinterpret_cast<uint32_t*>(
+                       dyn_lane_smem + mixed_dyn_bytes(blockDim.x, M.P.nmax, M.Lc.learned != 0, with_stage)) +
+                   warp_id * kMlpBuf;
+  int mfill = 0;  // warp-uniform
+  auto mflush = [&]() {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane_id == 0) base = atomicAdd(&M.V.ctl[WL_MLP], (unsigned long long)mfill);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int j = lane_id; j < mfill; j += 32) M.V.mlpi[base + j] = mbuf[j];
+    __syncwarp();
+    mfill = 0;
+  };
   unsigned long long rebuilds = 0, mlp_tiles = 0;
   Counters32 cnt;
   for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id; i < count; i += nw) {
@@ -2004,8 +2020,9 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
                                           defer_mask, off);
       __syncwarp();  // every lane has read the old counter
       if (lane_id == 0) M.V.draw[e] = d;
-      // initial-state ends whose network inputs changed: to the dense pass,
-      // in the event's own slots (no queue counter), flagged in bits 4..7
+      // initial-state ends whose network inputs changed: their inputs in the
+      // event's own slots, their index to the warp's buffer for the network
+      // pass's queue
       const bool mine = lane_id < 4 && ((defer_mask >> lane_id) & 1u);
       const unsigned m = __ballot_sync(0xffffffffu, mine) & 0xFu;
       if (mine) {
@@ -2015,9 +2032,15 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
         q[2] = make_float4(__uint_as_float((uint32_t)e), __int_as_float(lane_id | (row << 8)),
                            __uint_as_float((uint32_t)off), __uint_as_float((uint32_t)(off >> 32)));
       }
-      if (lane_id == 0) M.V.flags[e] = (flags & ~(0xF << kWaveMlpShift)) | (int)(m << kWaveMlpShift);
+      if (m) {
+        const int k = __popc(m);
+        if (mfill + k > kMlpBuf) mflush();
+        if (mine) mbuf[mfill + __popc(m & ((1u << lane_id) - 1u))] = (uint32_t)(4 * e + lane_id);
+        mfill += k;
+      }
     }
   }
+  if (mfill) mflush();
   flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, lane_id == 0 ? rebuilds : 0ull, lane_id == 0 ? mlp_tiles : 0ull,
                  lane_id);
 }
@@ -2029,9 +2052,9 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
 // counters the rebuild pass reserved for it, as the persistent kernel's
 // inline evaluation and first trial loop would give them.
 __global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ MixedCtx M) {
-  // the events the rebuild pass just took, 32 per warp step
-  const uint64_t count = M.V.ctl[WL_REBUILD];
-  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 32 >= count) return;  // nothing for this block
+  // the pass's queue of initial-state ends, four per warp step
+  const uint64_t count = M.V.ctl[WL_MLP];
+  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 4 >= count) return;  // nothing queued for this block
   __shared__ float dec[256];
   __shared__ float stage_s[8][64][4];
   __shared__ float ustage_s[8][64];
@@ -2056,88 +2079,59 @@ __global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ Mix
   const int lane_id = threadIdx.x & 31, warp_id = threadIdx.x >> 5;
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t k0 = (uint32_t)M.P.seed, k1 = (uint32_t)(M.P.seed >> 32);
-  const uint32_t* rebuilt = M.V.list + (size_t)WL_REBUILD * M.V.cap;
   Counters32 cnt;
   unsigned long long tiles = 0;
-  for (uint64_t g32 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id) * 32; g32 < count; g32 += nw * 32) {
-    // lane l: event l of the batch and its flagged ends; the warp's ends in
-    // order (event, end), taken four at a time
-    const uint64_t i = g32 + lane_id;
-    const uint32_t ev = i < count ? rebuilt[i] : 0u;
-    const unsigned fm = i < count ? ((unsigned)M.V.flags[ev] >> kWaveMlpShift) & 0xFu : 0u;
-    const int nc = __popc(fm);
-    int incl = nc;  // inclusive prefix sum of the counts
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane_id >= off) incl += t;
+  for (uint64_t g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id; 4 * g < count; g += nw) {
+    const uint64_t j = 4 * g + lane_id;
+    const bool have = lane_id < 4 && j < count;
+    float4 plain = make_float4(0.0f, 0.0f, 0.0f, 0.0f), in = plain, tag = plain;
+    if (have) {
+      const uint32_t idx = M.V.mlpi[j];
+      const float4* qe = M.V.mlpq + 3 * (uint64_t)idx;  // slot (event idx / 4, end idx % 4)
+      plain = qe[0];
+      in = qe[1];
+      tag = qe[2];
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int g = 0; g < total; g += 4) {
-      // end p = g + j (j < 4) belongs to the lane whose range [incl - c, incl) holds it
-      int src = 0;
+    const unsigned eval = __ballot_sync(0xffffffffu, have) & 0xFu;
+    const int e = (int)__float_as_uint(tag.x), qq = __float_as_int(tag.y) & 0xff, row = __float_as_int(tag.y) >> 8;
+    const float tc = have ? __expf(lnTc[row]) : 1.0f;
+    float scale0 = 0.0f, scale1 = 0.0f;
+    learned_heights(M, mlp_s, ls, stage_s[warp_id], ustage_s[warp_id], eval, tc, in.x, in.y, __float_as_int(in.z),
+                    __float_as_int(in.w), e, qq, lane_id, scale0, scale1, true);
+    tiles += __popc(eval);
+    if (have) {
+      const WS w{M.W, e, M.P.nmax};
+      float4 rec = plain;
+      rec.x *= scale0;
+      rec.y *= scale1;
+      w.End(qq) = rec;
+      // the end's trials, channel by channel, from its reserved counter
+      uint64_t dd = ((uint64_t)__float_as_uint(tag.w) << 32) | (uint64_t)__float_as_uint(tag.z);
+      const uint64_t id = M.first + (uint64_t)e;
+      const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
+      const float lnTmax = fminf(M.V.lnT[e], rec.z);
+      const bool live = lnTmax > lnTc[row];
+      // heavy-quark measure of an incoming c or b (its two channels)
+      const int fe = pdf_index(tag_fl(__float_as_uint(w.Aux(qq).z)));
+      const float m2 = fe > 0 ? (float)M.P.m2[fe] : 0.0f;
+      float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int p = g + j;
-        const unsigned own = __ballot_sync(0xffffffffu, p >= incl - nc && p < incl);
-        if (lane_id == j) src = own ? __ffs(own) - 1 : -1;
+      for (int c = 0; c < 2; ++c) {
+        const float ic = c == 0 ? rec.x : rec.y;
+        if (ic < 0.0f) continue;
+        const uint64_t dc = dd++;
+        if (!(live && ic > 0.0f)) continue;
+        uint32_t out[4];
+        philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
+        cnt.trials += 1;
+        cnt.isr_trials += 1;
+        const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
+        if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
+        else { tr.z = lt; tr.w = u24(out[3]); }
       }
-      const int base_src = __shfl_sync(0xffffffffu, incl - nc, src < 0 ? 0 : src);
-      const unsigned fm_src = __shfl_sync(0xffffffffu, fm, src < 0 ? 0 : src);
-      const uint32_t ev_src = __shfl_sync(0xffffffffu, ev, src < 0 ? 0 : src);
-      const bool have = lane_id < 4 && src >= 0;
-      float4 plain = make_float4(0.0f, 0.0f, 0.0f, 0.0f), in = plain, tag = plain;
-      if (have) {
-        // the (g + lane - base)-th flagged end of the event
-        unsigned bits = fm_src;
-        for (int r = g + lane_id - base_src; r > 0; --r) bits &= bits - 1u;
-        const int q = __ffs(bits) - 1;
-        const float4* qe = M.V.mlpq + 3 * (4 * (uint64_t)ev_src + q);
-        plain = qe[0];
-        in = qe[1];
-        tag = qe[2];
-      }
-      const unsigned eval = __ballot_sync(0xffffffffu, have) & 0xFu;
-      const int e = (int)__float_as_uint(tag.x), qq = __float_as_int(tag.y) & 0xff, row = __float_as_int(tag.y) >> 8;
-      const float tc = have ? __expf(lnTc[row]) : 1.0f;
-      float scale0 = 0.0f, scale1 = 0.0f;
-      learned_heights(M, mlp_s, ls, stage_s[warp_id], ustage_s[warp_id], eval, tc, in.x, in.y, __float_as_int(in.z),
-                      __float_as_int(in.w), e, qq, lane_id, scale0, scale1, true);
-      tiles += __popc(eval);
-      if (have) {
-        const WS w{M.W, e, M.P.nmax};
-        float4 rec = plain;
-        rec.x *= scale0;
-        rec.y *= scale1;
-        w.End(qq) = rec;
-        // the end's trials, channel by channel, from its reserved counter
-        uint64_t dd = ((uint64_t)__float_as_uint(tag.w) << 32) | (uint64_t)__float_as_uint(tag.z);
-        const uint64_t id = M.first + (uint64_t)e;
-        const uint32_t e0 = (uint32_t)id, e1 = (uint32_t)(id >> 32);
-        const float lnTmax = fminf(M.V.lnT[e], rec.z);
-        const bool live = lnTmax > lnTc[row];
-        // heavy-quark measure of an incoming c or b (its two channels)
-        const int fe = pdf_index(tag_fl(__float_as_uint(w.Aux(qq).z)));
-        const float m2 = fe > 0 ? (float)M.P.m2[fe] : 0.0f;
-        float4 tr = make_float4(-INFINITY, 0.5f, -INFINITY, 0.5f);
-  #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const float ic = c == 0 ? rec.x : rec.y;
-          if (ic < 0.0f) continue;
-          const uint64_t dc = dd++;
-          if (!(live && ic > 0.0f)) continue;
-          uint32_t out[4];
-          philox(e0, e1, (uint32_t)dc, (uint32_t)(dc >> 32), k0, k1, out);
-          cnt.trials += 1;
-          cnt.isr_trials += 1;
-          const float lt = trial_lnt(lnTmax, ic, __logf(u24(out[1])), m2);
-          if (c == 0) { tr.x = lt; tr.y = u24(out[3]); }
-          else { tr.z = lt; tr.w = u24(out[3]); }
-        }
-        w.SetTrial(qq, tr);
-      }
-      __syncwarp();
+      w.SetTrial(qq, tr);
     }
+    __syncwarp();
   }
   flush_counters(M, cnt, 0, 0, 0, 0, 0, 0, 0, lane_id == 0 ? tiles : 0ull, lane_id);
 }
@@ -2152,6 +2146,7 @@ __global__ void __launch_bounds__(256, MINB) k_wave_veto(const __grid_constant__
   const uint64_t n_work = M.V.ctl[M.wave_par];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     M.V.ctl[WL_REBUILD] = 0;  // filled by this pass's emissions
+    M.V.ctl[WL_MLP] = 0;      // filled by the next pass's rebuilds
   }
   // blocks with more lanes than the list has events leave before loading their tables
   if ((uint64_t)blockIdx.x * blockDim.x >= n_work) return;
@@ -2811,7 +2806,8 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 size_t wave_state_bytes(uint64_t cap) {
   return al256(cap * sizeof(float)) + 6 * al256(cap * sizeof(int)) + al256(2 * cap * sizeof(double)) +
          al256(cap * sizeof(uint64_t)) + al256(cap * (size_t)kWavePendBytes) + al256(4 * cap * sizeof(uint32_t)) +
-         al256(12 * cap * sizeof(float4)) + al256(WL_NCTL * sizeof(unsigned long long));
+         al256(12 * cap * sizeof(float4)) + al256(4 * cap * sizeof(uint32_t)) +
+         al256(WL_NCTL * sizeof(unsigned long long));
 }
 
 void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
@@ -2830,6 +2826,7 @@ void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
   V.pend = (unsigned char*)take(cap * (size_t)kWavePendBytes);
   V.list = (uint32_t*)take(4 * cap * sizeof(uint32_t));
   V.mlpq = (float4*)take(12 * cap * sizeof(float4));
+  V.mlpi = (uint32_t*)take(4 * cap * sizeof(uint32_t));
   V.ctl = (unsigned long long*)take(WL_NCTL * sizeof(unsigned long long));
 }
 
@@ -2852,7 +2849,9 @@ cudaError_t launch_shower_wave(const DevParams& P, const DevEvents& E, const Wor
   // only when it redraws (with kept trials the network pass does), the veto
   // kernel only decodes heights, the persistent kernel does both
   const bool learned = Lc.learned != 0;
-  const size_t dyn_ends = mixed_dyn_bytes(block_size, P.nmax, learned, P.trial_mode != GAPS_TRIALS_KEEP);
+  const bool keep = P.trial_mode == GAPS_TRIALS_KEEP;
+  const size_t dyn_ends = mixed_dyn_bytes(block_size, P.nmax, learned, !keep) +
+                          (learned && keep ? (size_t)(block_size / 32) * kMlpBuf * sizeof(uint32_t) : 0);
   const size_t dyn_veto = mixed_dyn_bytes(block_size, P.nmax, learned, false);
   const size_t dyn = mixed_dyn_bytes(block_size, P.nmax, learned, true);
   const int tier = mixed_tier(blocks, block_size, sm_count);
