@@ -112,7 +112,7 @@ constexpr int kWavePendBytes = 64;
 enum WaveList { WL_LIVE0 = 0, WL_LIVE1 = 1, WL_REBUILD = 3, WL_GRAB = 4, WL_MLP = 5, WL_NCTL = 8 };
 // entries of a rebuild warp's network-queue buffer in shared memory (one
 // atomic on the queue length per flush)
-constexpr int kMlpBuf = 256;
+constexpr int kMlpBuf = 64;
 // WaveSet::flags bits
 constexpr int kWaveParked = 8;
 // events of the live list a veto warp takes with one atomic on the work counter
