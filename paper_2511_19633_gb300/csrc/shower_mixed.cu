@@ -375,6 +375,23 @@ __device__ __forceinline__ void mlp_features(float eta, float s, float tc, int b
   f[3] = (float)cls * (1.0f / 21.5f) - 1.0f;
 }
 
+// channel_over's overestimate in FP32: the same shapes, and coefficients equal
+// to the FP64 ones rounded to float (2 C_F is the exact double of C_F, n_f T_R
+// / 2 = n_f / 4 is exact), without FP64 instructions, which run at 1/64 of
+// the FP32 rate here
+__device__ __forceinline__ void channel_over32(int ch, int type, int nf, int& shape, float& coef) {
+  constexpr float cf = (float)kCF, ca = (float)kCA, tr = (float)kTR;
+  switch (ch) {
+    case 0: shape = kSoft; coef = 2.0f * cf; break;
+    case 1: shape = kSoft; coef = ca; break;
+    case 2: shape = kFlat; coef = (float)nf * tr * 0.5f; break;
+    case 3: shape = kSoft; coef = 2.0f * cf; break;
+    case 4: shape = type == kIF ? kSoft : kFlat; coef = tr; break;
+    case 5: shape = kBoth; coef = ca; break;
+    default: shape = type == kIF ? kBoth : kInv; coef = cf; break;
+  }
+}
+
 struct IsrEval {
   float r, x, omx, u, omu, v, sumF;
   float fr;       // the PDF ratio F(eta/x)/F(eta) (corrected for a heavy quark)
@@ -442,7 +459,7 @@ __device__ IsrEval isr_eval32(const MixedCtx& M, const SmemPdf& S, int type, int
 // veto's inputs {s, eta, emitter tag, partner tag}.
 template <class W>
 __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, const uint32_t* tg,
-                             const unsigned char* own, int n, double eta0, double eta1, int row, int q,
+                             const unsigned char* own, int n, float eta0, float eta1, int row, int q,
                              float& s_out, float& eta_out, int& type_out, float4& aux_out) {
   type_out = -1;
   aux_out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -460,8 +477,8 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, co
   for (int mu = 0; mu < 4; ++mu) { pi[mu] = w.P(mu, i); pk[mu] = w.P(mu, k); }
   const float s = (float)(2.0 * dot4(pi, pk));  // FP64: near-collinear invariant
   float eta = 0.0f;
-  if (type == kFI) eta = (float)(k == 0 ? eta0 : eta1);
-  if (type == kIF || type == kII) eta = (float)(i == 0 ? eta0 : eta1);
+  if (type == kFI) eta = k == 0 ? eta0 : eta1;
+  if (type == kIF || type == kII) eta = i == 0 ? eta0 : eta1;
   s_out = s;
   eta_out = eta;
   type_out = type;
@@ -480,8 +497,8 @@ __device__ float4 end_record(const MixedCtx& M, const SmemPdf& S, const W& w, co
     if (!ok) continue;
     const int ch = first + c;
     int shape;
-    double coefd;
-    channel_over(ch, type, M.P.nf, shape, coefd);
+    float coefd;
+    channel_over32(ch, type, M.P.nf, shape, coefd);
     float B = 1.0f;
     if (type == kFI) {
       const int f = pdf_index(tag_fl(tg[k]));
@@ -555,19 +572,27 @@ __device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& m
                                              float isr_eta, float isr_s, int isr_type, int fl_i, int slot_j, int q_j,
                                              int lane_id, float& scale0, float& scale1, bool four = false) {
   int cls_j[2];  // margin row: (class, eta bucket)
+  // the end's two continuous inputs, once per end (lane j < 4), as
+  // mlp_features forms them
+  float fe[4];
+  {
+    const float eta_c = lane_id < 4 ? isr_eta : 1.0f, s_c = lane_id < 4 ? isr_s : 1.0f, tc_c = lane_id < 4 ? tc : 1.0f;
+    mlp_features(eta_c, s_c, tc_c, 0, 0, fe);
+  }
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int r = lane_id + 32 * j, e = r >> 4, c = (r >> 3) & 1, m = r & 7;
-    const float eta_e = __shfl_sync(0xffffffffu, isr_eta, e);
-    const float s_e = __shfl_sync(0xffffffffu, isr_s, e);
+    const float f0 = __shfl_sync(0xffffffffu, fe[0], e);
+    const float f1 = __shfl_sync(0xffffffffu, fe[1], e);
     const int type_e = __shfl_sync(0xffffffffu, isr_type, e);
     const int fl_e = __shfl_sync(0xffffffffu, fl_i, e);
-    const float tc_e = __shfl_sync(0xffffffffu, tc, e);
     cls_j[j] = 0;
     if ((eval >> e) & 1u) {
       const int cls = isr_class(type_e, (fl_e == 21 ? 5 : 3) + c, fl_e);
-      mlp_features(eta_e, s_e, tc_e, m, cls, stage[r]);
-      cls_j[j] = cls * kEtaBins + eta_bucket(stage[r][0]);
+      float f[4];
+      mlp_features(1.0f, 1.0f, 1.0f, m, cls, f);  // the bin and class inputs
+      *reinterpret_cast<float4*>(stage[r]) = make_float4(f0, f1, f[2], f[3]);
+      cls_j[j] = cls * kEtaBins + eta_bucket(f0);
     }
   }
   // calibration margins of (class, eta bucket, bin), after the parameters,
@@ -595,11 +620,20 @@ __device__ __noinline__ void learned_heights(const MixedCtx& M, const MlpSmem& m
     const int slot_e = __shfl_sync(0xffffffffu, slot_j, e);
     const int q_e = __shfl_sync(0xffffffffu, q_j, e);
     float U = 0.0f;
+    int hc = 0;
     if ((eval >> e) & 1u) {
-      const int hc = height_code(__expf(ustage[r] + mg[j]));
-      ls.at(q_e, c, slot_e)[m] = (unsigned char)hc;
+      hc = height_code(__expf(ustage[r] + mg[j]));
       U = ls.dec[hc];
     }
+    // the channel's eight codes, gathered by its first lane into one 8-byte store
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t v = (uint32_t)__shfl_sync(0xffffffffu, hc, (lane_id & ~7) + b) & 0xffu;
+      if (b < 4) lo |= v << (8 * b);
+      else hi |= v << (8 * (b - 4));
+    }
+    if (m == 0 && ((eval >> e) & 1u)) *reinterpret_cast<uint2*>(ls.at(q_e, c, slot_e)) = make_uint2(lo, hi);
     // the channel's sum over its 8 bins, in bin order (the order the veto sums them)
     float t = 0.0f;
 #pragma unroll
@@ -639,6 +673,7 @@ __device__ __forceinline__ int rebuild_body(const MixedCtx& M, const SmemPdf& S,
   // partner in one lookup; with a tag held by two partons (not a leading-
   // colour event) every end scans the tags instead, as the table cannot give
   // the first match
+  const float eta0f = (float)eta0, eta1f = (float)eta1;  // the veto's FP32 momentum fractions
   unsigned char* own = nullptr;
   if (stage_tags) {
     own = reinterpret_cast<unsigned char*>(tg + M.P.nmax);
@@ -674,7 +709,7 @@ __device__ __forceinline__ int rebuild_body(const MixedCtx& M, const SmemPdf& S,
     float s_, eta_;
     int type_;
     float4 aux;
-    const float4 rec = end_record(M, S, w, tg, own, n, eta0, eta1, row, q, s_, eta_, type_, aux);
+    const float4 rec = end_record(M, S, w, tg, own, n, eta0f, eta1f, row, q, s_, eta_, type_, aux);
     w.Aux(q) = aux;
     if (pp && q < 4) { isr_rec = rec; isr_s = s_; isr_eta = eta_; isr_type = type_; }
     else set_end(w, q, rec, keep_ends);
@@ -1032,9 +1067,8 @@ __device__ int step_veto(const MixedCtx& M, const SmemPdf& S, const LearnedSmem&
   const float s = ax.x;
   const float eta = ax.y;
   int shape;
-  double coefd;
-  channel_over(ch, type, M.P.nf, shape, coefd);
-  const float coef = (float)coefd;
+  float coef;
+  channel_over32(ch, type, M.P.nf, shape, coef);
   float zm, delta;
   zlim32(type, __expf(lnTc), s, eta, zm, delta);
   // learned bounds: pick the bin from R_z, then zeta inside it
@@ -1185,9 +1219,8 @@ __device__ __noinline__ ChannelWeight channel_weight(const MixedCtx& M, const Sm
   r.sumF = 0.0f;
   const float s = ax.x, eta = ax.y;
   int shape;
-  double coefd;
-  channel_over(r.ch, r.type, M.P.nf, shape, coefd);
-  const float coef = (float)coefd;
+  float coef;
+  channel_over32(r.ch, r.type, M.P.nf, shape, coef);
   float zm, delta;
   zlim32(r.type, __expf(lnTc), s, eta, zm, delta);
   shape_sample32(shape, zm, delta, Rz, r.z, r.omz);
@@ -2056,7 +2089,7 @@ __global__ void __launch_bounds__(256, 2) k_wave_mlp(const __grid_constant__ Mix
   const uint64_t count = M.V.ctl[WL_MLP];
   if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * 4 >= count) return;  // nothing queued for this block
   __shared__ float dec[256];
-  __shared__ float stage_s[8][64][4];
+  __shared__ __align__(16) float stage_s[8][64][4];
   __shared__ float ustage_s[8][64];
   __shared__ float lnTc[kMaxRows];
   __shared__ __align__(16) unsigned char wimg[kMlpSmemBytes];  // the network's BF16 image
@@ -2638,8 +2671,8 @@ __global__ void k_isr_targets(const __grid_constant__ MixedCtx M, const float4* 
   mlp_features(eta, s, tc, m, isr_class(type, ch, fl_i), f);
   for (int k = 0; k < 4; ++k) feats[4 * row + k] = f[k];
   int shape;
-  double coefd;
-  channel_over(ch, type, M.P.nf, shape, coefd);
+  float coefd;
+  channel_over32(ch, type, M.P.nf, shape, coefd);
   float zm, delta;
   float best = 0.0f;
   const float tk = tkin32(type, s, eta);
