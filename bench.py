@@ -81,13 +81,13 @@ OPS_PER_ACCEPT = 1200.0
 # 128 FP32 lanes x 2.07 GHz, and 1.25 TFLOP/s FP64 (dense).
 LANE_PEAK_TOPS_NOMINAL = 152 * 128 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
-# DRAM bytes (read + write) per event of the shower kernel, from one ncu capture
-# of the current kernel on a 262 144-event case of the same workload (the
-# persistent kernel's traffic grows with the events it processes); scaled to a
-# launch by its events. Workloads without a capture report null.
+# DRAM bytes (read + write) per event of the shower phase (every kernel of the
+# wavefront between the hard process and the observables), from one ncu
+# capture of the current kernels on a 262 144-event case of the same workload
+# (the traffic grows with the events showered); scaled to a chunk by its
+# events. Workloads and variants without a capture report null.
 SHOWER_DRAM_BYTES_PER_EVENT = {
-    ("pp_nlo_1e7", True): (19.126488e9 + 9.866132e9) / 262144,   # learned proposal
-    ("pp_nlo_1e7", False): (18.657529e9 + 8.961404e9) / 262144,  # plain bound
+    ("pp_nlo_1e7", True): (11426.4e6 + 5098.1e6) / 262144,   # learned proposal, wavefront
 }
 
 
@@ -565,7 +565,8 @@ def run_ours(args, ws, rank, local):
                 "unit": "Tops/s (operations of the scope's work units per second)",
                 "frac": achieved / lane_peak,
                 "traffic": None if bpe is None else bpe * per_launch_events,
-                "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by events)",
+                "traffic_unit": "bytes per chunk's shower phase (ncu DRAM read + write of its kernels on "
+                                "262 144 events, scaled by events)",
                 "peak_source": ("measured: FP32 FMA lane throughput of this GPU (gaps_alu_peak, "
                                 "median SM clock %s MHz)" % alu["clocks"].get("sm_mhz"))
                 if "error" not in alu else "nominal 152 x 128 lanes x 2.07 GHz (microbenchmark failed)",
