@@ -49,12 +49,13 @@ __device__ __forceinline__ void born_pair(int k, int& fa, int& fb) {
 }
 
 // pi (eta_a f_a)(eta_b f_b) |M|^2 / m^4 for one ordered pair (Appendix C.1)
-__device__ double born_pair_density(const DevParams& P, int k, double ea, double eb) {
+// (la, lb: the grid cells of eta_a, eta_b at Q^2 = m_Z^2)
+__device__ double born_pair_density(const DevParams& P, int k, const PdfLoc& la, const PdfLoc& lb) {
   int fa, fb;
   born_pair(k, fa, fb);
   double mz2 = kMZ * kMZ;
-  double Fa = pdf_xf(P, pdf_index(fa), ea, mz2);
-  double Fb = pdf_xf(P, pdf_index(fb), eb, mz2);
+  double Fa = pdf_at(P, pdf_index(fa), la);
+  double Fb = pdf_at(P, pdf_index(fb), lb);
   return kPi * Fa * Fb * born_me2(fa) / (mz2 * mz2);
 }
 
@@ -92,8 +93,9 @@ __device__ double collinear_leg(const DevParams& P, int fl, double eta, double R
   double mz2 = kMZ * kMZ;
   double x = eta + R * (1.0 - eta);
   double Fq = pdf_xf(P, pdf_index(fl), eta, mz2);
-  double rq = pdf_xf(P, pdf_index(fl), eta / x, mz2) / Fq;
-  double rg = pdf_xf(P, 0, eta / x, mz2) / Fq;
+  const PdfLoc lx = pdf_locate(P, eta / x, mz2);
+  double rq = pdf_at(P, pdf_index(fl), lx) / Fq;
+  double rg = pdf_at(P, 0, lx) / Fq;
   double logs = gm_log((1.0 - x) / x) + gm_log(1.0 - x) - L;
   double g = pf * (2.0 / (1.0 - x) * logs);
   double hqq = pf * (-(1.0 + x) * logs + (1.0 - x));
@@ -172,10 +174,11 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     double ea = ey * tau, eb = iey * tau;
     double c = 2.0 * R3 - 1.0;
     double dens[10], tot = 0.0;
+    const PdfLoc la = pdf_locate(P, ea, m2), lb = pdf_locate(P, eb, m2);
     for (int k = 0; k < 10; ++k) {
       int fa, fb;
       born_pair(k, fa, fb);
-      double Fa = pdf_xf(P, pdf_index(fa), ea, m2), Fb = pdf_xf(P, pdf_index(fb), eb, m2);
+      double Fa = pdf_at(P, pdf_index(fa), la), Fb = pdf_at(P, pdf_index(fb), lb);
       dens[k] = Fa * Fb * ll_dsigma_dcos(m2, fa > 0 ? fa : fb, fa > 0 ? c : -c);
       tot += dens[k];
     }
@@ -217,7 +220,8 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     double tau = kMZ / P.sqrt_s;
     double ea = gm_exp(y) * tau, eb = gm_exp(-y) * tau;
     double dens[10], tot = 0.0;
-    for (int k = 0; k < 10; ++k) { dens[k] = born_pair_density(P, k, ea, eb); tot += dens[k]; }
+    const PdfLoc la = pdf_locate(P, ea, kMZ * kMZ), lb = pdf_locate(P, eb, kMZ * kMZ);
+    for (int k = 0; k < 10; ++k) { dens[k] = born_pair_density(P, k, la, lb); tot += dens[k]; }
     int pick = 9;
     double target = R2 * tot, acc = 0.0;
     for (int k = 0; k < 10; ++k) { acc += dens[k]; if (target < acc) { pick = k; break; } }
@@ -260,6 +264,7 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
   double cpick = 0.0;
   {
     double cs[30];
+    const PdfLoc l1 = pdf_locate(P, e1, mz2), l2 = pdf_locate(P, e2, mz2);
     for (int k = 0; k < 30; ++k) {
       int fa, fb;
       double rs;
@@ -274,8 +279,8 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
         double ubar = -v * sbar;
         rs = 8.0 * kPi * as * kTR / m2 * born_me2(q) * ((2.0 * m2 - ubar) / sbar);
       }
-      double Fa = pdf_xf(P, pdf_index(fa), e1, mz2);
-      double Fb = pdf_xf(P, pdf_index(fb), e2, mz2);
+      double Fa = pdf_at(P, pdf_index(fa), l1);
+      double Fb = pdf_at(P, pdf_index(fb), l2);
       cs[k] = Fa * Fb * rs / (16.0 * kPi) / m2;
       tot += fabs(cs[k]);
     }

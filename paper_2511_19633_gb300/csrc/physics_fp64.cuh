@@ -40,6 +40,27 @@ __device__ __forceinline__ bool pdf_locate_q(const DevParams& P, double q2, int&
   return true;
 }
 
+// a point's cell and fractions on the grid, found once for several flavours
+// (pdf_xf's arithmetic, so the values are the same bits)
+struct PdfLoc {
+  int ix, iq;
+  double fx, fq;
+  bool ok;
+};
+__device__ __forceinline__ PdfLoc pdf_locate(const DevParams& P, double x, double q2) {
+  PdfLoc L;
+  L.ix = L.iq = 0;
+  L.fx = L.fq = 0.0;
+  L.ok = pdf_locate_x(P, x, L.ix, L.fx) && pdf_locate_q(P, q2, L.iq, L.fq);
+  return L;
+}
+__device__ __forceinline__ double pdf_at(const DevParams& P, int f, const PdfLoc& L) {
+  if (f < 0 || f > 11 || !L.ok) return 0.0;
+  double lo = (1.0 - L.fx) * pdf_node(P, f, L.ix, L.iq) + L.fx * pdf_node(P, f, L.ix + 1, L.iq);
+  double hi = (1.0 - L.fx) * pdf_node(P, f, L.ix, L.iq + 1) + L.fx * pdf_node(P, f, L.ix + 1, L.iq + 1);
+  return lo * (1.0 - L.fq) + hi * L.fq;
+}
+
 __device__ __forceinline__ double pdf_xf(const DevParams& P, int f, double x, double q2) {
   int ix, iq;
   double fx, fq;
