@@ -99,6 +99,8 @@ struct WaveSet {
                             // back; bit 2: write the status back only; bit 3: an emission
                             // is parked; bits 8..15: mix row
   int* keep;                // [cap] ends that may keep their trials at the next rebuild (-1: none)
+  int* chg;                 // [cap] slots the last emission changed, emitter | spectator << 8 |
+                            // new << 16, or -1: the next rebuild recomputes every end
   double* eta;              // [2][cap] momentum fractions of slots 0 and 1
   uint64_t* draw;           // [cap] next Philox block of the event's stream
   unsigned char* pend;      // [cap][kWavePendBytes] the parked emission of the pass

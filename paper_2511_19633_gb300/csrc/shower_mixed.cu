@@ -667,7 +667,7 @@ __device__ __forceinline__ int rebuild_body(const MixedCtx& M, const SmemPdf& S,
                                             int n, double eta0, double eta1, int row, bool learned_src,
                                             int keep_ends, int lane_id, bool defer = false,
                                             unsigned* defer_mask = nullptr, float4* deferred = nullptr,
-                                            float4* isr_plain = nullptr) {
+                                            float4* isr_plain = nullptr, int chg = -1) {
   // the event's tags in shared memory, and (lane kernels) the table of the
   // slot owning each colour and anticolour tag, so that an end finds its
   // partner in one lookup; with a tag held by two partons (not a leading-
@@ -706,6 +706,23 @@ __device__ __forceinline__ int rebuild_body(const MixedCtx& M, const SmemPdf& S,
   float isr_s = 0.0f, isr_eta = 0.0f;
   int isr_type = -1;
   for (int q = lane_id; q < 2 * n; q += 32) {
+    if (chg >= 0 && !(pp && q < 4) && q < keep_ends) {
+      // an end whose parton and colour partner the last emission left alone
+      // keeps its record (the same bits a recomputation gives): its inputs
+      // are the two momenta, the tags and the momentum fraction of an
+      // initial-state parton among them, and the emission changed only the
+      // emitter, the spectator and the new parton, whose ends and partners'
+      // ends take the new colour line
+      const int ci = chg & 0xff, ck = (chg >> 8) & 0xff, cj = (chg >> 16) & 0xff;
+      const int a = q >> 1;
+      if (a != ci && a != ck && a != cj) {
+        const int side = q & 1;
+        const uint32_t ta = tg[a];
+        const int tag = side == 0 ? tag_col(ta) : tag_acol(ta);
+        const int p = !tag ? -1 : (own ? partner_from_table(own, a, side, tag) : find_partner_tags(tg, n, a, side, tag));
+        if (p != ci && p != ck && p != cj) continue;
+      }
+    }
     float s_, eta_;
     int type_;
     float4 aux;
@@ -1915,6 +1932,7 @@ __global__ void k_wave_init(const __grid_constant__ MixedCtx M) {
       const int wb = live ? 2 : (L.status != M.E.status[e] ? 4 : 0);
       M.V.flags[e] = 1 | wb | (L.row << 8);
       M.V.keep[e] = cache ? 0 : -1;
+      M.V.chg[e] = -1;
       wave_store(M, L);
       if (!live) {
         finished += 1;
@@ -1997,6 +2015,41 @@ __device__ __forceinline__ uint64_t draw_marked_ends(const MixedCtx& M, const Sm
   return d;
 }
 
+// L2 prefetch of the rows a rebuild reads (one line per lane): the event's
+// scalars, its first 16 partons' momenta and tags, and its first 32 ends'
+// records, veto inputs and trial maxima. Addresses inside the arrays only.
+__device__ __forceinline__ void prefetch_event_rows(const MixedCtx& M, uint32_t e, int lane_id) {
+  const WaveSet& V = M.V;
+  const WorkSet& W = M.W;
+  const char* a = nullptr;
+  // momenta and end rows are both nmax x 32 bytes: lines past a short row are skipped
+  const size_t row_bytes = (size_t)M.P.nmax * 32;
+  const size_t row_p = (size_t)e * row_bytes, row_e = (size_t)e * row_bytes;
+  switch (lane_id) {
+    case 0: a = (const char*)(V.flags + e); break;
+    case 1: a = (const char*)(V.n + e); break;
+    case 2: a = (const char*)(V.keep + e); break;
+    case 3: a = (const char*)(V.chg + e); break;
+    case 4: a = (const char*)(V.eta + e); break;
+    case 5: a = (const char*)(V.eta + V.cap + e); break;
+    case 6: a = (const char*)(V.lnT + e); break;
+    case 7: a = (const char*)(V.draw + e); break;
+    case 8: case 9: case 10: case 11:
+      if (128 * (size_t)(lane_id - 8) < row_bytes) a = (const char*)W.p + row_p + 128 * (lane_id - 8);
+      break;
+    case 12: a = (const char*)(W.tag + (size_t)e * M.P.nmax); break;
+    case 13: case 14: case 15: case 16:
+      if (128 * (size_t)(lane_id - 13) < row_bytes) a = (const char*)W.end + row_e + 128 * (lane_id - 13);
+      break;
+    case 17: case 18: case 19: case 20:
+      if (128 * (size_t)(lane_id - 17) < row_bytes) a = (const char*)W.aux + row_e + 128 * (lane_id - 17);
+      break;
+    case 21: a = (const char*)(W.tmx + (size_t)e * tmx_stride(M.P.nmax)); break;
+    default: break;
+  }
+  if (a) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // One warp per event of the rebuild list: the end table, then (kept trials)
 // the trials of the ends it marked. Also clears, for the passes after it, the
 // lists this pass's later kernels fill.
@@ -2036,8 +2089,17 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
   };
   unsigned long long rebuilds = 0, mlp_tiles = 0;
   Counters32 cnt;
-  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id; i < count; i += nw) {
-    const uint64_t e = M.V.list[(size_t)WL_REBUILD * M.V.cap + i];
+  // the list two events ahead, so that the next event's rows can be brought
+  // into L2 while this one is rebuilt (its loads are a chain of dependent
+  // misses: scalars, tags, momenta, records)
+  const uint32_t* rl = M.V.list + (size_t)WL_REBUILD * M.V.cap;
+  const uint64_t i0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp_id;
+  uint32_t e_a = i0 < count ? rl[i0] : 0u, e_b = i0 + nw < count ? rl[i0 + nw] : 0u;
+  for (uint64_t i = i0; i < count; i += nw) {
+    const uint64_t e = e_a;
+    e_a = e_b;
+    e_b = i + 2 * nw < count ? rl[i + 2 * nw] : 0u;
+    if (i + nw < count) prefetch_event_rows(M, e_a, lane_id);
     const int flags = M.V.flags[e], n = M.V.n[e], row = (flags >> 8) & 0xff;
     const WS w{M.W, (int)e, M.P.nmax};
     unsigned defer_mask = 0;
@@ -2045,7 +2107,7 @@ __global__ void __launch_bounds__(256, MINB) k_wave_ends(const __grid_constant__
     mlp_tiles += rebuild_body(M, S, mlp_s, D.ls, D.stage[warp_id], D.ustage[warp_id], w,
                               D.tag_stage + warp_id * tag_stage_words(M.P.nmax), true, (int)e, e, n, M.V.eta[e],
                               M.V.eta[M.V.cap + e], row, (flags & 1) != 0, M.V.keep[e], lane_id, cache, &defer_mask,
-                              &deferred, &plain);
+                              &deferred, &plain, M.V.chg[e]);
     rebuilds += 1;
     if (cache) {
       uint64_t off = 0;
@@ -2299,7 +2361,7 @@ __global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ Mixed
       Lane L;
       wave_load(M, L, e);
       const Emission em = *reinterpret_cast<const Emission*>(M.V.pend + e * kWavePendBytes);
-      int keep = -1;
+      int keep = -1, chg = -1;
       if (em.kind == 1) {
         rebuild = true;
         keep = cache ? 0 : -1;
@@ -2307,11 +2369,15 @@ __global__ void __launch_bounds__(128) k_wave_emit(const __grid_constant__ Mixed
         cnt.accepts += 1;
         rebuild = true;
         keep = cache ? 2 * (L.n - 1) : -1;
+        // the partons the emission moved: emitter, spectator and the new one
+        // (an initial-initial emission kicks every final parton: all ends)
+        if (em.type != kII) chg = em.bi | (em.k << 8) | ((L.n - 1) << 16);
       } else {
         cnt.vetoes += 1;  // the map failed: the winner's end draws again
         if (cache) WS{M.W, (int)e, M.P.nmax}.MarkTrial(2 * em.bi + em.bside);
       }
       M.V.keep[e] = keep;
+      M.V.chg[e] = chg;
       wave_store(M, L);
     }
     wave_append(M, WL_REBUILD, rebuild, e, lane_id);
@@ -2837,7 +2903,7 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 }  // namespace
 
 size_t wave_state_bytes(uint64_t cap) {
-  return al256(cap * sizeof(float)) + 6 * al256(cap * sizeof(int)) + al256(2 * cap * sizeof(double)) +
+  return al256(cap * sizeof(float)) + 7 * al256(cap * sizeof(int)) + al256(2 * cap * sizeof(double)) +
          al256(cap * sizeof(uint64_t)) + al256(cap * (size_t)kWavePendBytes) + al256(4 * cap * sizeof(uint32_t)) +
          al256(12 * cap * sizeof(float4)) + al256(4 * cap * sizeof(uint32_t)) +
          al256(WL_NCTL * sizeof(unsigned long long));
@@ -2854,6 +2920,7 @@ void wave_state_carve(void* base, uint64_t cap, WaveSet& V) {
   V.steps = (int*)take(cap * sizeof(int));
   V.flags = (int*)take(cap * sizeof(int));
   V.keep = (int*)take(cap * sizeof(int));
+  V.chg = (int*)take(cap * sizeof(int));
   V.eta = (double*)take(2 * cap * sizeof(double));
   V.draw = (uint64_t*)take(cap * sizeof(uint64_t));
   V.pend = (unsigned char*)take(cap * (size_t)kWavePendBytes);
