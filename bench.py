@@ -464,6 +464,7 @@ def run_ours(args, ws, rank, local):
         from paper_2511_19633_gb300.sharding import max_over_ranks
         ms = max_over_ranks(ms, dist, device="cuda")
     value = total * args.steps * ws / (ms / 1e3)
+    G.gaps_destroy(ctx)  # its memory (two wavefront slots) goes back before the end-to-end contexts
     # kernels per chunk: hard process, the shower's kernels, observables
     if schedule == G.GAPS_SCHED_WAVE:
         P = shape.get("wave_passes", 24)
@@ -555,12 +556,19 @@ def run_ours(args, ws, rank, local):
         lane_peak, fp64_peak = LANE_PEAK_TOPS_NOMINAL, FP64_PEAK_TFLOPS_NOMINAL
     if mixed:
         ops = algorithmic_ops(stats)
-        achieved = ops / (sum(shower_ms) / 1e3) / 1e12
-        impl = implementation_ops_mixed(stats) / (sum(shower_ms) / 1e3) / 1e12
+        # the time the work units took: the shower launches' own CUDA-event
+        # time, or with the wavefront's two streams (chunks overlap) the timed
+        # region itself (hard process and observables included: a lower bound)
+        overlapped = schedule == G.GAPS_SCHED_WAVE and n_chunks > 1
+        busy_s = ms / 1e3 if overlapped else sum(shower_ms) / 1e3
+        achieved = ops / busy_s / 1e12
+        impl = implementation_ops_mixed(stats) / busy_s / 1e12
         bpe = SHOWER_DRAM_BYTES_PER_EVENT.get((name, learned is not None))
         kname = SHOWER_KERNEL if schedule != G.GAPS_SCHED_WAVE else (
-            "the shower phase of a chunk: k_wave_veto, k_wave_ends, k_wave_mlp, k_wave_emit, "
-            "k_wave_init/final and the k_shower_mixed drain, timed together")
+            "the shower phase: k_wave_veto, k_wave_ends, k_wave_mlp, k_wave_emit, k_wave_init/final and the "
+            "k_shower_mixed tail, timed together" + (
+                "; chunks run on two streams, so the time is the whole timed region (hard process and "
+                "observables included)" if overlapped else ""))
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": lane_peak,
                 "unit": "Tops/s (operations of the scope's work units per second)",
                 "frac": achieved / lane_peak,
@@ -632,7 +640,6 @@ def run_ours(args, ws, rank, local):
     if tuning is not None:
         line["autotune"] = {"best": tuning["best"], "sample_events": tuning["sample_events"],
                             "candidates": len(tuning["table"])}
-    G.gaps_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(process, sqrt_s, mix)
     if rank == 0:

@@ -458,7 +458,15 @@ int gaps_observables(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps
  * the context and launched on `stream` (asynchronous; the legacy default
  * stream is allowed). A later call with the same n and capacity updates the
  * graph's parameters in place instead of instantiating it again. Not to be
- * called while `stream` or the context's other calls are being captured. */
+ * called while `stream` or the context's other calls are being captured.
+ * With GAPS_MIXED and GAPS_SCHED_WAVE and two or more chunks the context
+ * allocates a second slot (records and observables like `ev` and obs_dev, and
+ * a second wavefront working set, about 100 GB for 2^22 events of 128 slots)
+ * and the graph runs the odd chunks there on a second stream, concurrently
+ * with the even ones in `ev`; obs_host and the histograms are the same, but
+ * after the call `ev` and obs_dev hold only the even chunks' records and
+ * observables. When that memory cannot be allocated the chunks run one after
+ * another as without it. */
 int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
                  double* obs_dev, double* obs_host, const gaps_hists* hists, void* stream);
 

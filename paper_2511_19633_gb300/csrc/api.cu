@@ -69,6 +69,18 @@ struct gaps_ctx {
   uint64_t graph_n = 0, graph_cap = 0;
   std::vector<cudaEvent_t> shower_ev;  // start/stop of each chunk's shower in the graph
   int graph_chunks = 0;
+  // gaps_process with the wavefront schedule: a second slot (event records,
+  // observables, working set) for every other chunk, run on a second stream so
+  // that the tail of one chunk's shower overlaps the next chunk
+  void* d_slot2 = nullptr;   // records and observables of the second slot
+  size_t slot2_bytes = 0;
+  gaps_events ev2{};
+  double* obs2 = nullptr;
+  void* d_wave2 = nullptr;   // its wavefront working set and state
+  size_t wave_bytes2 = 0;
+  uint64_t wave_cap2 = 0;
+  cudaStream_t cap_stream2 = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace gaps {
@@ -435,35 +447,38 @@ int ensure_workset(gaps_ctx* ctx, int& blocks, int& bs, WorkSet& W) {
 // (allocated on first use, grown when a larger capacity comes)
 constexpr int kWavePassesDefault = 24;
 constexpr int kWaveCyclesDefault = 64;  // veto cycles of one event in one pass
-int ensure_wave(gaps_ctx* ctx, uint64_t cap, WorkSet& W, WaveSet& V) {
+int ensure_wave(gaps_ctx* ctx, uint64_t cap, WorkSet& W, WaveSet& V, int slot = 0) {
   const int nmax = ctx->cfg.nmax_partons;
   // the kernels index the working set with unsigned 32-bit element offsets
   if (cap * 4 * (uint64_t)nmax >= ((uint64_t)1 << 32) || cap >= ((uint64_t)1 << 31)) return GAPS_ERR_INVALID_ARG;
+  void*& mem = slot ? ctx->d_wave2 : ctx->d_wave;
+  size_t& bytes = slot ? ctx->wave_bytes2 : ctx->wave_bytes;
+  uint64_t& have = slot ? ctx->wave_cap2 : ctx->wave_cap;
   const size_t wb = (workset_bytes((int)cap, nmax) + 255) / 256 * 256;
   const size_t need = wb + wave_state_bytes(cap);
-  if (need > ctx->wave_bytes || cap > ctx->wave_cap) {
-    if (ctx->d_wave) cudaFree(ctx->d_wave);
-    ctx->d_wave = nullptr;
-    ctx->wave_bytes = 0;
-    ctx->wave_cap = 0;
-    if (cudaMalloc(&ctx->d_wave, need) != cudaSuccess) {
+  if (need > bytes || cap > have) {
+    if (mem) cudaFree(mem);
+    mem = nullptr;
+    bytes = 0;
+    have = 0;
+    if (cudaMalloc(&mem, need) != cudaSuccess) {
       cudaGetLastError();
       return GAPS_ERR_CUDA;
     }
-    ctx->wave_bytes = need;
-    ctx->wave_cap = cap;
+    bytes = need;
+    have = cap;
   }
-  workset_carve(ctx->d_wave, (int)cap, nmax, W);
-  wave_state_carve((char*)ctx->d_wave + wb, cap, V);
+  workset_carve(mem, (int)cap, nmax, W);
+  wave_state_carve((char*)mem + wb, cap, V);
   return GAPS_OK;
 }
 
 int shower_wave(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, const LearnedCfg& Lc,
-                void* stream) {
+                void* stream, int slot = 0) {
   const gaps_config& c = ctx->cfg;
   WorkSet W;
   WaveSet V;
-  const int rc = ensure_wave(ctx, ev->capacity, W, V);
+  const int rc = ensure_wave(ctx, ev->capacity, W, V, slot);
   if (rc != GAPS_OK) return rc;
   const int bs = c.block_size > 0 ? c.block_size : 128;
   const int per_sm = c.blocks_per_sm > 0 ? c.blocks_per_sm : 4;
@@ -489,8 +504,9 @@ int shower_mixed(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_eve
 }
 }  // namespace
 
-int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, void* stream) {
-  if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
+namespace {
+// gaps_shower; slot 1: the second wavefront slot of gaps_process
+int shower_impl(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, void* stream, int slot) {
   const gaps_config& c = ctx->cfg;
   if (c.precision == GAPS_MIXED) {
     LearnedCfg Lc{};
@@ -510,7 +526,7 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
                                           per_sm, ctx->q_independent, ctx->d_counters + C_NCOUNTERS,
                                           (cudaStream_t)stream));
     }
-    if (c.schedule == GAPS_SCHED_WAVE) return shower_wave(ctx, first_event, n, ev, Lc, stream);
+    if (c.schedule == GAPS_SCHED_WAVE) return shower_wave(ctx, first_event, n, ev, Lc, stream, slot);
     return shower_mixed(ctx, first_event, n, ev, Lc, stream);
   }
   int bs = c.block_size > 0 ? c.block_size : 128;
@@ -521,6 +537,12 @@ int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_even
   }
   return cuda_fail(launch_shower_fp64(ctx->P, dev_events(ev), first_event, n, bs, pblocks,
                                       ctx->d_counters + C_NCOUNTERS, (cudaStream_t)stream));
+}
+}  // namespace
+
+int gaps_shower(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, void* stream) {
+  if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
+  return shower_impl(ctx, first_event, n, ev, stream, 0);
 }
 
 int gaps_collect_isr_states(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
@@ -846,6 +868,71 @@ int gaps_observables(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps
                                       ctx->cfg.precision == GAPS_MIXED, (cudaStream_t)stream));
 }
 
+namespace {
+void free_slot2(gaps_ctx* ctx) {
+  if (ctx->d_slot2) cudaFree(ctx->d_slot2);
+  if (ctx->d_wave2) cudaFree(ctx->d_wave2);
+  ctx->d_slot2 = ctx->d_wave2 = nullptr;
+  ctx->slot2_bytes = ctx->wave_bytes2 = 0;
+  ctx->wave_cap2 = 0;
+  ctx->ev2 = gaps_events{};
+  ctx->obs2 = nullptr;
+}
+
+// The second slot of gaps_process for records like `ev` (library-owned
+// records, observables and a wavefront working set), its stream and the
+// fork/join events. Returns false, holding nothing, when the memory is not
+// there: the call then runs its chunks one after another.
+bool ensure_slot2(gaps_ctx* ctx, const gaps_events* ev) {
+  const uint64_t cap = ev->capacity;
+  const int nmax = ev->nmax;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t need = al(4 * (size_t)nmax * cap * sizeof(double)) + 3 * al((size_t)nmax * cap * sizeof(int32_t)) +
+                      3 * al(cap * sizeof(int32_t)) + 4 * al(cap * sizeof(double)) + al(cap * sizeof(uint64_t)) +
+                      al((size_t)GAPS_NOBS * cap * sizeof(double));
+  if (!ctx->d_slot2 || ctx->slot2_bytes < need || ctx->ev2.capacity != cap || ctx->ev2.nmax != nmax) {
+    free_slot2(ctx);
+    if (cudaMalloc(&ctx->d_slot2, need) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->d_slot2 = nullptr;
+      return false;
+    }
+    ctx->slot2_bytes = need;
+    char* q = (char*)ctx->d_slot2;
+    auto take = [&](size_t b) { char* r = q; q += al(b); return r; };
+    gaps_events& e = ctx->ev2;
+    e.capacity = cap;
+    e.nmax = nmax;
+    e.p = (double*)take(4 * (size_t)nmax * cap * sizeof(double));
+    e.flav = (int32_t*)take((size_t)nmax * cap * sizeof(int32_t));
+    e.col = (int32_t*)take((size_t)nmax * cap * sizeof(int32_t));
+    e.acol = (int32_t*)take((size_t)nmax * cap * sizeof(int32_t));
+    e.npart = (int32_t*)take(cap * sizeof(int32_t));
+    e.status = (int32_t*)take(cap * sizeof(int32_t));
+    e.n_emit = (int32_t*)take(cap * sizeof(int32_t));
+    e.weight = (double*)take(cap * sizeof(double));
+    e.t = (double*)take(cap * sizeof(double));
+    e.eta = (double*)take(2 * cap * sizeof(double));
+    e.draw = (uint64_t*)take(cap * sizeof(uint64_t));
+    ctx->obs2 = (double*)take((size_t)GAPS_NOBS * cap * sizeof(double));
+  }
+  WorkSet W;
+  WaveSet V;
+  if (ensure_wave(ctx, cap, W, V, 1) != GAPS_OK) {
+    free_slot2(ctx);
+    return false;
+  }
+  if (!ctx->cap_stream2 && cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->cap_stream2 = nullptr;
+    return false;
+  }
+  if (!ctx->fork_ev && cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess) return false;
+  if (!ctx->join_ev && cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming) != cudaSuccess) return false;
+  return true;
+}
+}  // namespace
+
 int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev, double* obs_dev,
                  double* obs_host, const gaps_hists* hists, void* stream) {
   if (!ctx || !ev || ev->capacity == 0) return GAPS_ERR_INVALID_ARG;
@@ -875,24 +962,39 @@ int gaps_process(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_eve
     if (cudaEventCreate(&e) != cudaSuccess) return GAPS_ERR_CUDA;
     ctx->shower_ev.push_back(e);
   }
+  // with the wavefront schedule, odd chunks run in a second slot on a second
+  // stream (events are independent; counters and histograms are atomics)
+  const bool two = chunks >= 2 && ctx->cfg.precision == GAPS_MIXED && ctx->cfg.schedule == GAPS_SCHED_WAVE &&
+                   ensure_slot2(ctx, ev);
   cudaStream_t cs = ctx->cap_stream;
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GAPS_ERR_CUDA;
   int rc = GAPS_OK;
+  if (two && (cudaEventRecord(ctx->fork_ev, cs) != cudaSuccess ||
+              cudaStreamWaitEvent(ctx->cap_stream2, ctx->fork_ev, 0) != cudaSuccess))
+    rc = GAPS_ERR_CUDA;
   for (uint64_t f0 = 0, k = 0; f0 < n && rc == GAPS_OK; f0 += cap, ++k) {
     const uint64_t m = n - f0 < cap ? n - f0 : cap;
-    rc = gaps_generate_hard(ctx, first_event + f0, m, ev, cs);
-    if (rc == GAPS_OK && cudaEventRecordWithFlags(ctx->shower_ev[2 * k], cs, cudaEventRecordExternal) != cudaSuccess)
+    const int slot = two ? (int)(k & 1) : 0;
+    cudaStream_t s = slot ? ctx->cap_stream2 : cs;
+    const gaps_events* e = slot ? &ctx->ev2 : ev;
+    double* od = slot && obs_dev ? ctx->obs2 : obs_dev;
+    rc = gaps_generate_hard(ctx, first_event + f0, m, e, s);
+    if (rc == GAPS_OK && cudaEventRecordWithFlags(ctx->shower_ev[2 * k], s, cudaEventRecordExternal) != cudaSuccess)
       rc = GAPS_ERR_CUDA;
-    if (rc == GAPS_OK) rc = gaps_shower(ctx, first_event + f0, m, ev, cs);
+    if (rc == GAPS_OK) rc = shower_impl(ctx, first_event + f0, m, e, s, slot);
     if (rc == GAPS_OK &&
-        cudaEventRecordWithFlags(ctx->shower_ev[2 * k + 1], cs, cudaEventRecordExternal) != cudaSuccess)
+        cudaEventRecordWithFlags(ctx->shower_ev[2 * k + 1], s, cudaEventRecordExternal) != cudaSuccess)
       rc = GAPS_ERR_CUDA;
-    if (rc == GAPS_OK) rc = gaps_observables(ctx, first_event + f0, m, ev, obs_dev, hists, cs);
+    if (rc == GAPS_OK) rc = gaps_observables(ctx, first_event + f0, m, e, od, hists, s);
     if (rc == GAPS_OK && obs_host &&
-        cudaMemcpy2DAsync(obs_host + f0, n * sizeof(double), obs_dev, cap * sizeof(double), m * sizeof(double),
-                          GAPS_NOBS, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        cudaMemcpy2DAsync(obs_host + f0, n * sizeof(double), od, cap * sizeof(double), m * sizeof(double),
+                          GAPS_NOBS, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       rc = GAPS_ERR_CUDA;
   }
+  if (two && rc == GAPS_OK &&
+      (cudaEventRecord(ctx->join_ev, ctx->cap_stream2) != cudaSuccess ||
+       cudaStreamWaitEvent(cs, ctx->join_ev, 0) != cudaSuccess))
+    rc = GAPS_ERR_CUDA;
   cudaGraph_t g = nullptr;
   const cudaError_t end = cudaStreamEndCapture(cs, &g);
   if (rc == GAPS_OK && (end != cudaSuccess || !g)) rc = GAPS_ERR_CUDA;
@@ -979,6 +1081,10 @@ void gaps_destroy(gaps_ctx* ctx) {
   if (ctx->d_mlp_image) cudaFree(ctx->d_mlp_image);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  free_slot2(ctx);
+  if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   for (cudaEvent_t e : ctx->shower_ev) cudaEventDestroy(e);
   delete ctx;
 }

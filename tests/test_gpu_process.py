@@ -27,12 +27,14 @@ def _per_call(G, ctx, first, n, chunk, ev, obs, hists):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_graph_equals_per_call(G, pdf, precision):
+@pytest.mark.parametrize("precision,schedule", [(0, 1), (1, 1), (1, 3)])
+def test_graph_equals_per_call(G, pdf, precision, schedule):
+    """(1, 3): the wavefront schedule, whose graph runs every other chunk in a
+    second slot on a second stream."""
     import torch
     proc, sqrt_s = PROCESS["pp_nlo"]
     n, chunk = 25_000, 8192  # four chunks, the last one ragged
-    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=precision, schedule=1,
+    cfg = G.make_config(proc, sqrt_s, pdf_grid=pdf, nmax=128, precision=precision, schedule=schedule,
                         blocks_per_sm=2)
     ctx_a, ctx_b = G.gaps_init(cfg), G.gaps_init(cfg)
     try:
