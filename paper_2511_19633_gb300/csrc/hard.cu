@@ -121,19 +121,26 @@ __device__ __forceinline__ void incoming_quark_tags(int fl, int tag, int& c, int
   if (fl > 0) { c = 0; a = tag; } else { c = tag; a = 0; }
 }
 
-__global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint64_t n) {
+__global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E, uint64_t first, uint64_t n) {
   uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   uint64_t id = first + e;
-  DevParams P = P0;  // the event's row of a mixed batch
-  if (P0.n_rows > 1) apply_row(P, mix_row(P0, id));
+  // the event's row of a mixed batch: its process and energy (the other
+  // fields are common; no per-thread copy of the parameters)
+  int process = P.process;
+  double sqrt_s = P.sqrt_s;
+  if (P.n_rows > 1) {
+    const RowParams& R = P.rows[mix_row(P, id)];
+    process = R.process;
+    sqrt_s = R.sqrt_s;
+  }
   Rng rng;
   rng.init(P.seed, id, kHardDrawBase);
   double R0, R1, R2, R3, R4, R5;
   rng.next2(R0, R1);
   rng.next2(R2, R3);
   rng.next2(R4, R5);
-  double s = P.sqrt_s * P.sqrt_s;
+  double s = sqrt_s * sqrt_s;
   Rec rec{E, e};
   E.status[e] = GAPS_STATUS_ACTIVE;
   E.n_emit[e] = 0;
@@ -141,14 +148,14 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
   E.draw[e] = 0;
   E.eta[e] = 0.0;
   E.eta[E.cap + e] = 0.0;
-  if (P.process == GAPS_EE_QQ) {
+  if (process == GAPS_EE_QQ) {
     double c = 2.0 * R0 - 1.0;
     double cph, sph;
     gm_sincos2pi(R1, cph, sph);  // phi = 2 pi R1
     int f = 1 + (int)floor(R2 * P.nf);
     if (f > P.nf) f = P.nf;
     double st = sqrt((1.0 - c) * (1.0 + c));
-    double En = 0.5 * P.sqrt_s;
+    double En = 0.5 * sqrt_s;
     double n0 = st * cph, n1 = st * sph, n2 = c;
     rec.set(0, En, En * n0, En * n1, En * n2, f, 1, 0);
     rec.set(1, En, -En * n0, -En * n1, -En * n2, -f, 0, 1);
@@ -156,7 +163,7 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     E.weight[e] = ee_dsigma_dcos(s, f, c) * 2.0 * P.nf * kGeV2pb;
     return;
   }
-  if (P.process == GAPS_PP_LL) {
+  if (process == GAPS_PP_LL) {
     // m^2 by the Breit-Wigner map m^2 = m_Z^2 + m_Z Gamma_Z tan(2 pi r), y
     // uniform in [-Y, Y], cos(theta*) and phi of the electron uniform in the
     // dilepton rest frame (quark along +z when it comes from beam 1); the
@@ -167,9 +174,9 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     double mg = kMZ * kGZ;
     double m2 = kMZ * kMZ + mg * (sr / cr);
     double m = sqrt(m2);
-    double Y = gm_log(P.sqrt_s / m);
+    double Y = gm_log(sqrt_s / m);
     double y = (2.0 * R1 - 1.0) * Y;
-    double tau = m / P.sqrt_s;
+    double tau = m / sqrt_s;
     double ey = gm_exp(y), iey = gm_exp(-y);
     double ea = ey * tau, eb = iey * tau;
     double c = 2.0 * R3 - 1.0;
@@ -187,7 +194,7 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     for (int k = 0; k < 10; ++k) { acc += dens[k]; if (target < acc) { pick = k; break; } }
     int fa, fb;
     born_pair(pick, fa, fb);
-    double Ea = ea * 0.5 * P.sqrt_s, Eb = eb * 0.5 * P.sqrt_s;
+    double Ea = ea * 0.5 * sqrt_s, Eb = eb * 0.5 * sqrt_s;
     int c0, a0, c1, a1;
     incoming_quark_tags(fa, 1, c0, a0);
     incoming_quark_tags(fb, 1, c1, a1);
@@ -210,14 +217,14 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
   double mz2 = kMZ * kMZ;
   bool hevent = false;
   double wsel = 1.0;
-  if (P.process == GAPS_PP_Z_NLO) {
+  if (process == GAPS_PP_Z_NLO) {
     hevent = !(R0 < P.p_s);
     wsel = hevent ? 1.0 / (1.0 - P.p_s) : 1.0 / P.p_s;
   }
   if (!hevent) {
-    double Y = gm_log(P.sqrt_s / kMZ);
+    double Y = gm_log(sqrt_s / kMZ);
     double y = (2.0 * R1 - 1.0) * Y;
-    double tau = kMZ / P.sqrt_s;
+    double tau = kMZ / sqrt_s;
     double ea = gm_exp(y) * tau, eb = gm_exp(-y) * tau;
     double dens[10], tot = 0.0;
     const PdfLoc la = pdf_locate(P, ea, kMZ * kMZ), lb = pdf_locate(P, eb, kMZ * kMZ);
@@ -227,7 +234,7 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     for (int k = 0; k < 10; ++k) { acc += dens[k]; if (target < acc) { pick = k; break; } }
     int fa, fb;
     born_pair(pick, fa, fb);
-    double Ea = ea * 0.5 * P.sqrt_s, Eb = eb * 0.5 * P.sqrt_s;
+    double Ea = ea * 0.5 * sqrt_s, Eb = eb * 0.5 * sqrt_s;
     int c0, a0, c1, a1;
     incoming_quark_tags(fa, 1, c0, a0);
     incoming_quark_tags(fb, 1, c1, a1);
@@ -238,7 +245,7 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
     E.eta[E.cap + e] = eb;
     E.npart[e] = 3;
     double w = tot * 2.0 * Y * kGeV2pb;
-    if (P.process == GAPS_PP_Z_NLO) {
+    if (process == GAPS_PP_Z_NLO) {
       double corr = 1.0 + kCF * P.as_mz / (2.0 * kPi) * 2.0;
       corr += collinear_leg(P, fa, ea, R3);
       corr += collinear_leg(P, fb, eb, R4);
@@ -302,7 +309,7 @@ __global__ void k_generate_hard(DevParams P0, DevEvents E, uint64_t first, uint6
       if (grp < 2) { fa = 21; fb = fq; emitter = 0; } else { fa = fq; fb = 21; emitter = 1; }
       fj = fq;
     }
-    double E1 = e1 * 0.5 * P.sqrt_s, E2 = e2 * 0.5 * P.sqrt_s;
+    double E1 = e1 * 0.5 * sqrt_s, E2 = e2 * 0.5 * sqrt_s;
     double pa[4] = {E1, 0.0, 0.0, E1};
     double pb[4] = {E2, 0.0, 0.0, -E2};
     const double* pe = emitter == 0 ? pa : pb;
