@@ -12,7 +12,7 @@
 #include "gmath.cuh"
 
 namespace gaps {
-cudaError_t launch_generate_hard(const DevParams&, const DevEvents&, uint64_t, uint64_t, cudaStream_t);
+cudaError_t launch_generate_hard(const DevParams&, const DevEvents&, uint64_t, uint64_t, int, cudaStream_t);
 cudaError_t launch_shower_fp64(const DevParams&, const DevEvents&, uint64_t, uint64_t, int, int,
                                unsigned long long*, cudaStream_t);
 void workset_carve(void* base, int lanes, int nmax, WorkSet& W);
@@ -417,7 +417,8 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
 int gaps_generate_hard(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps_events* ev,
                        void* stream) {
   if (!ctx || !events_ok(ctx, ev, n)) return GAPS_ERR_INVALID_ARG;
-  return cuda_fail(launch_generate_hard(ctx->P, dev_events(ev), first_event, n, (cudaStream_t)stream));
+  return cuda_fail(launch_generate_hard(ctx->P, dev_events(ev), first_event, n,
+                                       ctx->cfg.precision == GAPS_MIXED ? 1 : 0, (cudaStream_t)stream));
 }
 
 namespace {

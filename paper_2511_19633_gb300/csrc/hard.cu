@@ -59,6 +59,93 @@ __device__ double born_pair_density(const DevParams& P, int k, const PdfLoc& la,
   return kPi * Fa * Fb * born_me2(fa) / (mz2 * mz2);
 }
 
+// ---- the hard process of GAPS_MIXED contexts (FAST): the same formulas in
+// FP32 where the result is an event weight or a density (FP64 runs at 1/64 of
+// the FP32 rate on GB300), FP64 for the momenta. The FP64 kernel keeps the
+// oracle's arithmetic, operation by operation.
+
+// Born |M|^2 per quark class, folded at compile time (born_me2's formula)
+__host__ __device__ constexpr double born_me2_const(double Q, double T3) {
+  return (1.0 / kNc) * 0.25 * 1.4142135623730951 * kGF * (kMZ * kMZ * kMZ * kMZ) *
+         ((2.0 * T3 - 4.0 * Q * kSin2W) * (2.0 * T3 - 4.0 * Q * kSin2W) + (2.0 * T3) * (2.0 * T3));
+}
+__device__ __forceinline__ float born_me2_f(int f) {
+  constexpr float up = (float)born_me2_const(2.0 / 3.0, 0.5);
+  constexpr float down = (float)born_me2_const(-1.0 / 3.0, -0.5);
+  const int a = f < 0 ? -f : f;
+  return (a == 2 || a == 4) ? up : down;
+}
+
+// a point's grid cell with FP32 logarithms, and the FP32 bilinear density
+struct PdfLocF {
+  int ix, iq;
+  float fx, fq;
+  bool ok;
+};
+__device__ __forceinline__ PdfLocF pdf_locate_f(const DevParams& P, double x, double q2) {
+  PdfLocF L;
+  L.ix = L.iq = 0;
+  L.fx = L.fq = 0.0f;
+  L.ok = x >= kXMin && x <= kXMax && q2 >= kQ2Min && q2 <= kQ2Max;
+  if (!L.ok) return L;
+  const float u = (logf((float)x) - (float)P.lxmin) / (float)P.dlx;
+  const float w = (logf((float)q2) - (float)P.lqmin) / (float)P.dlq;
+  L.ix = min(max((int)floorf(u), 0), kNX - 2);
+  L.iq = min(max((int)floorf(w), 0), kNQ - 2);
+  L.fx = u - (float)L.ix;
+  L.fq = w - (float)L.iq;
+  return L;
+}
+__device__ __forceinline__ float pdf_at_f(const DevParams& P, int f, const PdfLocF& L) {
+  if (f < 0 || f > 11 || !L.ok) return 0.0f;
+  auto node = [&](int ix, int iq) { return (float)pdf_node(P, f, ix, iq); };
+  const float lo = (1.0f - L.fx) * node(L.ix, L.iq) + L.fx * node(L.ix + 1, L.iq);
+  const float hi = (1.0f - L.fx) * node(L.ix, L.iq + 1) + L.fx * node(L.ix + 1, L.iq + 1);
+  return lo * (1.0f - L.fq) + hi * L.fq;
+}
+
+// Li2(x) for 0 <= x <= 1/2 from the series in u = -ln(1 - x) with Bernoulli
+// coefficients, Li2 = sum_n B_n u^(n+1) / (n+1)! (B_1 = -1/2, odd B_n > 1
+// vanish): u <= ln 2 < 2 pi, twelve terms reach the FP32 rounding
+__device__ __forceinline__ float li2_bernoulli(float x) {
+  const float u = -log1pf(-x), u2 = u * u;
+  // B_2k / (2k+1)! for k = 1..6 (B_2 = 1/6, B_4 = -1/30, B_6 = 1/42,
+  // B_8 = -1/30, B_10 = 5/66, B_12 = -691/2730)
+  const float c1 = 1.0f / 36.0f, c2 = -1.0f / 3600.0f, c3 = 1.0f / 211680.0f, c4 = -1.0f / 10886400.0f,
+              c5 = 1.0f / 526901760.0f, c6 = -4.0647616e-11f;
+  const float tail = u2 * (c1 + u2 * (c2 + u2 * (c3 + u2 * (c4 + u2 * (c5 + u2 * c6)))));
+  return u - 0.25f * u2 + u * tail;
+}
+__device__ __forceinline__ float li2_f(float x) {
+  if (x == 0.0f) return 0.0f;
+  const float pi2_6 = (float)(kPi * kPi / 6.0);
+  if (x == 1.0f) return pi2_6;
+  if (x > 0.5f) return pi2_6 - logf(x) * log1pf(-x) - li2_bernoulli(1.0f - x);
+  return li2_bernoulli(x);
+}
+
+// collinear_leg in FP32 (FAST)
+__device__ float collinear_leg_f(const DevParams& P, int fl, double eta_d, double R) {
+  const float eta = (float)eta_d;
+  const float pf = (float)(kCF * P.as_mz / (2.0 * kPi)), pt = (float)(kTR * P.as_mz / (2.0 * kPi));
+  const double mz2 = kMZ * kMZ;
+  const double xd = eta_d + R * (1.0 - eta_d);
+  const float x = (float)xd, omx = (float)((1.0 - eta_d) * (1.0 - R));  // 1 - x without cancellation
+  const PdfLocF l0 = pdf_locate_f(P, eta_d, mz2), lx = pdf_locate_f(P, eta_d / xd, mz2);
+  const float Fq = pdf_at_f(P, pdf_index(fl), l0);
+  const float rq = pdf_at_f(P, pdf_index(fl), lx) / Fq;
+  const float rg = pdf_at_f(P, 0, lx) / Fq;
+  const float logs = logf(omx / x) + logf(omx);
+  const float g = pf * (2.0f / omx * logs);
+  const float hqq = pf * (-(1.0f + x) * logs + omx);
+  const float hqg = pt * (2.0f * x * omx + (x * x + omx * omx) * logs);
+  const float A = pf * (-5.0f + (float)(2.0 * kPi * kPi / 3.0));
+  const float l1 = log1pf(-eta);
+  const float B = pf * (2.0f * ((float)(kPi * kPi / 6.0) - l1 * l1 - li2_f(1.0f - eta)));
+  const float integrand = (rq - 1.0f) * g + rq * hqq + rg * hqg;
+  return A - B + (1.0f - eta) * integrand;
+}
+
 // sum x^k/k^2 until a term falls below 1e-17 of the sum (x <= 1/2)
 __device__ double li2_series(double x) {
   double sum = 0.0, xk = x;
@@ -121,6 +208,7 @@ __device__ __forceinline__ void incoming_quark_tags(int fl, int tag, int& c, int
   if (fl > 0) { c = 0; a = tag; } else { c = tag; a = 0; }
 }
 
+template <bool FAST>
 __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E, uint64_t first, uint64_t n) {
   uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -222,13 +310,27 @@ __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E
     wsel = hevent ? 1.0 / (1.0 - P.p_s) : 1.0 / P.p_s;
   }
   if (!hevent) {
-    double Y = gm_log(sqrt_s / kMZ);
+    double Y = FAST ? log(sqrt_s / kMZ) : gm_log(sqrt_s / kMZ);
     double y = (2.0 * R1 - 1.0) * Y;
     double tau = kMZ / sqrt_s;
-    double ea = gm_exp(y) * tau, eb = gm_exp(-y) * tau;
+    double ea = (FAST ? exp(y) : gm_exp(y)) * tau, eb = (FAST ? exp(-y) : gm_exp(-y)) * tau;
     double dens[10], tot = 0.0;
-    const PdfLoc la = pdf_locate(P, ea, kMZ * kMZ), lb = pdf_locate(P, eb, kMZ * kMZ);
-    for (int k = 0; k < 10; ++k) { dens[k] = born_pair_density(P, k, la, lb); tot += dens[k]; }
+    if constexpr (FAST) {
+      const PdfLocF la = pdf_locate_f(P, ea, kMZ * kMZ), lb = pdf_locate_f(P, eb, kMZ * kMZ);
+      constexpr float norm = (float)(kPi / (kMZ * kMZ * kMZ * kMZ));
+      float tf = 0.0f;
+      for (int k = 0; k < 10; ++k) {
+        int fa, fb;
+        born_pair(k, fa, fb);
+        const float d = pdf_at_f(P, pdf_index(fa), la) * pdf_at_f(P, pdf_index(fb), lb) * born_me2_f(fa) * norm;
+        dens[k] = d;
+        tf += d;
+      }
+      tot = tf;
+    } else {
+      const PdfLoc la = pdf_locate(P, ea, kMZ * kMZ), lb = pdf_locate(P, eb, kMZ * kMZ);
+      for (int k = 0; k < 10; ++k) { dens[k] = born_pair_density(P, k, la, lb); tot += dens[k]; }
+    }
     int pick = 9;
     double target = R2 * tot, acc = 0.0;
     for (int k = 0; k < 10; ++k) { acc += dens[k]; if (target < acc) { pick = k; break; } }
@@ -247,8 +349,13 @@ __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E
     double w = tot * 2.0 * Y * kGeV2pb;
     if (process == GAPS_PP_Z_NLO) {
       double corr = 1.0 + kCF * P.as_mz / (2.0 * kPi) * 2.0;
-      corr += collinear_leg(P, fa, ea, R3);
-      corr += collinear_leg(P, fb, eb, R4);
+      if constexpr (FAST) {
+        corr += collinear_leg_f(P, fa, ea, R3);
+        corr += collinear_leg_f(P, fb, eb, R4);
+      } else {
+        corr += collinear_leg(P, fa, ea, R3);
+        corr += collinear_leg(P, fb, eb, R4);
+      }
       w = w * corr * wsel;
     }
     E.weight[e] = w;
@@ -259,10 +366,10 @@ __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E
   double x = xlo + R3 * (1.0 - xlo);
   double v = R4 * (1.0 - x);
   double sbar = mz2 / x;
-  double Y = 0.5 * gm_log(s / sbar);
+  double Y = 0.5 * (FAST ? log(s / sbar) : gm_log(s / sbar));
   double y = (2.0 * R1 - 1.0) * Y;
   double rt = sqrt(sbar / s);
-  double e1 = gm_exp(y) * rt, e2 = gm_exp(-y) * rt;
+  double e1 = (FAST ? exp(y) : gm_exp(y)) * rt, e2 = (FAST ? exp(-y) : gm_exp(-y)) * rt;
   double as = P.as_mz;
   double m2 = mz2;
   // 0..9 q qbar -> Z g, 10..14 g q, 15..19 g qbar (gluon from beam 1),
@@ -271,6 +378,32 @@ __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E
   double cpick = 0.0;
   {
     double cs[30];
+    if constexpr (FAST) {
+      // the 30 channels in FP32: the common factors once
+      const PdfLocF l1 = pdf_locate_f(P, e1, mz2), l2 = pdf_locate_f(P, e2, mz2);
+      const float pre = (float)(8.0 * kPi * as / m2 / (16.0 * kPi) / m2);
+      const float fqq = pre * (float)kCF * -2.0f;
+      const float fqg = pre * (float)kTR * (float)((2.0 * m2 + v * sbar) / sbar);
+      float tf = 0.0f;
+      for (int k = 0; k < 30; ++k) {
+        int fa, fb;
+        float rs;
+        if (k < 10) {
+          born_pair(k, fa, fb);
+          rs = fqq * born_me2_f(fa);
+        } else {
+          const int q = ((k - 10) % 5) + 1;
+          const int grp = (k - 10) / 5;
+          const int fq = (grp == 0 || grp == 2) ? q : -q;
+          if (grp < 2) { fa = 21; fb = fq; } else { fa = fq; fb = 21; }
+          rs = fqg * born_me2_f(q);
+        }
+        const float c = pdf_at_f(P, pdf_index(fa), l1) * pdf_at_f(P, pdf_index(fb), l2) * rs;
+        cs[k] = c;
+        tf += fabsf(c);
+      }
+      tot = tf;
+    } else {
     const PdfLoc l1 = pdf_locate(P, e1, mz2), l2 = pdf_locate(P, e2, mz2);
     for (int k = 0; k < 30; ++k) {
       int fa, fb;
@@ -290,6 +423,7 @@ __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E
       double Fb = pdf_at(P, pdf_index(fb), l2);
       cs[k] = Fa * Fb * rs / (16.0 * kPi) / m2;
       tot += fabs(cs[k]);
+    }
     }
     int pick = 29;
     double target = R2 * tot, acc = 0.0;
@@ -352,12 +486,14 @@ __global__ void k_generate_hard(const __grid_constant__ DevParams P, DevEvents E
 
 }  // namespace
 
-cudaError_t launch_generate_hard(const DevParams& P, const DevEvents& E, uint64_t first, uint64_t n,
+// fast: the FP32 weights of GAPS_MIXED contexts
+cudaError_t launch_generate_hard(const DevParams& P, const DevEvents& E, uint64_t first, uint64_t n, int fast,
                                  cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   int bs = 128;
   unsigned grid = (unsigned)((n + bs - 1) / bs);
-  k_generate_hard<<<grid, bs, 0, stream>>>(P, E, first, n);
+  if (fast) k_generate_hard<true><<<grid, bs, 0, stream>>>(P, E, first, n);
+  else k_generate_hard<false><<<grid, bs, 0, stream>>>(P, E, first, n);
   return cudaGetLastError();
 }
 
