@@ -27,7 +27,8 @@ cudaError_t launch_shower_warp(const DevParams&, const DevEvents&, const Learned
 cudaError_t launch_shower_wave(const DevParams&, const DevEvents&, const WorkSet&, const WaveSet&, const LearnedCfg&,
                                uint64_t, uint64_t, int, int, int, int, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_observables(const DevParams&, const DevEvents&, uint64_t, uint64_t, double*,
-                               const HistSet&, double*, double*, int, cudaStream_t);
+                               const HistSet&, double*, double*, int, int, cudaStream_t);
+cudaError_t observables_init();
 cudaError_t sort_states(float4*, uint64_t, cudaStream_t);
 cudaError_t floor_values(float*, uint64_t, float, cudaStream_t);
 cudaError_t mlp_init(float*, uint64_t, cudaStream_t);
@@ -399,6 +400,7 @@ int gaps_init(gaps_ctx** out, const gaps_config* cfg) {
     if ((rc = cuda_fail(cudaMalloc(&ctx->d_counters, (C_NCOUNTERS + 1) * sizeof(unsigned long long))))) break;
     if ((rc = cuda_fail(cudaMemset(ctx->d_counters, 0, (C_NCOUNTERS + 1) * sizeof(unsigned long long))))) break;
     if ((rc = cuda_fail(mixed_kernels_init()))) break;
+    if ((rc = cuda_fail(observables_init()))) break;
   } while (false);
   if (rc != GAPS_OK) {
     gaps_destroy(ctx);
@@ -866,7 +868,7 @@ int gaps_observables(gaps_ctx* ctx, uint64_t first_event, uint64_t n, const gaps
   if (hists && (!hists->sumw || !hists->sumw2)) return GAPS_ERR_INVALID_ARG;
   return cuda_fail(launch_observables(ctx->P, dev_events(ev), first_event, n, obs, ctx->H,
                                       hists ? hists->sumw : nullptr, hists ? hists->sumw2 : nullptr,
-                                      ctx->cfg.precision == GAPS_MIXED, (cudaStream_t)stream));
+                                      ctx->cfg.precision == GAPS_MIXED, ctx->n_sm, (cudaStream_t)stream));
 }
 
 namespace {

@@ -191,9 +191,11 @@ def test_shrunk_margins_are_caught_and_fall_back(G, pdf, trained):
     assert np.all((log[:, 0] > 0) & (log[:, 0] < 1))  # eta
 
 
-def test_learned_proposal_is_exact_and_cheaper(G, pdf, trained):
+def test_learned_proposal_draws_fewer_trials(G, pdf, trained):
     """Same events, learned vs plain bounds: no violation, fewer cycles and
-    trials; distributions agree (chi^2/ndf < 1.2)."""
+    trials; distributions agree (chi^2/ndf < 1.2). Fewer trials is all this
+    asserts: in wall time the network's evaluation costs more than the trials
+    it saves (the bench reports both rates on the same events)."""
     n = 1_000_000
     wl, wl2, sl = _shower_hists(G, pdf, trained["params"], trained["log_margins"], n)
     wp, wp2, sp = _shower_hists(G, pdf, None, 0.0, n)
