@@ -87,7 +87,7 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25
 # (the traffic grows with the events showered); scaled to a chunk by its
 # events. Workloads and variants without a capture report null.
 SHOWER_DRAM_BYTES_PER_EVENT = {
-    ("pp_nlo_1e7", True): (14023.3e6 + 4610.6e6) / 262144,   # learned proposal, wavefront
+    ("pp_nlo_1e7", True): (14015.0e6 + 4602.4e6) / 262144,   # learned proposal, wavefront
 }
 
 
