@@ -46,7 +46,7 @@ WORKLOADS = {
                   "mass 66-116 GeV, initial/final-state shower, synthetic 100x50 PDF, 1e7 events per "
                   "step in chunks of 2^22, mixed precision, learned proposal, one CUDA graph per step"),
     "mix_1e8": (2, 13600.0, 100_000_000, 1 << 22, 1, MIX_ROWS,
-                "mixed batch in one persistent launch per chunk: 50% NLO pp -> Z at 13.6 TeV "
+                "mixed batch, rows drawn per event inside every launch: 50% NLO pp -> Z at 13.6 TeV "
                 "(t_c 1 GeV^2), 25% e+e- at 91.2 GeV (t_c 0.5), 25% e+e- at 500 GeV (t_c 4), "
                 "1e8 events in chunks of 2^22, learned proposal, one CUDA graph per step"),
 }
@@ -378,7 +378,11 @@ def run_ours(args, ws, rank, local):
     learned_info = None
     if mixed and not args.no_learned:
         from paper_2511_19633_gb300 import learned as LP
-        tcfg = G.make_config(G.GAPS_PP_Z_NLO, 13600.0, pdf_grid=pdf, nmax=nmax, seed=1,
+        # the network learns the initial-state states of the workload's own
+        # hadronic process (a mixed batch: its first pp row)
+        t_proc, t_sqrt_s, t_cut = next(((r[0], r[1], r[2]) for r in mix if r[0]), (0, 0.0, 1.0)) if mix \
+            else (process, sqrt_s, 1.0)
+        tcfg = G.make_config(t_proc, t_sqrt_s, pdf_grid=pdf, nmax=nmax, seed=1, t_cut=t_cut,
                              precision=G.GAPS_MIXED, schedule=G.GAPS_SCHED_PERSISTENT,
                              blocks_per_sm=4, emit_batch=8)
         tctx = G.gaps_init(tcfg)

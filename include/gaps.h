@@ -329,7 +329,10 @@ int gaps_isr_targets(gaps_ctx* ctx, const float* states, uint64_t n_states,
  * the height of bin m of class c at eta bucket b is
  * min(1, exp(NN + log_margins[c][b][m])), rounded up to a power 2^(-k/16).
  * Later GAPS_MIXED showers of the context use them. params == NULL returns
- * to the plain bounds. Non-finite values give GAPS_ERR_INVALID_ARG. */
+ * to the plain bounds. Non-finite values give GAPS_ERR_INVALID_ARG. A network
+ * and its margins are calibrated for the hadronic process whose states they
+ * were fitted on; installed for another process, heights can fall below the
+ * ratio and the shower then counts violations. */
 int gaps_set_learned_proposal(gaps_ctx* ctx, const float* params, const float* log_margins);
 
 /* The whole training pipeline of the learned proposal behind one call, on the
