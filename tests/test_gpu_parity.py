@@ -93,6 +93,25 @@ def test_high_cutoff_and_large_event_ids(G, oracle_mod, pdf):
     assert len(compare(g, o)) <= _max_mismatch(2000)
 
 
+@pytest.mark.parametrize("proc,sqrt_s,n,above,count", [(0, 1.0e5, 1003, 96, 50), (2, 13600.0, 3001, 48, 10)])
+def test_high_multiplicity_events(G, oracle_mod, pdf, proc, sqrt_s, n, above, count):
+    """The lowest cutoff (0.5 GeV^2) and, for e+e-, a 100 TeV collision:
+    events up to the 128-slot capacity, so that the observables' clusterings
+    run over every word of their pseudo-jet masks and the thrust over the
+    candidate axes of up to 128 partons (some e+e- events end with the
+    capacity error), event by event against the oracle."""
+    g = run_gpu(G, proc, sqrt_s, 1000, n, pdf, t_cut=0.5)
+    o = run_oracle(oracle_mod, proc, sqrt_s, 1000, n, pdf, t_cut=0.5)
+    start = 2 if proc else 0
+    coloured = np.array([np.sum(~np.isin(o["flav"][e, start:int(o["npart"][e])], (23, 11, -11)))
+                         for e in range(n)])
+    assert (coloured > above).sum() > count
+    if proc == 0:
+        assert (o["status"] == -2).sum() > 0
+    assert np.array_equal(g["status"], o["status"])
+    assert len(compare(g, o)) <= _max_mismatch(n)
+
+
 @pytest.mark.parametrize("name", ["pp_lo", "pp_ll", "pp_nlo"])
 def test_full_size_lo_sampled_against_oracle(G, oracle_mod, pdf, name):
     """pp -> Z and pp -> Z/gamma* -> e+ e- at LO and NLO-matched pp -> Z,
