@@ -1,12 +1,14 @@
 // Per-event observables (Section 4.1 of arXiv:2511.19633; e+e- event shapes
-// as in GAPS 1) and weighted histograms. One warp per event: the event's
-// final-state momenta sit in the warp's shared memory and the lanes share the
-// pair scans of the clusterings, the thrust candidates and the histogram
-// fills. Every value is formed with the same operations, in the same order,
-// as a plain one-thread evaluation, and every minimum is taken in the order
-// of a plain scan (lowest index on ties), so the results do not depend on the
-// number of lanes. Histograms are privatised per block in shared memory and
-// merged with global atomics.
+// as in GAPS 1) and weighted histograms. Each warp takes groups of 32
+// events: per-event scalar work (the colourless final state, the boson
+// kinematics, the output and the histogram bins) runs with one lane per
+// event; the clusterings run one event at a time with the event's final-state
+// momenta in the warp's shared memory and the lanes sharing the pair scans and
+// the thrust candidates. Every value is formed with the same operations, in
+// the same order, as a plain one-thread evaluation, and every minimum is taken
+// in the order of a plain scan (lowest index on ties), so the results do not
+// depend on the number of lanes. Histograms are privatised per block in shared
+// memory and merged with global atomics.
 #include "physics_fp64.cuh"
 
 namespace gaps {
@@ -16,7 +18,7 @@ namespace {
 
 constexpr int kMaxFinal = 128;
 constexpr int kObsWords = kMaxFinal / 32;
-constexpr int kObsWarps = 8;  // events in flight per block
+constexpr int kObsWarps = 8;  // warps per block, each on its own group of events
 constexpr unsigned kFull = 0xffffffffu;
 static_assert(GAPS_NOBS == 8, "the kernel writes eight observables per event");
 
