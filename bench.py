@@ -376,12 +376,12 @@ def run_ours(args, ws, rank, local):
     # region, on shower states of events outside every timed range
     learned = None
     learned_info = None
-    if mixed and not args.no_learned:
+    # the network learns the initial-state states of the workload's own
+    # hadronic process (a mixed batch: its first pp row); e+e- has none
+    t_proc, t_sqrt_s, t_cut = next(((r[0], r[1], r[2]) for r in mix if r[0]), (0, 0.0, 1.0)) if mix \
+        else (process, sqrt_s, 1.0)
+    if mixed and not args.no_learned and t_proc != 0:
         from paper_2511_19633_gb300 import learned as LP
-        # the network learns the initial-state states of the workload's own
-        # hadronic process (a mixed batch: its first pp row)
-        t_proc, t_sqrt_s, t_cut = next(((r[0], r[1], r[2]) for r in mix if r[0]), (0, 0.0, 1.0)) if mix \
-            else (process, sqrt_s, 1.0)
         tcfg = G.make_config(t_proc, t_sqrt_s, pdf_grid=pdf, nmax=nmax, seed=1, t_cut=t_cut,
                              precision=G.GAPS_MIXED, schedule=G.GAPS_SCHED_PERSISTENT,
                              blocks_per_sm=4, emit_batch=8)
